@@ -1,0 +1,398 @@
+"""Physics pins of the oracle's BSSN right-hand side, boundary conditions and evolution.
+
+Each test pins the oracle to something other than itself:
+* flat space (alpha=W=1, rest 0) is an exact solution: RHS identically zero and
+  the state bitwise unchanged by RK4;
+* alpha = beta = B = 0 freezes the slice: every right-hand side is exactly zero
+  (this fixes the reading of Eq. Lambda_RHS_orig_final, whose printed form
+  lacks two factors of alpha);
+* Brill-Lindquist data: d_t K = -2 psi^-8 |grad psi|^2 and
+  d_t Abar_ij = -8 psi^-8 (psi_i psi_j - delta_ij |grad psi|^2/3) at t=0
+  (flat-space closed forms) are reached at 4th order;
+* the same conformally flat metric psi^4 delta put into the conformal metric
+  (W=1, Lambdabar = Delta) has Ricci tensor R_ij = -2 psi_ij/psi + 6 psi_i
+  psi_j/psi^2 - 2 |grad psi|^2 delta_ij/psi^2, reached at 4th order through
+  d_t Abar, and a Hamiltonian constraint converging to zero;
+* a constant Cartesian shift on flat space is a Killing vector: geometric
+  right-hand sides vanish at 4th order;
+* with alpha=0 the physical metric and extrinsic curvature evolve by a pure
+  Lie derivative: d_t gamma_ij = L_beta gamma_ij, d_t K_ij = L_beta K_ij;
+* an outgoing spherical wave f = f_inf + g(t-r)/r satisfies the radiation
+  condition exactly; the discrete outer-boundary RHS converges to d_t f;
+* the Hamiltonian constraint of evolved Brill-Lindquist data converges at
+  4th order over three resolutions.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle.oracle import Oracle
+from paper_2505_00097_gb300 import workloads as W
+
+SYM = [(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]
+
+
+def _flat_state(o):
+    y = o.zeros()
+    T = o.T
+    y[12 * T:13 * T] = 1.0
+    y[23 * T:24 * T] = 1.0
+    return y
+
+
+def _frames(o):
+    """orthonormal frame vectors e_d(x) at every point, shape (3 d, 3 cart, T)"""
+    n0, n1, n2 = o.n
+    x0 = o.xx(0); x1 = o.xx(1); x2 = o.xx(2)
+    one = np.ones((n2, n1, n0))
+    if o.spec["coords"] == W.SINH_CYLINDRICAL:
+        ph = (x1[None, :, None] * one).reshape(-1)
+        c, s = np.cos(ph), np.sin(ph)
+        z = np.zeros_like(ph)
+        return np.array([[c, s, z], [-s, c, z], [z, z, z + 1.0]])
+    th = (x1[None, :, None] * one).reshape(-1)
+    ph = (x2[:, None, None] * one).reshape(-1)
+    st, ct, sp, cp = np.sin(th), np.cos(th), np.sin(ph), np.cos(ph)
+    return np.array([[st * cp, st * sp, ct], [ct * cp, ct * sp, -st], [-sp, cp, np.zeros_like(sp)]])
+
+
+def _psi(x, masses, pos):
+    """Brill-Lindquist psi, grad psi, Hessian of psi (Cartesian) at points x (T,3)"""
+    psi = np.ones(len(x)); dpsi = np.zeros((len(x), 3)); ddpsi = np.zeros((len(x), 3, 3))
+    for m, p in zip(masses, pos):
+        d = x - np.asarray(p)
+        r = np.sqrt((d * d).sum(1))
+        psi += m / (2 * r)
+        dpsi += -m * d / (2 * r[:, None] ** 3)
+        ddpsi += m / 2 * (3 * d[:, :, None] * d[:, None, :] / r[:, None, None] ** 5
+                          - np.eye(3)[None] / r[:, None, None] ** 3)
+    return psi, dpsi, ddpsi
+
+
+def _to_frame_sym(E, Tc):
+    """frame components (6,T) of Cartesian symmetric tensors Tc (T,3,3)"""
+    return np.array([np.einsum("ap,pab,bp->p", E[a], Tc, E[b]) for a, b in SYM])
+
+
+def _to_frame_vec(E, V):
+    return np.array([np.einsum("ap,pa->p", E[d], V) for d in range(3)])
+
+
+def _region(o, rmin, rmax, margin=4, axis_dist=1.0):
+    """interior points at Cartesian radius in [rmin, rmax], away from the outer boundary and at
+    least axis_dist from the z axis.  Next to the coordinate axis the cell-centred points sit at a
+    distance proportional to the spacing, where an O(h^4) angular error divided by that distance
+    is O(h^3); the pins measure the order of the scheme away from the singular axis."""
+    x = o.cart()
+    r = np.sqrt((x * x).sum(1))
+    rho = np.sqrt(x[:, 0] ** 2 + x[:, 1] ** 2)
+    m = o.interior_mask().reshape(o.n[2], o.n[1], o.n[0]).copy()
+    NG = o.NG
+    m[:, :, o.n[0] - NG - margin:] = False
+    if o.spec["coords"] == W.SINH_CYLINDRICAL:
+        m[:NG + margin] = False
+        m[o.n[2] - NG - margin:] = False
+    return m.reshape(-1) & (r >= rmin) & (r <= rmax) & (rho >= axis_dist)
+
+
+def _orders(errs):
+    return [math.log2(a / b) for a, b in zip(errs, errs[1:])]
+
+
+# ------------------------------------------------------------------ exact
+
+
+@pytest.mark.parametrize("spec", [W.sinh_spherical((64, 16, 2)), W.sinh_cylindrical((16, 2, 24)),
+                                  W.spherical((8, 6, 8))], ids=["c1", "cyl", "sph3d"])
+def test_flat_space_stays_exactly_flat(spec):
+    o = Oracle(spec)
+    y = _flat_state(o)
+    assert np.all(o.full_rhs(y) == 0.0)
+    y0 = y.copy()
+    o.rk4(y, o.dt(), 20 if spec["N"] == (64, 16, 2) else 5)
+    assert np.array_equal(y, y0)
+
+
+@pytest.mark.parametrize("spec", [W.sinh_spherical((12, 8, 6), ko_sigma=0.0),
+                                  W.sinh_cylindrical((10, 4, 12), ko_sigma=0.0, rho_max=5.0, z_max=5.0)],
+                         ids=["sph", "cyl"])
+def test_lapse_and_shift_zero_freezes_the_slice(spec):
+    o = Oracle(spec)
+    y = W.random_state(o.n, seed=11, smooth=True)
+    T = o.T
+    for g in list(range(17, 24)):
+        y[g * T:(g + 1) * T] = 0.0   # vetU, betU, alpha
+    r = o.rhs(y)
+    assert np.all(r[np.tile(o.interior_mask(), 24)] == 0.0)
+
+
+# ------------------------------------------------------ Brill-Lindquist t=0
+
+BL_MASSES = (0.6, 0.4)
+BL_POS = ((0.3, 0.2, 0.9), (-0.2, 0.1, -0.7))
+
+
+def _bl_errors(N, coords="sph"):
+    if coords == "sph":
+        spec = W.sinh_spherical(N, ampl=12.0, w=0.3, ko_sigma=0.0)
+        rmin, rmax = 2.5, 5.0
+    else:
+        spec = W.sinh_cylindrical(N, rho_max=12.0, z_max=12.0, w=0.3, ko_sigma=0.0)
+        rmin, rmax = 2.5, 5.0
+    o = Oracle(spec)
+    y = o.brill_lindquist(BL_MASSES, BL_POS)
+    r = o.rhs(y)
+    T = o.T
+    x = o.cart()
+    E = _frames(o)
+    psi, dpsi, ddpsi = _psi(x, BL_MASSES, BL_POS)
+    g2 = (dpsi * dpsi).sum(1)
+    sel = _region(o, rmin, rmax)
+    eK = np.abs(r[13 * T:14 * T] - (-2.0 * psi ** -8 * g2))[sel].max()
+    # Abar closed form, built step by step in Cartesian (gammabar = delta, alpha = W = psi^-2, phi = ln psi)
+    dphi = dpsi / psi[:, None]
+    ddphi = ddpsi / psi[:, None, None] - dpsi[:, :, None] * dpsi[:, None, :] / psi[:, None, None] ** 2
+    al = psi ** -2
+    dal = -2 * psi[:, None] ** -3 * dpsi
+    ddal = -2 * psi[:, None, None] ** -3 * ddpsi + 6 * psi[:, None, None] ** -4 * dpsi[:, :, None] * dpsi[:, None, :]
+    X = (-2 * al[:, None, None] * ddphi + 4 * al[:, None, None] * dphi[:, :, None] * dphi[:, None, :]
+         + 2 * (dal[:, :, None] * dphi[:, None, :] + dal[:, None, :] * dphi[:, :, None]) - ddal)
+    XTF = X - np.eye(3)[None] * np.trace(X, axis1=1, axis2=2)[:, None, None] / 3
+    dA = psi[:, None, None] ** -4 * XTF
+    simple = -8 * psi[:, None, None] ** -8 * (dpsi[:, :, None] * dpsi[:, None, :] - np.eye(3)[None] * g2[:, None, None] / 3)
+    assert np.allclose(dA, simple, atol=1e-12)
+    a_exp = _to_frame_sym(E, dA)
+    eA = max(np.abs(r[(6 + s) * T:(7 + s) * T] - a_exp[s])[sel].max() for s in range(6))
+    others = np.concatenate([r[g * T:(g + 1) * T][o.interior_mask()] for g in list(range(0, 6)) + [12] + list(range(14, 24))])
+    return eK, eA, np.abs(others).max()
+
+
+@pytest.mark.parametrize("coords", ["sph", "cyl"])
+def test_brill_lindquist_rhs_closed_forms(coords):
+    Ns = [(32, 16, 8), (64, 32, 16), (128, 64, 32)] if coords == "sph" else [(32, 8, 64), (64, 16, 128), (128, 32, 256)]
+    res = [_bl_errors(N, coords) for N in Ns]
+    eK = [e[0] for e in res]
+    eA = [e[1] for e in res]
+    assert all(e[2] == 0.0 for e in res)          # every other RHS is exactly zero at t=0 (sigma=0)
+    assert _orders(eK)[-1] == pytest.approx(4.0, abs=0.6), eK
+    assert _orders(eA)[-1] == pytest.approx(4.0, abs=0.6), eA
+
+
+def test_brill_lindquist_data_and_hamiltonian_convergence():
+    errs = []
+    for N in [(32, 16, 8), (64, 32, 16), (128, 64, 32)]:
+        o = Oracle(W.sinh_spherical(N, ampl=12.0, w=0.3))
+        y = o.brill_lindquist(BL_MASSES, BL_POS)
+        T = o.T
+        x = o.cart()
+        psi = _psi(x, BL_MASSES, BL_POS)[0]
+        canon = o.build_map()[3] != 2
+        np.testing.assert_allclose(y[12 * T:13 * T][canon], psi[canon] ** -2, rtol=1e-14)
+        np.testing.assert_allclose(y[23 * T:24 * T][canon], psi[canon] ** -2, rtol=1e-14)
+        H, l2, linf, cnt = o.hamiltonian(y, 2.5, 5.0)
+        errs.append(linf)
+    assert _orders(errs)[-1] == pytest.approx(4.0, abs=0.6), errs
+
+
+# ------------------------------------------- Ricci of a conformally flat metric
+
+
+def _cf_metric_state(o, masses=BL_MASSES, pos=BL_POS):
+    T = o.T
+    x = o.cart()
+    E = _frames(o)
+    psi, dpsi, ddpsi = _psi(x, masses, pos)
+    y = o.zeros()
+    for s, (a, b) in enumerate(SYM):
+        if a == b:
+            y[s * T:(s + 1) * T] = psi ** 4 - 1.0
+    y[12 * T:13 * T] = 1.0
+    y[23 * T:24 * T] = 1.0
+    lam = _to_frame_vec(E, -2 * psi[:, None] ** -5 * dpsi)   # Lambdabar^i = Delta^i of psi^4 delta
+    for d in range(3):
+        y[(14 + d) * T:(15 + d) * T] = lam[d]
+    return y, psi, dpsi, ddpsi, E
+
+
+def test_ricci_of_conformally_flat_metric():
+    eA, eH = [], []
+    for N in [(32, 16, 8), (64, 32, 16), (128, 64, 32)]:
+        o = Oracle(W.sinh_spherical(N, ampl=12.0, w=0.3, ko_sigma=0.0))
+        y, psi, dpsi, ddpsi, E = _cf_metric_state(o)
+        T = o.T
+        r = o.rhs(y)
+        g2 = (dpsi * dpsi).sum(1)
+        Ric = (-2 * ddpsi / psi[:, None, None] + 6 * dpsi[:, :, None] * dpsi[:, None, :] / psi[:, None, None] ** 2
+               - 2 * np.eye(3)[None] * (g2 / psi ** 2)[:, None, None])
+        a_exp = _to_frame_sym(E, Ric)   # trace-free already (psi harmonic); W = alpha = 1
+        sel = _region(o, 2.5, 5.0)
+        eA.append(max(np.abs(r[(6 + s) * T:(7 + s) * T] - a_exp[s])[sel].max() for s in range(6)))
+        eH.append(o.hamiltonian(y, 2.5, 5.0)[2])
+    assert _orders(eA)[-1] == pytest.approx(4.0, abs=0.6), eA
+    assert _orders(eH)[-1] == pytest.approx(4.0, abs=0.6), eH
+
+
+# ------------------------------------------------------------ Killing shift
+
+
+@pytest.mark.parametrize("coords", ["sph", "cyl"])
+def test_constant_shift_in_flat_space(coords):
+    b = np.array([0.11, -0.07, 0.05])
+    errs = []
+    Ns = [(16, 16, 16), (32, 32, 32), (64, 64, 64)] if coords == "sph" else [(16, 16, 32), (32, 32, 64), (64, 64, 128)]
+    for N in Ns:
+        if coords == "sph":
+            o = Oracle(W.sinh_spherical(N, ampl=12.0, w=0.3, ko_sigma=0.0))
+        else:
+            o = Oracle(W.sinh_cylindrical(N, rho_max=12.0, z_max=12.0, w=0.3, ko_sigma=0.0))
+        y = _flat_state(o)
+        T = o.T
+        E = _frames(o)
+        v = _to_frame_vec(E, np.tile(b, (T, 1)))
+        for d in range(3):
+            y[(17 + d) * T:(18 + d) * T] = v[d]
+        r = o.rhs(y)
+        sel = _region(o, 2.0, 6.0)
+        errs.append(max(np.abs(r[g * T:(g + 1) * T])[sel].max() for g in list(range(0, 17)) + [20, 21, 22, 23]))
+    assert _orders(errs)[-1] == pytest.approx(4.0, abs=0.6), errs
+
+
+# ---------------------------------------------------------------- pure gauge
+
+
+def _gauge_fields(x):
+    """analytic Cartesian fields: conformal metric gb, W, Abar (gb-trace-free), K, shift b"""
+    X, Y, Z = x[:, 0], x[:, 1], x[:, 2]
+    T = len(X)
+    q = np.zeros((T, 3, 3)); dq = np.zeros((T, 3, 3, 3))
+    # q_ij = 0.05 * [[sin(.3X), .5 cos(.2Y) , 0],[., cos(.25Z), .1 sin(.2X)],[0, ., sin(.2Y+.1Z)]]
+    f = {
+        (0, 0): (lambda: 0.05 * np.sin(0.3 * X), lambda: [0.015 * np.cos(0.3 * X), 0 * X, 0 * X]),
+        (0, 1): (lambda: 0.025 * np.cos(0.2 * Y), lambda: [0 * X, -0.005 * np.sin(0.2 * Y), 0 * X]),
+        (1, 1): (lambda: 0.05 * np.cos(0.25 * Z), lambda: [0 * X, 0 * X, -0.0125 * np.sin(0.25 * Z)]),
+        (1, 2): (lambda: 0.005 * np.sin(0.2 * X), lambda: [0.001 * np.cos(0.2 * X), 0 * X, 0 * X]),
+        (2, 2): (lambda: 0.05 * np.sin(0.2 * Y + 0.1 * Z), lambda: [0 * X, 0.01 * np.cos(0.2 * Y + 0.1 * Z), 0.005 * np.cos(0.2 * Y + 0.1 * Z)]),
+    }
+    for (i, j), (v, dv) in f.items():
+        q[:, i, j] = q[:, j, i] = v()
+        d = dv()
+        for k in range(3):
+            dq[:, i, j, k] = dq[:, j, i, k] = d[k]
+    gb = np.eye(3)[None] + q
+    Wf = 1.0 / (1.2 + 0.1 * np.sin(0.2 * X + 0.1 * Y))
+    dW = -Wf[:, None] ** 2 * np.stack([0.02 * np.cos(0.2 * X + 0.1 * Y), 0.01 * np.cos(0.2 * X + 0.1 * Y), 0 * X], 1)
+    K = 0.1 * np.cos(0.15 * Z + 0.1 * X)
+    dK = np.stack([-0.01 * np.sin(0.15 * Z + 0.1 * X), 0 * X, -0.015 * np.sin(0.15 * Z + 0.1 * X)], 1)
+    M = np.zeros((T, 3, 3)); dM = np.zeros((T, 3, 3, 3))
+    M[:, 0, 1] = M[:, 1, 0] = 0.1 * np.sin(0.2 * Z); dM[:, 0, 1, 2] = dM[:, 1, 0, 2] = 0.02 * np.cos(0.2 * Z)
+    M[:, 2, 2] = 0.08 * np.cos(0.1 * X); dM[:, 2, 2, 0] = -0.008 * np.sin(0.1 * X)
+    M[:, 0, 0] = 0.05; M[:, 1, 2] = M[:, 2, 1] = 0.03 * np.cos(0.1 * Y); dM[:, 1, 2, 1] = dM[:, 2, 1, 1] = -0.003 * np.sin(0.1 * Y)
+    b = np.stack([0.05 * np.sin(0.1 * Y), 0.04 * np.cos(0.2 * X) + 0.01 * Z, 0.03 + 0.02 * np.sin(0.1 * X * 0 + 0.15 * Y)], 1)
+    db = np.zeros((T, 3, 3))  # db[:, i, k] = d_k b^i
+    db[:, 0, 1] = 0.005 * np.cos(0.1 * Y)
+    db[:, 1, 0] = -0.008 * np.sin(0.2 * X); db[:, 1, 2] = 0.01
+    db[:, 2, 1] = 0.003 * np.cos(0.15 * Y)
+    # make Abar trace-free w.r.t. gb: A = M - gb tr(gbinv M)/3 (derivatives by the product rule)
+    gbi = np.linalg.inv(gb)
+    tr = np.einsum("pij,pij->p", gbi, M)
+    dgbi = -np.einsum("pia,pabk,pbj->pijk", gbi, dq, gbi)
+    dtr = np.einsum("pijk,pij->pk", dgbi, M) + np.einsum("pij,pijk->pk", gbi, dM)
+    A = M - gb * tr[:, None, None] / 3
+    dA = dM - dq * tr[:, None, None, None] / 3 - gb[..., None] * dtr[:, None, None, :] / 3
+    return gb, dq, Wf, dW, A, dA, K, dK, b, db
+
+
+def _lie_sym(b, db, Tt, dT):
+    # (L_b T)_ij = b^k d_k T_ij + T_kj d_i b^k + T_ik d_j b^k
+    return (np.einsum("pk,pijk->pij", b, dT) + np.einsum("pkj,pki->pij", Tt, db) + np.einsum("pik,pkj->pij", Tt, db))
+
+
+def test_pure_gauge_evolution_is_a_lie_derivative():
+    eg, eK = [], []
+    for N in [(24, 24, 24), (48, 48, 48), (96, 96, 96)]:
+        o = Oracle(W.sinh_spherical(N, ampl=12.0, w=0.3, ko_sigma=0.0))
+        T = o.T
+        x = o.cart()
+        E = _frames(o)
+        gb, dgb, Wf, dW, A, dA, K, dK, b, db = _gauge_fields(x)
+        y = o.zeros()
+        h = _to_frame_sym(E, gb) - np.array([1, 0, 0, 1, 0, 1.0])[:, None]
+        a = _to_frame_sym(E, A)
+        v = _to_frame_vec(E, b)
+        for s in range(6):
+            y[s * T:(s + 1) * T] = h[s]
+            y[(6 + s) * T:(7 + s) * T] = a[s]
+        y[12 * T:13 * T] = Wf
+        y[13 * T:14 * T] = K
+        for d in range(3):
+            y[(17 + d) * T:(18 + d) * T] = v[d]
+        # alpha = 0, B = 0, Lambdabar = 0 (does not enter the metric, W, K, Abar equations at alpha=0... except via Ricci*alpha)
+        r = o.rhs(y)
+        rh = np.array([r[s * T:(s + 1) * T] for s in range(6)])
+        ra = np.array([r[(6 + s) * T:(7 + s) * T] for s in range(6)])
+        rW, rK = r[12 * T:13 * T], r[13 * T:14 * T]
+        hh = h + np.array([1, 0, 0, 1, 0, 1.0])[:, None]
+        # physical metric gamma = W^-2 gb, K_ij = W^-2 (A + gb K / 3)
+        dgam = -2 * Wf ** -3 * rW * hh + Wf ** -2 * rh
+        dKij = -2 * Wf ** -3 * rW * (a + hh * K / 3) + Wf ** -2 * (ra + rh * K / 3 + hh * rK / 3)
+        gam = gb / Wf[:, None, None] ** 2
+        dgam_c = dgb / Wf[:, None, None, None] ** 2 - 2 * gb[..., None] * dW[:, None, None, :] / Wf[:, None, None, None] ** 3
+        Kc = (A + gb * K[:, None, None] / 3) / Wf[:, None, None] ** 2
+        dKc = ((dA + dgb * K[:, None, None, None] / 3 + gb[..., None] * dK[:, None, None, :] / 3) / Wf[:, None, None, None] ** 2
+               - 2 * (A + gb * K[:, None, None] / 3)[..., None] * dW[:, None, None, :] / Wf[:, None, None, None] ** 3)
+        ex_g = _to_frame_sym(E, _lie_sym(b, db, gam, dgam_c))
+        ex_K = _to_frame_sym(E, _lie_sym(b, db, Kc, dKc))
+        sel = _region(o, 2.0, 6.0)
+        eg.append(np.abs(dgam - ex_g)[:, sel].max())
+        eK.append(np.abs(dKij - ex_K)[:, sel].max())
+    assert _orders(eg)[-1] == pytest.approx(4.0, abs=0.6), eg
+    assert _orders(eK)[-1] == pytest.approx(4.0, abs=0.6), eK
+
+
+# ----------------------------------------------------------------- Sommerfeld
+
+
+@pytest.mark.parametrize("coords", ["sph", "cyl"])
+def test_outgoing_wave_satisfies_radiation_condition(coords):
+    errs = []
+    Ns = [(32, 4, 4), (64, 4, 4), (128, 4, 4)] if coords == "sph" else [(32, 2, 64), (64, 2, 128), (128, 2, 256)]
+    for N in Ns:
+        if coords == "sph":
+            o = Oracle(W.sinh_spherical(N, ampl=10.0, w=0.5))
+        else:
+            o = Oracle(W.sinh_cylindrical(N, rho_max=10.0, z_max=10.0, w=0.5))
+        T = o.T
+        x = o.cart()
+        r = np.sqrt((x * x).sum(1))
+        cls = o.build_map()[3]
+        y = o.zeros()
+        finf = np.zeros(24); finf[12] = finf[23] = 1.0
+        for g in range(24):
+            y[g * T:(g + 1) * T] = finf[g] + (2.0 + np.cos(0.3 * r + 0.1 * g)) / r   # g(u) = 2 + cos(0.1 g - 0.3 u), t = 0
+        rhs = np.zeros_like(y)
+        o.outer_bc(y, rhs)
+        sel = cls == 1
+        e = 0.0
+        for g in range(24):
+            exact = 0.3 * np.sin(0.3 * r + 0.1 * g) / r   # d_t [g(t-r)/r] at t=0, g(u) = 2 + cos(0.1 g - 0.3 u)
+            e = max(e, np.abs(rhs[g * T:(g + 1) * T] - exact)[sel].max())
+        errs.append(e)
+    assert _orders(errs)[-1] == pytest.approx(4.0, abs=0.7), errs
+
+
+# ---------------------------------------------------------- evolved H order
+
+
+def test_hamiltonian_convergence_after_evolution():
+    errs = []
+    t_final = None
+    for N in [(32, 8, 2), (64, 16, 2), (128, 32, 2)]:
+        o = Oracle(W.sinh_spherical(N, ampl=10.0, w=0.4))
+        y = o.brill_lindquist((1.0,), ((0.0, 0.0, 0.0),))
+        if t_final is None:
+            t_final = 8 * o.dt()
+        n = int(math.ceil(t_final / o.dt() - 1e-9))
+        o.rk4(y, t_final / n, n)
+        errs.append(o.hamiltonian(y, 1.5, 4.0)[1])
+    assert _orders(errs)[-1] == pytest.approx(4.0, abs=0.5), errs
