@@ -1,0 +1,390 @@
+#!/usr/bin/env python
+"""Benchmark of the FP64 BSSN RK4 hot path on one GB300 (or N replicas).
+
+Metric: FP64 point-updates per second, counted as interior points x RK4
+substeps (4 per step) x steps, summed over ranks.  A "step" is one classic
+RK4 step of the whole hot path (RHS + dissipation + radiation and parity
+boundary conditions + det enforcement, fused RK update) over the workload;
+the Hamiltonian constraint is evaluated every `h_every` steps as the
+workload prescribes.
+
+Default workload: head-on Brill-Lindquist binary (bare masses 0.5+0.5 at
+z = +-0.5), SinhCylindrical (rho_max = z_max = 300, w = 0.2), 256x2x512
+interior points, 2000 RK4 steps at CFL 0.5, H every 100 steps.  Inputs are
+synthetic closed-form initial data generated on the GPU.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torch.distributed.run, one independent replica per GPU
+(the simulations do not exchange data: weak scaling, no collective on the
+data path).  --impl reference times the CPU oracle (plain C, OpenMP over the
+host cores) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2505_00097_gb300 import workloads as W  # noqa: E402
+
+METRIC = "BSSN FP64 point-updates/s (RK4 substeps)"
+UNIT = "point-updates/s"
+
+# FP64 operations (FMA = 2) per interior point of one k_rhs launch, counted
+# from the kernel's DADD/DMUL/DFMA instruction counts (ncu, see profiles/).
+F_ALG = None
+# algorithmic DRAM bytes per interior point of one fused RK stage launch:
+# stage input (read once) 24x8, y_n 24x8, acc read+write 2x24x8, output 24x8
+B_ALG_STAGE = 5 * 24 * 8
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["headon", "single_puncture", "large3d"], default="headon")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def workload(name: str) -> dict:
+    return {"headon": W.config_headon, "single_puncture": W.config_single_puncture,
+            "large3d": W.config_large3d}[name]()
+
+
+def config_of(spec: dict, extra: dict | None = None) -> dict:
+    c = {
+        "workload": spec["name"],
+        "coords": ["SinhSpherical", "SinhCylindrical", "Spherical"][spec["coords"]],
+        "grid_interior": list(spec["N"]),
+        "ghost_zones": spec["NG"],
+        "steps_in_config": spec["steps"],
+        "h_every": spec["h_every"],
+        "fd_order": 4,
+        "ko_sigma": spec["ko_sigma"],
+        "cfl": spec["cfl"],
+        "integrator": "RK4",
+        "l2_policy": "inputs larger than L2 (4 resident 24-gridfunction sets)",
+    }
+    if extra:
+        c.update(extra)
+    return c
+
+
+# ------------------------------------------------------------------ dist
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def dist_init(world: int, use_cuda: bool):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+
+    dist.init_process_group(backend="nccl" if use_cuda else "gloo")
+    return dist
+
+
+def reduce_max(dist, x: float, device=None) -> float:
+    """max of a float over ranks (identity without a process group)"""
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(dist, x: float, device=None) -> float:
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- clocks
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of the benchmarked GPU during the timed region."""
+
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            if self.uuid and self.uuid not in parts[0]:
+                continue
+            rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+
+        def num(s):
+            try:
+                return float(s)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        pw = [num(r[3]) for r in rows if num(r[3]) is not None]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(pw) if pw else None}
+
+
+# ------------------------------------------------------------- CPU oracle
+
+
+def oracle_threads() -> int:
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+
+
+def cpu_baseline(spec: dict, seconds: float) -> dict:
+    """The oracle as it stands, on the host cores: RK4 steps of the workload until `seconds` pass."""
+    from oracle.oracle import Oracle
+
+    o = Oracle(dict(spec, nthreads=0))
+    y = o.brill_lindquist(spec["masses"], spec["positions"], spec["perturb_amp"], spec["seed"])
+    dt = o.dt()
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        o.rk4(y, dt, 1)
+        steps += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    el = time.perf_counter() - t0
+    pts = math.prod(spec["N"])
+    return {"value": pts * 4 * steps / el, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
+            "sample": f"first {steps} RK4 steps of {spec['name']} (full grid), {el:.1f} s"}
+
+
+def run_reference(args, spec):
+    """--impl reference: the CPU oracle; each step is one RHS evaluation over a slab of
+    z-planes (or theta/phi planes) of the workload, sized so the whole run takes a few minutes."""
+    from oracle.oracle import Oracle
+
+    o = Oracle(dict(spec, nthreads=0))
+    y = o.brill_lindquist(spec["masses"], spec["positions"], spec["perturb_amp"], spec["seed"])
+    n_planes = spec["N"][2]
+    plane_pts = spec["N"][0] * spec["N"][1]
+    t0 = time.perf_counter()
+    o.rhs(y, 0, min(4, n_planes))
+    per_plane = max((time.perf_counter() - t0) / min(4, n_planes), 1e-6)
+    budget = 150.0 / max(1, args.steps + args.warmup)
+    m = int(max(1, min(n_planes, budget / per_plane)))
+    for s in range(args.warmup):
+        o.rhs(y, 0, m)
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        k0 = (s * m) % max(1, n_planes - m + 1)
+        o.rhs(y, k0, k0 + m)
+    el = time.perf_counter() - t0
+    value = plane_pts * m * args.steps / el
+    sample = f"{args.steps} RHS evaluations of {m} of {n_planes} planes ({plane_pts * m} interior points each) of {spec['name']}"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (Brill-Lindquist closed form)",
+        "config": config_of(spec, {"parallelism": "host cores (OpenMP)"}),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# -------------------------------------------------------------- GPU arm
+
+
+def run_ours(args, spec, world, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_2505_00097_gb300 import binding as B
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = dist_init(world, True)
+    B.lib()
+    g = B.Grid(spec, device=local)
+    g.set_brill_lindquist(spec["masses"], spec["positions"], spec["perturb_amp"], spec["seed"])
+    dt = g.dt_cfl
+    pts = g.interior
+    h_every = int(spec["h_every"])
+    stream = torch.cuda.current_stream(dev)   # the library's stream is the legacy stream of this device
+
+    def run_steps(n, start):
+        launches = 0
+        for s in range(n):
+            g.rk4_step(dt, 1)
+            launches += 12
+            if h_every and (start + s + 1) % h_every == 0:
+                g.hamiltonian()
+                launches += 2
+        return launches
+
+    # warm-up (graph capture happens on the first step)
+    run_steps(args.warmup, 0)
+    torch.cuda.synchronize()
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    launches = run_steps(args.steps, args.warmup)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    ck = clocks.stop()
+    if dist is not None:
+        dist.barrier()
+    ms_max = reduce_max(dist, ms, dev)
+    g.check_finite()
+    value = world * pts * 4 * args.steps / (ms_max * 1e-3)
+
+    # dominant kernel: k_rhs, timed alone with CUDA events on the same stream
+    T = g.T
+    ybuf = torch.empty(24 * T, dtype=torch.float64, device=dev)
+    obuf = torch.empty_like(ybuf)
+    g.get_state(ybuf, False)
+    for _ in range(3):
+        g.rhs(ybuf, obuf)
+    nrep = 20
+    r0 = torch.cuda.Event(enable_timing=True)
+    r1 = torch.cuda.Event(enable_timing=True)
+    r0.record(stream)
+    for _ in range(nrep):
+        g.rhs(ybuf, obuf)
+    r1.record(stream)
+    torch.cuda.synchronize()
+    rhs_ms = r0.elapsed_time(r1) / nrep
+    del ybuf, obuf
+    peak = B.fp64_peak(local)
+    roof = {"bound": "alu", "kernel": "k_rhs (FP64 BSSN RHS + KO + upwind)", "unit": "TFLOP/s",
+            "peak": peak / 1e12, "peak_source": "measured: FP64 FMA probe nr_fp64_peak on this GPU",
+            "launch_ms": rhs_ms, "points_per_launch": pts, "traffic": None}
+    if F_ALG:
+        ach = F_ALG * pts / (rhs_ms * 1e-3)
+        roof.update(achieved=ach / 1e12, frac=ach / peak, flops_per_point=F_ALG)
+    else:
+        roof.update(achieved=None, frac=None, flops_per_point=None)
+
+    # end to end through the C ABI with host buffers: every step uploads the state from
+    # pinned host memory, advances it, and reads the new state back
+    e2e = None
+    if not args.no_e2e:
+        n_e2e = min(args.steps, 100)
+        host_in = torch.empty(24 * T, dtype=torch.float64).pin_memory()
+        host_out = torch.empty(24 * T, dtype=torch.float64).pin_memory()
+        g.get_state(host_in.data_ptr(), True)
+        if dist is not None:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for s in range(n_e2e):
+            g.set_state(host_in.data_ptr(), True)
+            run_steps(1, args.warmup + args.steps + s)
+            g.get_state(host_out.data_ptr(), True)
+            host_in, host_out = host_out, host_in
+        torch.cuda.synchronize()
+        el = reduce_max(dist, time.perf_counter() - t0, dev)
+        nbytes = 24 * T * 8
+        e2e = {"value": world * pts * 4 * n_e2e / el, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes, "steps": n_e2e,
+               "path": "nr_set_state(pinned host) + nr_rk4_step + nr_get_state(pinned host) per step"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(spec, args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (Brill-Lindquist closed form on the GPU)",
+            "config": config_of(spec, {"parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                                       "dt": dt}),
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": ck,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    g.close()
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_env()
+    spec = workload(args.workload)
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        run_reference(args, spec)
+        return
+    run_ours(args, spec, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,192 @@
+/*
+ * nr.h -- C ABI of the GB300 FP64 BSSN library (libnrgpu.so).
+ *
+ * The library evolves the BSSN equations in the reference-metric formalism
+ * on one structured SinhSpherical, Spherical or SinhCylindrical grid per
+ * nr_grid, as stated in arXiv 2505.00097:
+ *   - Sec. 2.1: evolution equations (Eqs. metric_RHS_orig_final,
+ *     Abar_RHS_orig_final, W_RHS_orig_final, K_RHS_orig_final,
+ *     Lambda_RHS_orig_final), the conformal Ricci tensor, 1+log slicing and
+ *     the Gamma-driver shift (Eqs. gauge_eqns, damping_eta_final), the
+ *     Hamiltonian constraint (Eq. Hconstraint);
+ *   - Sec. 2.2: tensor rescaling by the scale factors S_i;
+ *   - Sec. 3: cell-centred logically rectangular grids, 4th-order centred
+ *     finite differences with upwinded shift advection and N_G = 3 ghost
+ *     layers, outer (radiation) and inner (parity) boundary points, and the
+ *     boundary order outer -> inner after every time-integrator substage;
+ *   - Sec. 4.1: the sinh coordinate map x'(x) = x_max sinh(x/w)/sinh(1/w),
+ *     Kreiss-Oliger dissipation and the CFL factor;
+ *   - Sec. 4.2.1: method-of-lines RK4.
+ *
+ * Conventions (all entry points):
+ *   - Return an nr_status; on failure nr_last_error() gives a thread-local
+ *     message.  No entry point aborts the process.
+ *   - A 24-gridfunction set is T*24 doubles laid out gfs[gf*T + idx],
+ *     idx = i0 + n0*(i1 + n1*i2), n_d = N_d + 2*NG, i0 fastest.  Gridfunction
+ *     order (rescaled components): hDD00,hDD01,hDD02,hDD11,hDD12,hDD22,
+ *     aDD00..aDD22, cf (W), trK, lambdaU0..2, vetU0..2, betU0..2, alpha.
+ *   - Pointers named *_dev are CUDA device pointers owned by the caller (for
+ *     example torch tensors); the library never frees them.  Buffers created
+ *     by nr_grid_create are owned by the library and released by
+ *     nr_grid_destroy.
+ *   - Device work is issued on params.stream (a cudaStream_t, NULL for the
+ *     legacy default stream) and is stream-ordered: an entry point returns
+ *     after enqueueing, except where it says it synchronises.
+ */
+#ifndef NR_H
+#define NR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    NR_OK = 0,
+    NR_EINVAL = 1,      /* bad argument (sizes, coordinates, null pointer, puncture on a grid point) */
+    NR_ENOMEM = 2,      /* device allocation failed */
+    NR_ECUDA = 3,       /* a CUDA runtime call failed */
+    NR_ETIMEOUT = 4,    /* a bounded device wait gave up */
+    NR_ENONFINITE = 5,  /* a NaN/Inf was found in the evolved state */
+    NR_EMAP = 6         /* a ghost point has no source on the grid (e.g. odd N_phi) */
+} nr_status;
+
+typedef enum { NR_SINH_SPHERICAL = 0, NR_SINH_CYLINDRICAL = 1, NR_SPHERICAL = 2 } nr_coords;
+
+enum { NR_NGF = 24 };
+
+/* Grid and physics parameters.
+ *   ampl/sinhw: per-axis map amplitude and sinh width (Sec. 4.1).
+ *     SinhSpherical: r = ampl[0] sinh(xx0/sinhw[0])/sinh(1/sinhw[0]), xx0 in [0,1],
+ *                    theta = xx1 in [0,pi], phi = xx2 in [-pi,pi].
+ *     Spherical:     r = ampl[0] xx0.
+ *     SinhCylindrical: rho from xx0 in [0,1] with ampl[0], sinhw[0];
+ *                    phi = xx1 in [-pi,pi]; z from xx2 in [-1,1] with ampl[2], sinhw[2].
+ *   ko_sigma: Kreiss-Oliger strength per gridfunction (Sec. 4.1).
+ *   eta: Gamma-driver damping; cfl: CFL factor.
+ *   wavespeed, f_inf: radiation condition d_t f = -v [(x^j/r) d_j f + (f - f_inf)/r].
+ *   h_rmin, h_rmax: radius band of the Hamiltonian-constraint norms.
+ *   NG must be 3.  enforce_detgb: rescale h so det(gammabar)=det(gammahat)
+ *   after every RK substage (the Lagrangian choice of Sec. 2.1).
+ *   stream: cudaStream_t used for all device work of the grid (NULL: legacy stream). */
+typedef struct {
+    double ampl[3];
+    double sinhw[3];
+    double ko_sigma[24];
+    double eta;
+    double cfl;
+    double wavespeed[24];
+    double f_inf[24];
+    double h_rmin;
+    double h_rmax;
+    int NG;
+    int enforce_detgb;
+    int device;
+    int reserved;
+    void* stream;
+} nr_params;
+
+typedef struct nr_grid nr_grid;
+
+typedef struct {
+    int N[3];          /* interior cells */
+    int n[3];          /* padded dimensions N + 2 NG */
+    int64_t T;         /* points per gridfunction (padded) */
+    int64_t interior;  /* N0 N1 N2 */
+    int64_t n_outer;   /* pure outer ghost points (radiation condition) */
+    int64_t n_inner;   /* inner ghost points (parity copies) */
+    double dt_cfl;     /* cfl * min over interior points and axes of |S_d| dxx_d */
+    size_t device_bytes; /* device memory held by the grid */
+} nr_grid_info;
+
+/* Defaults: ko_sigma 0.3, eta 2, cfl 0.5, wavespeed 1, f_inf 1 for W and alpha
+ * (0 otherwise), NG 3, enforce_detgb 1, h band [0, inf), stream NULL, and
+ * ampl/sinhw of 10/0.2 (spherical) or 300/0.2 (cylindrical). */
+int nr_params_default(int coords, nr_params* out);
+
+/* Create a grid: builds the per-axis reference-metric arrays, the boundary
+ * maps and the CFL step on the host, uploads them and allocates the state
+ * (y_n) and RK4 work sets (three more 24-gf sets) on params->device.
+ * Nxx: interior cells per axis; N_phi must be even.  *out owned by the caller,
+ * release with nr_grid_destroy.  Errors: NR_EINVAL, NR_EMAP, NR_ENOMEM, NR_ECUDA. */
+int nr_grid_create(int coords, const int Nxx[3], const nr_params* params, nr_grid** out);
+void nr_grid_destroy(nr_grid* grid);
+int nr_query(const nr_grid* grid, nr_grid_info* info);
+
+/* Brill-Lindquist puncture data on the grid-owned state (textbook closed form,
+ * psi = 1 + sum_n m_n/(2|x - x_n|), gammabar = gammahat, W = alpha = psi^-2,
+ * K = Abar = Lambdabar = beta = B = 0) at interior and outer points, an
+ * optional SplitMix64 perturbation perturb_amp * U[-1,1) of the six hDD at
+ * those points (counter (gf << 40) | idx, seed), then inner parity copies.
+ * xyz: 3*npunct Cartesian positions (host).  NR_EINVAL if a grid point lies
+ * within 1e-12 of a puncture (checked on the host). */
+int nr_set_brill_lindquist(nr_grid* grid, int npunct, const double* mass, const double* xyz, double perturb_amp,
+                           uint64_t seed);
+
+/* Right-hand side of all 24 gridfunctions (Sec. 2.1 equations, upwinded
+ * advection, Kreiss-Oliger dissipation) at interior points, from the
+ * 24-gf set y_dev (its ghost points must be valid).  Ghost points of rhs_dev
+ * are not written.  y_dev and rhs_dev: caller-owned device buffers of 24*T
+ * doubles, distinct. */
+int nr_rhs(nr_grid* grid, const double* y_dev, double* rhs_dev);
+
+/* Boundary conditions on a right-hand side (Sec. 3, outer then inner):
+ * radiation condition at pure-outer ghosts computed from y_dev, then parity
+ * copies rhs[ghost] = p * rhs[source] at inner ghosts. */
+int nr_apply_bcs(nr_grid* grid, const double* y_dev, double* rhs_dev);
+
+/* Inner parity copies on any caller-owned 24-gf device set (in place). */
+int nr_apply_inner_bcs(nr_grid* grid, double* gfs_dev);
+
+/* Advance the grid-owned state by nsteps classic RK4 steps of size dt (Sec.
+ * 4.2.1): per substage, the interior RHS with the RK update fused into its
+ * epilogue, the radiation condition at outer ghosts, parity copies at inner
+ * ghosts, and (enforce_detgb) det(gammabar) enforcement.  The 12 launches of
+ * one step are captured once in a CUDA graph (re-captured when dt changes)
+ * and replayed.  dt > 0, nsteps >= 0. */
+int nr_rk4_step(nr_grid* grid, double dt, int nsteps);
+
+/* Hamiltonian constraint (Eq. Hconstraint) at interior points of y_dev (NULL:
+ * the grid-owned state).  H_dev (NULL allowed): caller-owned T doubles, ghost
+ * points set to 0.  l2_out = sqrt(mean H^2), linf_out = max |H| over interior
+ * points with Cartesian radius in [h_rmin, h_rmax]; either may be NULL.  The
+ * norms are reduced on the device in a fixed order and copied to the host:
+ * this call synchronises params.stream when l2_out or linf_out is given. */
+int nr_hamiltonian(nr_grid* grid, const double* y_dev, double* H_dev, double* l2_out, double* linf_out);
+
+/* Copy the grid-owned state (24*T doubles) to / from dst / src.  to_host /
+ * from_host = 1: dst/src is host memory (pinned or pageable) and the call
+ * synchronises; 0: device memory, stream-ordered. */
+int nr_get_state(nr_grid* grid, double* dst, int to_host);
+int nr_set_state(nr_grid* grid, const double* src, int from_host);
+
+/* Wait for all work of the grid's stream. */
+int nr_sync(nr_grid* grid);
+
+/* NaN/Inf guard: NR_ENONFINITE if alpha or W of the grid-owned state holds a
+ * non-finite value (synchronises). */
+int nr_check_finite(nr_grid* grid);
+
+/* Host-only helpers (no GPU needed).
+ * nr_build_maps: boundary maps of a grid, closed-form integer mirrors:
+ *   cls[T]: 0 interior, 1 pure outer ghost, 2 inner ghost; src[T]: source flat
+ *   index (self for cls 0/1); parity[10*T]: sign per tensor type (scalar,
+ *   U0..U2, DD00,DD01,DD02,DD11,DD12,DD22).  Caller-owned host arrays.
+ * nr_dt_cfl: the CFL step of a grid. */
+int nr_build_maps(int coords, const int Nxx[3], int NG, int32_t* src, int8_t* parity, int32_t* cls);
+int nr_dt_cfl(int coords, const int Nxx[3], const nr_params* params, double* dt_out);
+
+/* Measured FP64 FMA throughput of a device (FLOP/s, FMA = 2 FLOP): a fixed-size
+ * kernel of independent FMA chains, best of five timed launches with CUDA events.
+ * The roofline denominator of the FP64-bound kernels.  Synchronises. */
+int nr_fp64_peak(int device, double* flops_out);
+
+/* Thread-local message of the last error (empty string if none). */
+const char* nr_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

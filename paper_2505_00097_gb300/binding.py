@@ -1,0 +1,249 @@
+"""Thin ctypes binding of libnrgpu (include/nr.h).
+
+Argument marshalling only: every step of the evolution runs in the library's
+CUDA kernels.  Device buffers handed to the library are torch CUDA tensors
+(torch provides device memory and streams, nothing else).  If the compiled
+library is missing this module raises instead of falling back to anything.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+NGF = 24
+NR_OK = 0
+STATUS = {0: "NR_OK", 1: "NR_EINVAL", 2: "NR_ENOMEM", 3: "NR_ECUDA", 4: "NR_ETIMEOUT", 5: "NR_ENONFINITE",
+          6: "NR_EMAP"}
+COORDS = {"sinh_spherical": 0, "sinh_cylindrical": 1, "spherical": 2}
+
+# every entry point declared in include/nr.h
+EXPORTS = (
+    "nr_params_default", "nr_grid_create", "nr_grid_destroy", "nr_query", "nr_set_brill_lindquist", "nr_rhs",
+    "nr_apply_bcs", "nr_apply_inner_bcs", "nr_rk4_step", "nr_hamiltonian", "nr_get_state", "nr_set_state",
+    "nr_sync", "nr_check_finite", "nr_build_maps", "nr_dt_cfl", "nr_fp64_peak", "nr_last_error",
+)
+
+
+class NrError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class NrParams(ctypes.Structure):
+    _fields_ = [
+        ("ampl", ctypes.c_double * 3),
+        ("sinhw", ctypes.c_double * 3),
+        ("ko_sigma", ctypes.c_double * 24),
+        ("eta", ctypes.c_double),
+        ("cfl", ctypes.c_double),
+        ("wavespeed", ctypes.c_double * 24),
+        ("f_inf", ctypes.c_double * 24),
+        ("h_rmin", ctypes.c_double),
+        ("h_rmax", ctypes.c_double),
+        ("NG", ctypes.c_int),
+        ("enforce_detgb", ctypes.c_int),
+        ("device", ctypes.c_int),
+        ("reserved", ctypes.c_int),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+class NrGridInfo(ctypes.Structure):
+    _fields_ = [
+        ("N", ctypes.c_int * 3),
+        ("n", ctypes.c_int * 3),
+        ("T", ctypes.c_int64),
+        ("interior", ctypes.c_int64),
+        ("n_outer", ctypes.c_int64),
+        ("n_inner", ctypes.c_int64),
+        ("dt_cfl", ctypes.c_double),
+        ("device_bytes", ctypes.c_size_t),
+    ]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib() -> ctypes.CDLL:
+    """Load libnrgpu.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(f"libnrgpu.so is missing ({path}); run __graft_entry__.build() first")
+    L = ctypes.CDLL(path)
+    vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
+    P = ctypes.POINTER(NrParams)
+    L.nr_params_default.argtypes = [ctypes.c_int, P]
+    L.nr_grid_create.argtypes = [ctypes.c_int, ip, P, ctypes.POINTER(vp)]
+    L.nr_grid_destroy.argtypes = [vp]
+    L.nr_grid_destroy.restype = None
+    L.nr_query.argtypes = [vp, ctypes.POINTER(NrGridInfo)]
+    L.nr_set_brill_lindquist.argtypes = [vp, ctypes.c_int, dp, dp, ctypes.c_double, ctypes.c_uint64]
+    L.nr_rhs.argtypes = [vp, vp, vp]
+    L.nr_apply_bcs.argtypes = [vp, vp, vp]
+    L.nr_apply_inner_bcs.argtypes = [vp, vp]
+    L.nr_rk4_step.argtypes = [vp, ctypes.c_double, ctypes.c_int]
+    L.nr_hamiltonian.argtypes = [vp, vp, vp, dp, dp]
+    L.nr_get_state.argtypes = [vp, vp, ctypes.c_int]
+    L.nr_set_state.argtypes = [vp, vp, ctypes.c_int]
+    L.nr_sync.argtypes = [vp]
+    L.nr_check_finite.argtypes = [vp]
+    L.nr_build_maps.argtypes = [ctypes.c_int, ip, ctypes.c_int, ctypes.POINTER(ctypes.c_int32),
+                                ctypes.POINTER(ctypes.c_int8), ctypes.POINTER(ctypes.c_int32)]
+    L.nr_dt_cfl.argtypes = [ctypes.c_int, ip, P, dp]
+    L.nr_fp64_peak.argtypes = [ctypes.c_int, dp]
+    L.nr_last_error.argtypes = []
+    L.nr_last_error.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def _check(rc: int) -> None:
+    if rc != NR_OK:
+        raise NrError(rc, lib().nr_last_error().decode())
+
+
+def _ptr(t) -> int:
+    """device pointer of a contiguous float64 torch tensor (or an int address)"""
+    if isinstance(t, int):
+        return t
+    assert t.is_cuda and t.dtype.itemsize == 8 and t.is_contiguous()
+    return t.data_ptr()
+
+
+def make_params(spec: dict, stream=None, device: int = 0) -> NrParams:
+    """nr_params from a workload dict (see workloads.py)."""
+    p = NrParams()
+    _check(lib().nr_params_default(int(spec["coords"]), ctypes.byref(p)))
+    for d in range(3):
+        p.ampl[d] = float(spec["ampl"][d])
+        p.sinhw[d] = float(spec["sinhw"][d])
+    ko = spec.get("ko_sigma", 0.3)
+    ko = [float(ko)] * NGF if np.isscalar(ko) else [float(v) for v in ko]
+    ws = spec.get("wavespeed", 1.0)
+    ws = [float(ws)] * NGF if np.isscalar(ws) else [float(v) for v in ws]
+    for g in range(NGF):
+        p.ko_sigma[g] = ko[g]
+        p.wavespeed[g] = ws[g]
+    if spec.get("f_inf") is not None:
+        for g in range(NGF):
+            p.f_inf[g] = float(spec["f_inf"][g])
+    p.eta = float(spec.get("eta", 2.0))
+    p.cfl = float(spec.get("cfl", 0.5))
+    p.h_rmin = float(spec.get("h_rmin", 0.0))
+    p.h_rmax = float(spec.get("h_rmax", 1e300))
+    p.NG = int(spec.get("NG", 3))
+    p.enforce_detgb = int(spec.get("enforce_detgb", 1))
+    p.device = int(device)
+    p.stream = stream
+    return p
+
+
+def build_maps(coords: int, N, NG: int = 3):
+    """Host-only closed-form boundary maps: (src, parity[T,10], cls)."""
+    n = [int(v) + 2 * NG for v in N]
+    T = n[0] * n[1] * n[2]
+    src = np.zeros(T, dtype=np.int32)
+    par = np.zeros(10 * T, dtype=np.int8)
+    cls = np.zeros(T, dtype=np.int32)
+    Nx = (ctypes.c_int * 3)(*[int(v) for v in N])
+    _check(lib().nr_build_maps(int(coords), Nx, NG, src.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                               par.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)),
+                               cls.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
+    return src, par.reshape(T, 10), cls
+
+
+def dt_cfl(spec: dict) -> float:
+    p = make_params(spec)
+    Nx = (ctypes.c_int * 3)(*[int(v) for v in spec["N"]])
+    out = ctypes.c_double()
+    _check(lib().nr_dt_cfl(int(spec["coords"]), Nx, ctypes.byref(p), ctypes.byref(out)))
+    return out.value
+
+
+def fp64_peak(device: int = 0) -> float:
+    """measured FP64 FMA throughput of the device in FLOP/s"""
+    out = ctypes.c_double()
+    _check(lib().nr_fp64_peak(int(device), ctypes.byref(out)))
+    return out.value
+
+
+class Grid:
+    """One nr_grid (library-owned state on the GPU)."""
+
+    def __init__(self, spec: dict, stream=None, device: int = 0):
+        self.spec = dict(spec)
+        self.params = make_params(spec, stream=stream, device=device)
+        h = ctypes.c_void_p()
+        Nx = (ctypes.c_int * 3)(*[int(v) for v in spec["N"]])
+        _check(lib().nr_grid_create(int(spec["coords"]), Nx, ctypes.byref(self.params), ctypes.byref(h)))
+        self.h = h
+        info = NrGridInfo()
+        _check(lib().nr_query(self.h, ctypes.byref(info)))
+        self.info = info
+        self.T = int(info.T)
+        self.n = tuple(int(v) for v in info.n)
+        self.N = tuple(int(v) for v in info.N)
+        self.interior = int(info.interior)
+        self.dt_cfl = float(info.dt_cfl)
+
+    def close(self) -> None:
+        if self.h:
+            lib().nr_grid_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_brill_lindquist(self, masses, positions, perturb_amp: float = 0.0, seed: int = 0) -> None:
+        m = np.ascontiguousarray(masses, dtype=np.float64)
+        x = np.ascontiguousarray(positions, dtype=np.float64).reshape(-1)
+        _check(lib().nr_set_brill_lindquist(self.h, len(m), m.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                            x.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(perturb_amp),
+                                            ctypes.c_uint64(int(seed))))
+
+    def rhs(self, y, out) -> None:
+        _check(lib().nr_rhs(self.h, _ptr(y), _ptr(out)))
+
+    def apply_bcs(self, y, rhs) -> None:
+        _check(lib().nr_apply_bcs(self.h, _ptr(y), _ptr(rhs)))
+
+    def apply_inner_bcs(self, gfs) -> None:
+        _check(lib().nr_apply_inner_bcs(self.h, _ptr(gfs)))
+
+    def rk4_step(self, dt: float, nsteps: int = 1) -> None:
+        _check(lib().nr_rk4_step(self.h, float(dt), int(nsteps)))
+
+    def hamiltonian(self, y=None, H=None):
+        l2, linf = ctypes.c_double(), ctypes.c_double()
+        _check(lib().nr_hamiltonian(self.h, None if y is None else _ptr(y), None if H is None else _ptr(H),
+                                    ctypes.byref(l2), ctypes.byref(linf)))
+        return l2.value, linf.value
+
+    def get_state(self, dst, to_host: bool) -> None:
+        addr = dst.ctypes.data if isinstance(dst, np.ndarray) else (dst.data_ptr() if not isinstance(dst, int) else dst)
+        _check(lib().nr_get_state(self.h, addr, int(bool(to_host))))
+
+    def set_state(self, src, from_host: bool) -> None:
+        addr = src.ctypes.data if isinstance(src, np.ndarray) else (src.data_ptr() if not isinstance(src, int) else src)
+        _check(lib().nr_set_state(self.h, addr, int(bool(from_host))))
+
+    def sync(self) -> None:
+        _check(lib().nr_sync(self.h))
+
+    def check_finite(self) -> None:
+        _check(lib().nr_check_finite(self.h))

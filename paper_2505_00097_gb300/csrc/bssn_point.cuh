@@ -1,0 +1,795 @@
+// bssn_point.cuh -- per-point BSSN right-hand side in the orthonormal
+// (rescaled) frame, FP64, for sm_103a.
+//
+// The evolved gridfunctions are the rescaled components of arXiv 2505.00097
+// Sec. 2.2: h_ij, a_ij, lambda^i, vet^i, bet^i are the components of
+// eps_ij, Abar_ij, Lambdabar^i, beta^i, B^i in the basis e~_i = e^_i / S_i,
+// in which the reference metric is the identity.  This kernel evaluates the
+// BSSN system of Sec. 2.1 (Eqs. metric_RHS_orig_final .. Lambda_RHS_orig_final,
+// the Ricci tensor and the gauge Eqs. gauge_eqns, damping_eta_final) directly
+// in that frame.  The flat reference connection Dhat then only contributes
+// rotation generators with a handful of nonzero coefficients:
+//   spherical-like:   Omega_1 = a J01,  Omega_2 = b J02 + c J12  (a=b=1/r, c=cot(th)/r)
+//   cylindrical-like: Omega_1 = a J01                          (a=1/rho)
+// where (J_pq V)_q = V_p, (J_pq V)_p = -V_q.  Only the rescaled
+// gridfunctions are finite-differenced (4th-order centred; mixed second
+// derivatives as products of first-derivative stencils; upwind-biased
+// stencils for the beta^k d_k parts; 6th-difference Kreiss-Oliger
+// dissipation), exactly as in the coordinate-basis formulation, so both give
+// the same discrete right-hand side up to rounding.
+//
+// Readings of the paper used here: Eq. Lambda_RHS_orig_final with the two
+// factors of alpha restored (-2 Abar^ij (d_j alpha - 6 alpha d_j phi) +
+// 2 alpha Abar^jk Delta^i_jk); d_perp = d_t - L_beta with only the
+// beta^k d_k parts upwinded; beta_j in 2 Dhat_(i beta_j) lowered with
+// gammahat; Delta^k_ij built from Dhat eps only; the gauge equations with
+// coordinate partial derivatives of the unrescaled beta^i, B^i, and the full
+// d_t Lambdabar^i (without dissipation) inside d_t B^i.
+#pragma once
+
+#include <stdint.h>
+
+namespace nrk {
+
+constexpr int NGF = 24;
+enum : int { G_HDD = 0, G_ADD = 6, G_CF = 12, G_TRK = 13, G_LAM = 14, G_VET = 17, G_BET = 20, G_ALPHA = 23 };
+enum : int { FAM_SPH = 0, FAM_CYL = 1 };
+
+// symmetric pair index: (0,0)=0 (0,1)=1 (0,2)=2 (1,1)=3 (1,2)=4 (2,2)=5
+__host__ __device__ constexpr int sp(int i, int j) { return (i > j) ? sp(j, i) : (i == 0 ? j : (i == 1 ? j + 2 : 5)); }
+__host__ __device__ constexpr int spi(int s) { return s < 3 ? 0 : (s < 5 ? 1 : 2); }
+__host__ __device__ constexpr int spj(int s) { return s < 3 ? s : (s < 5 ? s - 2 : 2); }
+__host__ __device__ constexpr bool offd(int s) { return s == 1 || s == 2 || s == 4; }
+
+// Frame geometry at one point, assembled from per-axis 1D arrays.
+struct Geo {
+    double D[3];   // e_k f = D[k] * d1raw_k(f),  D = 1/(12 dxx_k S_k)
+    double D2[3];  // 1/(12 dxx_k^2 S_k^2)
+    double DD[3];  // D0 D1, D0 D2, D1 D2
+    double a, b, c;                // rotation coefficients
+    double d00, d22;               // dS_0/dxx0 / S_0^2, dS_2/dxx2 / S_2^2 (cylindrical)
+    double e0a, e0b, e0c, e1c;     // frame derivatives of a, b, c
+};
+
+__device__ __forceinline__ double ld(const double* p) { return __ldg(p); }
+
+// ---- raw stencil sums (weights only; spacing and scale factors in Geo)
+__device__ __forceinline__ double d1raw(const double* f, long s)
+{
+    return fma(8.0, ld(f + s) - ld(f - s), ld(f - 2 * s) - ld(f + 2 * s));
+}
+__device__ __forceinline__ double d2raw(const double* f, long s)
+{
+    return fma(-30.0, ld(f), fma(16.0, ld(f + s) + ld(f - s), -(ld(f + 2 * s) + ld(f - 2 * s))));
+}
+__device__ __forceinline__ double mixraw(const double* f, long sa, long sb)
+{
+    double m2 = d1raw(f - 2 * sb, sa), m1 = d1raw(f - sb, sa);
+    double p1 = d1raw(f + sb, sa), p2 = d1raw(f + 2 * sb, sa);
+    return fma(8.0, p1 - m1, m2 - p2);
+}
+// upwind-biased: -3 g[-1] - 10 g[0] + 18 g[1] - 6 g[2] + g[3], g[o] = f[o*s]
+// (s = -stride gives the mirrored stencil up to an overall sign)
+__device__ __forceinline__ double upraw(const double* f, long s)
+{
+    double t1 = fma(-3.0, ld(f - s), ld(f + 3 * s));
+    double t2 = fma(3.0, ld(f + s), -ld(f + 2 * s));
+    return fma(-10.0, ld(f), fma(6.0, t2, t1));
+}
+// sixth difference without its centre term: (f-3+f3) - 6 (f-2+f2) + 15 (f-1+f1)
+__device__ __forceinline__ double koraw(const double* f, long s)
+{
+    return fma(15.0, ld(f - s) + ld(f + s), fma(-6.0, ld(f - 2 * s) + ld(f + 2 * s), ld(f - 3 * s) + ld(f + 3 * s)));
+}
+
+// ---- frame Hessian of a component function:
+// H_kl f = e_k e_l f - omega^m_kl e_m f  (symmetric in kl)
+template <int FAM, int KL>
+__device__ __forceinline__ double hess(const double* f, const long st[3], const Geo& g, const double df[3])
+{
+    if constexpr (KL == 0) return fma(g.D2[0], d2raw(f, st[0]), -g.d00 * df[0]);
+    if constexpr (KL == 1) return fma(g.DD[0], mixraw(f, st[0], st[1]), -g.a * df[1]);
+    if constexpr (KL == 2) {
+        if constexpr (FAM == FAM_SPH) return fma(g.DD[1], mixraw(f, st[0], st[2]), -g.b * df[2]);
+        else return g.DD[1] * mixraw(f, st[0], st[2]);
+    }
+    if constexpr (KL == 3) return fma(g.D2[1], d2raw(f, st[1]), g.a * df[0]);
+    if constexpr (KL == 4) {
+        if constexpr (FAM == FAM_SPH) return fma(g.DD[2], mixraw(f, st[1], st[2]), -g.c * df[2]);
+        else return g.DD[2] * mixraw(f, st[1], st[2]);
+    }
+    if constexpr (KL == 5) {
+        if constexpr (FAM == FAM_SPH) return fma(g.D2[2], d2raw(f, st[2]), fma(g.b, df[0], g.c * df[1]));
+        else return fma(g.D2[2], d2raw(f, st[2]), -g.d22 * df[2]);
+    }
+    return 0.0;
+}
+
+template <int FAM>
+__device__ __forceinline__ void hess6(const double* f, const long st[3], const Geo& g, const double df[3], double H[6])
+{
+    H[0] = hess<FAM, 0>(f, st, g, df);
+    H[1] = hess<FAM, 1>(f, st, g, df);
+    H[2] = hess<FAM, 2>(f, st, g, df);
+    H[3] = hess<FAM, 3>(f, st, g, df);
+    H[4] = hess<FAM, 4>(f, st, g, df);
+    H[5] = hess<FAM, 5>(f, st, g, df);
+}
+
+// ---- rotation generators acting on vectors / symmetric tensors: out += c * J_pq (.)
+__device__ __forceinline__ void j01v(double c, const double V[3], double o[3]) { o[1] = fma(c, V[0], o[1]); o[0] = fma(-c, V[1], o[0]); }
+__device__ __forceinline__ void j02v(double c, const double V[3], double o[3]) { o[2] = fma(c, V[0], o[2]); o[0] = fma(-c, V[2], o[0]); }
+__device__ __forceinline__ void j12v(double c, const double V[3], double o[3]) { o[2] = fma(c, V[1], o[2]); o[1] = fma(-c, V[2], o[1]); }
+
+__device__ __forceinline__ void j01s(double c, const double T[6], double o[6])
+{
+    double c2 = c + c;
+    o[0] = fma(-c2, T[1], o[0]);
+    o[1] = fma(c, T[0] - T[3], o[1]);
+    o[2] = fma(-c, T[4], o[2]);
+    o[3] = fma(c2, T[1], o[3]);
+    o[4] = fma(c, T[2], o[4]);
+}
+__device__ __forceinline__ void j02s(double c, const double T[6], double o[6])
+{
+    double c2 = c + c;
+    o[0] = fma(-c2, T[2], o[0]);
+    o[1] = fma(-c, T[4], o[1]);
+    o[2] = fma(c, T[0] - T[5], o[2]);
+    o[4] = fma(c, T[1], o[4]);
+    o[5] = fma(c2, T[2], o[5]);
+}
+__device__ __forceinline__ void j12s(double c, const double T[6], double o[6])
+{
+    double c2 = c + c;
+    o[1] = fma(-c, T[2], o[1]);
+    o[2] = fma(c, T[1], o[2]);
+    o[3] = fma(-c2, T[4], o[3]);
+    o[4] = fma(c, T[3] - T[5], o[4]);
+    o[5] = fma(c2, T[4], o[5]);
+}
+
+// Omega_k acting on a vector / symmetric tensor, accumulated into o
+template <int FAM, int K>
+__device__ __forceinline__ void omv(const Geo& g, double s, const double V[3], double o[3])
+{
+    if constexpr (K == 1) j01v(g.a * s, V, o);
+    if constexpr (K == 2 && FAM == FAM_SPH) { j02v(g.b * s, V, o); j12v(g.c * s, V, o); }
+}
+template <int FAM, int K>
+__device__ __forceinline__ void oms(const Geo& g, double s, const double T[6], double o[6])
+{
+    if constexpr (K == 1) j01s(g.a * s, T, o);
+    if constexpr (K == 2 && FAM == FAM_SPH) { j02s(g.b * s, T, o); j12s(g.c * s, T, o); }
+}
+
+__device__ __forceinline__ double gsym(const double m[6], int i, int j) { return m[sp(i, j)]; }
+
+// Inputs of the point evaluation that the kernel precomputes once.
+struct PointIn {
+    const double* y;  // state at this point: y + idx (gridfunction g at y[g*T])
+    long T;
+    long st[3];
+    Geo g;
+};
+
+// Metric-sector quantities shared by the right-hand side and the
+// Hamiltonian constraint.
+struct MetricPart {
+    double h[6], gi[6], gw[6];
+    double dh[3][6];
+    double GH[6];        // gammabar^ij H_kl h_ij
+    double Dl[3][6];     // Delta_kij (first index lowered)
+    double Dup[3][6];    // Delta^k_ij
+    double Dvec[3];      // Delta^k
+    double Dtr[3];       // Delta^k_km
+    double Ric[6];       // Rbar_ij
+    double W, iW, dphi[3], DDphi[6];
+};
+
+template <int FAM, bool NEED_GH>
+__device__ __forceinline__ void metric_part(const PointIn& P, MetricPart& M)
+{
+    const double* y = P.y;
+    const long T = P.T;
+    const Geo& g = P.g;
+    const long* st = P.st;
+    auto F = [&](int gf) { return y + (long)gf * T; };
+    double* h = M.h;
+    double* gi = M.gi;
+    double* gw = M.gw;
+#pragma unroll
+    for (int s = 0; s < 6; s++) h[s] = ld(F(G_HDD + s));
+    const double W = ld(F(G_CF));
+    M.W = W;
+
+    // ---------------- conformal metric gammabar_ij = delta_ij + h_ij and its inverse
+    const double g00 = 1.0 + h[0], g11 = 1.0 + h[3], g22 = 1.0 + h[5];
+    gi[0] = fma(g11, g22, -h[4] * h[4]);
+    gi[1] = fma(h[2], h[4], -h[1] * g22);
+    gi[2] = fma(h[1], h[4], -h[2] * g11);
+    gi[3] = fma(g00, g22, -h[2] * h[2]);
+    gi[4] = fma(h[1], h[2], -g00 * h[4]);
+    gi[5] = fma(g00, g11, -h[1] * h[1]);
+    const double det = fma(g00, gi[0], fma(h[1], gi[1], h[2] * gi[2]));
+    const double rdw = 1.0 / (det * W);   // one division gives 1/det and 1/W
+    const double idet = rdw * W;
+    M.iW = rdw * det;
+#pragma unroll
+    for (int s = 0; s < 6; s++) gi[s] *= idet;
+#pragma unroll
+    for (int s = 0; s < 6; s++) gw[s] = offd(s) ? gi[s] + gi[s] : gi[s];
+
+    // ---------------- first frame derivatives of h
+    double (*dh)[6] = M.dh;
+#pragma unroll
+    for (int k = 0; k < 3; k++)
+#pragma unroll
+        for (int s = 0; s < 6; s++) dh[k][s] = g.D[k] * d1raw(F(G_HDD + s), st[k]);
+
+    // ---------------- Hessians of h contracted two ways:
+    // Lh_ij = gammabar^kl H_kl h_ij,  GH_kl = gammabar^ij H_kl h_ij
+    double Lh[6];
+#pragma unroll
+    for (int s = 0; s < 6; s++) {
+        double df[3] = {dh[0][s], dh[1][s], dh[2][s]};
+        double H[6];
+        hess6<FAM>(F(G_HDD + s), st, g, df, H);
+        Lh[s] = gw[0] * H[0];
+#pragma unroll
+        for (int kl = 1; kl < 6; kl++) Lh[s] = fma(gw[kl], H[kl], Lh[s]);
+        if constexpr (NEED_GH) {
+            if (s == 0) {
+#pragma unroll
+                for (int kl = 0; kl < 6; kl++) M.GH[kl] = gw[0] * H[kl];
+            } else {
+#pragma unroll
+                for (int kl = 0; kl < 6; kl++) M.GH[kl] = fma(gw[s], H[kl], M.GH[kl]);
+            }
+        }
+    }
+
+    // ---------------- Dhat_k h_ij, Delta_kij (first index lowered), Delta^k_ij, Delta^k
+    double Dh[3][6];
+#pragma unroll
+    for (int s = 0; s < 6; s++) { Dh[0][s] = dh[0][s]; Dh[1][s] = dh[1][s]; Dh[2][s] = dh[2][s]; }
+    oms<FAM, 1>(g, 1.0, h, Dh[1]);
+    oms<FAM, 2>(g, 1.0, h, Dh[2]);
+    double (*Dl)[6] = M.Dl;
+#pragma unroll
+    for (int k = 0; k < 3; k++)
+#pragma unroll
+        for (int s = 0; s < 6; s++) {
+            const int i = spi(s), j = spj(s);
+            Dl[k][s] = 0.5 * (Dh[i][sp(j, k)] + Dh[j][sp(i, k)] - Dh[k][s]);
+        }
+    double (*Dup)[6] = M.Dup;
+#pragma unroll
+    for (int k = 0; k < 3; k++)
+#pragma unroll
+        for (int s = 0; s < 6; s++)
+            Dup[k][s] = fma(gsym(gi, k, 2), Dl[2][s], fma(gsym(gi, k, 1), Dl[1][s], gsym(gi, k, 0) * Dl[0][s]));
+    double* Dvec = M.Dvec;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        double t = gw[0] * Dup[k][0];
+#pragma unroll
+        for (int s = 1; s < 6; s++) t = fma(gw[s], Dup[k][s], t);
+        Dvec[k] = t;
+    }
+    // Delta^k_km = 1/2 gammabar^ab e_m h_ab
+#pragma unroll
+    for (int m = 0; m < 3; m++) {
+        double t = gw[0] * dh[m][0];
+#pragma unroll
+        for (int s = 1; s < 6; s++) t = fma(gw[s], dh[m][s], t);
+        M.Dtr[m] = 0.5 * t;
+    }
+
+    // ---------------- Ricci tensor
+    // gammabar^kl Dhat_k Dhat_l h_ij = Lh + 2 Omega_l.V_l + (linear and quadratic generator terms).h
+    double Lfull[6];
+    {
+        double V1[6], V2[6], Y1[6] = {0, 0, 0, 0, 0, 0}, Y2[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll
+        for (int s = 0; s < 6; s++) {
+            V1[s] = fma(gi[4], dh[2][s], fma(gi[3], dh[1][s], gi[1] * dh[0][s]));
+            V2[s] = fma(gi[5], dh[2][s], fma(gi[4], dh[1][s], gi[2] * dh[0][s]));
+        }
+        j01s(g.a, h, Y1);                                                        // Y1 = Omega_1 h
+        if constexpr (FAM == FAM_SPH) { j02s(g.b, h, Y2); j12s(g.c, h, Y2); }    // Y2 = Omega_2 h
+        double X01[6], X02[6], X12[6];
+        const double a2 = g.a + g.a;
+        if constexpr (FAM == FAM_SPH) {
+            const double c1 = fma(g.a, gi[1], -g.c * gi[5]);
+            const double c2 = fma(g.b, gi[2], g.c * gi[4]);
+            const double g01 = fma(gi[1], g.e0a, -c1 * g.a);
+            const double g02 = fma(gi[2], g.e0b, -c2 * g.b);
+            const double g12 = fma(gi[2], g.e0c, fma(gi[4], g.e1c, -c2 * g.c));
+            const double b2 = g.b + g.b, cc2 = g.c + g.c;
+            const double a11 = g.a * gi[3], a12 = g.a * gi[4];
+            const double b12 = g.b * gi[4], b22 = g.b * gi[5];
+            const double k12 = g.c * gi[4], k22 = g.c * gi[5];
+#pragma unroll
+            for (int s = 0; s < 6; s++) {
+                X01[s] = fma(a2, V1[s], fma(g01, h[s], fma(a11, Y1[s], a12 * Y2[s])));
+                X02[s] = fma(b2, V2[s], fma(g02, h[s], fma(b12, Y1[s], b22 * Y2[s])));
+                X12[s] = fma(cc2, V2[s], fma(g12, h[s], fma(k12, Y1[s], k22 * Y2[s])));
+            }
+        } else {
+            const double g01 = gi[1] * (g.e0a - g.a * g.a);
+            const double a11 = g.a * gi[3];
+#pragma unroll
+            for (int s = 0; s < 6; s++) X01[s] = fma(a2, V1[s], fma(g01, h[s], a11 * Y1[s]));
+        }
+#pragma unroll
+        for (int s = 0; s < 6; s++) Lfull[s] = Lh[s];
+        j01s(1.0, X01, Lfull);
+        if constexpr (FAM == FAM_SPH) { j02s(1.0, X02, Lfull); j12s(1.0, X12, Lfull); }
+    }
+    // Dhat_j lambda^k
+    double lam[3], Dlam[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; i++) lam[i] = ld(F(G_LAM + i));
+#pragma unroll
+    for (int j = 0; j < 3; j++)
+#pragma unroll
+        for (int k = 0; k < 3; k++) Dlam[j][k] = g.D[j] * d1raw(F(G_LAM + k), st[j]);
+    omv<FAM, 1>(g, 1.0, lam, Dlam[1]);
+    omv<FAM, 2>(g, 1.0, lam, Dlam[2]);
+    // Y[j][m][k] = gammabar^kl Delta_jml
+    double Yv[3][3][3];
+#pragma unroll
+    for (int j = 0; j < 3; j++)
+#pragma unroll
+        for (int m = 0; m < 3; m++)
+#pragma unroll
+            for (int k = 0; k < 3; k++)
+                Yv[j][m][k] = fma(gsym(gi, k, 2), Dl[j][sp(m, 2)], fma(gsym(gi, k, 1), Dl[j][sp(m, 1)], gsym(gi, k, 0) * Dl[j][sp(m, 0)]));
+    {
+        double Aij[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                double t = Dup[0][sp(0, i)] * Yv[j][0][0];
+#pragma unroll
+                for (int q = 1; q < 9; q++) {
+                    const int k = q / 3, m = q % 3;
+                    t = fma(Dup[m][sp(k, i)], Yv[j][m][k], t);
+                }
+                Aij[i][j] = t;
+            }
+#pragma unroll
+        for (int s = 0; s < 6; s++) {
+            const int i = spi(s), j = spj(s);
+            double C = Dup[0][sp(i, 0)] * Yv[0][j][0];
+#pragma unroll
+            for (int q = 1; q < 9; q++) {
+                const int k = q / 3, m = q % 3;
+                C = fma(Dup[m][sp(i, k)], Yv[m][j][k], C);
+            }
+            // 1/2 (gammabar_ki Dhat_j lambda^k + gammabar_kj Dhat_i lambda^k)
+            double t2 = Dlam[j][i] + Dlam[i][j];
+#pragma unroll
+            for (int k = 0; k < 3; k++) t2 = fma(h[sp(k, i)], Dlam[j][k], fma(h[sp(k, j)], Dlam[i][k], t2));
+            // Delta^k Delta_(ij)k
+            double t3 = Dvec[0] * (Dl[i][sp(j, 0)] + Dl[j][sp(i, 0)]);
+            t3 = fma(Dvec[1], Dl[i][sp(j, 1)] + Dl[j][sp(i, 1)], t3);
+            t3 = fma(Dvec[2], Dl[i][sp(j, 2)] + Dl[j][sp(i, 2)], t3);
+            M.Ric[s] = fma(-0.5, Lfull[s], fma(0.5, t2 + t3, Aij[i][j] + Aij[j][i] + C));
+        }
+    }
+
+    // ---------------- conformal factor: phi = -1/2 ln W
+    double dW[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) dW[k] = g.D[k] * d1raw(F(G_CF), st[k]);
+    const double mhiW = -0.5 * M.iW;
+#pragma unroll
+    for (int k = 0; k < 3; k++) M.dphi[k] = mhiW * dW[k];
+    {
+        double HW[6];
+        hess6<FAM>(F(G_CF), st, g, dW, HW);
+#pragma unroll
+        for (int s = 0; s < 6; s++) {
+            const int i = spi(s), j = spj(s);
+            const double Hphi = fma(mhiW, HW[s], 2.0 * M.dphi[i] * M.dphi[j]);
+            M.DDphi[s] = Hphi - fma(Dup[2][s], M.dphi[2], fma(Dup[1][s], M.dphi[1], Dup[0][s] * M.dphi[0]));
+        }
+    }
+}
+
+// Output: the 24 right-hand sides without the beta^k d_k advection and
+// without Kreiss-Oliger dissipation (added by the caller, see adv_ko()).
+template <int FAM>
+__device__ __forceinline__ void rhs_core(const PointIn& P, double eta, double out[NGF])
+{
+    const double* y = P.y;
+    const long T = P.T;
+    const Geo& g = P.g;
+    const long* st = P.st;
+    auto F = [&](int gf) { return y + (long)gf * T; };
+
+    MetricPart M;
+    metric_part<FAM, true>(P, M);
+    const double* h = M.h;
+    const double* gi = M.gi;
+    const double* gw = M.gw;
+    const double (*dh)[6] = M.dh;
+    const double (*Dup)[6] = M.Dup;
+    const double* Dvec = M.Dvec;
+    const double* Dtr = M.Dtr;
+    const double* GH = M.GH;
+    const double* Ric = M.Ric;
+    const double* dphi = M.dphi;
+    const double* DDphi = M.DDphi;
+    const double W = M.W;
+
+    double a[6], lam[3], vet[3], bet[3];
+#pragma unroll
+    for (int s = 0; s < 6; s++) a[s] = ld(F(G_ADD + s));
+#pragma unroll
+    for (int i = 0; i < 3; i++) { lam[i] = ld(F(G_LAM + i)); vet[i] = ld(F(G_VET + i)); bet[i] = ld(F(G_BET + i)); }
+    const double K = ld(F(G_TRK)), al = ld(F(G_ALPHA));
+    double dK[3], dal[3], dvet[3][3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        dK[k] = g.D[k] * d1raw(F(G_TRK), st[k]);
+        dal[k] = g.D[k] * d1raw(F(G_ALPHA), st[k]);
+#pragma unroll
+        for (int i = 0; i < 3; i++) dvet[k][i] = g.D[k] * d1raw(F(G_VET + i), st[k]);
+    }
+    double DDal[6];
+    {
+        double Hal[6];
+        hess6<FAM>(F(G_ALPHA), st, g, dal, Hal);
+#pragma unroll
+        for (int s = 0; s < 6; s++) DDal[s] = Hal[s] - fma(Dup[2][s], dal[2], fma(Dup[1][s], dal[1], Dup[0][s] * dal[0]));
+    }
+
+    // ---------------- Abar with raised indices
+    double Aud[3][3];  // Abar^k_j
+#pragma unroll
+    for (int k = 0; k < 3; k++)
+#pragma unroll
+        for (int j = 0; j < 3; j++)
+            Aud[k][j] = fma(gsym(gi, k, 2), a[sp(2, j)], fma(gsym(gi, k, 1), a[sp(1, j)], gsym(gi, k, 0) * a[sp(0, j)]));
+    double Auu[6];
+#pragma unroll
+    for (int s = 0; s < 6; s++) {
+        const int i = spi(s), j = spj(s);
+        Auu[s] = fma(Aud[i][2], gsym(gi, 2, j), fma(Aud[i][1], gsym(gi, 1, j), Aud[i][0] * gsym(gi, 0, j)));
+    }
+    const double trA = Aud[0][0] + Aud[1][1] + Aud[2][2];
+    double AA = a[0] * Auu[0];
+#pragma unroll
+    for (int s = 1; s < 6; s++) AA = fma(offd(s) ? a[s] + a[s] : a[s], Auu[s], AA);
+
+    // ---------------- shift: Dhat_k beta^i, second covariant derivatives, divergences
+    double Db[3][3];  // Db[i][k] = Dhat_k beta^i
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int k = 0; k < 3; k++) Db[i][k] = dvet[k][i];
+    {
+        double t1[3] = {0, 0, 0}, t2[3] = {0, 0, 0};
+        omv<FAM, 1>(g, 1.0, vet, t1);
+        omv<FAM, 2>(g, 1.0, vet, t2);
+#pragma unroll
+        for (int i = 0; i < 3; i++) { Db[i][1] += t1[i]; Db[i][2] += t2[i]; }
+    }
+    const double divhat = Db[0][0] + Db[1][1] + Db[2][2];
+    const double divbar = fma(Dtr[2], vet[2], fma(Dtr[1], vet[1], fma(Dtr[0], vet[0], divhat)));
+    // DDb[kl][i] = Dhat_k Dhat_l beta^i
+    double DDb[6][3];
+    {
+        double Hv[3][6];
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            double df[3] = {dvet[0][i], dvet[1][i], dvet[2][i]};
+            hess6<FAM>(F(G_VET + i), st, g, df, Hv[i]);
+        }
+#pragma unroll
+        for (int kl = 0; kl < 6; kl++)
+#pragma unroll
+            for (int i = 0; i < 3; i++) DDb[kl][i] = Hv[i][kl];
+        // (0,1): J01 (a e_0 vet + e0a vet)
+        {
+            double t[3];
+#pragma unroll
+            for (int i = 0; i < 3; i++) t[i] = fma(g.a, dvet[0][i], g.e0a * vet[i]);
+            j01v(1.0, t, DDb[1]);
+        }
+        // (1,1): J01 (2 a e_1 vet + a^2 J01 vet)
+        {
+            double u[3] = {0, 0, 0};
+            j01v(g.a * g.a, vet, u);
+            double t[3];
+#pragma unroll
+            for (int i = 0; i < 3; i++) t[i] = fma(g.a + g.a, dvet[1][i], u[i]);
+            j01v(1.0, t, DDb[3]);
+        }
+        if constexpr (FAM == FAM_SPH) {
+            // (0,2): J02 (b e_0 vet + e0b vet) + J12 (c e_0 vet + e0c vet)
+            {
+                double t[3], u[3];
+#pragma unroll
+                for (int i = 0; i < 3; i++) { t[i] = fma(g.b, dvet[0][i], g.e0b * vet[i]); u[i] = fma(g.c, dvet[0][i], g.e0c * vet[i]); }
+                j02v(1.0, t, DDb[2]);
+                j12v(1.0, u, DDb[2]);
+            }
+            // Z = Omega_2 vet
+            double Z[3] = {0, 0, 0};
+            j02v(g.b, vet, Z);
+            j12v(g.c, vet, Z);
+            // (1,2): J02 (b e_1 vet) + J12 (c e_1 vet + e1c vet) + J01 (a e_2 vet + a Z)
+            {
+                double t[3], u[3], w[3];
+#pragma unroll
+                for (int i = 0; i < 3; i++) {
+                    t[i] = g.b * dvet[1][i];
+                    u[i] = fma(g.c, dvet[1][i], g.e1c * vet[i]);
+                    w[i] = g.a * (dvet[2][i] + Z[i]);
+                }
+                j02v(1.0, t, DDb[4]);
+                j12v(1.0, u, DDb[4]);
+                j01v(1.0, w, DDb[4]);
+            }
+            // (2,2): J01 (c a vet) + J02 (2 b e_2 vet + b Z) + J12 (2 c e_2 vet + c Z)
+            {
+                double t[3], u[3];
+#pragma unroll
+                for (int i = 0; i < 3; i++) {
+                    const double e2 = dvet[2][i] + dvet[2][i];
+                    t[i] = g.b * (e2 + Z[i]);
+                    u[i] = g.c * (e2 + Z[i]);
+                }
+                j01v(g.c * g.a, vet, DDb[5]);
+                j02v(1.0, t, DDb[5]);
+                j12v(1.0, u, DDb[5]);
+            }
+        } else {
+            // (1,2): J01 (a e_2 vet)
+            double w[3];
+#pragma unroll
+            for (int i = 0; i < 3; i++) w[i] = g.a * dvet[2][i];
+            j01v(1.0, w, DDb[4]);
+        }
+    }
+    // gammabar^kl Dhat_k Dhat_l beta^i
+    double LapB[3];
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        double t = gw[0] * DDb[0][i];
+#pragma unroll
+        for (int kl = 1; kl < 6; kl++) t = fma(gw[kl], DDb[kl][i], t);
+        LapB[i] = t;
+    }
+    // e_l (Dbar_k beta^k) = sum_k DDb[kl][k] + sum_m [e_l(Delta^k_km) vet^m + Delta^k_km e_l vet^m]
+    // e_l(Delta^k_km) = 1/2 (GH_lm - Q_lm) - (Omega_l Dtr)_m,  Q_lm = tr(gbinv e_l h gbinv e_m h)
+    double gdiv[3];
+    {
+        double M[3][3][3];  // M[l] = gbinv . e_l h
+#pragma unroll
+        for (int l = 0; l < 3; l++)
+#pragma unroll
+            for (int i = 0; i < 3; i++)
+#pragma unroll
+                for (int j = 0; j < 3; j++)
+                    M[l][i][j] = fma(gsym(gi, i, 2), dh[l][sp(2, j)], fma(gsym(gi, i, 1), dh[l][sp(1, j)], gsym(gi, i, 0) * dh[l][sp(0, j)]));
+        double Q[6];
+#pragma unroll
+        for (int s = 0; s < 6; s++) {
+            const int l = spi(s), m = spj(s);
+            double t = M[l][0][0] * M[m][0][0];
+#pragma unroll
+            for (int q = 1; q < 9; q++) t = fma(M[l][q / 3][q % 3], M[m][q % 3][q / 3], t);
+            Q[s] = t;
+        }
+        double OD[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};  // (Omega_l Dtr)
+        omv<FAM, 1>(g, 1.0, Dtr, OD[1]);
+        omv<FAM, 2>(g, 1.0, Dtr, OD[2]);
+#pragma unroll
+        for (int l = 0; l < 3; l++) {
+            double t = DDb[sp(l, 0)][0] + DDb[sp(l, 1)][1] + DDb[sp(l, 2)][2];
+#pragma unroll
+            for (int m = 0; m < 3; m++) {
+                const double edtr = fma(0.5, GH[sp(l, m)] - Q[sp(l, m)], -OD[l][m]);
+                t = fma(edtr, vet[m], fma(Dtr[m], dvet[l][m], t));
+            }
+            gdiv[l] = t;
+        }
+    }
+
+    // ================= right-hand sides (advection and dissipation excluded)
+    // Eq. metric_RHS_orig_final + Lie terms:
+    // d_t h_ij = [Omega part of beta^k Dhat_k h_ij] + gammabar_kj Dhat_i beta^k + gammabar_ik Dhat_j beta^k
+    //            - 2/3 gammabar_ij (Dbar.beta - alpha Abar^k_k) - 2 alpha a_ij
+    {
+        double r[6];
+        const double tt = (2.0 / 3.0) * fma(-al, trA, divbar);
+#pragma unroll
+        for (int s = 0; s < 6; s++) {
+            const int i = spi(s), j = spj(s);
+            double t = Db[j][i] + Db[i][j];
+#pragma unroll
+            for (int k = 0; k < 3; k++) t = fma(h[sp(k, j)], Db[k][i], fma(h[sp(i, k)], Db[k][j], t));
+            const double gij = (i == j) ? 1.0 + h[s] : h[s];
+            r[s] = fma(-2.0 * al, a[s], fma(-tt, gij, t));
+        }
+        oms<FAM, 1>(g, vet[1], h, r);
+        oms<FAM, 2>(g, vet[2], h, r);
+#pragma unroll
+        for (int s = 0; s < 6; s++) out[G_HDD + s] = r[s];
+    }
+    // Eq. Abar_RHS_orig_final + Lie terms
+    {
+        double X[6];
+#pragma unroll
+        for (int s = 0; s < 6; s++) {
+            const int i = spi(s), j = spj(s);
+            const double t = fma(2.0 * al, fma(2.0, dphi[i] * dphi[j], -DDphi[s]), -DDal[s]);
+            X[s] = fma(al, Ric[s], fma(2.0, fma(dal[i], dphi[j], dal[j] * dphi[i]), t));
+        }
+        double trX = gw[0] * X[0];
+#pragma unroll
+        for (int s = 1; s < 6; s++) trX = fma(gw[s], X[s], trX);
+        const double W2 = W * W;
+        const double third_trX = trX * (1.0 / 3.0);
+        const double c_div = (-2.0 / 3.0) * divbar + al * K;
+        double r[6];
+#pragma unroll
+        for (int s = 0; s < 6; s++) {
+            const int i = spi(s), j = spj(s);
+            double t = 0.0;
+            t = fma(a[sp(0, j)], Db[0][i], a[sp(i, 0)] * Db[0][j]);
+#pragma unroll
+            for (int k = 1; k < 3; k++) t = fma(a[sp(k, j)], Db[k][i], fma(a[sp(i, k)], Db[k][j], t));
+            const double AAij = fma(a[sp(i, 2)], Aud[2][j], fma(a[sp(i, 1)], Aud[1][j], a[sp(i, 0)] * Aud[0][j]));
+            const double gij = (i == j) ? 1.0 + h[s] : h[s];
+            const double XTF = fma(-third_trX, gij, X[s]);
+            r[s] = fma(W2, XTF, fma(-2.0 * al, AAij, fma(c_div, a[s], t)));
+        }
+        oms<FAM, 1>(g, vet[1], a, r);
+        oms<FAM, 2>(g, vet[2], a, r);
+#pragma unroll
+        for (int s = 0; s < 6; s++) out[G_ADD + s] = r[s];
+        // Eq. W_RHS_orig_final
+        out[G_CF] = (-1.0 / 3.0) * W * fma(-al, K, divbar);
+        // Eq. K_RHS_orig_final
+        double lapal = gw[0] * DDal[0], gap = gw[0] * dal[0] * dphi[0];
+#pragma unroll
+        for (int s = 1; s < 6; s++) {
+            const int i = spi(s), j = spj(s);
+            lapal = fma(gw[s], DDal[s], lapal);
+            gap = fma(gi[s], fma(dal[i], dphi[j], (i == j) ? 0.0 : dal[j] * dphi[i]), gap);
+        }
+        out[G_TRK] = fma(al, fma((1.0 / 3.0) * K, K, AA), -W2 * fma(2.0, gap, lapal));
+    }
+    // Eq. Lambda_RHS_orig_final (with the alpha factors restored) + Lie terms
+    double rl[3];
+    {
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            // - lambda^j Dhat_j beta^i + (2/3) Delta^i Dbar.beta + (1/3) gammabar^ik e_k Dbar.beta
+            double t = fma(-lam[2], Db[i][2], fma(-lam[1], Db[i][1], fma(-lam[0], Db[i][0], LapB[i])));
+            t = fma((2.0 / 3.0) * Dvec[i], divbar, t);
+            t = fma((1.0 / 3.0), fma(gsym(gi, i, 2), gdiv[2], fma(gsym(gi, i, 1), gdiv[1], gsym(gi, i, 0) * gdiv[0])), t);
+            // -2 Abar^ij (d_j alpha - 6 alpha d_j phi) - 4/3 alpha gammabar^ij d_j K
+            double u = 0.0;
+            u = Auu[sp(i, 0)] * fma(-6.0 * al, dphi[0], dal[0]);
+            u = fma(Auu[sp(i, 1)], fma(-6.0 * al, dphi[1], dal[1]), u);
+            u = fma(Auu[sp(i, 2)], fma(-6.0 * al, dphi[2], dal[2]), u);
+            double v = fma(gsym(gi, i, 2), dK[2], fma(gsym(gi, i, 1), dK[1], gsym(gi, i, 0) * dK[0]));
+            t = fma(-2.0, u, fma((-4.0 / 3.0) * al, v, t));
+            // + 2 alpha Abar^jk Delta^i_jk
+            double w = Auu[0] * Dup[i][0];
+#pragma unroll
+            for (int s = 1; s < 6; s++) w = fma(offd(s) ? Auu[s] + Auu[s] : Auu[s], Dup[i][s], w);
+            rl[i] = fma(2.0 * al, w, t);
+        }
+        // + beta^j (Omega_j lambda)^i
+        omv<FAM, 1>(g, vet[1], lam, rl);
+        omv<FAM, 2>(g, vet[2], lam, rl);
+#pragma unroll
+        for (int i = 0; i < 3; i++) out[G_LAM + i] = rl[i];
+    }
+    // gauge: d_t alpha = -2 alpha K (+ advection);  d_t beta^i = B^i (+ coordinate advection);
+    //        d_t B^i = 3/4 d_t Lambdabar^i - eta B^i (+ coordinate advection)
+    {
+        // partial-derivative advection of unrescaled components: - v^i sum_j d_ij vet^j
+        double dv[3];
+        dv[0] = g.d00 * vet[0];
+        dv[1] = g.a * vet[0];
+        if constexpr (FAM == FAM_SPH) dv[2] = fma(g.b, vet[0], g.c * vet[1]);
+        else dv[2] = g.d22 * vet[2];
+        out[G_ALPHA] = -2.0 * al * K;
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            out[G_VET + i] = fma(-vet[i], dv[i], bet[i]);
+            out[G_BET + i] = fma(-bet[i], dv[i], fma(0.75, rl[i], -eta * bet[i]));
+        }
+    }
+}
+
+// Hamiltonian constraint, Eq. Hconstraint:
+// H = 2/3 K^2 - Abar_ij Abar^ij + W^2 (Rbar - 8 gammabar^ij d_i phi d_j phi - 8 gammabar^ij Dbar_i Dbar_j phi)
+template <int FAM>
+__device__ __forceinline__ double ham_core(const PointIn& P)
+{
+    MetricPart M;
+    metric_part<FAM, false>(P, M);
+    const double* gi = M.gi;
+    const double* gw = M.gw;
+    double a[6];
+#pragma unroll
+    for (int s = 0; s < 6; s++) a[s] = ld(P.y + (long)(G_ADD + s) * P.T);
+    const double K = ld(P.y + (long)G_TRK * P.T);
+    double Aud[3][3];
+#pragma unroll
+    for (int k = 0; k < 3; k++)
+#pragma unroll
+        for (int j = 0; j < 3; j++)
+            Aud[k][j] = fma(gsym(gi, k, 2), a[sp(2, j)], fma(gsym(gi, k, 1), a[sp(1, j)], gsym(gi, k, 0) * a[sp(0, j)]));
+    // Abar_ij Abar^ij = Abar^i_j Abar^j_i
+    double AA = Aud[0][0] * Aud[0][0];
+#pragma unroll
+    for (int q = 1; q < 9; q++) AA = fma(Aud[q / 3][q % 3], Aud[q % 3][q / 3], AA);
+    double R = gw[0] * M.Ric[0], gp = gw[0] * M.dphi[0] * M.dphi[0], lp = gw[0] * M.DDphi[0];
+#pragma unroll
+    for (int s = 1; s < 6; s++) {
+        R = fma(gw[s], M.Ric[s], R);
+        gp = fma(gw[s], M.dphi[spi(s)] * M.dphi[spj(s)], gp);
+        lp = fma(gw[s], M.DDphi[s], lp);
+    }
+    return fma((2.0 / 3.0) * K, K, fma(M.W * M.W, fma(-8.0, gp + lp, R), -AA));
+}
+
+// beta^k d_k f, upwinded: u[k] = |vet^k| D_k, us[k] = +-stride selecting the
+// stencil side by the sign of vet^k
+__device__ __forceinline__ double adv(const double* f, const double u[3], const long us[3])
+{
+    double a = u[0] * upraw(f, us[0]);
+    a = fma(u[1], upraw(f, us[1]), a);
+    return fma(u[2], upraw(f, us[2]), a);
+}
+
+// Kreiss-Oliger dissipation sum_k delta^6_k f / (64 dxx_k) (times sigma by the caller);
+// kod[k] = 1/(64 dxx_k), kosum = sum_k kod[k]
+__device__ __forceinline__ double ko(const double* f, const long st[3], const double kod[3], double kosum)
+{
+    double k = kod[0] * koraw(f, st[0]);
+    k = fma(kod[1], koraw(f, st[1]), k);
+    k = fma(kod[2], koraw(f, st[2]), k);
+    return fma(-20.0 * kosum, ld(f), k);
+}
+
+// Adds the upwinded advection and the dissipation to the 24 right-hand sides
+// of rhs_core.  d_t B^i contains 3/4 of the full d_t Lambdabar^i, so it also
+// receives 3/4 of the advection of lambda^i.
+__device__ __forceinline__ void add_adv_ko(const double* y, long T, const long st[3], const double D[3],
+                                           const double kod[3], double kosum, const double* sigma, double k[NGF])
+{
+    double u[3];
+    long us[3];
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        const double v = ld(y + (long)(G_VET + d) * T);
+        u[d] = fabs(v) * D[d];
+        us[d] = (v > 0.0) ? st[d] : -st[d];
+    }
+    double alam[3];
+#pragma unroll
+    for (int g = 0; g < NGF; g++) {
+        const double a = adv(y + (long)g * T, u, us);
+        if (g >= G_LAM && g < G_LAM + 3) alam[g - G_LAM] = a;
+        k[g] += a;
+    }
+#pragma unroll
+    for (int i = 0; i < 3; i++) k[G_BET + i] = fma(0.75, alam[i], k[G_BET + i]);
+#pragma unroll
+    for (int g = 0; g < NGF; g++) k[g] = fma(sigma[g], ko(y + (long)g * T, st, kod, kosum), k[g]);
+}
+
+}  // namespace nrk

@@ -1,0 +1,81 @@
+// nr_internal.h -- structures shared by the host side of libnrgpu and its kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/nr.h"
+
+namespace nrk {
+
+// Per-axis 1D reference-metric arrays (device pointers), one value per
+// padded index.  Spherical-like: ax0 = {1/r', 1/r, r''/r'^2, r},
+// ax1 = {1/sin th, cot th, sin th, cos th}, ax2 = {sin ph, cos ph}.
+// Cylindrical-like: ax0 = {1/rho', 1/rho, rho''/rho'^2, rho},
+// ax1 = {sin ph, cos ph}, ax2 = {1/z', z''/z'^2, z}.
+struct Rfm {
+    const double* ax0;
+    const double* ax1;
+    const double* ax2;
+};
+
+// Launch-invariant description of one grid, passed by value to kernels.
+struct GridK {
+    int n0, n1, n2;     // padded sizes
+    int N0, N1, N2;     // interior sizes
+    int NG;
+    int fam;            // FAM_SPH / FAM_CYL
+    long T;
+    double inv12dx[3];  // 1/(12 dxx_k)
+    double inv12dx2[3]; // 1/(12 dxx_k^2)
+    double kod[3];      // 1/(64 dxx_k)
+    double kosum;
+    double sigma[24];
+    double eta;
+    Rfm rfm;
+};
+
+// Pure-outer ghost point: radiation condition data (precomputed on the host).
+struct OuterPt {
+    int idx;            // flat index
+    int kind;           // one-sided stencil kind, axis 0 (low byte) and axis 2 (next byte)
+    double w0, w2;      // (x^j/r) dxx^d/dx^j / (12 dxx_d) for d = 0, 2
+    double invr;        // 1/r
+};
+
+// Inner ghost point: parity copy.
+struct InnerPt {
+    int dst, src;
+    int negmask;        // bit t set: parity -1 for tensor type t
+    int pad;
+};
+
+enum { MODE_RHS = 0, MODE_STAGE1 = 1, MODE_STAGE23 = 2, MODE_STAGE4 = 3 };
+
+// RK4 stage description for the fused epilogues.
+struct Stage {
+    int mode;
+    int enforce;
+    double cnext;       // y_next = y_n + cnext * k          (stages 1-3)
+    double cacc;        // acc (=|+=) cacc * k; stage 4: y_n = acc + cacc * k
+};
+
+// kernel launchers (nr_kernels.cu)
+cudaError_t launch_rhs(const GridK& G, const double* yin, double* out, const double* yn, double* acc, Stage st,
+                       cudaStream_t s);
+cudaError_t launch_outer(const GridK& G, const OuterPt* pts, int npts, const double* yin, double* out,
+                         const double* yn, double* acc, const double* finf, const double* wspeed, Stage st,
+                         cudaStream_t s);
+cudaError_t launch_inner(const GridK& G, const InnerPt* pts, int npts, double* y, cudaStream_t s);
+cudaError_t launch_bl(const GridK& G, const int* canon_idx, long ncanon, int np, const double* mxyz, double amp,
+                      uint64_t seed, double* y, cudaStream_t s);
+cudaError_t launch_ham(const GridK& G, const double* y, double* H, double rmin, double rmax, double* partials,
+                       int nparts, double* result, cudaStream_t s);
+int ham_partials_needed(const GridK& G);
+cudaError_t launch_finite(const GridK& G, const double* y, int* flag, cudaStream_t s);
+cudaError_t launch_fp64_probe(int blocks, int iters, double* sink, cudaStream_t s);
+
+}  // namespace nrk

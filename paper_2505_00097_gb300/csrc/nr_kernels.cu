@@ -1,0 +1,425 @@
+// nr_kernels.cu -- sm_103a FP64 kernels of the BSSN hot path.
+//
+//   k_rhs     interior right-hand side (Sec. 2.1 equations, upwinded advection,
+//             Kreiss-Oliger dissipation) with the RK4 stage update and the
+//             det(gammabar) enforcement fused into its epilogue
+//   k_outer   radiation condition at pure-outer ghosts (Sec. 3), same epilogue
+//   k_inner   parity copies at inner ghosts (Sec. 3), one warp-coalesced gather
+//             per gridfunction
+//   k_bl      Brill-Lindquist data + SplitMix64 perturbation
+//   k_ham     Hamiltonian constraint (Eq. Hconstraint) + per-block norm partials
+//   k_ham_reduce  fixed-order reduction of the partials
+//   k_finite  NaN/Inf guard on alpha and W
+#include <math.h>
+
+#include "bssn_point.cuh"
+#include "nr_internal.h"
+
+namespace nrk {
+
+constexpr int RHS_BX = 32, RHS_BY = 4;
+
+template <int FAM>
+__device__ __forceinline__ Geo make_geo(const GridK& G, int i0, int i1, int i2)
+{
+    Geo g;
+    const double* A0 = G.rfm.ax0;
+    const double s0 = ld(A0 + i0), a = ld(A0 + G.n0 + i0);
+    g.d00 = ld(A0 + 2 * G.n0 + i0);
+    g.a = a;
+    double s2;
+    if constexpr (FAM == FAM_SPH) {
+        const double isn = ld(G.rfm.ax1 + i1), cot = ld(G.rfm.ax1 + G.n1 + i1);
+        s2 = a * isn;
+        g.b = a;
+        g.c = a * cot;
+        g.d22 = 0.0;
+        g.e0a = -a * a;
+        g.e0b = g.e0a;
+        g.e0c = -a * g.c;
+        g.e1c = -s2 * s2;
+    } else {
+        s2 = ld(G.rfm.ax2 + i2);
+        g.d22 = ld(G.rfm.ax2 + G.n2 + i2);
+        g.b = 0.0;
+        g.c = 0.0;
+        g.e0a = -a * a;
+        g.e0b = 0.0;
+        g.e0c = 0.0;
+        g.e1c = 0.0;
+    }
+    g.D[0] = s0 * G.inv12dx[0];
+    g.D[1] = a * G.inv12dx[1];
+    g.D[2] = s2 * G.inv12dx[2];
+    g.D2[0] = s0 * s0 * G.inv12dx2[0];
+    g.D2[1] = a * a * G.inv12dx2[1];
+    g.D2[2] = s2 * s2 * G.inv12dx2[2];
+    g.DD[0] = g.D[0] * g.D[1];
+    g.DD[1] = g.D[0] * g.D[2];
+    g.DD[2] = g.D[1] * g.D[2];
+    return g;
+}
+
+// det(delta_ij + h_ij) := 1 (Lagrangian choice of Sec. 2.1), in place
+__device__ __forceinline__ void enforce_det(double* v)
+{
+    const double g00 = 1.0 + v[0], g11 = 1.0 + v[3], g22 = 1.0 + v[5];
+    const double c00 = fma(g11, g22, -v[4] * v[4]);
+    const double c01 = fma(v[2], v[4], -v[1] * g22);
+    const double c02 = fma(v[1], v[4], -v[2] * g11);
+    const double det = fma(g00, c00, fma(v[1], c01, v[2] * c02));
+    const double f = rcbrt(det);
+    v[0] = fma(g00, f, -1.0);
+    v[1] *= f;
+    v[2] *= f;
+    v[3] = fma(g11, f, -1.0);
+    v[4] *= f;
+    v[5] = fma(g22, f, -1.0);
+}
+
+// RK4 stage epilogue for one point: k -> (y_next, acc) or the plain RHS.
+__device__ __forceinline__ void stage_store(const Stage& st, long T, long idx, const double k[NGF],
+                                            const double* __restrict__ yn, double* __restrict__ out,
+                                            double* __restrict__ acc)
+{
+    if (st.mode == MODE_RHS) {
+#pragma unroll
+        for (int g = 0; g < NGF; g++) out[g * T + idx] = k[g];
+        return;
+    }
+    double v[NGF];
+    if (st.mode == MODE_STAGE4) {
+#pragma unroll
+        for (int g = 0; g < NGF; g++) v[g] = fma(st.cacc, k[g], acc[g * T + idx]);
+    } else {
+#pragma unroll
+        for (int g = 0; g < NGF; g++) {
+            const double y0 = yn[g * T + idx];
+            v[g] = fma(st.cnext, k[g], y0);
+            acc[g * T + idx] = fma(st.cacc, k[g], st.mode == MODE_STAGE1 ? y0 : acc[g * T + idx]);
+        }
+    }
+    if (st.enforce) enforce_det(v);
+#pragma unroll
+    for (int g = 0; g < NGF; g++) out[g * T + idx] = v[g];
+}
+
+template <int FAM>
+__global__ void __launch_bounds__(RHS_BX* RHS_BY) k_rhs(GridK G, const double* __restrict__ yin, double* out,
+                                                        const double* yn, double* acc, Stage st)
+{
+    // blocks tile (i0, j = i1 + N1 i2) in 32 x 4 points, flattened into blockIdx.x
+    const int nbx = (G.N0 + RHS_BX - 1) / RHS_BX;
+    const int i = (int)(blockIdx.x % nbx) * RHS_BX + threadIdx.x;
+    const int j = (int)(blockIdx.x / nbx) * RHS_BY + threadIdx.y;
+    if (i >= G.N0 || j >= G.N1 * G.N2) return;
+    const int p0 = i + G.NG, p1 = j % G.N1 + G.NG, p2 = j / G.N1 + G.NG;
+    const long idx = p0 + (long)G.n0 * (p1 + (long)G.n1 * p2);
+    PointIn P;
+    P.y = yin + idx;
+    P.T = G.T;
+    P.st[0] = 1;
+    P.st[1] = G.n0;
+    P.st[2] = (long)G.n0 * G.n1;
+    P.g = make_geo<FAM>(G, p0, p1, p2);
+    double k[NGF];
+    rhs_core<FAM>(P, G.eta, k);
+    add_adv_ko(P.y, G.T, P.st, P.g.D, G.kod, G.kosum, G.sigma, k);
+    stage_store(st, G.T, idx, k, yn, out, acc);
+}
+
+// one-sided / centred first-derivative stencil sums (weights of 12 h f')
+__device__ __forceinline__ double osraw(const double* f, long s, int kind)
+{
+    switch (kind) {
+    case 0: return fma(8.0, ld(f + s) - ld(f - s), ld(f - 2 * s) - ld(f + 2 * s));
+    case 1: return fma(3.0, ld(f + s), fma(10.0, ld(f), fma(-18.0, ld(f - s), fma(6.0, ld(f - 2 * s), -ld(f - 3 * s)))));
+    case 2: return fma(25.0, ld(f), fma(-48.0, ld(f - s), fma(36.0, ld(f - 2 * s), fma(-16.0, ld(f - 3 * s), 3.0 * ld(f - 4 * s)))));
+    case 3: return fma(-3.0, ld(f - s), fma(-10.0, ld(f), fma(18.0, ld(f + s), fma(-6.0, ld(f + 2 * s), ld(f + 3 * s)))));
+    default: return fma(-25.0, ld(f), fma(48.0, ld(f + s), fma(-36.0, ld(f + 2 * s), fma(16.0, ld(f + 3 * s), -3.0 * ld(f + 4 * s)))));
+    }
+}
+
+template <int FAM>
+__global__ void __launch_bounds__(128) k_outer(GridK G, const OuterPt* __restrict__ pts, int npts,
+                                               const double* __restrict__ yin, double* out, const double* yn,
+                                               double* acc, const double* __restrict__ finf,
+                                               const double* __restrict__ wspeed, Stage st)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= npts) return;
+    const OuterPt p = pts[t];
+    const long idx = p.idx;
+    const long s2 = (long)G.n0 * G.n1;
+    const int k0 = p.kind & 0xff, k2 = (p.kind >> 8) & 0xff;
+    double k[NGF];
+#pragma unroll
+    for (int g = 0; g < NGF; g++) {
+        const double* f = yin + (long)g * G.T + idx;
+        double rad = p.w0 * osraw(f, 1, k0);
+        if constexpr (FAM == FAM_CYL) rad = fma(p.w2, osraw(f, s2, k2), rad);
+        k[g] = -ld(wspeed + g) * fma(ld(f) - ld(finf + g), p.invr, rad);
+    }
+    stage_store(st, G.T, idx, k, yn, out, acc);
+}
+
+__device__ __forceinline__ int gf_type(int g)
+{
+    if (g < 6) return 4 + g;
+    if (g < 12) return g - 2;
+    if (g == G_CF || g == G_TRK || g == G_ALPHA) return 0;
+    if (g < G_VET) return g - G_LAM + 1;
+    if (g < G_BET) return g - G_VET + 1;
+    return g - G_BET + 1;
+}
+
+// y[ghost] = p * y[source]; the sign is applied to the bit pattern (exact)
+__global__ void __launch_bounds__(256) k_inner(long T, const InnerPt* __restrict__ pts, int npts, double* y)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int g = blockIdx.y;
+    if (t >= npts) return;
+    const InnerPt p = pts[t];
+    const long long sgn = (long long)((p.negmask >> gf_type(g)) & 1) << 63;
+    const double v = y[(long)g * T + p.src];
+    y[(long)g * T + p.dst] = __longlong_as_double(__double_as_longlong(v) ^ sgn);
+}
+
+// SplitMix64 (Steele, Lea & Flood 2014) first output for state x
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x)
+{
+    uint64_t z = x + 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ void cart_of(const GridK& G, int i0, int i1, int i2, double x[3])
+{
+    if (G.fam == FAM_SPH) {
+        const double r = G.rfm.ax0[3 * G.n0 + i0];
+        const double st = G.rfm.ax1[2 * G.n1 + i1], ct = G.rfm.ax1[3 * G.n1 + i1];
+        const double sp_ = G.rfm.ax2[i2], cp = G.rfm.ax2[G.n2 + i2];
+        x[0] = r * st * cp;
+        x[1] = r * st * sp_;
+        x[2] = r * ct;
+    } else {
+        const double rho = G.rfm.ax0[3 * G.n0 + i0];
+        const double sp_ = G.rfm.ax1[i1], cp = G.rfm.ax1[G.n1 + i1];
+        x[0] = rho * cp;
+        x[1] = rho * sp_;
+        x[2] = G.rfm.ax2[2 * G.n2 + i2];
+    }
+}
+
+__global__ void k_bl(GridK G, const int* __restrict__ canon, long ncanon, int np, const double* __restrict__ mxyz,
+                     double amp, uint64_t seed, double* y)
+{
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ncanon) return;
+    const long idx = canon[t];
+    const int i0 = (int)(idx % G.n0), i1 = (int)((idx / G.n0) % G.n1), i2 = (int)(idx / ((long)G.n0 * G.n1));
+    double x[3];
+    cart_of(G, i0, i1, i2, x);
+    double psi = 1.0;
+    for (int q = 0; q < np; q++) {
+        const double dx = x[0] - mxyz[4 * q + 1], dy = x[1] - mxyz[4 * q + 2], dz = x[2] - mxyz[4 * q + 3];
+        psi += mxyz[4 * q] / (2.0 * sqrt(dx * dx + dy * dy + dz * dz));
+    }
+    const double w = 1.0 / (psi * psi);
+    for (int g = 0; g < NGF; g++) y[(long)g * G.T + idx] = 0.0;
+    y[(long)G_CF * G.T + idx] = w;
+    y[(long)G_ALPHA * G.T + idx] = w;
+    if (amp != 0.0) {
+        for (int s = 0; s < 6; s++) {
+            const uint64_t u = splitmix64(seed ^ (((uint64_t)(G_HDD + s) << 40) | (uint64_t)idx));
+            y[(long)(G_HDD + s) * G.T + idx] = amp * (2.0 * ((double)(u >> 11) * 0x1.0p-53) - 1.0);
+        }
+    }
+}
+
+constexpr int HAM_THREADS = 128;
+
+template <int FAM>
+__global__ void __launch_bounds__(HAM_THREADS) k_ham(GridK G, const double* __restrict__ y, double* H, double rmin,
+                                                      double rmax, double* partials)
+{
+    const long t = (long)blockIdx.x * HAM_THREADS + threadIdx.x;
+    const long nint = (long)G.N0 * G.N1 * G.N2;
+    double s2 = 0.0, mx = 0.0, cnt = 0.0;
+    if (t < nint) {
+        const int i = (int)(t % G.N0), j = (int)(t / G.N0);
+        const int p0 = i + G.NG, p1 = j % G.N1 + G.NG, p2 = j / G.N1 + G.NG;
+        const long idx = p0 + (long)G.n0 * (p1 + (long)G.n1 * p2);
+        PointIn P;
+        P.y = y + idx;
+        P.T = G.T;
+        P.st[0] = 1;
+        P.st[1] = G.n0;
+        P.st[2] = (long)G.n0 * G.n1;
+        P.g = make_geo<FAM>(G, p0, p1, p2);
+        const double h = ham_core<FAM>(P);
+        if (H) H[idx] = h;
+        double x[3];
+        cart_of(G, p0, p1, p2, x);
+        const double r = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+        if (r >= rmin && r <= rmax) {
+            s2 = h * h;
+            mx = fabs(h);
+            cnt = 1.0;
+        }
+    }
+    __shared__ double sh[3][HAM_THREADS];
+    sh[0][threadIdx.x] = s2;
+    sh[1][threadIdx.x] = mx;
+    sh[2][threadIdx.x] = cnt;
+    __syncthreads();
+    for (int w = HAM_THREADS / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            sh[0][threadIdx.x] += sh[0][threadIdx.x + w];
+            sh[1][threadIdx.x] = fmax(sh[1][threadIdx.x], sh[1][threadIdx.x + w]);
+            sh[2][threadIdx.x] += sh[2][threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        partials[3 * blockIdx.x + 0] = sh[0][0];
+        partials[3 * blockIdx.x + 1] = sh[1][0];
+        partials[3 * blockIdx.x + 2] = sh[2][0];
+    }
+}
+
+// one block; fixed order: thread t sums partials t, t+256, ..., then a tree
+__global__ void __launch_bounds__(256) k_ham_reduce(const double* __restrict__ partials, int nparts, double* result)
+{
+    __shared__ double sh[3][256];
+    double s = 0.0, m = 0.0, c = 0.0;
+    for (int p = threadIdx.x; p < nparts; p += 256) {
+        s += partials[3 * p];
+        m = fmax(m, partials[3 * p + 1]);
+        c += partials[3 * p + 2];
+    }
+    sh[0][threadIdx.x] = s;
+    sh[1][threadIdx.x] = m;
+    sh[2][threadIdx.x] = c;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            sh[0][threadIdx.x] += sh[0][threadIdx.x + w];
+            sh[1][threadIdx.x] = fmax(sh[1][threadIdx.x], sh[1][threadIdx.x + w]);
+            sh[2][threadIdx.x] += sh[2][threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double cnt = sh[2][0];
+        result[0] = cnt > 0.0 ? sqrt(sh[0][0] / cnt) : 0.0;
+        result[1] = sh[1][0];
+        result[2] = cnt;
+    }
+}
+
+__global__ void k_finite(long T, const double* __restrict__ y, int* flag)
+{
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    const double w = y[(long)G_CF * T + t], a = y[(long)G_ALPHA * T + t];
+    if (!isfinite(w) || !isfinite(a)) atomicOr(flag, 1);
+}
+
+// FP64 FMA throughput probe: 8 independent FMA chains per thread, a fixed
+// number of iterations (no data-dependent trip count), one store per thread.
+__global__ void __launch_bounds__(256) k_fp64_probe(int iters, double seed, double* sink)
+{
+    double a[8];
+#pragma unroll
+    for (int q = 0; q < 8; q++) a[q] = seed + (double)(threadIdx.x + q);
+    const double m = 0.999999999, c = 1e-9;
+    for (int it = 0; it < iters; it++) {
+#pragma unroll
+        for (int q = 0; q < 8; q++) a[q] = fma(a[q], m, c);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; q++) s += a[q];
+    sink[(long)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+cudaError_t launch_fp64_probe(int blocks, int iters, double* sink, cudaStream_t s)
+{
+    k_fp64_probe<<<blocks, 256, 0, s>>>(iters, 1.0, sink);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ launchers
+
+cudaError_t launch_rhs(const GridK& G, const double* yin, double* out, const double* yn, double* acc, Stage st,
+                       cudaStream_t s)
+{
+    dim3 blk(RHS_BX, RHS_BY);
+    const long nb = (long)((G.N0 + RHS_BX - 1) / RHS_BX) * ((G.N1 * G.N2 + RHS_BY - 1) / RHS_BY);
+    dim3 grd((unsigned)nb);
+    if (G.fam == FAM_SPH)
+        k_rhs<FAM_SPH><<<grd, blk, 0, s>>>(G, yin, out, yn, acc, st);
+    else
+        k_rhs<FAM_CYL><<<grd, blk, 0, s>>>(G, yin, out, yn, acc, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_outer(const GridK& G, const OuterPt* pts, int npts, const double* yin, double* out,
+                         const double* yn, double* acc, const double* finf, const double* wspeed, Stage st,
+                         cudaStream_t s)
+{
+    if (npts == 0) return cudaSuccess;
+    const int b = 128, n = (npts + b - 1) / b;
+    if (G.fam == FAM_SPH)
+        k_outer<FAM_SPH><<<n, b, 0, s>>>(G, pts, npts, yin, out, yn, acc, finf, wspeed, st);
+    else
+        k_outer<FAM_CYL><<<n, b, 0, s>>>(G, pts, npts, yin, out, yn, acc, finf, wspeed, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_inner(const GridK& G, const InnerPt* pts, int npts, double* y, cudaStream_t s)
+{
+    if (npts == 0) return cudaSuccess;
+    dim3 grd((npts + 255) / 256, NGF);
+    k_inner<<<grd, 256, 0, s>>>(G.T, pts, npts, y);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bl(const GridK& G, const int* canon_idx, long ncanon, int np, const double* mxyz, double amp,
+                      uint64_t seed, double* y, cudaStream_t s)
+{
+    const int b = 256;
+    const long n = (ncanon + b - 1) / b;
+    k_bl<<<(unsigned)n, b, 0, s>>>(G, canon_idx, ncanon, np, mxyz, amp, seed, y);
+    return cudaGetLastError();
+}
+
+int ham_partials_needed(const GridK& G)
+{
+    const long nint = (long)G.N0 * G.N1 * G.N2;
+    return (int)((nint + HAM_THREADS - 1) / HAM_THREADS);
+}
+
+cudaError_t launch_ham(const GridK& G, const double* y, double* H, double rmin, double rmax, double* partials,
+                       int nparts, double* result, cudaStream_t s)
+{
+    if (G.fam == FAM_SPH)
+        k_ham<FAM_SPH><<<nparts, HAM_THREADS, 0, s>>>(G, y, H, rmin, rmax, partials);
+    else
+        k_ham<FAM_CYL><<<nparts, HAM_THREADS, 0, s>>>(G, y, H, rmin, rmax, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_ham_reduce<<<1, 256, 0, s>>>(partials, nparts, result);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finite(const GridK& G, const double* y, int* flag, cudaStream_t s)
+{
+    const int b = 256;
+    k_finite<<<(unsigned)((G.T + b - 1) / b), b, 0, s>>>(G.T, y, flag);
+    return cudaGetLastError();
+}
+
+}  // namespace nrk

@@ -1,0 +1,86 @@
+"""Host-side checks of the C-ABI library (no GPU needed): it loads, exports every
+entry point declared in include/nr.h, and its host logic -- closed-form boundary
+maps and the CFL step -- agrees bit-exactly with the oracle's independent
+inverse-coordinate maps."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle.oracle import Oracle
+from paper_2505_00097_gb300 import binding as B
+from paper_2505_00097_gb300 import build as BUILD
+from paper_2505_00097_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    BUILD.build()
+
+
+def _declared():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", h)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(nr_[a-z0-9_]+)\s*\(", src))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    L = B.lib()
+    declared = _declared()
+    assert declared, "no declarations found"
+    missing = [n for n in sorted(declared) if not hasattr(L, n)]
+    assert not missing, missing
+    assert set(B.EXPORTS) == declared
+
+
+def test_params_default():
+    p = B.NrParams()
+    assert B.lib().nr_params_default(0, ctypes.byref(p)) == 0
+    assert p.NG == 3 and p.eta == 2.0 and p.cfl == 0.5 and p.enforce_detgb == 1
+    assert list(p.ko_sigma) == [0.3] * 24
+    assert p.f_inf[12] == 1.0 and p.f_inf[23] == 1.0 and sum(p.f_inf) == 2.0
+
+
+def test_invalid_arguments_are_reported():
+    Nx = (ctypes.c_int * 3)(64, 16, 3)   # odd N_phi cannot map r<0 ghosts
+    src = np.zeros(70 * 22 * 9, dtype=np.int32); cls = src.copy(); par = np.zeros(10 * src.size, dtype=np.int8)
+    rc = B.lib().nr_build_maps(0, Nx, 3, src.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                               par.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)),
+                               cls.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    assert rc == 6 and b"even" in B.lib().nr_last_error()
+    Nx = (ctypes.c_int * 3)(64, 16, 2)
+    assert B.lib().nr_build_maps(0, Nx, 2, src.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                 par.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)),
+                                 cls.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))) == 1
+
+
+MAP_SPECS = [
+    W.sinh_spherical((64, 16, 2)), W.sinh_spherical((6, 4, 2)), W.sinh_spherical((5, 3, 4)), W.spherical((4, 5, 6)),
+    W.sinh_spherical((12, 8, 10)), W.sinh_cylindrical((16, 2, 32)), W.sinh_cylindrical((6, 2, 5)),
+    W.sinh_cylindrical((4, 6, 4), w=0.4), W.sinh_cylindrical((7, 8, 3)),
+]
+
+
+@pytest.mark.parametrize("spec", MAP_SPECS, ids=[f"{s['coords']}-{'x'.join(map(str, s['N']))}" for s in MAP_SPECS])
+def test_maps_bit_exact_vs_oracle(spec):
+    o = Oracle(spec)
+    rc, s1, p1, c1 = o.build_map()
+    assert rc == 0
+    s2, p2, c2 = B.build_maps(spec["coords"], spec["N"])
+    np.testing.assert_array_equal(c2, c1)
+    np.testing.assert_array_equal(s2, s1)
+    np.testing.assert_array_equal(p2, p1)
+
+
+@pytest.mark.parametrize("spec", [W.config_single_puncture(), W.config_headon(), W.spherical((72, 12, 24)),
+                                  W.sinh_spherical((24, 12, 8))], ids=["c1", "c2", "sph", "sph3d"])
+def test_dt_cfl_vs_oracle(spec):
+    assert B.dt_cfl(spec) == pytest.approx(Oracle(spec).dt(), rel=1e-15)
