@@ -1062,22 +1062,34 @@ int orc_full_rhs(const orc_params* p, const double* gfs, double* rhs)
     return bad;
 }
 
-/* det(gammabar_ij)/det(gammahat_ij) = det(delta_ij + h_ij) := 1 */
+/* det(gammabar_ij)/det(gammahat_ij) = det(delta_ij + h_ij) := 1 (the
+ * Lagrangian choice of Sec. 2.1), by rescaling gammabar_ij = delta_ij + h_ij
+ * with det^(-1/3).  Written in terms of the deviation h so that small h keeps
+ * its relative precision: det(I + h) - 1 = e1 + e2 + e3 with the invariants
+ * e1 = tr h, e2 = ((tr h)^2 - tr(h^2))/2, e3 = det h, the factor minus one is
+ * f1 = expm1(-log1p(det - 1)/3), and h_ij <- h_ij + f1 (delta_ij + h_ij). */
 void orc_enforce_detgb(const orc_params* p, double* gfs)
 {
     long T = orc_sizes(p, NULL);
     for (long idx = 0; idx < T; idx++) {
-        double g[3][3], inv[3][3];
+        double h[3][3], inv[3][3];
         for (int s = 0; s < 6; s++) {
-            double v = gfs[(G_HDD + s) * T + idx] + (SYM_I[s] == SYM_J[s] ? 1.0 : 0.0);
-            g[SYM_I[s]][SYM_J[s]] = v;
-            g[SYM_J[s]][SYM_I[s]] = v;
+            double v = gfs[(G_HDD + s) * T + idx];
+            h[SYM_I[s]][SYM_J[s]] = v;
+            h[SYM_J[s]][SYM_I[s]] = v;
         }
-        double det = inv3(g, inv);
-        double fac = 1.0 / cbrt(det);
+        double e1 = 0.0, trh2 = 0.0;
+        for (int i = 0; i < 3; i++) {
+            e1 += h[i][i];
+            for (int j = 0; j < 3; j++) trh2 += h[i][j] * h[j][i];
+        }
+        double e2 = 0.5 * (e1 * e1 - trh2);
+        double e3 = inv3(h, inv);
+        double f1 = expm1(-log1p(e1 + e2 + e3) / 3.0);
         for (int s = 0; s < 6; s++) {
             double delta = SYM_I[s] == SYM_J[s] ? 1.0 : 0.0;
-            gfs[(G_HDD + s) * T + idx] = g[SYM_I[s]][SYM_J[s]] * fac - delta;
+            double v = gfs[(G_HDD + s) * T + idx];
+            gfs[(G_HDD + s) * T + idx] = v + f1 * (delta + v);
         }
     }
 }

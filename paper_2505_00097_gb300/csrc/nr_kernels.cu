@@ -60,21 +60,25 @@ __device__ __forceinline__ Geo make_geo(const GridK& G, int i0, int i1, int i2)
     return g;
 }
 
-// det(delta_ij + h_ij) := 1 (Lagrangian choice of Sec. 2.1), in place
+// det(delta_ij + h_ij) := 1 (Lagrangian choice of Sec. 2.1), in place, in
+// terms of the deviation h so that small h keeps its relative precision:
+// det(I + h) - 1 = tr h + (sum of principal 2x2 minors of h) + det h,
+// f1 = det^(-1/3) - 1 = expm1(-log1p(det - 1)/3), h <- h + f1 (delta + h).
 __device__ __forceinline__ void enforce_det(double* v)
 {
-    const double g00 = 1.0 + v[0], g11 = 1.0 + v[3], g22 = 1.0 + v[5];
-    const double c00 = fma(g11, g22, -v[4] * v[4]);
-    const double c01 = fma(v[2], v[4], -v[1] * g22);
-    const double c02 = fma(v[1], v[4], -v[2] * g11);
-    const double det = fma(g00, c00, fma(v[1], c01, v[2] * c02));
-    const double f = rcbrt(det);
-    v[0] = fma(g00, f, -1.0);
-    v[1] *= f;
-    v[2] *= f;
-    v[3] = fma(g11, f, -1.0);
-    v[4] *= f;
-    v[5] = fma(g22, f, -1.0);
+    const double m2 = fma(v[0], v[3], fma(v[0], v[5], fma(v[3], v[5], -fma(v[1], v[1], fma(v[2], v[2], v[4] * v[4])))));
+    const double c0 = fma(v[3], v[5], -v[4] * v[4]);
+    const double c1 = fma(v[2], v[4], -v[1] * v[5]);
+    const double c2 = fma(v[1], v[4], -v[2] * v[3]);
+    const double d3 = fma(v[0], c0, fma(v[1], c1, v[2] * c2));
+    const double dm1 = (v[0] + v[3] + v[5]) + (m2 + d3);
+    const double f1 = expm1(log1p(dm1) * (-1.0 / 3.0));
+    v[0] = fma(f1, v[0], v[0] + f1);
+    v[1] = fma(f1, v[1], v[1]);
+    v[2] = fma(f1, v[2], v[2]);
+    v[3] = fma(f1, v[3], v[3] + f1);
+    v[4] = fma(f1, v[4], v[4]);
+    v[5] = fma(f1, v[5], v[5] + f1);
 }
 
 // RK4 stage epilogue for one point: k -> (y_next, acc) or the plain RHS.

@@ -147,3 +147,42 @@ def test_splitmix_uniform_range_and_reference_value():
     vals = np.array([L.orc_splitmix_uniform(12345, c) for c in range(2000)])
     assert vals.min() >= -1.0 and vals.max() < 1.0
     assert abs(vals.mean()) < 0.05
+
+
+def _det_state(o, h6):
+    y = o.zeros()
+    T = o.T
+    for s in range(6):
+        y[s * T:(s + 1) * T] = h6[s]
+    return y
+
+
+def test_det_enforcement_exact_and_precise():
+    """det(gammabar) = det(gammahat) enforcement: det(I + h) = 1 afterwards; the result equals
+    (I + h) det^(-1/3) - I evaluated in 50-digit arithmetic; tiny h keeps its relative precision."""
+    mpmath = pytest.importorskip("mpmath")
+    from oracle.oracle import Oracle
+    from paper_2505_00097_gb300 import workloads as W
+    o = Oracle(W.sinh_spherical((2, 2, 2)))
+    T = o.T
+    rng = np.random.default_rng(3)
+    for amp in (0.1, 1e-6, 1e-11):
+        h6 = rng.uniform(-amp, amp, size=(6, T))
+        y = _det_state(o, h6)
+        o.enforce_detgb(y)
+        mpmath.mp.dps = 50
+        for p in range(0, T, max(1, T // 40)):
+            H = mpmath.matrix(3, 3)
+            for s, (a, b) in enumerate([(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]):
+                H[a, b] = H[b, a] = mpmath.mpf(h6[s, p])
+            G = mpmath.eye(3) + H
+            f = mpmath.det(G) ** (-mpmath.mpf(1) / 3)
+            for s, (a, b) in enumerate([(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]):
+                exact = G[a, b] * f - (1 if a == b else 0)
+                got = y[s * T + p]
+                assert abs(got - float(exact)) <= 4e-16 * max(abs(float(exact)), amp), (amp, s, got, exact)
+            Gn = np.eye(3)
+            for s, (a, b) in enumerate([(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]):
+                Gn[a, b] += y[s * T + p]
+                Gn[b, a] = Gn[a, b]
+            assert abs(np.linalg.det(Gn) - 1.0) < 1e-14
