@@ -31,8 +31,12 @@
  *     unrescaled components; the d_t Lambdabar^i substituted into d_t B^i is
  *     the full right-hand side of Eq. Lambda (with its advection term, without
  *     Kreiss-Oliger dissipation).
- *   R-KO: rhs_g += sigma/(64 dxx_d) * sum_d delta^6_d g on the rescaled g,
- *     dxx_d the logical spacing.
+ *   R-KO: rhs_g += sum_d sigma/(64 S_d dxx_d) delta^6_d g on the rescaled g:
+ *     the strength refers to the physical spacing S_d dxx_d.  With the
+ *     logical spacing dxx_d alone, the damping rate sigma/dxx_d of the Nyquist
+ *     mode exceeds the RK4 stability bound (2.785/dt) on the stretched sinh
+ *     grids of Sec. 4.1 at the CFL factor 0.5, since dt is set by the physical
+ *     spacing.
  *   R-Sommerfeld: at pure-outer ghosts d_t f = -v [ (x^j/r) d_j f + (f - f_inf)/r ]
  *     on each rescaled gridfunction; one-sided 4th-order stencils where the
  *     centred one does not fit.
@@ -1035,10 +1039,11 @@ void orc_rhs(const orc_params* p, const double* gfs, double* rhs, int k_lo, int 
                 refmet_from(&R, &M);
                 load_point(p, n, T, gfs, idx, &R, &F);
                 rhs_at_point(p, &R, &M, &F, out);
-                /* Kreiss-Oliger dissipation (reading R-KO) */
+                /* Kreiss-Oliger dissipation (reading R-KO): physical spacing S_d dxx_d */
                 for (int gf = 0; gf < NGF; gf++) {
                     double ko = 0.0;
-                    for (int d = 0; d < 3; d++) ko += p->ko_sigma[gf] / (64.0 * h[d]) * orc_ko6(&gfs[gf * T + idx], st[d]);
+                    for (int d = 0; d < 3; d++)
+                        ko += p->ko_sigma[gf] / (64.0 * h[d] * R.S[d]) * orc_ko6(&gfs[gf * T + idx], st[d]);
                     rhs[gf * T + idx] = out[gf] + ko;
                 }
             }

@@ -755,8 +755,8 @@ __device__ __forceinline__ double adv(const double* f, const double u[3], const 
     return fma(u[2], upraw(f, us[2]), a);
 }
 
-// Kreiss-Oliger dissipation sum_k delta^6_k f / (64 dxx_k) (times sigma by the caller);
-// kod[k] = 1/(64 dxx_k), kosum = sum_k kod[k]
+// Kreiss-Oliger dissipation sum_k kod[k] delta^6_k f (times sigma by the caller);
+// kod[k] = 1/(64 S_k dxx_k), kosum = sum_k kod[k]
 __device__ __forceinline__ double ko(const double* f, const long st[3], const double kod[3], double kosum)
 {
     double k = kod[0] * koraw(f, st[0]);
@@ -767,10 +767,15 @@ __device__ __forceinline__ double ko(const double* f, const long st[3], const do
 
 // Adds the upwinded advection and the dissipation to the 24 right-hand sides
 // of rhs_core.  d_t B^i contains 3/4 of the full d_t Lambdabar^i, so it also
-// receives 3/4 of the advection of lambda^i.
+// receives 3/4 of the advection of lambda^i.  The dissipation strength refers
+// to the physical spacing S_d dxx_d: 1/(64 S_d dxx_d) = (12/64) D[d].
 __device__ __forceinline__ void add_adv_ko(const double* y, long T, const long st[3], const double D[3],
-                                           const double kod[3], double kosum, const double* sigma, double k[NGF])
+                                           const double* sigma, double k[NGF])
 {
+    double kod[3];
+#pragma unroll
+    for (int d = 0; d < 3; d++) kod[d] = 0.1875 * D[d];
+    const double kosum = kod[0] + kod[1] + kod[2];
     double u[3];
     long us[3];
 #pragma unroll

@@ -533,12 +533,9 @@ int nr_grid_create(int coords, const int Nxx[3], const nr_params* params, nr_gri
     K.NG = G.NG;
     K.fam = G.fam;
     K.T = G.T;
-    K.kosum = 0.0;
     for (int d = 0; d < 3; d++) {
         K.inv12dx[d] = 1.0 / (12.0 * G.dxx[d]);
         K.inv12dx2[d] = 1.0 / (12.0 * G.dxx[d] * G.dxx[d]);
-        K.kod[d] = 1.0 / (64.0 * G.dxx[d]);
-        K.kosum += K.kod[d];
     }
     for (int q = 0; q < NR_NGF; q++) K.sigma[q] = P.ko_sigma[q];
     K.eta = P.eta;

@@ -31,8 +31,6 @@ struct GridK {
     long T;
     double inv12dx[3];  // 1/(12 dxx_k)
     double inv12dx2[3]; // 1/(12 dxx_k^2)
-    double kod[3];      // 1/(64 dxx_k)
-    double kosum;
     double sigma[24];
     double eta;
     Rfm rfm;

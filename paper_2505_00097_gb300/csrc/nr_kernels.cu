@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(RHS_BX* RHS_BY) k_rhs(GridK G, const double* _
     P.g = make_geo<FAM>(G, p0, p1, p2);
     double k[NGF];
     rhs_core<FAM>(P, G.eta, k);
-    add_adv_ko(P.y, G.T, P.st, P.g.D, G.kod, G.kosum, G.sigma, k);
+    add_adv_ko(P.y, G.T, P.st, P.g.D, G.sigma, k);
     stage_store(st, G.T, idx, k, yn, out, acc);
 }
 
