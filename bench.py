@@ -41,8 +41,13 @@ METRIC = "BSSN FP64 point-updates/s (RK4 substeps)"
 UNIT = "point-updates/s"
 
 # FP64 operations (FMA = 2) per interior point of one k_rhs launch, counted
-# from the kernel's DADD/DMUL/DFMA instruction counts (ncu, see profiles/).
-F_ALG = None
+# from the kernel's DADD/DMUL/DFMA thread-instruction counts in one ncu
+# capture of the head-on 256x2x512 workload (profiles/k_rhs_headon_256x2x512.md):
+# (DADD + DMUL + 2 DFMA) / interior points.
+F_ALG = 5102.0
+# FP64 pipe of one SM: 2 DFMA per clock (ncu peak_sustained of
+# sm__sass_thread_inst_executed_op_dfma_pred_on), i.e. 4 FLOP per clock
+FP64_FLOP_PER_CLK_SM = 4.0
 # algorithmic DRAM bytes per interior point of one fused RK stage launch:
 # stage input (read once) 24x8, y_n 24x8, acc read+write 2x24x8, output 24x8
 B_ALG_STAGE = 5 * 24 * 8
@@ -321,10 +326,14 @@ def run_ours(args, spec, world, rank, local):
     torch.cuda.synchronize()
     rhs_ms = r0.elapsed_time(r1) / nrep
     del ybuf, obuf
-    peak = B.fp64_peak(local)
+    probe = B.fp64_peak(local)
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    mhz = (ck or {}).get("sm_mhz") or (ck or {}).get("sm_max_mhz") or 2070.0
+    peak = FP64_FLOP_PER_CLK_SM * n_sm * mhz * 1e6
     roof = {"bound": "alu", "kernel": "k_rhs (FP64 BSSN RHS + KO + upwind)", "unit": "TFLOP/s",
-            "peak": peak / 1e12, "peak_source": "measured: FP64 FMA probe nr_fp64_peak on this GPU",
-            "launch_ms": rhs_ms, "points_per_launch": pts, "traffic": None}
+            "peak": peak / 1e12,
+            "peak_source": f"derived: 2 DFMA/clk/SM x {n_sm} SMs x {mhz:.0f} MHz (median SM clock in the timed region)",
+            "probe_tflops": probe / 1e12, "launch_ms": rhs_ms, "points_per_launch": pts, "traffic": None}
     if F_ALG:
         ach = F_ALG * pts / (rhs_ms * 1e-3)
         roof.update(achieved=ach / 1e12, frac=ach / peak, flops_per_point=F_ALG)
