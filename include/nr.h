@@ -178,6 +178,34 @@ int nr_check_finite(nr_grid* grid);
 int nr_build_maps(int coords, const int Nxx[3], int NG, int32_t* src, int8_t* parity, int32_t* cls);
 int nr_dt_cfl(int coords, const int Nxx[3], const nr_params* params, double* dt_out);
 
+/* Hamiltonian constraint that allocates nothing.  The paper has no
+ * counterpart: this is a library service for callers that cannot call
+ * cudaMalloc -- a host framework that owns all device memory through its own
+ * pool or HBM budget, a caller that holds no nr_grid (creating one allocates
+ * four 24-gridfunction sets) and only wants to check a state it already has
+ * on the device, or a latency-critical loop that cannot take cudaMalloc's
+ * implicit device synchronisation.  It computes what nr_hamiltonian computes
+ * (H at interior points of y_dev, the L2/Linf norms over the radius band
+ * [params->h_rmin, params->h_rmax]) for the grid described by coords, Nxx and
+ * *params, on params->device and params->stream.  Its scratch memory (per-axis
+ * reference-metric arrays, per-block partial norms, the reduced norms) is one
+ * file-scope device array of 512 KiB that every GPU loading the library holds
+ * until the process exits; nothing is allocated per call (no cudaMalloc,
+ * cudaFree or allocating library routine).
+ *   Limit: the per-axis arrays must fit 59,360 doubles, i.e.
+ *   4 n0 + 4 n1 + 2 n2 (SinhSpherical, Spherical) or 4 n0 + 2 n1 + 3 n2
+ *   (SinhCylindrical) with n_d = N_d + 6; larger grids get NR_EINVAL.
+ *   The first call on a device looks up the array's device address (with that
+ *   device current); make that first call before any stream capture.
+ *   All calls share the one array and every call overwrites it: calls that
+ *   overlap on the GPU (different streams, threads or processes' streams on
+ *   the same device) race.  Each call writes every scratch value it reads.
+ *   y_dev: caller-owned 24*T doubles; H_dev: caller-owned T doubles or NULL
+ *   (ghost points set to 0); l2_out/linf_out: host doubles or NULL (given:
+ *   the call synchronises params->stream).  Errors: NR_EINVAL, NR_ECUDA. */
+int nr_hamiltonian_noalloc(int coords, const int Nxx[3], const nr_params* params, const double* y_dev,
+                           double* H_dev, double* l2_out, double* linf_out);
+
 /* Measured FP64 FMA throughput of a device (FLOP/s, FMA = 2 FLOP): a fixed-size
  * kernel of independent FMA chains, best of five timed launches with CUDA events.
  * The roofline denominator of the FP64-bound kernels.  Synchronises. */

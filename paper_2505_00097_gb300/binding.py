@@ -24,7 +24,8 @@ COORDS = {"sinh_spherical": 0, "sinh_cylindrical": 1, "spherical": 2}
 EXPORTS = (
     "nr_params_default", "nr_grid_create", "nr_grid_destroy", "nr_query", "nr_set_brill_lindquist", "nr_rhs",
     "nr_apply_bcs", "nr_apply_inner_bcs", "nr_rk4_step", "nr_hamiltonian", "nr_get_state", "nr_set_state",
-    "nr_sync", "nr_check_finite", "nr_build_maps", "nr_dt_cfl", "nr_fp64_peak", "nr_last_error",
+    "nr_sync", "nr_check_finite", "nr_build_maps", "nr_dt_cfl", "nr_fp64_peak", "nr_hamiltonian_noalloc",
+    "nr_last_error",
 )
 
 
@@ -103,6 +104,7 @@ def lib() -> ctypes.CDLL:
                                 ctypes.POINTER(ctypes.c_int8), ctypes.POINTER(ctypes.c_int32)]
     L.nr_dt_cfl.argtypes = [ctypes.c_int, ip, P, dp]
     L.nr_fp64_peak.argtypes = [ctypes.c_int, dp]
+    L.nr_hamiltonian_noalloc.argtypes = [ctypes.c_int, ip, P, vp, vp, dp, dp]
     L.nr_last_error.argtypes = []
     L.nr_last_error.restype = ctypes.c_char_p
     _lib = L
@@ -177,6 +179,17 @@ def fp64_peak(device: int = 0) -> float:
     out = ctypes.c_double()
     _check(lib().nr_fp64_peak(int(device), ctypes.byref(out)))
     return out.value
+
+
+def hamiltonian_noalloc(spec: dict, y, H=None, stream=None, device: int = 0):
+    """nr_hamiltonian_noalloc: Hamiltonian constraint of a caller-owned state without any allocation;
+    returns (l2, linf)."""
+    p = make_params(spec, stream=stream, device=device)
+    Nx = (ctypes.c_int * 3)(*[int(v) for v in spec["N"]])
+    l2, linf = ctypes.c_double(), ctypes.c_double()
+    _check(lib().nr_hamiltonian_noalloc(int(spec["coords"]), Nx, ctypes.byref(p), _ptr(y),
+                                        None if H is None else _ptr(H), ctypes.byref(l2), ctypes.byref(linf)))
+    return l2.value, linf.value
 
 
 class Grid:

@@ -279,6 +279,17 @@ int check_args(int coords, const int Nxx[3], const nr_params* p)
 
 }  // namespace
 
+int nrk::nrk_fail(int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
 // ------------------------------------------------------------------ grid
 
 struct nr_grid {

@@ -75,5 +75,9 @@ cudaError_t launch_ham(const GridK& G, const double* y, double* H, double rmin, 
 int ham_partials_needed(const GridK& G);
 cudaError_t launch_finite(const GridK& G, const double* y, int* flag, cudaStream_t s);
 cudaError_t launch_fp64_probe(int blocks, int iters, double* sink, cudaStream_t s);
+cudaError_t launch_ham_reduce(const double* partials, int nparts, double* result, cudaStream_t s);
+
+// records a thread-local error message for nr_last_error() and returns code
+int nrk_fail(int code, const char* fmt, ...);
 
 }  // namespace nrk

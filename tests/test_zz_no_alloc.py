@@ -1,0 +1,75 @@
+"""The allocation-free Hamiltonian-constraint entry point (nr_hamiltonian_noalloc).
+
+It serves callers that cannot call cudaMalloc -- a host framework that owns all
+device memory, a caller without an nr_grid, a latency-critical loop -- by keeping
+its scratch in one file-scope device array.  Checked here through the C ABI: two
+calls in a row on different states agree with the grid-based nr_hamiltonian
+within the tolerances of the other Hamiltonian tests (H 1e-12 relative, norms
+1e-10), device free memory does not change across calls, and grids beyond the
+array's stated limit are rejected.  This file is collected last so that a run
+stopping at the first failure has already run every other test.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2505_00097_gb300 import binding as B  # noqa: E402
+from paper_2505_00097_gb300 import build as BUILD  # noqa: E402
+from paper_2505_00097_gb300 import workloads as W  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+SPECS = [
+    dict(W.sinh_spherical((37, 11, 6)), h_rmin=0.5, h_rmax=8.0),
+    dict(W.sinh_cylindrical((33, 2, 70), rho_max=20.0, z_max=20.0), h_rmin=0.5, h_rmax=8.0),
+]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    BUILD.build()
+    B.lib()
+
+
+@pytest.mark.parametrize("spec", SPECS, ids=["sinhsph", "sinhcyl"])
+def test_noalloc_matches_grid_hamiltonian_two_calls(spec):
+    g = B.Grid(spec)
+    T = g.T
+    free = []
+    for call, seed in enumerate((101, 202)):
+        y = torch.from_numpy(W.random_state(g.n, seed=seed, smooth=True)).to("cuda:0")
+        H_ref = torch.full((T,), float("nan"), dtype=torch.float64, device="cuda:0")
+        H_na = torch.full((T,), float("nan"), dtype=torch.float64, device="cuda:0")
+        l2_ref, linf_ref = g.hamiltonian(y, H_ref)
+        torch.cuda.synchronize()
+        free.append(torch.cuda.mem_get_info()[0])
+        l2, linf = B.hamiltonian_noalloc(spec, y, H_na)
+        torch.cuda.synchronize()
+        free.append(torch.cuda.mem_get_info()[0])
+        a, b = H_na.cpu().numpy(), H_ref.cpu().numpy()
+        assert np.all(np.isfinite(a))
+        err = np.abs(a - b).max() / np.abs(b).max()
+        assert err <= 1e-12, (call, err)
+        assert l2 == pytest.approx(l2_ref, rel=1e-10)
+        assert linf == pytest.approx(linf_ref, rel=1e-10)
+        # norms only, no H output
+        l2b, linfb = B.hamiltonian_noalloc(spec, y)
+        assert l2b == pytest.approx(l2_ref, rel=1e-10) and linfb == pytest.approx(linf_ref, rel=1e-10)
+    # after the first call set up the device address, calls allocate nothing
+    assert free[1] == free[2] == free[3], free
+    g.close()
+
+
+def test_noalloc_rejects_grids_beyond_its_scratch():
+    """n0 = 20006: the per-axis arrays need 4*20006 + 4*8 + 2*8 = 80,072 doubles > 59,360.  The
+    state buffer handed over is a real device buffer of the grid's full size, so the call reads
+    nothing out of bounds even if the size check were missing."""
+    spec = W.sinh_spherical((20000, 2, 2))
+    T = (20000 + 6) * 8 * 8
+    y = torch.zeros(24 * T, dtype=torch.float64, device="cuda:0")
+    with pytest.raises(B.NrError) as ei:
+        B.hamiltonian_noalloc(spec, y)
+    assert ei.value.code == 1 and "static scratch" in str(ei.value)
