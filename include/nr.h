@@ -178,6 +178,34 @@ int nr_check_finite(nr_grid* grid);
 int nr_build_maps(int coords, const int Nxx[3], int NG, int32_t* src, int8_t* parity, int32_t* cls);
 int nr_dt_cfl(int coords, const int Nxx[3], const nr_params* params, double* dt_out);
 
+/* Batched mode (the uneven-grid workload of the paper's single-node and
+ * scaling tests run many times over): many grids of uneven sizes, all of one
+ * coordinate family (spherical-like or cylindrical-like) and one device,
+ * advanced together.  Each RK4 substage is one persistent launch in which
+ * thread blocks take work items -- a tile of one grid's interior points or a
+ * chunk of its pure-outer ghost points -- from an atomic counter until the
+ * list is exhausted, followed by one parity-copy launch for all grids; one
+ * step is captured in a CUDA graph (re-captured when the step sizes or the
+ * tile shape change) and replayed.  Every point runs the same arithmetic as
+ * nr_rk4_step, so each grid's state is bitwise what nr_rk4_step would give,
+ * for any tile shape and any batch composition.
+ *   nr_batch_create: grids stay owned by the caller and must outlive the
+ *     batch; their library-owned states are advanced in place.  Work is issued
+ *     on the first grid's stream.  Errors: NR_EINVAL (mixed families or
+ *     devices, duplicates), NR_ENOMEM, NR_ECUDA.
+ *   nr_batch_set_tile: tile shape tile_x x tile_y of interior points per work
+ *     item, one of 32x4, 64x2, 128x1, 16x8, 32x2, 64x1, 32x1 (default 32x4).
+ *   nr_batch_autotune: times one substage launch of each compiled tile shape
+ *     on the batch (it writes only the RK work buffers, not the states), keeps
+ *     the fastest and returns it (synchronises).
+ *   nr_batch_rk4_step: dts[ngrids] per-grid step sizes (host), nsteps steps. */
+typedef struct nr_batch nr_batch;
+int nr_batch_create(nr_grid* const* grids, int ngrids, nr_batch** out);
+void nr_batch_destroy(nr_batch* batch);
+int nr_batch_set_tile(nr_batch* batch, int tile_x, int tile_y);
+int nr_batch_autotune(nr_batch* batch, const double* dts, int* tile_x, int* tile_y, double* best_ms);
+int nr_batch_rk4_step(nr_batch* batch, const double* dts, int nsteps);
+
 /* Hamiltonian constraint that allocates nothing.  The paper has no
  * counterpart: this is a library service for callers that cannot call
  * cudaMalloc -- a host framework that owns all device memory through its own

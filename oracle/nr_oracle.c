@@ -29,8 +29,9 @@
  *     - Dhat_l eps_ij), never Gammabar - Gammahat evaluated separately.
  *   R-gauge: d_t beta^i and d_t B^i use coordinate partial derivatives of the
  *     unrescaled components; the d_t Lambdabar^i substituted into d_t B^i is
- *     the full right-hand side of Eq. Lambda (with its advection term, without
- *     Kreiss-Oliger dissipation).
+ *     the right-hand side of Eq. Lambda as printed, i.e. d_perp Lambdabar^i
+ *     (the Lie derivative is not added back), without Kreiss-Oliger
+ *     dissipation.
  *   R-KO: rhs_g += sum_d sigma/(64 S_d dxx_d) delta^6_d g on the rescaled g:
  *     the strength refers to the physical spacing S_d dxx_d.  With the
  *     logical spacing dxx_d alone, the damping rate sigma/dxx_d of the Nyquist
@@ -973,10 +974,10 @@ static void rhs_at_point(const orc_params* p, const rfm_pt* R, const refmet* M, 
             grad_ap += G.gbinv[i][j] * F->dalpha[i] * G.dphi[j];
         }
     double r_K = F->adv_K + (1.0 / 3.0) * al * K * K + al * G.AA - W2 * (lapl_al + 2.0 * grad_ap);
-    /* Eq. Lambda_RHS_orig_final (reading R-Lambda) + L_beta Lambda^i */
+    /* Eq. Lambda_RHS_orig_final (reading R-Lambda): d_perp Lambda^i, then + L_beta Lambda^i */
+    double r_Lam_perp[3];
     for (int i = 0; i < 3; i++) {
-        double t = F->adv_Lam[i];
-        for (int j = 0; j < 3; j++) t -= F->Lam[j] * F->dbeta[i][j];
+        double t = 0.0;
         for (int j = 0; j < 3; j++)
             for (int k = 0; k < 3; k++) t += G.gbinv[j][k] * DDb[i][j][k];
         t += (2.0 / 3.0) * G.Dvec[i] * divbar;
@@ -985,13 +986,16 @@ static void rhs_at_point(const orc_params* p, const rfm_pt* R, const refmet* M, 
         for (int j = 0; j < 3; j++)
             for (int k = 0; k < 3; k++) t += 2.0 * al * G.Auu[j][k] * G.Dup[i][j][k];
         for (int j = 0; j < 3; j++) t -= (4.0 / 3.0) * al * G.gbinv[i][j] * F->dK[j];
-        r_Lam[i] = t;
+        r_Lam_perp[i] = t;
+        double lie = F->adv_Lam[i];
+        for (int j = 0; j < 3; j++) lie -= F->Lam[j] * F->dbeta[i][j];
+        r_Lam[i] = lie + t;
     }
     /* Eqs. gauge_eqns, damping_eta_final */
     double r_al = -2.0 * al * K + F->adv_alpha;
     for (int i = 0; i < 3; i++) {
         r_beta[i] = F->B[i] + F->adv_beta[i];
-        r_B[i] = 0.75 * r_Lam[i] - p->eta * F->B[i] + F->adv_B[i];
+        r_B[i] = 0.75 * r_Lam_perp[i] - p->eta * F->B[i] + F->adv_B[i];
     }
     /* back to rescaled gridfunctions (S is time independent) */
     for (int s = 0; s < 6; s++) {

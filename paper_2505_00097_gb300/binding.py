@@ -25,6 +25,7 @@ EXPORTS = (
     "nr_params_default", "nr_grid_create", "nr_grid_destroy", "nr_query", "nr_set_brill_lindquist", "nr_rhs",
     "nr_apply_bcs", "nr_apply_inner_bcs", "nr_rk4_step", "nr_hamiltonian", "nr_get_state", "nr_set_state",
     "nr_sync", "nr_check_finite", "nr_build_maps", "nr_dt_cfl", "nr_fp64_peak", "nr_hamiltonian_noalloc",
+    "nr_batch_create", "nr_batch_destroy", "nr_batch_set_tile", "nr_batch_autotune", "nr_batch_rk4_step",
     "nr_last_error",
 )
 
@@ -105,6 +106,12 @@ def lib() -> ctypes.CDLL:
     L.nr_dt_cfl.argtypes = [ctypes.c_int, ip, P, dp]
     L.nr_fp64_peak.argtypes = [ctypes.c_int, dp]
     L.nr_hamiltonian_noalloc.argtypes = [ctypes.c_int, ip, P, vp, vp, dp, dp]
+    L.nr_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp)]
+    L.nr_batch_destroy.argtypes = [vp]
+    L.nr_batch_destroy.restype = None
+    L.nr_batch_set_tile.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+    L.nr_batch_autotune.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), dp]
+    L.nr_batch_rk4_step.argtypes = [vp, dp, ctypes.c_int]
     L.nr_last_error.argtypes = []
     L.nr_last_error.restype = ctypes.c_char_p
     _lib = L
@@ -260,3 +267,44 @@ class Grid:
 
     def check_finite(self) -> None:
         _check(lib().nr_check_finite(self.h))
+
+
+class Batch:
+    """nr_batch over a list of Grid objects (which must outlive it)."""
+
+    def __init__(self, grids):
+        self.grids = list(grids)
+        arr = (ctypes.c_void_p * len(self.grids))(*[g.h.value for g in self.grids])
+        h = ctypes.c_void_p()
+        _check(lib().nr_batch_create(arr, len(self.grids), ctypes.byref(h)))
+        self.h = h
+
+    def close(self) -> None:
+        if self.h:
+            lib().nr_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _dts(self, dts):
+        a = np.ascontiguousarray(dts, dtype=np.float64)
+        assert a.size == len(self.grids)
+        return a
+
+    def set_tile(self, tx: int, ty: int) -> None:
+        _check(lib().nr_batch_set_tile(self.h, int(tx), int(ty)))
+
+    def autotune(self, dts):
+        a = self._dts(dts)
+        tx, ty, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        _check(lib().nr_batch_autotune(self.h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(tx),
+                                       ctypes.byref(ty), ctypes.byref(ms)))
+        return tx.value, ty.value, ms.value
+
+    def rk4_step(self, dts, nsteps: int = 1) -> None:
+        a = self._dts(dts)
+        _check(lib().nr_batch_rk4_step(self.h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(nsteps)))

@@ -24,7 +24,8 @@
 // beta^k d_k parts upwinded; beta_j in 2 Dhat_(i beta_j) lowered with
 // gammahat; Delta^k_ij built from Dhat eps only; the gauge equations with
 // coordinate partial derivatives of the unrescaled beta^i, B^i, and the full
-// d_t Lambdabar^i (without dissipation) inside d_t B^i.
+// right-hand side of Eq. Lambda_RHS_orig_final (d_perp Lambdabar^i, without the Lie
+// derivative and without dissipation) inside d_t B^i.
 #pragma once
 
 #include <stdint.h>
@@ -668,12 +669,13 @@ __device__ __forceinline__ void rhs_core(const PointIn& P, double eta, double ou
         out[G_TRK] = fma(al, fma((1.0 / 3.0) * K, K, AA), -W2 * fma(2.0, gap, lapal));
     }
     // Eq. Lambda_RHS_orig_final (with the alpha factors restored) + Lie terms
-    double rl[3];
+    double rl[3], rperp[3];
     {
 #pragma unroll
         for (int i = 0; i < 3; i++) {
-            // - lambda^j Dhat_j beta^i + (2/3) Delta^i Dbar.beta + (1/3) gammabar^ik e_k Dbar.beta
-            double t = fma(-lam[2], Db[i][2], fma(-lam[1], Db[i][1], fma(-lam[0], Db[i][0], LapB[i])));
+            // (2/3) Delta^i Dbar.beta + (1/3) gammabar^ik e_k Dbar.beta (the Lie-derivative part
+            // - lambda^j Dhat_j beta^i + beta^j (Omega_j lambda)^i is added after this block)
+            double t = LapB[i];
             t = fma((2.0 / 3.0) * Dvec[i], divbar, t);
             t = fma((1.0 / 3.0), fma(gsym(gi, i, 2), gdiv[2], fma(gsym(gi, i, 1), gdiv[1], gsym(gi, i, 0) * gdiv[0])), t);
             // -2 Abar^ij (d_j alpha - 6 alpha d_j phi) - 4/3 alpha gammabar^ij d_j K
@@ -689,14 +691,19 @@ __device__ __forceinline__ void rhs_core(const PointIn& P, double eta, double ou
             for (int s = 1; s < 6; s++) w = fma(offd(s) ? Auu[s] + Auu[s] : Auu[s], Dup[i][s], w);
             rl[i] = fma(2.0 * al, w, t);
         }
-        // + beta^j (Omega_j lambda)^i
+        // Lie-derivative part: - lambda^j Dhat_j beta^i + beta^j (Omega_j lambda)^i
+#pragma unroll
+        for (int i = 0; i < 3; i++) rperp[i] = rl[i];
+#pragma unroll
+        for (int i = 0; i < 3; i++) rl[i] = fma(-lam[2], Db[i][2], fma(-lam[1], Db[i][1], fma(-lam[0], Db[i][0], rl[i])));
         omv<FAM, 1>(g, vet[1], lam, rl);
         omv<FAM, 2>(g, vet[2], lam, rl);
 #pragma unroll
         for (int i = 0; i < 3; i++) out[G_LAM + i] = rl[i];
     }
     // gauge: d_t alpha = -2 alpha K (+ advection);  d_t beta^i = B^i (+ coordinate advection);
-    //        d_t B^i = 3/4 d_t Lambdabar^i - eta B^i (+ coordinate advection)
+    //        d_t B^i = 3/4 [right-hand side of Eq. Lambda, i.e. d_perp Lambdabar^i] - eta B^i
+    //                  (+ coordinate advection)
     {
         // partial-derivative advection of unrescaled components: - v^i sum_j d_ij vet^j
         double dv[3];
@@ -708,7 +715,7 @@ __device__ __forceinline__ void rhs_core(const PointIn& P, double eta, double ou
 #pragma unroll
         for (int i = 0; i < 3; i++) {
             out[G_VET + i] = fma(-vet[i], dv[i], bet[i]);
-            out[G_BET + i] = fma(-bet[i], dv[i], fma(0.75, rl[i], -eta * bet[i]));
+            out[G_BET + i] = fma(-bet[i], dv[i], fma(0.75, rperp[i], -eta * bet[i]));
         }
     }
 }
@@ -766,9 +773,8 @@ __device__ __forceinline__ double ko(const double* f, const long st[3], const do
 }
 
 // Adds the upwinded advection and the dissipation to the 24 right-hand sides
-// of rhs_core.  d_t B^i contains 3/4 of the full d_t Lambdabar^i, so it also
-// receives 3/4 of the advection of lambda^i.  The dissipation strength refers
-// to the physical spacing S_d dxx_d: 1/(64 S_d dxx_d) = (12/64) D[d].
+// of rhs_core.  The dissipation strength refers to the physical spacing
+// S_d dxx_d: 1/(64 S_d dxx_d) = (12/64) D[d].
 __device__ __forceinline__ void add_adv_ko(const double* y, long T, const long st[3], const double D[3],
                                            const double* sigma, double k[NGF])
 {
@@ -784,15 +790,8 @@ __device__ __forceinline__ void add_adv_ko(const double* y, long T, const long s
         u[d] = fabs(v) * D[d];
         us[d] = (v > 0.0) ? st[d] : -st[d];
     }
-    double alam[3];
 #pragma unroll
-    for (int g = 0; g < NGF; g++) {
-        const double a = adv(y + (long)g * T, u, us);
-        if (g >= G_LAM && g < G_LAM + 3) alam[g - G_LAM] = a;
-        k[g] += a;
-    }
-#pragma unroll
-    for (int i = 0; i < 3; i++) k[G_BET + i] = fma(0.75, alam[i], k[G_BET + i]);
+    for (int g = 0; g < NGF; g++) k[g] += adv(y + (long)g * T, u, us);
 #pragma unroll
     for (int g = 0; g < NGF; g++) k[g] = fma(sigma[g], ko(y + (long)g * T, st, kod, kosum), k[g]);
 }

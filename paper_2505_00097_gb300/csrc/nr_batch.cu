@@ -1,0 +1,418 @@
+// nr_batch.cu -- batched mode: many grids of uneven sizes advanced together,
+// one persistent launch per RK4 substage plus one parity-copy launch, the
+// whole step captured in a CUDA graph; the tile shape is chosen by timing.
+//
+// A work item is either a TX x TY tile of one grid's interior points or a
+// chunk of TX*TY of its pure-outer ghost points.  Blocks of the persistent
+// kernel take items from an atomic counter until the list is exhausted (a
+// bounded loop: each block stops at the first index past the end).  Every
+// point runs the same per-point code as the single-grid kernels
+// (nr_stage.cuh), so a grid's state after n batched steps is bitwise the
+// state after n single-grid steps, whatever the tile shape or the company.
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "nr_stage.cuh"
+
+namespace nrk {
+
+struct BGrid {
+    GridK K;
+    double *y, *ya, *yb, *acc;
+    const OuterPt* outer;
+    const double* finf;
+    const double* wspeed;
+    int n_outer;
+    int tiles_x;
+    int w_begin, w_rhs_end, w_end;
+    int pad;
+    Stage st[4];
+};
+
+struct BInner {
+    int grid, dst, src, negmask;
+};
+
+__device__ __forceinline__ void stage_buffers(const BGrid& B, int stage, const double*& yin, double*& out,
+                                              const double*& yn)
+{
+    switch (stage) {
+    case 0: yin = B.y; out = B.ya; yn = B.y; break;
+    case 1: yin = B.ya; out = B.yb; yn = B.y; break;
+    case 2: yin = B.yb; out = B.ya; yn = B.y; break;
+    default: yin = B.ya; out = B.y; yn = nullptr; break;
+    }
+}
+
+template <int FAM, int TX, int TY>
+__global__ void __launch_bounds__(TX* TY) k_batch_stage(const BGrid* __restrict__ grids, int ngrids, int total,
+                                                         int* counter, int stage)
+{
+    __shared__ int s_w;
+    const int tid = threadIdx.x;
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s_w = atomicAdd(counter, 1);
+        __syncthreads();
+        const int w = s_w;
+        if (w >= total) return;
+        int lo = 0, hi = ngrids - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (grids[mid].w_begin <= w) lo = mid;
+            else hi = mid - 1;
+        }
+        const BGrid& B = grids[lo];
+        const double* yin;
+        const double* yn;
+        double* out;
+        stage_buffers(B, stage, yin, out, yn);
+        if (w < B.w_rhs_end) {
+            const int t = w - B.w_begin;
+            const int i = (t % B.tiles_x) * TX + tid % TX;
+            const int j = (t / B.tiles_x) * TY + tid / TX;
+            if (i < B.K.N0 && j < B.K.N1 * B.K.N2) rhs_point_stage<FAM>(B.K, yin, out, yn, B.acc, B.st[stage], i, j);
+        } else {
+            const int p = (w - B.w_rhs_end) * (TX * TY) + tid;
+            if (p < B.n_outer)
+                outer_point_stage<FAM>(B.K, B.outer[p], yin, out, yn, B.acc, B.finf, B.wspeed, B.st[stage]);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_batch_inner(const BGrid* __restrict__ grids, const BInner* __restrict__ pts,
+                                                      int npts, int stage)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= npts) return;
+    const BInner q = pts[t];
+    const BGrid& B = grids[q.grid];
+    const double* yin;
+    const double* yn;
+    double* out;
+    stage_buffers(B, stage, yin, out, yn);
+    InnerPt p{q.dst, q.src, q.negmask, 0};
+    inner_copy(B.K.T, p, blockIdx.y, out);
+}
+
+// tile shapes the autotuner tries (threads per block = TX * TY)
+struct TileShape {
+    int tx, ty;
+};
+constexpr TileShape kTiles[] = {{32, 4}, {64, 2}, {128, 1}, {16, 8}, {32, 2}, {64, 1}, {32, 1}};
+constexpr int kNumTiles = sizeof(kTiles) / sizeof(kTiles[0]);
+
+template <int FAM, int TX, int TY>
+cudaError_t launch_bstage(const BGrid* g, int n, int total, int* counter, int stage, int blocks, cudaStream_t s)
+{
+    k_batch_stage<FAM, TX, TY><<<blocks, TX * TY, 0, s>>>(g, n, total, counter, stage);
+    return cudaGetLastError();
+}
+
+template <int FAM, int TX, int TY>
+int occupancy_blocks(int sms)
+{
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_stage<FAM, TX, TY>, TX * TY, 0) != cudaSuccess)
+        return 0;
+    return std::max(nb, 1) * sms;
+}
+
+template <int FAM>
+cudaError_t dispatch_stage(int tile, const BGrid* g, int n, int total, int* counter, int stage, int blocks,
+                           cudaStream_t s)
+{
+    switch (tile) {
+    case 0: return launch_bstage<FAM, 32, 4>(g, n, total, counter, stage, blocks, s);
+    case 1: return launch_bstage<FAM, 64, 2>(g, n, total, counter, stage, blocks, s);
+    case 2: return launch_bstage<FAM, 128, 1>(g, n, total, counter, stage, blocks, s);
+    case 3: return launch_bstage<FAM, 16, 8>(g, n, total, counter, stage, blocks, s);
+    case 4: return launch_bstage<FAM, 32, 2>(g, n, total, counter, stage, blocks, s);
+    case 5: return launch_bstage<FAM, 64, 1>(g, n, total, counter, stage, blocks, s);
+    default: return launch_bstage<FAM, 32, 1>(g, n, total, counter, stage, blocks, s);
+    }
+}
+
+template <int FAM>
+int dispatch_occupancy(int tile, int sms)
+{
+    switch (tile) {
+    case 0: return occupancy_blocks<FAM, 32, 4>(sms);
+    case 1: return occupancy_blocks<FAM, 64, 2>(sms);
+    case 2: return occupancy_blocks<FAM, 128, 1>(sms);
+    case 3: return occupancy_blocks<FAM, 16, 8>(sms);
+    case 4: return occupancy_blocks<FAM, 32, 2>(sms);
+    case 5: return occupancy_blocks<FAM, 64, 1>(sms);
+    default: return occupancy_blocks<FAM, 32, 1>(sms);
+    }
+}
+
+}  // namespace nrk
+
+using namespace nrk;
+
+struct nr_batch {
+    std::vector<nr_grid*> grids;
+    int fam = FAM_SPH;
+    int device = 0;
+    int sms = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap = nullptr;
+    int tile = 0;
+    int blocks = 0;
+    int total = 0;
+    BGrid* d_grids = nullptr;
+    BInner* d_inner = nullptr;
+    int n_inner = 0;
+    int* d_counter = nullptr;
+    std::vector<double> dts;   // dts of the current table
+    bool table_ok = false;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+struct DevGuard {
+    int prev = 0;
+    explicit DevGuard(int d) { cudaGetDevice(&prev); cudaSetDevice(d); }
+    ~DevGuard() { cudaSetDevice(prev); }
+};
+
+// work list and per-grid stage constants for tile shape b->tile and step sizes dts
+int build_table(nr_batch* b, const double* dts)
+{
+    const TileShape ts = kTiles[b->tile];
+    std::vector<BGrid> h(b->grids.size());
+    int w = 0;
+    for (size_t q = 0; q < b->grids.size(); q++) {
+        nr_grid* g = b->grids[q];
+        BGrid& B = h[q];
+        memset(&B, 0, sizeof B);
+        B.K = g->K;
+        B.y = g->y;
+        B.ya = g->ya;
+        B.yb = g->yb;
+        B.acc = g->acc;
+        B.outer = g->outer;
+        B.finf = g->finf;
+        B.wspeed = g->wspeed;
+        B.n_outer = g->n_outer;
+        B.tiles_x = (g->K.N0 + ts.tx - 1) / ts.tx;
+        const int tiles_y = (g->K.N1 * g->K.N2 + ts.ty - 1) / ts.ty;
+        B.w_begin = w;
+        B.w_rhs_end = w + B.tiles_x * tiles_y;
+        B.w_end = B.w_rhs_end + (g->n_outer + ts.tx * ts.ty - 1) / (ts.tx * ts.ty);
+        w = B.w_end;
+        // the same stage constants as the single-grid RK4 driver
+        const double dt = dts[q];
+        const int enf = g->P.enforce_detgb;
+        B.st[0] = Stage{MODE_STAGE1, enf, 0.5 * dt, dt / 6.0};
+        B.st[1] = Stage{MODE_STAGE23, enf, 0.5 * dt, dt / 3.0};
+        B.st[2] = Stage{MODE_STAGE23, enf, dt, dt / 3.0};
+        B.st[3] = Stage{MODE_STAGE4, enf, 0.0, dt / 6.0};
+    }
+    b->total = w;
+    cudaError_t e = cudaMemcpy(b->d_grids, h.data(), sizeof(BGrid) * h.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return nrk_fail(NR_ECUDA, "batch table upload: %s", cudaGetErrorString(e));
+    b->blocks = b->fam == FAM_SPH ? dispatch_occupancy<FAM_SPH>(b->tile, b->sms)
+                                  : dispatch_occupancy<FAM_CYL>(b->tile, b->sms);
+    if (b->blocks <= 0) return nrk_fail(NR_ECUDA, "occupancy query failed");
+    b->dts.assign(dts, dts + b->grids.size());
+    b->table_ok = true;
+    return NR_OK;
+}
+
+cudaError_t enqueue_stage_launch(nr_batch* b, int stage, cudaStream_t s)
+{
+    return b->fam == FAM_SPH
+               ? dispatch_stage<FAM_SPH>(b->tile, b->d_grids, (int)b->grids.size(), b->total, b->d_counter + stage,
+                                         stage, b->blocks, s)
+               : dispatch_stage<FAM_CYL>(b->tile, b->d_grids, (int)b->grids.size(), b->total, b->d_counter + stage,
+                                         stage, b->blocks, s);
+}
+
+cudaError_t enqueue_step(nr_batch* b, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(b->d_counter, 0, 4 * sizeof(int), s);
+    for (int stage = 0; stage < 4 && e == cudaSuccess; stage++) {
+        e = enqueue_stage_launch(b, stage, s);
+        if (e == cudaSuccess && b->n_inner) {
+            dim3 grd((b->n_inner + 255) / 256, NR_NGF);
+            k_batch_inner<<<grd, 256, 0, s>>>(b->d_grids, b->d_inner, b->n_inner, stage);
+            e = cudaGetLastError();
+        }
+    }
+    return e;
+}
+
+void drop_graph(nr_batch* b)
+{
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+}
+
+bool same_dts(const nr_batch* b, const double* dts)
+{
+    for (size_t q = 0; q < b->grids.size(); q++)
+        if (b->dts[q] != dts[q]) return false;
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+int nr_batch_create(nr_grid* const* grids, int ngrids, nr_batch** out)
+{
+    if (!out) return nrk_fail(NR_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!grids || ngrids < 1) return nrk_fail(NR_EINVAL, "no grids");
+    for (int q = 0; q < ngrids; q++) {
+        if (!grids[q]) return nrk_fail(NR_EINVAL, "grid %d is NULL", q);
+        if (grids[q]->device != grids[0]->device) return nrk_fail(NR_EINVAL, "grids on different devices");
+        if (grids[q]->geo.fam != grids[0]->geo.fam)
+            return nrk_fail(NR_EINVAL, "grids of spherical-like and cylindrical-like coordinates cannot share a batch");
+        for (int r = 0; r < q; r++)
+            if (grids[r] == grids[q]) return nrk_fail(NR_EINVAL, "grid %d appears twice", q);
+    }
+    nr_batch* b = new nr_batch();
+    b->grids.assign(grids, grids + ngrids);
+    b->fam = grids[0]->geo.fam;
+    b->device = grids[0]->device;
+    b->stream = grids[0]->stream;
+    DevGuard dg(b->device);
+    std::vector<BInner> inner;
+    for (int q = 0; q < ngrids; q++) {
+        const nr_grid* g = grids[q];
+        for (long idx = 0; idx < g->geo.T; idx++) {
+            if (g->cls[idx] != 2) continue;
+            int m = 0;
+            for (int t = 0; t < 10; t++)
+                if (g->par[10 * idx + t] < 0) m |= 1 << t;
+            inner.push_back(BInner{q, (int)idx, g->src[idx], m});
+        }
+    }
+    b->n_inner = (int)inner.size();
+    cudaError_t e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_grids, sizeof(BGrid) * ngrids);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_inner, sizeof(BInner) * std::max<size_t>(inner.size(), 1));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, 4 * sizeof(int));
+    if (e == cudaSuccess && !inner.empty())
+        e = cudaMemcpy(b->d_inner, inner.data(), sizeof(BInner) * inner.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        nr_batch_destroy(b);
+        return nrk_fail(e == cudaErrorMemoryAllocation ? NR_ENOMEM : NR_ECUDA, "batch set-up: %s",
+                        cudaGetErrorString(e));
+    }
+    *out = b;
+    return NR_OK;
+}
+
+void nr_batch_destroy(nr_batch* b)
+{
+    if (!b) return;
+    DevGuard dg(b->device);
+    drop_graph(b);
+    if (b->d_grids) cudaFree(b->d_grids);
+    if (b->d_inner) cudaFree(b->d_inner);
+    if (b->d_counter) cudaFree(b->d_counter);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    delete b;
+}
+
+int nr_batch_set_tile(nr_batch* b, int tile_x, int tile_y)
+{
+    if (!b) return nrk_fail(NR_EINVAL, "batch is NULL");
+    for (int t = 0; t < kNumTiles; t++)
+        if (kTiles[t].tx == tile_x && kTiles[t].ty == tile_y) {
+            if (t != b->tile) {
+                b->tile = t;
+                b->table_ok = false;
+                drop_graph(b);
+            }
+            return NR_OK;
+        }
+    return nrk_fail(NR_EINVAL, "tile %dx%d is not one of the compiled shapes", tile_x, tile_y);
+}
+
+int nr_batch_autotune(nr_batch* b, const double* dts, int* tile_x, int* tile_y, double* best_ms)
+{
+    if (!b || !dts) return nrk_fail(NR_EINVAL, "bad nr_batch_autotune arguments");
+    DevGuard dg(b->device);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int best = -1;
+    float best_t = 1e30f;
+    int rc = NR_OK;
+    for (int t = 0; t < kNumTiles && rc == NR_OK; t++) {
+        b->tile = t;
+        if ((rc = build_table(b, dts))) break;
+        // stage 1 writes only the stage buffer and the accumulator: the state is untouched
+        float tt = 0.f;
+        for (int rep = 0; rep < 4; rep++) {
+            cudaMemsetAsync(b->d_counter, 0, sizeof(int), b->stream);
+            cudaEventRecord(e0, b->stream);
+            cudaError_t e = enqueue_stage_launch(b, 0, b->stream);
+            cudaEventRecord(e1, b->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (e != cudaSuccess) {
+                rc = nrk_fail(NR_ECUDA, "autotune launch: %s", cudaGetErrorString(e));
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) tt = rep == 1 ? ms : std::min(tt, ms);
+        }
+        if (rc == NR_OK && tt < best_t) {
+            best_t = tt;
+            best = t;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    b->tile = best;
+    drop_graph(b);
+    if ((rc = build_table(b, dts))) return rc;
+    if (tile_x) *tile_x = kTiles[best].tx;
+    if (tile_y) *tile_y = kTiles[best].ty;
+    if (best_ms) *best_ms = best_t;
+    return NR_OK;
+}
+
+int nr_batch_rk4_step(nr_batch* b, const double* dts, int nsteps)
+{
+    if (!b || !dts || nsteps < 0) return nrk_fail(NR_EINVAL, "bad nr_batch_rk4_step arguments");
+    for (size_t q = 0; q < b->grids.size(); q++)
+        if (!(dts[q] > 0.0)) return nrk_fail(NR_EINVAL, "dt of grid %zu must be positive", q);
+    if (nsteps == 0) return NR_OK;
+    DevGuard dg(b->device);
+    int rc;
+    if (!b->table_ok || !same_dts(b, dts)) {
+        drop_graph(b);
+        if ((rc = build_table(b, dts))) return rc;
+    }
+    if (!b->exec) {
+        cudaGraph_t graph;
+        cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return nrk_fail(NR_ECUDA, "capture: %s", cudaGetErrorString(e));
+        cudaError_t le = enqueue_step(b, b->cap);
+        e = cudaStreamEndCapture(b->cap, &graph);
+        if (le != cudaSuccess) return nrk_fail(NR_ECUDA, "batch step: %s", cudaGetErrorString(le));
+        if (e != cudaSuccess) return nrk_fail(NR_ECUDA, "capture end: %s", cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&b->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return nrk_fail(NR_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    }
+    for (int n = 0; n < nsteps; n++) {
+        cudaError_t e = cudaGraphLaunch(b->exec, b->stream);
+        if (e != cudaSuccess) return nrk_fail(NR_ECUDA, "graph launch: %s", cudaGetErrorString(e));
+    }
+    return NR_OK;
+}
+
+}  // extern "C"

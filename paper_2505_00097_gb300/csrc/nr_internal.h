@@ -80,4 +80,47 @@ cudaError_t launch_ham_reduce(const double* partials, int nparts, double* result
 // records a thread-local error message for nr_last_error() and returns code
 int nrk_fail(int code, const char* fmt, ...);
 
+// host-side description of a grid's logical coordinates
+struct HostGeom {
+    int coords, fam;
+    int N[3], n[3], NG;
+    long T;
+    double dxx[3], lo[3];
+    double xx(int d, int i) const { return lo[d] + ((double)(i - NG) + 0.5) * dxx[d]; }
+};
+
 }  // namespace nrk
+
+// one grid: host maps, device buffers and the CUDA-graph RK4 driver state
+struct nr_grid {
+    nrk::HostGeom geo;
+    nr_params P;
+    nrk::GridK K;
+    cudaStream_t stream = nullptr;   // user stream (may be the legacy stream)
+    cudaStream_t cap = nullptr;      // internal stream used for graph capture
+    int device = 0;
+    // device buffers
+    double *y = nullptr, *ya = nullptr, *yb = nullptr, *acc = nullptr;
+    double *ax0 = nullptr, *ax1 = nullptr, *ax2 = nullptr;
+    nrk::OuterPt* outer = nullptr;
+    nrk::InnerPt* inner = nullptr;
+    int* canon = nullptr;
+    double* finf = nullptr;
+    double* wspeed = nullptr;
+    double* partials = nullptr;
+    double* hres = nullptr;
+    int* flag = nullptr;
+    double* mxyz = nullptr;
+    int n_outer = 0, n_inner = 0, nparts = 0;
+    long n_canon = 0;
+    size_t bytes = 0;
+    double dt_cfl = 0.0;
+    // host copies
+    std::vector<int32_t> src, cls;
+    std::vector<int8_t> par;
+    std::vector<double> cart_canon;  // for the puncture-distance check
+    // graph
+    cudaGraphExec_t exec = nullptr;
+    double graph_dt = 0.0;
+};
+

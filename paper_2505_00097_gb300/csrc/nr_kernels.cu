@@ -15,58 +15,11 @@
 #include "bssn_point.cuh"
 #include "nr_geo.cuh"
 #include "nr_internal.h"
+#include "nr_stage.cuh"
 
 namespace nrk {
 
 constexpr int RHS_BX = 32, RHS_BY = 4;
-
-// det(delta_ij + h_ij) := 1 (Lagrangian choice of Sec. 2.1), in place, in
-// terms of the deviation h so that small h keeps its relative precision:
-// det(I + h) - 1 = tr h + (sum of principal 2x2 minors of h) + det h,
-// f1 = det^(-1/3) - 1 = expm1(-log1p(det - 1)/3), h <- h + f1 (delta + h).
-__device__ __forceinline__ void enforce_det(double* v)
-{
-    const double m2 = fma(v[0], v[3], fma(v[0], v[5], fma(v[3], v[5], -fma(v[1], v[1], fma(v[2], v[2], v[4] * v[4])))));
-    const double c0 = fma(v[3], v[5], -v[4] * v[4]);
-    const double c1 = fma(v[2], v[4], -v[1] * v[5]);
-    const double c2 = fma(v[1], v[4], -v[2] * v[3]);
-    const double d3 = fma(v[0], c0, fma(v[1], c1, v[2] * c2));
-    const double dm1 = (v[0] + v[3] + v[5]) + (m2 + d3);
-    const double f1 = expm1(log1p(dm1) * (-1.0 / 3.0));
-    v[0] = fma(f1, v[0], v[0] + f1);
-    v[1] = fma(f1, v[1], v[1]);
-    v[2] = fma(f1, v[2], v[2]);
-    v[3] = fma(f1, v[3], v[3] + f1);
-    v[4] = fma(f1, v[4], v[4]);
-    v[5] = fma(f1, v[5], v[5] + f1);
-}
-
-// RK4 stage epilogue for one point: k -> (y_next, acc) or the plain RHS.
-__device__ __forceinline__ void stage_store(const Stage& st, long T, long idx, const double k[NGF],
-                                            const double* __restrict__ yn, double* __restrict__ out,
-                                            double* __restrict__ acc)
-{
-    if (st.mode == MODE_RHS) {
-#pragma unroll
-        for (int g = 0; g < NGF; g++) out[g * T + idx] = k[g];
-        return;
-    }
-    double v[NGF];
-    if (st.mode == MODE_STAGE4) {
-#pragma unroll
-        for (int g = 0; g < NGF; g++) v[g] = fma(st.cacc, k[g], acc[g * T + idx]);
-    } else {
-#pragma unroll
-        for (int g = 0; g < NGF; g++) {
-            const double y0 = yn[g * T + idx];
-            v[g] = fma(st.cnext, k[g], y0);
-            acc[g * T + idx] = fma(st.cacc, k[g], st.mode == MODE_STAGE1 ? y0 : acc[g * T + idx]);
-        }
-    }
-    if (st.enforce) enforce_det(v);
-#pragma unroll
-    for (int g = 0; g < NGF; g++) out[g * T + idx] = v[g];
-}
 
 template <int FAM>
 __global__ void __launch_bounds__(RHS_BX* RHS_BY) k_rhs(GridK G, const double* __restrict__ yin, double* out,
@@ -77,31 +30,7 @@ __global__ void __launch_bounds__(RHS_BX* RHS_BY) k_rhs(GridK G, const double* _
     const int i = (int)(blockIdx.x % nbx) * RHS_BX + threadIdx.x;
     const int j = (int)(blockIdx.x / nbx) * RHS_BY + threadIdx.y;
     if (i >= G.N0 || j >= G.N1 * G.N2) return;
-    const int p0 = i + G.NG, p1 = j % G.N1 + G.NG, p2 = j / G.N1 + G.NG;
-    const long idx = p0 + (long)G.n0 * (p1 + (long)G.n1 * p2);
-    PointIn P;
-    P.y = yin + idx;
-    P.T = G.T;
-    P.st[0] = 1;
-    P.st[1] = G.n0;
-    P.st[2] = (long)G.n0 * G.n1;
-    P.g = make_geo<FAM>(G, p0, p1, p2);
-    double k[NGF];
-    rhs_core<FAM>(P, G.eta, k);
-    add_adv_ko(P.y, G.T, P.st, P.g.D, G.sigma, k);
-    stage_store(st, G.T, idx, k, yn, out, acc);
-}
-
-// one-sided / centred first-derivative stencil sums (weights of 12 h f')
-__device__ __forceinline__ double osraw(const double* f, long s, int kind)
-{
-    switch (kind) {
-    case 0: return fma(8.0, ld(f + s) - ld(f - s), ld(f - 2 * s) - ld(f + 2 * s));
-    case 1: return fma(3.0, ld(f + s), fma(10.0, ld(f), fma(-18.0, ld(f - s), fma(6.0, ld(f - 2 * s), -ld(f - 3 * s)))));
-    case 2: return fma(25.0, ld(f), fma(-48.0, ld(f - s), fma(36.0, ld(f - 2 * s), fma(-16.0, ld(f - 3 * s), 3.0 * ld(f - 4 * s)))));
-    case 3: return fma(-3.0, ld(f - s), fma(-10.0, ld(f), fma(18.0, ld(f + s), fma(-6.0, ld(f + 2 * s), ld(f + 3 * s)))));
-    default: return fma(-25.0, ld(f), fma(48.0, ld(f + s), fma(-36.0, ld(f + 2 * s), fma(16.0, ld(f + 3 * s), -3.0 * ld(f + 4 * s)))));
-    }
+    rhs_point_stage<FAM>(G, yin, out, yn, acc, st, i, j);
 }
 
 template <int FAM>
@@ -112,41 +41,14 @@ __global__ void __launch_bounds__(128) k_outer(GridK G, const OuterPt* __restric
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= npts) return;
-    const OuterPt p = pts[t];
-    const long idx = p.idx;
-    const long s2 = (long)G.n0 * G.n1;
-    const int k0 = p.kind & 0xff, k2 = (p.kind >> 8) & 0xff;
-    double k[NGF];
-#pragma unroll
-    for (int g = 0; g < NGF; g++) {
-        const double* f = yin + (long)g * G.T + idx;
-        double rad = p.w0 * osraw(f, 1, k0);
-        if constexpr (FAM == FAM_CYL) rad = fma(p.w2, osraw(f, s2, k2), rad);
-        k[g] = -ld(wspeed + g) * fma(ld(f) - ld(finf + g), p.invr, rad);
-    }
-    stage_store(st, G.T, idx, k, yn, out, acc);
+    outer_point_stage<FAM>(G, pts[t], yin, out, yn, acc, finf, wspeed, st);
 }
 
-__device__ __forceinline__ int gf_type(int g)
-{
-    if (g < 6) return 4 + g;
-    if (g < 12) return g - 2;
-    if (g == G_CF || g == G_TRK || g == G_ALPHA) return 0;
-    if (g < G_VET) return g - G_LAM + 1;
-    if (g < G_BET) return g - G_VET + 1;
-    return g - G_BET + 1;
-}
-
-// y[ghost] = p * y[source]; the sign is applied to the bit pattern (exact)
 __global__ void __launch_bounds__(256) k_inner(long T, const InnerPt* __restrict__ pts, int npts, double* y)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int g = blockIdx.y;
     if (t >= npts) return;
-    const InnerPt p = pts[t];
-    const long long sgn = (long long)((p.negmask >> gf_type(g)) & 1) << 63;
-    const double v = y[(long)g * T + p.src];
-    y[(long)g * T + p.dst] = __longlong_as_double(__double_as_longlong(v) ^ sgn);
+    inner_copy(T, pts[t], blockIdx.y, y);
 }
 
 // SplitMix64 (Steele, Lea & Flood 2014) first output for state x

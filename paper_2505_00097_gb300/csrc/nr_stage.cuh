@@ -1,0 +1,132 @@
+// nr_stage.cuh -- per-point bodies of the RK4-stage kernels, shared by the
+// single-grid kernels (nr_kernels.cu) and the batched persistent kernel
+// (nr_batch.cu) so that both run bit-identical arithmetic per point.
+#pragma once
+
+#include "bssn_point.cuh"
+#include "nr_geo.cuh"
+#include "nr_internal.h"
+
+namespace nrk {
+
+// det(delta_ij + h_ij) := 1 (Lagrangian choice of Sec. 2.1), in place, in
+// terms of the deviation h so that small h keeps its relative precision:
+// det(I + h) - 1 = tr h + (sum of principal 2x2 minors of h) + det h,
+// f1 = det^(-1/3) - 1 = expm1(-log1p(det - 1)/3), h <- h + f1 (delta + h).
+__device__ __forceinline__ void enforce_det(double* v)
+{
+    const double m2 = fma(v[0], v[3], fma(v[0], v[5], fma(v[3], v[5], -fma(v[1], v[1], fma(v[2], v[2], v[4] * v[4])))));
+    const double c0 = fma(v[3], v[5], -v[4] * v[4]);
+    const double c1 = fma(v[2], v[4], -v[1] * v[5]);
+    const double c2 = fma(v[1], v[4], -v[2] * v[3]);
+    const double d3 = fma(v[0], c0, fma(v[1], c1, v[2] * c2));
+    const double dm1 = (v[0] + v[3] + v[5]) + (m2 + d3);
+    const double f1 = expm1(log1p(dm1) * (-1.0 / 3.0));
+    v[0] = fma(f1, v[0], v[0] + f1);
+    v[1] = fma(f1, v[1], v[1]);
+    v[2] = fma(f1, v[2], v[2]);
+    v[3] = fma(f1, v[3], v[3] + f1);
+    v[4] = fma(f1, v[4], v[4]);
+    v[5] = fma(f1, v[5], v[5] + f1);
+}
+
+// RK4 stage epilogue for one point: k -> (y_next, acc) or the plain RHS.
+__device__ __forceinline__ void stage_store(const Stage& st, long T, long idx, const double k[NGF],
+                                            const double* __restrict__ yn, double* __restrict__ out,
+                                            double* __restrict__ acc)
+{
+    if (st.mode == MODE_RHS) {
+#pragma unroll
+        for (int g = 0; g < NGF; g++) out[g * T + idx] = k[g];
+        return;
+    }
+    double v[NGF];
+    if (st.mode == MODE_STAGE4) {
+#pragma unroll
+        for (int g = 0; g < NGF; g++) v[g] = fma(st.cacc, k[g], acc[g * T + idx]);
+    } else {
+#pragma unroll
+        for (int g = 0; g < NGF; g++) {
+            const double y0 = yn[g * T + idx];
+            v[g] = fma(st.cnext, k[g], y0);
+            acc[g * T + idx] = fma(st.cacc, k[g], st.mode == MODE_STAGE1 ? y0 : acc[g * T + idx]);
+        }
+    }
+    if (st.enforce) enforce_det(v);
+#pragma unroll
+    for (int g = 0; g < NGF; g++) out[g * T + idx] = v[g];
+}
+
+// one-sided / centred first-derivative stencil sums (weights of 12 h f')
+__device__ __forceinline__ double osraw(const double* f, long s, int kind)
+{
+    switch (kind) {
+    case 0: return fma(8.0, ld(f + s) - ld(f - s), ld(f - 2 * s) - ld(f + 2 * s));
+    case 1: return fma(3.0, ld(f + s), fma(10.0, ld(f), fma(-18.0, ld(f - s), fma(6.0, ld(f - 2 * s), -ld(f - 3 * s)))));
+    case 2: return fma(25.0, ld(f), fma(-48.0, ld(f - s), fma(36.0, ld(f - 2 * s), fma(-16.0, ld(f - 3 * s), 3.0 * ld(f - 4 * s)))));
+    case 3: return fma(-3.0, ld(f - s), fma(-10.0, ld(f), fma(18.0, ld(f + s), fma(-6.0, ld(f + 2 * s), ld(f + 3 * s)))));
+    default: return fma(-25.0, ld(f), fma(48.0, ld(f + s), fma(-36.0, ld(f + 2 * s), fma(16.0, ld(f + 3 * s), -3.0 * ld(f + 4 * s)))));
+    }
+}
+
+__device__ __forceinline__ int gf_type(int g)
+{
+    if (g < 6) return 4 + g;
+    if (g < 12) return g - 2;
+    if (g == G_CF || g == G_TRK || g == G_ALPHA) return 0;
+    if (g < G_VET) return g - G_LAM + 1;
+    if (g < G_BET) return g - G_VET + 1;
+    return g - G_BET + 1;
+}
+
+// one interior point (interior-relative i in [0,N0), j = i1 + N1 i2 in [0, N1 N2)) of an RK stage:
+// right-hand side, upwinded advection, dissipation and the stage epilogue
+template <int FAM>
+__device__ __forceinline__ void rhs_point_stage(const GridK& G, const double* __restrict__ yin, double* out,
+                                                const double* yn, double* acc, const Stage& st, int i, int j)
+{
+    const int p0 = i + G.NG, p1 = j % G.N1 + G.NG, p2 = j / G.N1 + G.NG;
+    const long idx = p0 + (long)G.n0 * (p1 + (long)G.n1 * p2);
+    PointIn P;
+    P.y = yin + idx;
+    P.T = G.T;
+    P.st[0] = 1;
+    P.st[1] = G.n0;
+    P.st[2] = (long)G.n0 * G.n1;
+    P.g = make_geo<FAM>(G, p0, p1, p2);
+    double k[NGF];
+    rhs_core<FAM>(P, G.eta, k);
+    add_adv_ko(P.y, G.T, P.st, P.g.D, G.sigma, k);
+    stage_store(st, G.T, idx, k, yn, out, acc);
+}
+
+// one pure-outer ghost point of an RK stage: radiation condition and the stage epilogue
+template <int FAM>
+__device__ __forceinline__ void outer_point_stage(const GridK& G, const OuterPt p, const double* __restrict__ yin,
+                                                  double* out, const double* yn, double* acc,
+                                                  const double* __restrict__ finf, const double* __restrict__ wspeed,
+                                                  const Stage& st)
+{
+    const long idx = p.idx;
+    const long s2 = (long)G.n0 * G.n1;
+    const int k0 = p.kind & 0xff, k2 = (p.kind >> 8) & 0xff;
+    double k[NGF];
+#pragma unroll
+    for (int g = 0; g < NGF; g++) {
+        const double* f = yin + (long)g * G.T + idx;
+        double rad = p.w0 * osraw(f, 1, k0);
+        if constexpr (FAM == FAM_CYL) rad = fma(p.w2, osraw(f, s2, k2), rad);
+        k[g] = -ld(wspeed + g) * fma(ld(f) - ld(finf + g), p.invr, rad);
+    }
+    stage_store(st, G.T, idx, k, yn, out, acc);
+}
+
+// y[ghost] = p * y[source] for gridfunction g; the sign is applied to the bit pattern (exact)
+__device__ __forceinline__ void inner_copy(long T, const InnerPt p, int g, double* y)
+{
+    const long long sgn = (long long)((p.negmask >> gf_type(g)) & 1) << 63;
+    const double v = y[(long)g * T + p.src];
+    y[(long)g * T + p.dst] = __longlong_as_double(__double_as_longlong(v) ^ sgn);
+}
+
+}  // namespace nrk

@@ -1,0 +1,117 @@
+"""Batched mode: many uneven grids advanced by one persistent launch per RK4 substage.
+
+Each grid's state after n batched steps must be bitwise the state after n
+single-grid steps (nr_rk4_step) from the same initial data -- for every tile
+shape the autotuner can pick and in any batch composition -- and therefore
+within the oracle tolerance of the single-grid path.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2505_00097_gb300 import binding as B  # noqa: E402
+from paper_2505_00097_gb300 import build as BUILD  # noqa: E402
+from paper_2505_00097_gb300 import workloads as W  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+TILES = [(32, 4), (64, 2), (128, 1), (16, 8), (32, 2), (64, 1), (32, 1)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    BUILD.build()
+    B.lib()
+
+
+def _cyl_runs():
+    runs = []
+    for k, (nr, m1, d) in enumerate([(12, 0.5, 1.0), (20, 0.7, 0.6), (33, 0.4, 1.5), (16, 0.8, 2.0)]):
+        s = W.sinh_cylindrical((nr, 2, 2 * nr + k), rho_max=30.0, z_max=30.0)
+        s.update(masses=(m1, 1 - m1), positions=((0, 0, d * (1 - m1)), (0, 0, -d * m1)))
+        runs.append(s)
+    return runs
+
+
+def _sph_runs():
+    runs = []
+    for k, N in enumerate([(20, 8, 2), (13, 6, 4), (30, 10, 2)]):
+        s = W.sinh_spherical(N)
+        s.update(masses=(1.0,), positions=((0, 0, 0.01 * k),), perturb=1e-8 * (k + 1))
+        runs.append(s)
+    return runs
+
+
+def _states(runs, nsteps, batched, tile=None, autotune=False):
+    grids = [B.Grid(s) for s in runs]
+    for g, s in zip(grids, runs):
+        g.set_brill_lindquist(s["masses"], s["positions"], s.get("perturb", 0.0), 7)
+    dts = [g.dt_cfl for g in grids]
+    chosen = None
+    if batched:
+        b = B.Batch(grids)
+        if tile:
+            b.set_tile(*tile)
+        if autotune:
+            chosen = b.autotune(dts)
+        b.rk4_step(dts, nsteps)
+    else:
+        for g, dt in zip(grids, dts):
+            g.rk4_step(dt, nsteps)
+    out = []
+    for g in grids:
+        st = np.empty(24 * g.T)
+        g.get_state(st, True)
+        out.append(st)
+    if batched:
+        b.close()
+    for g in grids:
+        g.close()
+    return out, chosen
+
+
+@pytest.mark.parametrize("tile", TILES, ids=[f"{a}x{b}" for a, b in TILES])
+def test_batched_cylindrical_bitwise_equals_single_grid(tile):
+    runs = _cyl_runs()
+    ref, _ = _states(runs, 6, batched=False)
+    got, _ = _states(runs, 6, batched=True, tile=tile)
+    for a, b in zip(got, ref):
+        assert np.all(np.isfinite(a))
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("tile", [(32, 4), (16, 8), (32, 1)], ids=["32x4", "16x8", "32x1"])
+def test_batched_spherical_bitwise_equals_single_grid(tile):
+    runs = _sph_runs()
+    ref, _ = _states(runs, 5, batched=False)
+    got, _ = _states(runs, 5, batched=True, tile=tile)
+    for a, b in zip(got, ref):
+        assert np.array_equal(a, b)
+
+
+def test_batch_membership_does_not_change_results():
+    runs = _cyl_runs()
+    alone, _ = _states(runs[1:2], 4, batched=True)
+    mixed, _ = _states(runs, 4, batched=True)
+    assert np.array_equal(alone[0], mixed[1])
+
+
+def test_autotune_picks_a_compiled_shape_and_keeps_results():
+    runs = _cyl_runs()
+    ref, _ = _states(runs, 3, batched=False)
+    got, chosen = _states(runs, 3, batched=True, autotune=True)
+    assert tuple(chosen[:2]) in TILES and chosen[2] > 0
+    for a, b in zip(got, ref):
+        assert np.array_equal(a, b)
+
+
+def test_mixed_families_rejected():
+    g1 = B.Grid(W.sinh_cylindrical((8, 2, 16), rho_max=10.0, z_max=10.0))
+    g2 = B.Grid(W.sinh_spherical((8, 4, 2)))
+    with pytest.raises(B.NrError):
+        B.Batch([g1, g2])
+    with pytest.raises(B.NrError):
+        B.Batch([g1, g1])

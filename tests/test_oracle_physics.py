@@ -446,3 +446,31 @@ def test_ko_keeps_rk4_stable_on_stretched_grid():
     o.rk4(y, o.dt(), 10)
     a1 = np.abs(y - flat)[m].max()
     assert np.isfinite(a1) and a1 < 10.0 * a0, (a0, a1)
+
+
+def test_gamma_driver_uses_d_perp_lambda():
+    """d_t B^i is driven by the right-hand side of Eq. Lambda_RHS_orig_final as printed,
+    d_perp Lambdabar^i, not by the full d_t Lambdabar^i = d_perp Lambdabar^i + L_beta Lambdabar^i.
+    Flat space, constant Cartesian shift (a Killing vector), B = 0 and a nonzero smooth Lambdabar:
+    every term of d_perp Lambdabar^i vanishes in the continuum, so d_t B^i -> 0 at 4th order, while
+    the full d_t Lambdabar^i would leave 3/4 L_beta Lambdabar^i = O(1)."""
+    b = np.array([0.11, -0.07, 0.05])
+    errs, lie = [], []
+    for N in [(16, 16, 16), (32, 32, 32), (64, 64, 64)]:
+        o = Oracle(W.sinh_spherical(N, ampl=12.0, w=0.3, ko_sigma=0.0))
+        y = _flat_state(o)
+        T = o.T
+        E = _frames(o)
+        x = o.cart()
+        v = _to_frame_vec(E, np.tile(b, (T, 1)))
+        lam_c = np.stack([0.1 * np.sin(0.3 * x[:, 1]), 0.05 * np.cos(0.2 * x[:, 2]), 0.08 * np.sin(0.25 * x[:, 0])], 1)
+        lam = _to_frame_vec(E, lam_c)
+        for d in range(3):
+            y[(17 + d) * T:(18 + d) * T] = v[d]
+            y[(14 + d) * T:(15 + d) * T] = lam[d]
+        r = o.rhs(y)
+        sel = _region(o, 2.0, 6.0)
+        errs.append(max(np.abs(r[(20 + d) * T:(21 + d) * T])[sel].max() for d in range(3)))
+        lie.append(max(np.abs(r[(14 + d) * T:(15 + d) * T])[sel].max() for d in range(3)))   # = L_b Lambdabar
+    assert min(lie) > 1e-3                                   # the Lie derivative itself is O(1)
+    assert _orders(errs)[-1] == pytest.approx(4.0, abs=0.6), errs
