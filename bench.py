@@ -59,7 +59,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["headon", "single_puncture", "large3d"], default="headon")
+    ap.add_argument("--workload", choices=["headon", "single_puncture", "large3d", "batch", "served"],
+                    default="headon")
+    ap.add_argument("--batch-runs", type=int, default=64)
+    ap.add_argument("--served-requests", type=int, default=24)
+    ap.add_argument("--served-tfinal", type=float, default=2.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -383,9 +387,182 @@ def run_ours(args, spec, world, rank, local):
     g.close()
 
 
+# ------------------------------------------------------- batched / served
+
+
+def run_batch(args, world, rank, local):
+    """64 uneven head-on runs (the batched workload): plain one-grid-at-a-time nr_rk4_step versus
+    one nr_batch (one persistent launch per substage for all grids, autotuned tile), same steps."""
+    import torch
+
+    from paper_2505_00097_gb300 import binding as B
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = dist_init(world, True)
+    runs = W.config_batch(n_runs=args.batch_runs, steps=args.steps)
+    grids = [B.Grid(s, device=local) for s in runs]
+    for g, s in zip(grids, runs):
+        g.set_brill_lindquist(s["masses"], s["positions"])
+    dts = [g.dt_cfl for g in grids]
+    pts = sum(g.interior for g in grids)
+    init = []
+    for g in grids:
+        t = torch.empty(24 * g.T, dtype=torch.float64, device=dev)
+        g.get_state(t, False)
+        init.append(t)
+
+    def reset():
+        for g, t in zip(grids, init):
+            g.set_state(t, False)
+
+    n = args.steps
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    for g, dt in zip(grids, dts):       # warm-up: graph capture of every grid
+        g.rk4_step(dt, 1)
+    reset()
+    torch.cuda.synchronize()
+    a0, a1 = ev(), ev()
+    a0.record()
+    for g, dt in zip(grids, dts):
+        g.rk4_step(dt, n)
+    a1.record()
+    torch.cuda.synchronize()
+    t_plain = a0.elapsed_time(a1) * 1e-3
+    plain_final = []
+    for g in grids:
+        t = torch.empty(24 * g.T, dtype=torch.float64, device=dev)
+        g.get_state(t, False)
+        plain_final.append(t)
+    reset()
+    batch = B.Batch(grids)
+    tx, ty, tune_ms = batch.autotune(dts)
+    batch.rk4_step(dts, 1)              # warm-up: graph capture
+    reset()
+    clocks = ClockSampler(None)
+    torch.cuda.synchronize()
+    clocks.start()
+    b0, b1 = ev(), ev()
+    b0.record()
+    batch.rk4_step(dts, n)
+    b1.record()
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    t_batch = b0.elapsed_time(b1) * 1e-3
+    same = True
+    for g, ref in zip(grids, plain_final):
+        t = torch.empty(24 * g.T, dtype=torch.float64, device=dev)
+        g.get_state(t, False)
+        same = same and bool(torch.equal(t, ref))
+    t_batch = reduce_max(dist, t_batch, dev)
+    t_plain = reduce_max(dist, t_plain, dev)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": world * pts * 4 * n / t_batch, "unit": UNIT, "n_gpus": world, "steps": n,
+            "warmup": 1, "ms_per_step": 1e3 * t_batch / n, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (Brill-Lindquist head-on binaries, seeded)",
+            "config": {"workload": f"batch_{len(runs)}_headon_sinhcyl", "runs": len(runs), "interior_points": pts,
+                       "grid_sizes_rho": sorted({s["N"][0] for s in runs}), "steps_per_run": n,
+                       "tile": f"{tx}x{ty}", "autotune_stage_ms": tune_ms},
+            "plain": {"value": world * pts * 4 * n / t_plain, "unit": UNIT,
+                      "mode": "one grid at a time, nr_rk4_step graph per grid"},
+            "speedup_vs_plain": t_plain / t_batch, "bitwise_equal_to_plain": same, "clocks": ck,
+        }
+        print(json.dumps(line), flush=True)
+    batch.close()
+    for g in grids:
+        g.close()
+
+
+def run_served(args, world, rank, local):
+    """The served workload: a seeded Poisson stream (mean 20 requests per minute) of single-puncture and
+    head-on requests of 1e5..4e6 points, admitted under an 80 GB budget and advanced by continuous
+    batching, versus the same stream served by a FIFO queue of single-grid runs."""
+    import torch
+
+    from paper_2505_00097_gb300 import binding as B
+
+    torch.cuda.set_device(local)
+    reqs = W.config_served(n_requests=args.served_requests, t_final=args.served_tfinal)
+    pts_of = {}
+
+    def serve(batched: bool):
+        start = time.perf_counter()
+        done, arrive, submitted = {}, {}, []
+        upd = 0.0
+        if batched:
+            srv = B.Server(80 * 10 ** 9, 64, device=local)
+            srv.set_tile(32, 4)
+        queue = []
+        nxt = 0
+        while len(done) < len(reqs):
+            now = time.perf_counter() - start
+            while nxt < len(reqs) and reqs[nxt]["arrival_s"] <= now:
+                r = reqs[nxt]
+                if batched:
+                    rid = srv.submit(r, r["t_final"])
+                    submitted.append((rid, nxt))
+                else:
+                    queue.append(nxt)
+                arrive[nxt] = reqs[nxt]["arrival_s"]
+                nxt += 1
+            if batched:
+                nrun, nq = srv.advance(20)
+                for rid, k in submitted:
+                    if k in done:
+                        continue
+                    info = srv.poll(rid)
+                    if info["status"] in (2, 3):
+                        done[k] = time.perf_counter() - start
+                        n = reqs[k]["N"]
+                        upd += 4.0 * info["steps_done"] * n[0] * n[1] * n[2]
+                idle = nrun == 0 and nq == 0
+            else:
+                idle = not queue
+                if queue:
+                    k = queue.pop(0)
+                    g = B.Grid(reqs[k], device=local)
+                    g.set_brill_lindquist(reqs[k]["masses"], reqs[k]["positions"])
+                    steps = max(1, int(math.ceil(reqs[k]["t_final"] / g.dt_cfl - 1e-9)))
+                    g.rk4_step(g.dt_cfl, steps)
+                    g.hamiltonian()
+                    g.close()
+                    done[k] = time.perf_counter() - start
+                    upd += 4.0 * steps * g.interior
+            if idle and nxt < len(reqs):
+                time.sleep(max(0.0, min(0.05, reqs[nxt]["arrival_s"] - (time.perf_counter() - start))))
+        makespan = time.perf_counter() - start
+        if batched:
+            srv.close()
+        ttc = sorted(done[k] - arrive[k] for k in done)
+        q = lambda p: ttc[min(len(ttc) - 1, int(round(p * (len(ttc) - 1))))]  # noqa: E731
+        return {"value": upd / makespan, "p50_ttc_s": q(0.5), "p99_ttc_s": q(0.99), "makespan_s": makespan}
+
+    served = serve(True)
+    plain = serve(False)
+    line = {
+        "metric": METRIC, "value": served["value"], "unit": UNIT, "n_gpus": 1, "steps": None, "warmup": 0,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded Poisson request stream)",
+        "config": {"workload": f"served_{len(reqs)}_requests", "rate_per_min": 20, "t_final": args.served_tfinal,
+                   "points_range": [1e5, 4e6], "hbm_budget_gb": 80},
+        "served": served, "plain_fifo": plain, "speedup_vs_plain": served["value"] / plain["value"],
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local = dist_env()
+    if args.workload == "batch":
+        if args.steps == 2000:
+            args.steps = 100
+        run_batch(args, world, rank, local)
+        return
+    if args.workload == "served":
+        if rank == 0:
+            run_served(args, world, rank, local)
+        return
     spec = workload(args.workload)
     if args.impl == "reference":
         if rank != 0:

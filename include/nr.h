@@ -206,6 +206,39 @@ int nr_batch_set_tile(nr_batch* batch, int tile_x, int tile_y);
 int nr_batch_autotune(nr_batch* batch, const double* dts, int* tile_x, int* tile_y, double* best_ms);
 int nr_batch_rk4_step(nr_batch* batch, const double* dts, int nsteps);
 
+/* Served mode: continuous batching of evolution requests on one device.
+ * A request is one grid (coords, Nxx, params) with Brill-Lindquist data
+ * (npunct masses at xyz) evolved by RK4 at its own CFL step until t_final.
+ *   nr_server_create: hbm_budget_bytes caps the summed device bytes of the
+ *     running requests; max_slots caps their number; work is issued on stream.
+ *   nr_server_submit: queues a request and returns its id (no device work).
+ *     keep_state = 1 keeps the final 24-gf state on the host for
+ *     nr_server_fetch_state.
+ *   nr_server_advance: admits queued requests in arrival order while the
+ *     budget and the slots allow, then advances all running requests
+ *     together -- one nr_batch, one persistent launch per RK4 substage for all
+ *     of them -- by up to nsteps steps.  Membership changes only at step
+ *     boundaries: a request reaching t_final is retired (Hamiltonian-
+ *     constraint norms recorded, state kept if asked, device memory released)
+ *     and queued requests are admitted into the freed budget.  A request that
+ *     cannot fit even alone is marked failed.  Synchronises at retirements.
+ *   nr_server_poll: status 0 queued, 1 running, 2 done, 3 failed; steps done
+ *     and total; the final L2/Linf Hamiltonian-constraint norms when done.
+ *   nr_server_set_tile: fixed tile shape for the batches (default: autotune at
+ *     every membership change).
+ * Each request's result is bitwise what running it alone with nr_rk4_step
+ * gives, whichever requests shared the GPU with it. */
+typedef struct nr_server nr_server;
+int nr_server_create(size_t hbm_budget_bytes, int max_slots, int device, void* stream, nr_server** out);
+void nr_server_destroy(nr_server* server);
+int nr_server_set_tile(nr_server* server, int tile_x, int tile_y);
+int nr_server_submit(nr_server* server, int coords, const int Nxx[3], const nr_params* params, int npunct,
+                     const double* mass, const double* xyz, double t_final, int keep_state, int64_t* id_out);
+int nr_server_advance(nr_server* server, int nsteps, int* n_running, int* n_queued);
+int nr_server_poll(nr_server* server, int64_t id, int* status, int64_t* steps_done, int64_t* steps_total,
+                   double* l2, double* linf);
+int nr_server_fetch_state(nr_server* server, int64_t id, double* host_state, size_t capacity_doubles);
+
 /* Hamiltonian constraint that allocates nothing.  The paper has no
  * counterpart: this is a library service for callers that cannot call
  * cudaMalloc -- a host framework that owns all device memory through its own

@@ -26,7 +26,8 @@ EXPORTS = (
     "nr_apply_bcs", "nr_apply_inner_bcs", "nr_rk4_step", "nr_hamiltonian", "nr_get_state", "nr_set_state",
     "nr_sync", "nr_check_finite", "nr_build_maps", "nr_dt_cfl", "nr_fp64_peak", "nr_hamiltonian_noalloc",
     "nr_batch_create", "nr_batch_destroy", "nr_batch_set_tile", "nr_batch_autotune", "nr_batch_rk4_step",
-    "nr_last_error",
+    "nr_server_create", "nr_server_destroy", "nr_server_set_tile", "nr_server_submit", "nr_server_advance",
+    "nr_server_poll", "nr_server_fetch_state", "nr_last_error",
 )
 
 
@@ -112,6 +113,16 @@ def lib() -> ctypes.CDLL:
     L.nr_batch_set_tile.argtypes = [vp, ctypes.c_int, ctypes.c_int]
     L.nr_batch_autotune.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), dp]
     L.nr_batch_rk4_step.argtypes = [vp, dp, ctypes.c_int]
+    L.nr_server_create.argtypes = [ctypes.c_size_t, ctypes.c_int, ctypes.c_int, vp, ctypes.POINTER(vp)]
+    L.nr_server_destroy.argtypes = [vp]
+    L.nr_server_destroy.restype = None
+    L.nr_server_set_tile.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+    L.nr_server_submit.argtypes = [vp, ctypes.c_int, ip, P, ctypes.c_int, dp, dp, ctypes.c_double, ctypes.c_int,
+                                   ctypes.POINTER(ctypes.c_int64)]
+    L.nr_server_advance.argtypes = [vp, ctypes.c_int, ip, ip]
+    L.nr_server_poll.argtypes = [vp, ctypes.c_int64, ip, ctypes.POINTER(ctypes.c_int64),
+                                 ctypes.POINTER(ctypes.c_int64), dp, dp]
+    L.nr_server_fetch_state.argtypes = [vp, ctypes.c_int64, dp, ctypes.c_size_t]
     L.nr_last_error.argtypes = []
     L.nr_last_error.restype = ctypes.c_char_p
     _lib = L
@@ -308,3 +319,58 @@ class Batch:
     def rk4_step(self, dts, nsteps: int = 1) -> None:
         a = self._dts(dts)
         _check(lib().nr_batch_rk4_step(self.h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(nsteps)))
+
+
+class Server:
+    """nr_server: continuous batching of evolution requests on one device."""
+
+    def __init__(self, hbm_budget_bytes: int, max_slots: int, device: int = 0, stream=None):
+        h = ctypes.c_void_p()
+        _check(lib().nr_server_create(int(hbm_budget_bytes), int(max_slots), int(device), stream, ctypes.byref(h)))
+        self.h = h
+        self.device = device
+
+    def close(self) -> None:
+        if self.h:
+            lib().nr_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_tile(self, tx: int, ty: int) -> None:
+        _check(lib().nr_server_set_tile(self.h, int(tx), int(ty)))
+
+    def submit(self, spec: dict, t_final: float, keep_state: bool = False) -> int:
+        p = make_params(spec, device=self.device)
+        Nx = (ctypes.c_int * 3)(*[int(v) for v in spec["N"]])
+        m = np.ascontiguousarray(spec["masses"], dtype=np.float64)
+        x = np.ascontiguousarray(spec["positions"], dtype=np.float64).reshape(-1)
+        rid = ctypes.c_int64()
+        _check(lib().nr_server_submit(self.h, int(spec["coords"]), Nx, ctypes.byref(p), len(m),
+                                      m.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                      x.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(t_final),
+                                      int(bool(keep_state)), ctypes.byref(rid)))
+        return rid.value
+
+    def advance(self, nsteps: int):
+        nr, nq = ctypes.c_int(), ctypes.c_int()
+        _check(lib().nr_server_advance(self.h, int(nsteps), ctypes.byref(nr), ctypes.byref(nq)))
+        return nr.value, nq.value
+
+    def poll(self, rid: int) -> dict:
+        st, sd, stt = ctypes.c_int(), ctypes.c_int64(), ctypes.c_int64()
+        l2, linf = ctypes.c_double(), ctypes.c_double()
+        _check(lib().nr_server_poll(self.h, int(rid), ctypes.byref(st), ctypes.byref(sd), ctypes.byref(stt),
+                                    ctypes.byref(l2), ctypes.byref(linf)))
+        return {"status": st.value, "steps_done": sd.value, "steps_total": stt.value, "l2": l2.value,
+                "linf": linf.value}
+
+    def fetch_state(self, rid: int, size: int) -> np.ndarray:
+        out = np.empty(size)
+        _check(lib().nr_server_fetch_state(self.h, int(rid), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                           size))
+        return out

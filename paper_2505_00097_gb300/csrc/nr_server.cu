@@ -1,0 +1,292 @@
+// nr_server.cu -- served mode: continuous batching of evolution requests.
+//
+// Requests (one grid + Brill-Lindquist data + a final time each) are queued
+// by nr_server_submit.  nr_server_advance admits queued requests in arrival
+// order while the summed device bytes stay within the HBM budget and a slot
+// is free, then advances every running request together as one nr_batch
+// (one persistent launch per RK4 substage for all of them).  Membership
+// changes only at step boundaries: a request that reaches its final time is
+// retired (its Hamiltonian-constraint norms recorded, optionally its final
+// state copied to the host, its device memory released) and the freed budget
+// admits the next queued requests.  Each request advances with its own CFL
+// step; since every point runs the single-grid arithmetic, a request's result
+// does not depend on which other requests shared the GPU with it.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <deque>
+#include <map>
+#include <vector>
+
+#include "nr_internal.h"
+
+using nrk::nrk_fail;
+
+namespace {
+
+struct Request {
+    int64_t id = 0;
+    int coords = 0;
+    int N[3] = {0, 0, 0};
+    nr_params P{};
+    int np = 0;
+    double mass[16] = {0};
+    double xyz[48] = {0};
+    double t_final = 0.0;
+    int keep_state = 0;
+    size_t bytes = 0;
+    // progress
+    int status = 0;          // 0 queued, 1 running, 2 done, 3 failed
+    nr_grid* grid = nullptr;
+    double dt = 0.0;
+    int64_t steps_total = 0, steps_done = 0;
+    double l2 = 0.0, linf = 0.0;
+    std::vector<double> state;
+};
+
+size_t grid_bytes_estimate(const int N[3])
+{
+    const size_t T = (size_t)(N[0] + 6) * (N[1] + 6) * (N[2] + 6);
+    // four 24-gridfunction sets + maps/lists (generous per-point allowance)
+    return T * (4 * 24 * sizeof(double) + 64);
+}
+
+}  // namespace
+
+struct nr_server {
+    size_t budget = 0;
+    int max_slots = 0;
+    int device = 0;
+    void* stream = nullptr;
+    int64_t next_id = 1;
+    std::deque<Request*> queue;
+    std::vector<Request*> running;
+    std::map<int64_t, Request*> all;
+    nr_batch* batch = nullptr;
+    bool batch_dirty = true;
+    size_t used = 0;
+    int tile_x = 0, tile_y = 0;   // 0: autotune on every rebuild
+};
+
+namespace {
+
+void drop_batch(nr_server* s)
+{
+    if (s->batch) nr_batch_destroy(s->batch);
+    s->batch = nullptr;
+    s->batch_dirty = true;
+}
+
+int start_request(nr_server* s, Request* r)
+{
+    nr_params P = r->P;
+    P.device = s->device;
+    P.stream = s->stream;
+    int rc = nr_grid_create(r->coords, r->N, &P, &r->grid);
+    if (rc) return rc;
+    rc = nr_set_brill_lindquist(r->grid, r->np, r->mass, r->xyz, 0.0, 0);
+    if (rc) {
+        nr_grid_destroy(r->grid);
+        r->grid = nullptr;
+        return rc;
+    }
+    r->dt = r->grid->dt_cfl;
+    r->steps_total = (int64_t)ceil(r->t_final / r->dt - 1e-9);
+    if (r->steps_total < 1) r->steps_total = 1;
+    r->steps_done = 0;
+    r->status = 1;
+    return NR_OK;
+}
+
+int finish_request(nr_server* s, Request* r)
+{
+    int rc = nr_hamiltonian(r->grid, nullptr, nullptr, &r->l2, &r->linf);
+    if (rc == NR_OK && r->keep_state) {
+        r->state.resize((size_t)NR_NGF * r->grid->geo.T);
+        rc = nr_get_state(r->grid, r->state.data(), 1);
+    }
+    if (rc == NR_OK && nr_check_finite(r->grid) != NR_OK) rc = NR_ENONFINITE;
+    r->status = rc == NR_OK ? 2 : 3;
+    nr_grid_destroy(r->grid);
+    r->grid = nullptr;
+    s->used -= std::min(s->used, r->bytes);
+    return NR_OK;
+}
+
+// admit queued requests in arrival order while budget and slots allow
+int admit(nr_server* s)
+{
+    while (!s->queue.empty()) {
+        Request* r = s->queue.front();
+        if ((int)s->running.size() >= s->max_slots) break;
+        if (s->used + r->bytes > s->budget) {
+            if (s->running.empty())  // can never fit
+            {
+                r->status = 3;
+                s->queue.pop_front();
+                continue;
+            }
+            break;
+        }
+        s->queue.pop_front();
+        if (start_request(s, r) != NR_OK) {
+            r->status = 3;
+            continue;
+        }
+        s->used += r->bytes;
+        s->running.push_back(r);
+        s->batch_dirty = true;
+    }
+    return NR_OK;
+}
+
+int rebuild_batch(nr_server* s)
+{
+    drop_batch(s);
+    if (s->running.empty()) return NR_OK;
+    std::vector<nr_grid*> g;
+    std::vector<double> dts;
+    for (Request* r : s->running) {
+        g.push_back(r->grid);
+        dts.push_back(r->dt);
+    }
+    int rc = nr_batch_create(g.data(), (int)g.size(), &s->batch);
+    if (rc) return rc;
+    if (s->tile_x > 0)
+        rc = nr_batch_set_tile(s->batch, s->tile_x, s->tile_y);
+    else
+        rc = nr_batch_autotune(s->batch, dts.data(), nullptr, nullptr, nullptr);
+    if (rc) return rc;
+    s->batch_dirty = false;
+    return NR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int nr_server_create(size_t hbm_budget_bytes, int max_slots, int device, void* stream, nr_server** out)
+{
+    if (!out || max_slots < 1 || hbm_budget_bytes == 0) return nrk_fail(NR_EINVAL, "bad nr_server_create arguments");
+    nr_server* s = new nr_server();
+    s->budget = hbm_budget_bytes;
+    s->max_slots = max_slots;
+    s->device = device;
+    s->stream = stream;
+    *out = s;
+    return NR_OK;
+}
+
+void nr_server_destroy(nr_server* s)
+{
+    if (!s) return;
+    drop_batch(s);
+    for (auto& kv : s->all) {
+        if (kv.second->grid) nr_grid_destroy(kv.second->grid);
+        delete kv.second;
+    }
+    delete s;
+}
+
+int nr_server_set_tile(nr_server* s, int tile_x, int tile_y)
+{
+    if (!s) return nrk_fail(NR_EINVAL, "server is NULL");
+    s->tile_x = tile_x;
+    s->tile_y = tile_y;
+    s->batch_dirty = true;
+    return NR_OK;
+}
+
+int nr_server_submit(nr_server* s, int coords, const int Nxx[3], const nr_params* params, int npunct,
+                     const double* mass, const double* xyz, double t_final, int keep_state, int64_t* id_out)
+{
+    if (!s || !Nxx || !params || npunct < 0 || npunct > 16 || (npunct && (!mass || !xyz)) || !(t_final > 0.0))
+        return nrk_fail(NR_EINVAL, "bad nr_server_submit arguments");
+    if (s->running.size() + s->queue.size() > 0 && s->all.size() > 1000000)
+        return nrk_fail(NR_EINVAL, "too many requests");
+    Request* r = new Request();
+    r->id = s->next_id++;
+    r->coords = coords;
+    memcpy(r->N, Nxx, sizeof r->N);
+    r->P = *params;
+    r->np = npunct;
+    for (int q = 0; q < npunct; q++) {
+        r->mass[q] = mass[q];
+        for (int d = 0; d < 3; d++) r->xyz[3 * q + d] = xyz[3 * q + d];
+    }
+    r->t_final = t_final;
+    r->keep_state = keep_state;
+    r->bytes = grid_bytes_estimate(Nxx);
+    s->queue.push_back(r);
+    s->all[r->id] = r;
+    if (id_out) *id_out = r->id;
+    return NR_OK;
+}
+
+int nr_server_advance(nr_server* s, int nsteps, int* n_running, int* n_queued)
+{
+    if (!s || nsteps < 0) return nrk_fail(NR_EINVAL, "bad nr_server_advance arguments");
+    int rc = admit(s);
+    int left = nsteps;
+    while (left > 0 && !s->running.empty()) {
+        if (s->batch_dirty && (rc = rebuild_batch(s))) return rc;
+        int64_t k = left;
+        for (Request* r : s->running) k = std::min(k, r->steps_total - r->steps_done);
+        std::vector<double> dts;
+        for (Request* r : s->running) dts.push_back(r->dt);
+        if ((rc = nr_batch_rk4_step(s->batch, dts.data(), (int)k))) return rc;
+        left -= (int)k;
+        bool retired = false;
+        for (Request* r : s->running) r->steps_done += k;
+        for (size_t q = 0; q < s->running.size();) {
+            Request* r = s->running[q];
+            if (r->steps_done >= r->steps_total) {
+                if (!retired) {
+                    drop_batch(s);  // the batch refers to the grids about to be released
+                    retired = true;
+                }
+                finish_request(s, r);
+                s->running.erase(s->running.begin() + q);
+            } else {
+                q++;
+            }
+        }
+        if (retired) {
+            s->batch_dirty = true;
+            admit(s);
+        }
+    }
+    if (n_running) *n_running = (int)s->running.size();
+    if (n_queued) *n_queued = (int)s->queue.size();
+    return NR_OK;
+}
+
+int nr_server_poll(nr_server* s, int64_t id, int* status, int64_t* steps_done, int64_t* steps_total, double* l2,
+                   double* linf)
+{
+    if (!s) return nrk_fail(NR_EINVAL, "server is NULL");
+    auto it = s->all.find(id);
+    if (it == s->all.end()) return nrk_fail(NR_EINVAL, "unknown request %lld", (long long)id);
+    const Request* r = it->second;
+    if (status) *status = r->status;
+    if (steps_done) *steps_done = r->steps_done;
+    if (steps_total) *steps_total = r->steps_total;
+    if (l2) *l2 = r->l2;
+    if (linf) *linf = r->linf;
+    return NR_OK;
+}
+
+int nr_server_fetch_state(nr_server* s, int64_t id, double* host_state, size_t capacity_doubles)
+{
+    if (!s || !host_state) return nrk_fail(NR_EINVAL, "bad nr_server_fetch_state arguments");
+    auto it = s->all.find(id);
+    if (it == s->all.end()) return nrk_fail(NR_EINVAL, "unknown request %lld", (long long)id);
+    Request* r = it->second;
+    if (r->status != 2 || r->state.empty()) return nrk_fail(NR_EINVAL, "request %lld has no kept state", (long long)id);
+    if (capacity_doubles < r->state.size()) return nrk_fail(NR_EINVAL, "buffer too small");
+    memcpy(host_state, r->state.data(), sizeof(double) * r->state.size());
+    return NR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,93 @@
+"""Served mode: continuous batching of evolution requests (nr_server_*).
+
+Requests that arrive while others are running are admitted at step
+boundaries as the HBM budget and slots allow; all running requests advance
+together in one batch.  Each result must be bitwise what the same request
+gives run alone with nr_rk4_step, whatever shared the GPU with it.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2505_00097_gb300 import binding as B  # noqa: E402
+from paper_2505_00097_gb300 import build as BUILD  # noqa: E402
+from paper_2505_00097_gb300 import workloads as W  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    BUILD.build()
+    B.lib()
+
+
+def _requests():
+    reqs = []
+    for k, (nr, masses, pos) in enumerate([
+        (12, (1.0,), ((0, 0, 0),)),
+        (20, (0.6, 0.4), ((0, 0, 0.4), (0, 0, -0.6))),
+        (16, (0.8,), ((0, 0, 0),)),
+        (24, (0.5, 0.5), ((0, 0, 0.5), (0, 0, -0.5))),
+    ]):
+        s = W.sinh_cylindrical((nr, 2, 2 * nr), rho_max=30.0, z_max=30.0)
+        s.update(masses=masses, positions=pos)
+        reqs.append(s)
+    return reqs
+
+
+def _alone(spec, t_final):
+    g = B.Grid(spec)
+    g.set_brill_lindquist(spec["masses"], spec["positions"])
+    n = max(1, int(np.ceil(t_final / g.dt_cfl - 1e-9)))
+    g.rk4_step(g.dt_cfl, n)
+    st = np.empty(24 * g.T)
+    g.get_state(st, True)
+    T = g.T
+    g.close()
+    return st, n, T
+
+
+@pytest.mark.parametrize("budget_gb,slots", [(80, 8), (80, 1)], ids=["mixed", "one-slot"])
+def test_results_equal_alone_and_in_the_mix(budget_gb, slots):
+    reqs = _requests()
+    t_final = 0.8
+    srv = B.Server(int(budget_gb * 2 ** 30), slots)
+    srv.set_tile(32, 4)
+    ids = [srv.submit(reqs[0], t_final, keep_state=True), srv.submit(reqs[1], t_final, keep_state=True)]
+    srv.advance(3)                      # the first two start; the others arrive while they run
+    ids += [srv.submit(reqs[2], t_final, keep_state=True), srv.submit(reqs[3], t_final, keep_state=True)]
+    for _ in range(1000):
+        nrun, nq = srv.advance(5)
+        if nrun == 0 and nq == 0:
+            break
+    for rid, spec in zip(ids, reqs):
+        info = srv.poll(rid)
+        assert info["status"] == 2, info
+        ref, n, T = _alone(spec, t_final)
+        assert info["steps_done"] == n == info["steps_total"]
+        got = srv.fetch_state(rid, 24 * T)
+        assert np.array_equal(got, ref)
+        assert np.isfinite(info["l2"]) and info["linf"] > 0.0
+    srv.close()
+
+
+def test_autotuned_server_and_oversized_request():
+    reqs = _requests()
+    srv = B.Server(int(0.05 * 2 ** 30), 4)   # 51 MiB: the small grids fit, a 1024x2x2048 grid never does
+    big = W.sinh_cylindrical((1024, 2, 2048))
+    big.update(masses=(1.0,), positions=((0, 0, 0),))
+    rid_big = srv.submit(big, 0.5)
+    rid = srv.submit(reqs[0], 0.5, keep_state=True)
+    for _ in range(1000):
+        nrun, nq = srv.advance(10)
+        if nrun == 0 and nq == 0:
+            break
+    assert srv.poll(rid_big)["status"] == 3
+    assert srv.poll(rid)["status"] == 2
+    ref, n, T = _alone(reqs[0], 0.5)
+    assert np.array_equal(srv.fetch_state(rid, 24 * T), ref)
+    srv.close()
