@@ -40,11 +40,13 @@ from paper_2505_00097_gb300 import workloads as W  # noqa: E402
 METRIC = "BSSN FP64 point-updates/s (RK4 substeps)"
 UNIT = "point-updates/s"
 
-# FP64 operations (FMA = 2) per interior point of one k_rhs launch, counted
-# from the kernel's DADD/DMUL/DFMA thread-instruction counts in one ncu
-# capture of the head-on 256x2x512 workload (profiles/k_rhs_headon_256x2x512.md):
-# (DADD + DMUL + 2 DFMA) / interior points.
-F_ALG = 5102.0
+# FP64 operations (FMA = 2) per interior point of one k_rhs launch, by
+# workload (the kernel variant it runs), counted from the kernel's
+# DADD/DMUL/DFMA thread-instruction counts in one ncu capture:
+# (DADD + DMUL + 2 DFMA) / interior points.  Head-on 256x2x512
+# (k_rhs<cylindrical, two-point azimuth>, profiles/k_rhs_headon_256x2x512.md):
+# 417 + 372 + 2 x 1295.  A workload without a capture reports no FLOP rate.
+F_ALG = {"headon": 3379.0}
 # FP64 pipe of one SM: 2 DFMA per clock (ncu peak_sustained of
 # sm__sass_thread_inst_executed_op_dfma_pred_on), i.e. 4 FLOP per clock
 FP64_FLOP_PER_CLK_SM = 4.0
@@ -64,6 +66,9 @@ def parse():
     ap.add_argument("--batch-runs", type=int, default=64)
     ap.add_argument("--served-requests", type=int, default=24)
     ap.add_argument("--served-tfinal", type=float, default=2.0)
+    ap.add_argument("--served-policy", choices=("srpt", "fifo"), default="srpt")
+    ap.add_argument("--served-cap", type=int, default=1000000,
+                    help="interior points advanced together by the served arm (0: no cap)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -338,9 +343,10 @@ def run_ours(args, spec, world, rank, local):
             "peak": peak / 1e12,
             "peak_source": f"derived: 2 DFMA/clk/SM x {n_sm} SMs x {mhz:.0f} MHz (median SM clock in the timed region)",
             "probe_tflops": probe / 1e12, "launch_ms": rhs_ms, "points_per_launch": pts, "traffic": None}
-    if F_ALG:
-        ach = F_ALG * pts / (rhs_ms * 1e-3)
-        roof.update(achieved=ach / 1e12, frac=ach / peak, flops_per_point=F_ALG)
+    f_alg = F_ALG.get(args.workload)
+    if f_alg:
+        ach = f_alg * pts / (rhs_ms * 1e-3)
+        roof.update(achieved=ach / 1e12, frac=ach / peak, flops_per_point=f_alg)
     else:
         roof.update(achieved=None, frac=None, flops_per_point=None)
 
@@ -474,10 +480,15 @@ def run_batch(args, world, rank, local):
         g.close()
 
 
+def other_name(policy: str) -> str:
+    return "fifo" if policy == "srpt" else "srpt"
+
+
 def run_served(args, world, rank, local):
     """The served workload: a seeded Poisson stream (mean 20 requests per minute) of single-puncture and
     head-on requests of 1e5..4e6 points, admitted under an 80 GB budget and advanced by continuous
-    batching, versus the same stream served by a FIFO queue of single-grid runs."""
+    batching under the chosen policy (and under the other one), versus the same stream served by a FIFO
+    queue of single-grid runs."""
     import torch
 
     from paper_2505_00097_gb300 import binding as B
@@ -486,13 +497,17 @@ def run_served(args, world, rank, local):
     reqs = W.config_served(n_requests=args.served_requests, t_final=args.served_tfinal)
     pts_of = {}
 
-    def serve(batched: bool):
+    def serve(mode: str):
+        """mode "srpt" / "fifo": nr_server with that policy and the points cap; "plain": a FIFO queue of
+        single-grid runs, one at a time."""
+        batched = mode != "plain"
         start = time.perf_counter()
         done, arrive, submitted = {}, {}, []
         upd = 0.0
         if batched:
             srv = B.Server(80 * 10 ** 9, 64, device=local)
             srv.set_tile(32, 4)
+            srv.set_policy(mode, args.served_cap)
         queue = []
         nxt = 0
         while len(done) < len(reqs):
@@ -507,7 +522,7 @@ def run_served(args, world, rank, local):
                 arrive[nxt] = reqs[nxt]["arrival_s"]
                 nxt += 1
             if batched:
-                nrun, nq = srv.advance(20)
+                nrun, nq = srv.advance(5)
                 for rid, k in submitted:
                     if k in done:
                         continue
@@ -536,17 +551,22 @@ def run_served(args, world, rank, local):
             srv.close()
         ttc = sorted(done[k] - arrive[k] for k in done)
         q = lambda p: ttc[min(len(ttc) - 1, int(round(p * (len(ttc) - 1))))]  # noqa: E731
-        return {"value": upd / makespan, "p50_ttc_s": q(0.5), "p99_ttc_s": q(0.99), "makespan_s": makespan}
+        return {"value": upd / makespan, "p50_ttc_s": q(0.5), "p99_ttc_s": q(0.99),
+                "mean_ttc_s": sum(ttc) / len(ttc), "makespan_s": makespan}
 
-    served = serve(True)
-    plain = serve(False)
+    served = serve(args.served_policy)
+    other = serve(other_name(args.served_policy))
+    plain = serve("plain")
     line = {
         "metric": METRIC, "value": served["value"], "unit": UNIT, "n_gpus": 1, "steps": None, "warmup": 0,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded Poisson request stream)",
         "config": {"workload": f"served_{len(reqs)}_requests", "rate_per_min": 20, "t_final": args.served_tfinal,
-                   "points_range": [1e5, 4e6], "hbm_budget_gb": 80},
-        "served": served, "plain_fifo": plain, "speedup_vs_plain": served["value"] / plain["value"],
+                   "points_range": [1e5, 4e6], "hbm_budget_gb": 80, "policy": args.served_policy,
+                   "max_batch_points": args.served_cap},
+        "served": served, f"served_{other_name(args.served_policy)}": other, "plain_fifo": plain,
+        "speedup_vs_plain": served["value"] / plain["value"],
+        "p50_ttc_vs_plain": served["p50_ttc_s"] / plain["p50_ttc_s"],
     }
     print(json.dumps(line), flush=True)
 

@@ -64,7 +64,10 @@ enum { NR_NGF = 24 };
  *     Spherical:     r = ampl[0] xx0.
  *     SinhCylindrical: rho from xx0 in [0,1] with ampl[0], sinhw[0];
  *                    phi = xx1 in [-pi,pi]; z from xx2 in [-1,1] with ampl[2], sinhw[2].
- *   ko_sigma: Kreiss-Oliger strength per gridfunction (Sec. 4.1).
+ *   ko_sigma: Kreiss-Oliger strength per gridfunction (Sec. 4.1); it must take
+ *     one value on the 17 metric gridfunctions 0-16 (hDD, aDD, cf, trK,
+ *     lambdaU) and one on the 7 gauge gridfunctions 17-23 (vetU, betU, alpha),
+ *     as in the paper's runs (0.3 metric / 0.99 gauge); NR_EINVAL otherwise.
  *   eta: Gamma-driver damping; cfl: CFL factor.
  *   wavespeed, f_inf: radiation condition d_t f = -v [(x^j/r) d_j f + (f - f_inf)/r].
  *   h_rmin, h_rmax: radius band of the Hamiltonian-constraint norms.
@@ -127,7 +130,10 @@ int nr_set_brill_lindquist(nr_grid* grid, int npunct, const double* mass, const 
 
 /* Right-hand side of all 24 gridfunctions (Sec. 2.1 equations, upwinded
  * advection, Kreiss-Oliger dissipation) at interior points, from the
- * 24-gf set y_dev (its ghost points must be valid).  Ghost points of rhs_dev
+ * 24-gf set y_dev.  Its ghost points must be valid: outer ghosts set, inner
+ * ghosts holding the parity copies (nr_apply_inner_bcs), as in every state
+ * the RK4 driver produces.  Where the azimuth holds two points, its stencils
+ * read the other azimuthal slice in place of the ghost copies of it.  Ghost points of rhs_dev
  * are not written.  y_dev and rhs_dev: caller-owned device buffers of 24*T
  * doubles, distinct. */
 int nr_rhs(nr_grid* grid, const double* y_dev, double* rhs_dev);
@@ -180,8 +186,9 @@ int nr_dt_cfl(int coords, const int Nxx[3], const nr_params* params, double* dt_
 
 /* Batched mode (the uneven-grid workload of the paper's single-node and
  * scaling tests run many times over): many grids of uneven sizes, all of one
- * coordinate family (spherical-like or cylindrical-like) and one device,
- * advanced together.  Each RK4 substage is one persistent launch in which
+ * coordinate family (spherical-like or cylindrical-like), one azimuth kind
+ * (two points, or more: the right-hand-side kernel is specialised for a
+ * two-point azimuth) and one device, advanced together.  Each RK4 substage is one persistent launch in which
  * thread blocks take work items -- a tile of one grid's interior points or a
  * chunk of its pure-outer ghost points -- from an atomic counter until the
  * list is exhausted, followed by one parity-copy launch for all grids; one
@@ -192,7 +199,7 @@ int nr_dt_cfl(int coords, const int Nxx[3], const nr_params* params, double* dt_
  *   nr_batch_create: grids stay owned by the caller and must outlive the
  *     batch; their library-owned states are advanced in place.  Work is issued
  *     on the first grid's stream.  Errors: NR_EINVAL (mixed families or
- *     devices, duplicates), NR_ENOMEM, NR_ECUDA.
+ *     devices, mixed azimuth kinds, duplicates), NR_ENOMEM, NR_ECUDA.
  *   nr_batch_set_tile: tile shape tile_x x tile_y of interior points per work
  *     item, one of 32x4, 64x2, 128x1, 16x8, 32x2, 64x1, 32x1 (default 32x4).
  *   nr_batch_autotune: times one substage launch of each compiled tile shape
@@ -211,27 +218,44 @@ int nr_batch_rk4_step(nr_batch* batch, const double* dts, int nsteps);
  * (npunct masses at xyz) evolved by RK4 at its own CFL step until t_final.
  *   nr_server_create: hbm_budget_bytes caps the summed device bytes of the
  *     running requests; max_slots caps their number; work is issued on stream.
- *   nr_server_submit: queues a request and returns its id (no device work).
+ *   nr_server_submit: queues a request and returns its id (no device work;
+ *     NR_EINVAL if its grid has no valid CFL step).
  *     keep_state = 1 keeps the final 24-gf state on the host for
  *     nr_server_fetch_state.
- *   nr_server_advance: admits queued requests in arrival order while the
- *     budget and the slots allow, then advances all running requests
- *     together -- one nr_batch, one persistent launch per RK4 substage for all
- *     of them -- by up to nsteps steps.  Membership changes only at step
- *     boundaries: a request reaching t_final is retired (Hamiltonian-
- *     constraint norms recorded, state kept if asked, device memory released)
- *     and queued requests are admitted into the freed budget.  A request that
- *     cannot fit even alone is marked failed.  Synchronises at retirements.
+ *   nr_server_advance: makes queued requests resident (running) in policy
+ *     order while the budget and the slots allow, then advances the selected
+ *     running requests together -- one nr_batch per kind of grid (coordinate
+ *     family x azimuth kind), one persistent launch per RK4 substage for each
+ *     -- by up to nsteps steps.  Membership changes only at step boundaries:
+ *     a request reaching t_final is retired (Hamiltonian-constraint norms
+ *     recorded, state kept if asked, device memory released) and queued
+ *     requests are admitted into the freed budget.  A request that
+ *     cannot fit even alone is marked failed.  Synchronises at retirements;
+ *     after enqueuing a chunk of steps it waits for the chunk before it, so
+ *     at most one chunk is queued behind the one the GPU runs and the policy
+ *     acts on new arrivals within about a chunk of GPU time.
  *   nr_server_poll: status 0 queued, 1 running, 2 done, 3 failed; steps done
  *     and total; the final L2/Linf Hamiltonian-constraint norms when done.
  *   nr_server_set_tile: fixed tile shape for the batches (default: autotune at
  *     every membership change).
+ *   nr_server_set_policy: the order in which queued requests become resident
+ *     and running requests are advanced.  NR_SERVE_FIFO (default): arrival
+ *     order.  NR_SERVE_SRPT: least remaining work first (remaining steps x
+ *     interior points; for a queued request the steps follow from its CFL
+ *     step), preemptive at chunk boundaries: a running request that is not
+ *     selected keeps its state in HBM and resumes later, with a result that is
+ *     still bitwise the one it gets alone.  Each chunk advances the longest
+ *     prefix of that order whose interior points sum to at most
+ *     max_batch_points (at least one request; 0 = no cap, so every running
+ *     request advances).  NR_EINVAL for an unknown policy or a negative cap.
  * Each request's result is bitwise what running it alone with nr_rk4_step
  * gives, whichever requests shared the GPU with it. */
 typedef struct nr_server nr_server;
+enum { NR_SERVE_FIFO = 0, NR_SERVE_SRPT = 1 };
 int nr_server_create(size_t hbm_budget_bytes, int max_slots, int device, void* stream, nr_server** out);
 void nr_server_destroy(nr_server* server);
 int nr_server_set_tile(nr_server* server, int tile_x, int tile_y);
+int nr_server_set_policy(nr_server* server, int policy, int64_t max_batch_points);
 int nr_server_submit(nr_server* server, int coords, const int Nxx[3], const nr_params* params, int npunct,
                      const double* mass, const double* xyz, double t_final, int keep_state, int64_t* id_out);
 int nr_server_advance(nr_server* server, int nsteps, int* n_running, int* n_queued);

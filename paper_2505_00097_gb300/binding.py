@@ -26,7 +26,8 @@ EXPORTS = (
     "nr_apply_bcs", "nr_apply_inner_bcs", "nr_rk4_step", "nr_hamiltonian", "nr_get_state", "nr_set_state",
     "nr_sync", "nr_check_finite", "nr_build_maps", "nr_dt_cfl", "nr_fp64_peak", "nr_hamiltonian_noalloc",
     "nr_batch_create", "nr_batch_destroy", "nr_batch_set_tile", "nr_batch_autotune", "nr_batch_rk4_step",
-    "nr_server_create", "nr_server_destroy", "nr_server_set_tile", "nr_server_submit", "nr_server_advance",
+    "nr_server_create", "nr_server_destroy", "nr_server_set_tile", "nr_server_set_policy", "nr_server_submit",
+    "nr_server_advance",
     "nr_server_poll", "nr_server_fetch_state", "nr_last_error",
 )
 
@@ -117,6 +118,7 @@ def lib() -> ctypes.CDLL:
     L.nr_server_destroy.argtypes = [vp]
     L.nr_server_destroy.restype = None
     L.nr_server_set_tile.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+    L.nr_server_set_policy.argtypes = [vp, ctypes.c_int, ctypes.c_int64]
     L.nr_server_submit.argtypes = [vp, ctypes.c_int, ip, P, ctypes.c_int, dp, dp, ctypes.c_double, ctypes.c_int,
                                    ctypes.POINTER(ctypes.c_int64)]
     L.nr_server_advance.argtypes = [vp, ctypes.c_int, ip, ip]
@@ -321,6 +323,9 @@ class Batch:
         _check(lib().nr_batch_rk4_step(self.h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(nsteps)))
 
 
+SERVE_FIFO, SERVE_SRPT = 0, 1
+
+
 class Server:
     """nr_server: continuous batching of evolution requests on one device."""
 
@@ -343,6 +348,11 @@ class Server:
 
     def set_tile(self, tx: int, ty: int) -> None:
         _check(lib().nr_server_set_tile(self.h, int(tx), int(ty)))
+
+    def set_policy(self, policy: str, max_batch_points: int = 0) -> None:
+        """policy "fifo" or "srpt"; max_batch_points caps the interior points advanced together (0: no cap)."""
+        code = {"fifo": SERVE_FIFO, "srpt": SERVE_SRPT}.get(policy, -1)
+        _check(lib().nr_server_set_policy(self.h, code, int(max_batch_points)))
 
     def submit(self, spec: dict, t_final: float, keep_state: bool = False) -> int:
         p = make_params(spec, device=self.device)

@@ -83,38 +83,89 @@ __device__ __forceinline__ double koraw(const double* f, long s)
     return fma(15.0, ld(f - s) + ld(f + s), fma(-6.0, ld(f - 2 * s) + ld(f + 2 * s), ld(f - 3 * s) + ld(f + 3 * s)));
 }
 
-// ---- frame Hessian of a component function:
-// H_kl f = e_k e_l f - omega^m_kl e_m f  (symmetric in kl)
-template <int FAM, int KL>
-__device__ __forceinline__ double hess(const double* f, const long st[3], const Geo& g, const double df[3])
+// ---- a periodic azimuthal axis that holds two points (AX = 1 for
+// cylindrical-like, AX = 2 for spherical-like coordinates; AX = -1: none).
+// Along it the neighbours at offsets +-1 and +-3 are the other slice and those
+// at +-2 the point itself, so the centred first difference and every mixed
+// difference that involves the axis vanish identically, and the second,
+// upwind and sixth differences are 32, 16 and 32 times f_other - f.  The
+// kernels then skip those stencils; the result is the same discrete operator.
+template <int FAM, int AX>
+__host__ __device__ constexpr bool ax_ok()
 {
+    return AX == -1 || (FAM == FAM_CYL && AX == 1) || (FAM == FAM_SPH && AX == 2);
+}
+// a Hessian component known to vanish: a mixed pair that involves the axis
+__host__ __device__ constexpr bool hzero(int AX, int kl) { return AX >= 0 && offd(kl) && (spi(kl) == AX || spj(kl) == AX); }
+
+// e_k f (zero along the two-point axis)
+template <int AX>
+__device__ __forceinline__ double e1(const double* f, const long st[3], const double D[3], int k)
+{
+    return k == AX ? 0.0 : D[k] * d1raw(f, st[k]);
+}
+// sum_k a_k x_k, skipping k = AX where x vanishes (AX is never 0)
+template <int AX>
+__device__ __forceinline__ double dot3(double a0, double a1, double a2, const double x[3])
+{
+    double t = a0 * x[0];
+    if constexpr (AX != 1) t = fma(a1, x[1], t);
+    if constexpr (AX != 2) t = fma(a2, x[2], t);
+    return t;
+}
+
+// ---- frame Hessian of a component function:
+// H_kl f = e_k e_l f - omega^m_kl e_m f  (symmetric in kl); ox is the offset of
+// the other slice of the two-point axis
+template <int FAM, int KL, int AX>
+__device__ __forceinline__ double hess(const double* f, const long st[3], long ox, const Geo& g, const double df[3])
+{
+    if constexpr (hzero(AX, KL)) return 0.0;
     if constexpr (KL == 0) return fma(g.D2[0], d2raw(f, st[0]), -g.d00 * df[0]);
     if constexpr (KL == 1) return fma(g.DD[0], mixraw(f, st[0], st[1]), -g.a * df[1]);
     if constexpr (KL == 2) {
         if constexpr (FAM == FAM_SPH) return fma(g.DD[1], mixraw(f, st[0], st[2]), -g.b * df[2]);
         else return g.DD[1] * mixraw(f, st[0], st[2]);
     }
-    if constexpr (KL == 3) return fma(g.D2[1], d2raw(f, st[1]), g.a * df[0]);
+    if constexpr (KL == 3) {
+        if constexpr (AX == 1) return fma(32.0 * g.D2[1], ld(f + ox) - ld(f), g.a * df[0]);
+        else return fma(g.D2[1], d2raw(f, st[1]), g.a * df[0]);
+    }
     if constexpr (KL == 4) {
         if constexpr (FAM == FAM_SPH) return fma(g.DD[2], mixraw(f, st[1], st[2]), -g.c * df[2]);
         else return g.DD[2] * mixraw(f, st[1], st[2]);
     }
     if constexpr (KL == 5) {
-        if constexpr (FAM == FAM_SPH) return fma(g.D2[2], d2raw(f, st[2]), fma(g.b, df[0], g.c * df[1]));
-        else return fma(g.D2[2], d2raw(f, st[2]), -g.d22 * df[2]);
+        if constexpr (FAM == FAM_SPH) {
+            if constexpr (AX == 2) return fma(32.0 * g.D2[2], ld(f + ox) - ld(f), fma(g.b, df[0], g.c * df[1]));
+            else return fma(g.D2[2], d2raw(f, st[2]), fma(g.b, df[0], g.c * df[1]));
+        } else {
+            return fma(g.D2[2], d2raw(f, st[2]), -g.d22 * df[2]);
+        }
     }
     return 0.0;
 }
 
-template <int FAM>
-__device__ __forceinline__ void hess6(const double* f, const long st[3], const Geo& g, const double df[3], double H[6])
+template <int FAM, int AX>
+__device__ __forceinline__ void hess6(const double* f, const long st[3], long ox, const Geo& g, const double df[3],
+                                      double H[6])
 {
-    H[0] = hess<FAM, 0>(f, st, g, df);
-    H[1] = hess<FAM, 1>(f, st, g, df);
-    H[2] = hess<FAM, 2>(f, st, g, df);
-    H[3] = hess<FAM, 3>(f, st, g, df);
-    H[4] = hess<FAM, 4>(f, st, g, df);
-    H[5] = hess<FAM, 5>(f, st, g, df);
+    H[0] = hess<FAM, 0, AX>(f, st, ox, g, df);
+    H[1] = hess<FAM, 1, AX>(f, st, ox, g, df);
+    H[2] = hess<FAM, 2, AX>(f, st, ox, g, df);
+    H[3] = hess<FAM, 3, AX>(f, st, ox, g, df);
+    H[4] = hess<FAM, 4, AX>(f, st, ox, g, df);
+    H[5] = hess<FAM, 5, AX>(f, st, ox, g, df);
+}
+// gammabar^kl H_kl (gw: off-diagonal entries doubled), skipping vanishing components
+template <int AX>
+__device__ __forceinline__ double contract6(const double gw[6], const double H[6])
+{
+    double t = gw[0] * H[0];
+#pragma unroll
+    for (int kl = 1; kl < 6; kl++)
+        if (!hzero(AX, kl)) t = fma(gw[kl], H[kl], t);
+    return t;
 }
 
 // ---- rotation generators acting on vectors / symmetric tensors: out += c * J_pq (.)
@@ -171,6 +222,7 @@ struct PointIn {
     const double* y;  // state at this point: y + idx (gridfunction g at y[g*T])
     long T;
     long st[3];
+    long ox;          // offset of the other slice of a two-point azimuthal axis (unused otherwise)
     Geo g;
 };
 
@@ -188,9 +240,10 @@ struct MetricPart {
     double W, iW, dphi[3], DDphi[6];
 };
 
-template <int FAM, bool NEED_GH>
+template <int FAM, bool NEED_GH, int AX>
 __device__ __forceinline__ void metric_part(const PointIn& P, MetricPart& M)
 {
+    static_assert(ax_ok<FAM, AX>(), "two-point axis must be the azimuth");
     const double* y = P.y;
     const long T = P.T;
     const Geo& g = P.g;
@@ -226,7 +279,7 @@ __device__ __forceinline__ void metric_part(const PointIn& P, MetricPart& M)
 #pragma unroll
     for (int k = 0; k < 3; k++)
 #pragma unroll
-        for (int s = 0; s < 6; s++) dh[k][s] = g.D[k] * d1raw(F(G_HDD + s), st[k]);
+        for (int s = 0; s < 6; s++) dh[k][s] = e1<AX>(F(G_HDD + s), st, g.D, k);
 
     // ---------------- Hessians of h contracted two ways:
     // Lh_ij = gammabar^kl H_kl h_ij,  GH_kl = gammabar^ij H_kl h_ij
@@ -235,17 +288,13 @@ __device__ __forceinline__ void metric_part(const PointIn& P, MetricPart& M)
     for (int s = 0; s < 6; s++) {
         double df[3] = {dh[0][s], dh[1][s], dh[2][s]};
         double H[6];
-        hess6<FAM>(F(G_HDD + s), st, g, df, H);
-        Lh[s] = gw[0] * H[0];
-#pragma unroll
-        for (int kl = 1; kl < 6; kl++) Lh[s] = fma(gw[kl], H[kl], Lh[s]);
+        hess6<FAM, AX>(F(G_HDD + s), st, P.ox, g, df, H);
+        Lh[s] = contract6<AX>(gw, H);
         if constexpr (NEED_GH) {
-            if (s == 0) {
 #pragma unroll
-                for (int kl = 0; kl < 6; kl++) M.GH[kl] = gw[0] * H[kl];
-            } else {
-#pragma unroll
-                for (int kl = 0; kl < 6; kl++) M.GH[kl] = fma(gw[s], H[kl], M.GH[kl]);
+            for (int kl = 0; kl < 6; kl++) {
+                if (hzero(AX, kl)) M.GH[kl] = 0.0;
+                else M.GH[kl] = s == 0 ? gw[0] * H[kl] : fma(gw[s], H[kl], M.GH[kl]);
             }
         }
     }
@@ -284,7 +333,7 @@ __device__ __forceinline__ void metric_part(const PointIn& P, MetricPart& M)
         double t = gw[0] * dh[m][0];
 #pragma unroll
         for (int s = 1; s < 6; s++) t = fma(gw[s], dh[m][s], t);
-        M.Dtr[m] = 0.5 * t;
+        M.Dtr[m] = m == AX ? 0.0 : 0.5 * t;
     }
 
     // ---------------- Ricci tensor
@@ -294,8 +343,9 @@ __device__ __forceinline__ void metric_part(const PointIn& P, MetricPart& M)
         double V1[6], V2[6], Y1[6] = {0, 0, 0, 0, 0, 0}, Y2[6] = {0, 0, 0, 0, 0, 0};
 #pragma unroll
         for (int s = 0; s < 6; s++) {
-            V1[s] = fma(gi[4], dh[2][s], fma(gi[3], dh[1][s], gi[1] * dh[0][s]));
-            V2[s] = fma(gi[5], dh[2][s], fma(gi[4], dh[1][s], gi[2] * dh[0][s]));
+            const double d[3] = {dh[0][s], dh[1][s], dh[2][s]};
+            V1[s] = dot3<AX>(gi[1], gi[3], gi[4], d);
+            V2[s] = dot3<AX>(gi[2], gi[4], gi[5], d);
         }
         j01s(g.a, h, Y1);                                                        // Y1 = Omega_1 h
         if constexpr (FAM == FAM_SPH) { j02s(g.b, h, Y2); j12s(g.c, h, Y2); }    // Y2 = Omega_2 h
@@ -335,7 +385,7 @@ __device__ __forceinline__ void metric_part(const PointIn& P, MetricPart& M)
 #pragma unroll
     for (int j = 0; j < 3; j++)
 #pragma unroll
-        for (int k = 0; k < 3; k++) Dlam[j][k] = g.D[j] * d1raw(F(G_LAM + k), st[j]);
+        for (int k = 0; k < 3; k++) Dlam[j][k] = e1<AX>(F(G_LAM + k), st, g.D, j);
     omv<FAM, 1>(g, 1.0, lam, Dlam[1]);
     omv<FAM, 2>(g, 1.0, lam, Dlam[2]);
     // Y[j][m][k] = gammabar^kl Delta_jml
@@ -385,25 +435,25 @@ __device__ __forceinline__ void metric_part(const PointIn& P, MetricPart& M)
     // ---------------- conformal factor: phi = -1/2 ln W
     double dW[3];
 #pragma unroll
-    for (int k = 0; k < 3; k++) dW[k] = g.D[k] * d1raw(F(G_CF), st[k]);
+    for (int k = 0; k < 3; k++) dW[k] = e1<AX>(F(G_CF), st, g.D, k);
     const double mhiW = -0.5 * M.iW;
 #pragma unroll
-    for (int k = 0; k < 3; k++) M.dphi[k] = mhiW * dW[k];
+    for (int k = 0; k < 3; k++) M.dphi[k] = k == AX ? 0.0 : mhiW * dW[k];
     {
         double HW[6];
-        hess6<FAM>(F(G_CF), st, g, dW, HW);
+        hess6<FAM, AX>(F(G_CF), st, P.ox, g, dW, HW);
 #pragma unroll
         for (int s = 0; s < 6; s++) {
             const int i = spi(s), j = spj(s);
-            const double Hphi = fma(mhiW, HW[s], 2.0 * M.dphi[i] * M.dphi[j]);
-            M.DDphi[s] = Hphi - fma(Dup[2][s], M.dphi[2], fma(Dup[1][s], M.dphi[1], Dup[0][s] * M.dphi[0]));
+            const double Hphi = hzero(AX, s) ? 0.0 : fma(mhiW, HW[s], 2.0 * M.dphi[i] * M.dphi[j]);
+            M.DDphi[s] = Hphi - dot3<AX>(Dup[0][s], Dup[1][s], Dup[2][s], M.dphi);
         }
     }
 }
 
 // Output: the 24 right-hand sides without the beta^k d_k advection and
 // without Kreiss-Oliger dissipation (added by the caller, see adv_ko()).
-template <int FAM>
+template <int FAM, int AX>
 __device__ __forceinline__ void rhs_core(const PointIn& P, double eta, double out[NGF])
 {
     const double* y = P.y;
@@ -413,7 +463,7 @@ __device__ __forceinline__ void rhs_core(const PointIn& P, double eta, double ou
     auto F = [&](int gf) { return y + (long)gf * T; };
 
     MetricPart M;
-    metric_part<FAM, true>(P, M);
+    metric_part<FAM, true, AX>(P, M);
     const double* h = M.h;
     const double* gi = M.gi;
     const double* gw = M.gw;
@@ -436,17 +486,17 @@ __device__ __forceinline__ void rhs_core(const PointIn& P, double eta, double ou
     double dK[3], dal[3], dvet[3][3];
 #pragma unroll
     for (int k = 0; k < 3; k++) {
-        dK[k] = g.D[k] * d1raw(F(G_TRK), st[k]);
-        dal[k] = g.D[k] * d1raw(F(G_ALPHA), st[k]);
+        dK[k] = e1<AX>(F(G_TRK), st, g.D, k);
+        dal[k] = e1<AX>(F(G_ALPHA), st, g.D, k);
 #pragma unroll
-        for (int i = 0; i < 3; i++) dvet[k][i] = g.D[k] * d1raw(F(G_VET + i), st[k]);
+        for (int i = 0; i < 3; i++) dvet[k][i] = e1<AX>(F(G_VET + i), st, g.D, k);
     }
     double DDal[6];
     {
         double Hal[6];
-        hess6<FAM>(F(G_ALPHA), st, g, dal, Hal);
+        hess6<FAM, AX>(F(G_ALPHA), st, P.ox, g, dal, Hal);
 #pragma unroll
-        for (int s = 0; s < 6; s++) DDal[s] = Hal[s] - fma(Dup[2][s], dal[2], fma(Dup[1][s], dal[1], Dup[0][s] * dal[0]));
+        for (int s = 0; s < 6; s++) DDal[s] = Hal[s] - dot3<AX>(Dup[0][s], Dup[1][s], Dup[2][s], dal);
     }
 
     // ---------------- Abar with raised indices
@@ -489,7 +539,7 @@ __device__ __forceinline__ void rhs_core(const PointIn& P, double eta, double ou
 #pragma unroll
         for (int i = 0; i < 3; i++) {
             double df[3] = {dvet[0][i], dvet[1][i], dvet[2][i]};
-            hess6<FAM>(F(G_VET + i), st, g, df, Hv[i]);
+            hess6<FAM, AX>(F(G_VET + i), st, P.ox, g, df, Hv[i]);
         }
 #pragma unroll
         for (int kl = 0; kl < 6; kl++)
@@ -571,18 +621,22 @@ __device__ __forceinline__ void rhs_core(const PointIn& P, double eta, double ou
     // e_l(Delta^k_km) = 1/2 (GH_lm - Q_lm) - (Omega_l Dtr)_m,  Q_lm = tr(gbinv e_l h gbinv e_m h)
     double gdiv[3];
     {
-        double M[3][3][3];  // M[l] = gbinv . e_l h
+        double M[3][3][3];  // M[l] = gbinv . e_l h  (zero along the two-point axis)
 #pragma unroll
         for (int l = 0; l < 3; l++)
 #pragma unroll
             for (int i = 0; i < 3; i++)
 #pragma unroll
                 for (int j = 0; j < 3; j++)
-                    M[l][i][j] = fma(gsym(gi, i, 2), dh[l][sp(2, j)], fma(gsym(gi, i, 1), dh[l][sp(1, j)], gsym(gi, i, 0) * dh[l][sp(0, j)]));
+                    M[l][i][j] = l == AX ? 0.0 : fma(gsym(gi, i, 2), dh[l][sp(2, j)], fma(gsym(gi, i, 1), dh[l][sp(1, j)], gsym(gi, i, 0) * dh[l][sp(0, j)]));
         double Q[6];
 #pragma unroll
         for (int s = 0; s < 6; s++) {
             const int l = spi(s), m = spj(s);
+            if (l == AX || m == AX) {
+                Q[s] = 0.0;
+                continue;
+            }
             double t = M[l][0][0] * M[m][0][0];
 #pragma unroll
             for (int q = 1; q < 9; q++) t = fma(M[l][q / 3][q % 3], M[m][q % 3][q / 3], t);
@@ -726,7 +780,7 @@ template <int FAM>
 __device__ __forceinline__ double ham_core(const PointIn& P)
 {
     MetricPart M;
-    metric_part<FAM, false>(P, M);
+    metric_part<FAM, false, -1>(P, M);
     const double* gi = M.gi;
     const double* gw = M.gw;
     double a[6];
@@ -753,47 +807,88 @@ __device__ __forceinline__ double ham_core(const PointIn& P)
     return fma((2.0 / 3.0) * K, K, fma(M.W * M.W, fma(-8.0, gp + lp, R), -AA));
 }
 
-// beta^k d_k f, upwinded: u[k] = |vet^k| D_k, us[k] = +-stride selecting the
-// stencil side by the sign of vet^k
-__device__ __forceinline__ double adv(const double* f, const double u[3], const long us[3])
+// beta^k d_k f, upwinded, and the Kreiss-Oliger dissipation of f, evaluated as
+// one 7-point stencil per axis whose weights are formed once per point.  Along
+// axis k, with u = |vet^k| D_k (D_k = 1/(12 dxx_k S_k)), p = u, q = 0 for
+// vet^k > 0 (upwind offsets -1..+3) and p = 0, q = u otherwise (offsets
+// -3..+1), and kap = sigma/(64 S_k dxx_k) = (12/64) sigma D_k (the strength
+// refers to the physical spacing), the weights at offsets -3..+3 are
+//   q+kap, -6(q+kap), 18q-3p+15kap, -10u-20kap, 18p-3q+15kap, -6(p+kap), p+kap,
+// i.e. u times the upwind weights (-3,-10,18,-6,1)/(12 dxx_k S_k) on the side
+// of vet^k, plus kap times the sixth difference (1,-6,15,-20,15,-6,1).  Along
+// a two-point axis the sum is (16u + 32kap)(f_other - f).
+struct AdvKoW {
+    double w[3][6];   // per axis: offsets -3, -2, -1, +1, +2, +3
+    double c0;        // centre weight summed over the axes
+    double cax;       // two-point axis: weight of f_other - f
+};
+
+template <int AX>
+__device__ __forceinline__ void advko_weights(const double u[3], const bool fwd[3], const double D[3], double sigma,
+                                              AdvKoW& W)
 {
-    double a = u[0] * upraw(f, us[0]);
-    a = fma(u[1], upraw(f, us[1]), a);
-    return fma(u[2], upraw(f, us[2]), a);
+    double c0 = 0.0;
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        const double kap = (0.1875 * sigma) * D[d];
+        if (d == AX) {
+            W.cax = fma(16.0, u[d], 32.0 * kap);
+            continue;
+        }
+        const double p = fwd[d] ? u[d] : 0.0, q = fwd[d] ? 0.0 : u[d];
+        const double pk = p + kap, qk = q + kap, k15 = 15.0 * kap;
+        W.w[d][0] = qk;
+        W.w[d][1] = -6.0 * qk;
+        W.w[d][2] = fma(18.0, q, fma(-3.0, p, k15));
+        W.w[d][3] = fma(18.0, p, fma(-3.0, q, k15));
+        W.w[d][4] = -6.0 * pk;
+        W.w[d][5] = pk;
+        c0 = d == 0 ? fma(-10.0, u[d], -20.0 * kap) : c0 + fma(-10.0, u[d], -20.0 * kap);
+    }
+    W.c0 = c0;
 }
 
-// Kreiss-Oliger dissipation sum_k kod[k] delta^6_k f (times sigma by the caller);
-// kod[k] = 1/(64 S_k dxx_k), kosum = sum_k kod[k]
-__device__ __forceinline__ double ko(const double* f, const long st[3], const double kod[3], double kosum)
+template <int AX>
+__device__ __forceinline__ double advko_apply(const double* f, const long st[3], long ox, const AdvKoW& W, double k)
 {
-    double k = kod[0] * koraw(f, st[0]);
-    k = fma(kod[1], koraw(f, st[1]), k);
-    k = fma(kod[2], koraw(f, st[2]), k);
-    return fma(-20.0 * kosum, ld(f), k);
+    k = fma(W.c0, ld(f), k);
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        if (d == AX) {
+            k = fma(W.cax, ld(f + ox) - ld(f), k);
+            continue;
+        }
+        const long s = st[d];
+        k = fma(W.w[d][0], ld(f - 3 * s), k);
+        k = fma(W.w[d][1], ld(f - 2 * s), k);
+        k = fma(W.w[d][2], ld(f - s), k);
+        k = fma(W.w[d][3], ld(f + s), k);
+        k = fma(W.w[d][4], ld(f + 2 * s), k);
+        k = fma(W.w[d][5], ld(f + 3 * s), k);
+    }
+    return k;
 }
 
 // Adds the upwinded advection and the dissipation to the 24 right-hand sides
-// of rhs_core.  The dissipation strength refers to the physical spacing
-// S_d dxx_d: 1/(64 S_d dxx_d) = (12/64) D[d].
-__device__ __forceinline__ void add_adv_ko(const double* y, long T, const long st[3], const double D[3],
-                                           const double* sigma, double k[NGF])
+// of rhs_core: sigma_metric on the 17 metric gridfunctions (h, a, W, K,
+// lambda), sigma_gauge on the 7 gauge gridfunctions (vet, bet, alpha).
+template <int AX>
+__device__ __forceinline__ void add_adv_ko(const double* y, long T, const long st[3], long ox, const double D[3],
+                                           double sigma_metric, double sigma_gauge, double k[NGF])
 {
-    double kod[3];
-#pragma unroll
-    for (int d = 0; d < 3; d++) kod[d] = 0.1875 * D[d];
-    const double kosum = kod[0] + kod[1] + kod[2];
     double u[3];
-    long us[3];
+    bool fwd[3];
 #pragma unroll
     for (int d = 0; d < 3; d++) {
         const double v = ld(y + (long)(G_VET + d) * T);
         u[d] = fabs(v) * D[d];
-        us[d] = (v > 0.0) ? st[d] : -st[d];
+        fwd[d] = v > 0.0;
     }
+    AdvKoW Wm, Wg;
+    advko_weights<AX>(u, fwd, D, sigma_metric, Wm);
+    advko_weights<AX>(u, fwd, D, sigma_gauge, Wg);
 #pragma unroll
-    for (int g = 0; g < NGF; g++) k[g] += adv(y + (long)g * T, u, us);
-#pragma unroll
-    for (int g = 0; g < NGF; g++) k[g] = fma(sigma[g], ko(y + (long)g * T, st, kod, kosum), k[g]);
+    for (int g = 0; g < NGF; g++) k[g] = advko_apply<AX>(y + (long)g * T, st, ox, g < G_VET ? Wm : Wg, k[g]);
 }
 
 }  // namespace nrk

@@ -2,85 +2,15 @@
 // one persistent launch per RK4 substage plus one parity-copy launch, the
 // whole step captured in a CUDA graph; the tile shape is chosen by timing.
 //
-// A work item is either a TX x TY tile of one grid's interior points or a
-// chunk of TX*TY of its pure-outer ghost points.  Blocks of the persistent
-// kernel take items from an atomic counter until the list is exhausted (a
-// bounded loop: each block stops at the first index past the end).  Every
-// point runs the same per-point code as the single-grid kernels
-// (nr_stage.cuh), so a grid's state after n batched steps is bitwise the
-// state after n single-grid steps, whatever the tile shape or the company.
+// The persistent kernel and its work items: nr_batch_kernels.cuh.
 #include <string.h>
 
 #include <algorithm>
 #include <vector>
 
-#include "nr_stage.cuh"
+#include "nr_batch_kernels.cuh"
 
 namespace nrk {
-
-struct BGrid {
-    GridK K;
-    double *y, *ya, *yb, *acc;
-    const OuterPt* outer;
-    const double* finf;
-    const double* wspeed;
-    int n_outer;
-    int tiles_x;
-    int w_begin, w_rhs_end, w_end;
-    int pad;
-    Stage st[4];
-};
-
-struct BInner {
-    int grid, dst, src, negmask;
-};
-
-__device__ __forceinline__ void stage_buffers(const BGrid& B, int stage, const double*& yin, double*& out,
-                                              const double*& yn)
-{
-    switch (stage) {
-    case 0: yin = B.y; out = B.ya; yn = B.y; break;
-    case 1: yin = B.ya; out = B.yb; yn = B.y; break;
-    case 2: yin = B.yb; out = B.ya; yn = B.y; break;
-    default: yin = B.ya; out = B.y; yn = nullptr; break;
-    }
-}
-
-template <int FAM, int TX, int TY>
-__global__ void __launch_bounds__(TX* TY) k_batch_stage(const BGrid* __restrict__ grids, int ngrids, int total,
-                                                         int* counter, int stage)
-{
-    __shared__ int s_w;
-    const int tid = threadIdx.x;
-    for (;;) {
-        __syncthreads();
-        if (tid == 0) s_w = atomicAdd(counter, 1);
-        __syncthreads();
-        const int w = s_w;
-        if (w >= total) return;
-        int lo = 0, hi = ngrids - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (grids[mid].w_begin <= w) lo = mid;
-            else hi = mid - 1;
-        }
-        const BGrid& B = grids[lo];
-        const double* yin;
-        const double* yn;
-        double* out;
-        stage_buffers(B, stage, yin, out, yn);
-        if (w < B.w_rhs_end) {
-            const int t = w - B.w_begin;
-            const int i = (t % B.tiles_x) * TX + tid % TX;
-            const int j = (t / B.tiles_x) * TY + tid / TX;
-            if (i < B.K.N0 && j < B.K.N1 * B.K.N2) rhs_point_stage<FAM>(B.K, yin, out, yn, B.acc, B.st[stage], i, j);
-        } else {
-            const int p = (w - B.w_rhs_end) * (TX * TY) + tid;
-            if (p < B.n_outer)
-                outer_point_stage<FAM>(B.K, B.outer[p], yin, out, yn, B.acc, B.finf, B.wspeed, B.st[stage]);
-        }
-    }
-}
 
 __global__ void __launch_bounds__(256) k_batch_inner(const BGrid* __restrict__ grids, const BInner* __restrict__ pts,
                                                       int npts, int stage)
@@ -97,58 +27,6 @@ __global__ void __launch_bounds__(256) k_batch_inner(const BGrid* __restrict__ g
     inner_copy(B.K.T, p, blockIdx.y, out);
 }
 
-// tile shapes the autotuner tries (threads per block = TX * TY)
-struct TileShape {
-    int tx, ty;
-};
-constexpr TileShape kTiles[] = {{32, 4}, {64, 2}, {128, 1}, {16, 8}, {32, 2}, {64, 1}, {32, 1}};
-constexpr int kNumTiles = sizeof(kTiles) / sizeof(kTiles[0]);
-
-template <int FAM, int TX, int TY>
-cudaError_t launch_bstage(const BGrid* g, int n, int total, int* counter, int stage, int blocks, cudaStream_t s)
-{
-    k_batch_stage<FAM, TX, TY><<<blocks, TX * TY, 0, s>>>(g, n, total, counter, stage);
-    return cudaGetLastError();
-}
-
-template <int FAM, int TX, int TY>
-int occupancy_blocks(int sms)
-{
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_stage<FAM, TX, TY>, TX * TY, 0) != cudaSuccess)
-        return 0;
-    return std::max(nb, 1) * sms;
-}
-
-template <int FAM>
-cudaError_t dispatch_stage(int tile, const BGrid* g, int n, int total, int* counter, int stage, int blocks,
-                           cudaStream_t s)
-{
-    switch (tile) {
-    case 0: return launch_bstage<FAM, 32, 4>(g, n, total, counter, stage, blocks, s);
-    case 1: return launch_bstage<FAM, 64, 2>(g, n, total, counter, stage, blocks, s);
-    case 2: return launch_bstage<FAM, 128, 1>(g, n, total, counter, stage, blocks, s);
-    case 3: return launch_bstage<FAM, 16, 8>(g, n, total, counter, stage, blocks, s);
-    case 4: return launch_bstage<FAM, 32, 2>(g, n, total, counter, stage, blocks, s);
-    case 5: return launch_bstage<FAM, 64, 1>(g, n, total, counter, stage, blocks, s);
-    default: return launch_bstage<FAM, 32, 1>(g, n, total, counter, stage, blocks, s);
-    }
-}
-
-template <int FAM>
-int dispatch_occupancy(int tile, int sms)
-{
-    switch (tile) {
-    case 0: return occupancy_blocks<FAM, 32, 4>(sms);
-    case 1: return occupancy_blocks<FAM, 64, 2>(sms);
-    case 2: return occupancy_blocks<FAM, 128, 1>(sms);
-    case 3: return occupancy_blocks<FAM, 16, 8>(sms);
-    case 4: return occupancy_blocks<FAM, 32, 2>(sms);
-    case 5: return occupancy_blocks<FAM, 64, 1>(sms);
-    default: return occupancy_blocks<FAM, 32, 1>(sms);
-    }
-}
-
 }  // namespace nrk
 
 using namespace nrk;
@@ -156,6 +34,7 @@ using namespace nrk;
 struct nr_batch {
     std::vector<nr_grid*> grids;
     int fam = FAM_SPH;
+    bool two_point = false;   // the grids' azimuth holds two points
     int device = 0;
     int sms = 0;
     cudaStream_t stream = nullptr;
@@ -216,8 +95,8 @@ int build_table(nr_batch* b, const double* dts)
     b->total = w;
     cudaError_t e = cudaMemcpy(b->d_grids, h.data(), sizeof(BGrid) * h.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return nrk_fail(NR_ECUDA, "batch table upload: %s", cudaGetErrorString(e));
-    b->blocks = b->fam == FAM_SPH ? dispatch_occupancy<FAM_SPH>(b->tile, b->sms)
-                                  : dispatch_occupancy<FAM_CYL>(b->tile, b->sms);
+    b->blocks = b->fam == FAM_SPH ? batch_occupancy_sph(b->two_point, b->tile, b->sms)
+                                  : batch_occupancy_cyl(b->two_point, b->tile, b->sms);
     if (b->blocks <= 0) return nrk_fail(NR_ECUDA, "occupancy query failed");
     b->dts.assign(dts, dts + b->grids.size());
     b->table_ok = true;
@@ -226,11 +105,10 @@ int build_table(nr_batch* b, const double* dts)
 
 cudaError_t enqueue_stage_launch(nr_batch* b, int stage, cudaStream_t s)
 {
-    return b->fam == FAM_SPH
-               ? dispatch_stage<FAM_SPH>(b->tile, b->d_grids, (int)b->grids.size(), b->total, b->d_counter + stage,
-                                         stage, b->blocks, s)
-               : dispatch_stage<FAM_CYL>(b->tile, b->d_grids, (int)b->grids.size(), b->total, b->d_counter + stage,
-                                         stage, b->blocks, s);
+    return b->fam == FAM_SPH ? batch_stage_launch_sph(b->two_point, b->tile, b->d_grids, (int)b->grids.size(),
+                                                      b->total, b->d_counter + stage, stage, b->blocks, s)
+                             : batch_stage_launch_cyl(b->two_point, b->tile, b->d_grids, (int)b->grids.size(),
+                                                      b->total, b->d_counter + stage, stage, b->blocks, s);
 }
 
 cudaError_t enqueue_step(nr_batch* b, cudaStream_t s)
@@ -274,12 +152,16 @@ int nr_batch_create(nr_grid* const* grids, int ngrids, nr_batch** out)
         if (grids[q]->device != grids[0]->device) return nrk_fail(NR_EINVAL, "grids on different devices");
         if (grids[q]->geo.fam != grids[0]->geo.fam)
             return nrk_fail(NR_EINVAL, "grids of spherical-like and cylindrical-like coordinates cannot share a batch");
+        if ((grids[q]->K.ax >= 0) != (grids[0]->K.ax >= 0))
+            return nrk_fail(NR_EINVAL, "grids whose azimuth holds two points and grids whose azimuth holds more "
+                                       "cannot share a batch");
         for (int r = 0; r < q; r++)
             if (grids[r] == grids[q]) return nrk_fail(NR_EINVAL, "grid %d appears twice", q);
     }
     nr_batch* b = new nr_batch();
     b->grids.assign(grids, grids + ngrids);
     b->fam = grids[0]->geo.fam;
+    b->two_point = grids[0]->K.ax >= 0;
     b->device = grids[0]->device;
     b->stream = grids[0]->stream;
     DevGuard dg(b->device);

@@ -260,6 +260,16 @@ int check_args(int coords, const int Nxx[3], const nr_params* p)
         return fail(NR_EINVAL, "unknown coordinate system %d", coords);
     if (!Nxx) return fail(NR_EINVAL, "Nxx is NULL");
     if (p && p->NG != 3) return fail(NR_EINVAL, "NG must be 3 (4th-order FD with upwinding), got %d", p->NG);
+    if (p) {
+        for (int g = 1; g < NR_NGF; g++) {
+            const int first = g < 17 ? 0 : 17;
+            if (!(p->ko_sigma[g] == p->ko_sigma[first]))
+                return fail(NR_EINVAL, "ko_sigma must take one value on gridfunctions 0-16 (metric) and one on 17-23 "
+                                       "(gauge); gridfunction %d differs", g);
+        }
+        if (!(p->ko_sigma[0] >= 0.0) || !(p->ko_sigma[17] >= 0.0))
+            return fail(NR_EINVAL, "ko_sigma must be non-negative");
+    }
     long T = 1;
     for (int d = 0; d < 3; d++) {
         if (Nxx[d] < 1 || Nxx[d] > (1 << 20)) return fail(NR_EINVAL, "Nxx[%d] = %d out of range", d, Nxx[d]);
@@ -503,12 +513,14 @@ int nr_grid_create(int coords, const int Nxx[3], const nr_params* params, nr_gri
     K.N0 = G.N[0]; K.N1 = G.N[1]; K.N2 = G.N[2];
     K.NG = G.NG;
     K.fam = G.fam;
+    K.ax = (G.fam == FAM_CYL && G.N[1] == 2) ? 1 : (G.fam == FAM_SPH && G.N[2] == 2) ? 2 : -1;
     K.T = G.T;
     for (int d = 0; d < 3; d++) {
         K.inv12dx[d] = 1.0 / (12.0 * G.dxx[d]);
         K.inv12dx2[d] = 1.0 / (12.0 * G.dxx[d] * G.dxx[d]);
     }
-    for (int q = 0; q < NR_NGF; q++) K.sigma[q] = P.ko_sigma[q];
+    K.sigma_metric = P.ko_sigma[0];
+    K.sigma_gauge = P.ko_sigma[17];
     K.eta = P.eta;
     g->nparts = ham_partials_needed(K);
     if ((rc = dmalloc(g, &g->y, set)) || (rc = dmalloc(g, &g->ya, set)) || (rc = dmalloc(g, &g->yb, set)) ||

@@ -28,10 +28,12 @@ struct GridK {
     int N0, N1, N2;     // interior sizes
     int NG;
     int fam;            // FAM_SPH / FAM_CYL
+    int ax;             // azimuthal axis when it holds two points (1 cylindrical-like, 2 spherical-like), else -1
     long T;
     double inv12dx[3];  // 1/(12 dxx_k)
     double inv12dx2[3]; // 1/(12 dxx_k^2)
-    double sigma[24];
+    double sigma_metric;  // Kreiss-Oliger strength on gridfunctions 0-16 (h, a, W, K, lambda)
+    double sigma_gauge;   // and on 17-23 (vet, bet, alpha)
     double eta;
     Rfm rfm;
 };

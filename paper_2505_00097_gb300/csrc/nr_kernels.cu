@@ -21,7 +21,7 @@ namespace nrk {
 
 constexpr int RHS_BX = 32, RHS_BY = 4;
 
-template <int FAM>
+template <int FAM, int AX>
 __global__ void __launch_bounds__(RHS_BX* RHS_BY) k_rhs(GridK G, const double* __restrict__ yin, double* out,
                                                         const double* yn, double* acc, Stage st)
 {
@@ -30,7 +30,7 @@ __global__ void __launch_bounds__(RHS_BX* RHS_BY) k_rhs(GridK G, const double* _
     const int i = (int)(blockIdx.x % nbx) * RHS_BX + threadIdx.x;
     const int j = (int)(blockIdx.x / nbx) * RHS_BY + threadIdx.y;
     if (i >= G.N0 || j >= G.N1 * G.N2) return;
-    rhs_point_stage<FAM>(G, yin, out, yn, acc, st, i, j);
+    rhs_point_stage<FAM, AX>(G, yin, out, yn, acc, st, i, j);
 }
 
 template <int FAM>
@@ -105,6 +105,7 @@ __global__ void __launch_bounds__(HAM_THREADS) k_ham(GridK G, const double* __re
         P.st[0] = 1;
         P.st[1] = G.n0;
         P.st[2] = (long)G.n0 * G.n1;
+        P.ox = 0;
         P.g = make_geo<FAM>(G, p0, p1, p2);
         const double h = ham_core<FAM>(P);
         if (H) H[idx] = h;
@@ -207,10 +208,13 @@ cudaError_t launch_rhs(const GridK& G, const double* yin, double* out, const dou
     dim3 blk(RHS_BX, RHS_BY);
     const long nb = (long)((G.N0 + RHS_BX - 1) / RHS_BX) * ((G.N1 * G.N2 + RHS_BY - 1) / RHS_BY);
     dim3 grd((unsigned)nb);
-    if (G.fam == FAM_SPH)
-        k_rhs<FAM_SPH><<<grd, blk, 0, s>>>(G, yin, out, yn, acc, st);
-    else
-        k_rhs<FAM_CYL><<<grd, blk, 0, s>>>(G, yin, out, yn, acc, st);
+    if (G.fam == FAM_SPH) {
+        if (G.ax == 2) k_rhs<FAM_SPH, 2><<<grd, blk, 0, s>>>(G, yin, out, yn, acc, st);
+        else k_rhs<FAM_SPH, -1><<<grd, blk, 0, s>>>(G, yin, out, yn, acc, st);
+    } else {
+        if (G.ax == 1) k_rhs<FAM_CYL, 1><<<grd, blk, 0, s>>>(G, yin, out, yn, acc, st);
+        else k_rhs<FAM_CYL, -1><<<grd, blk, 0, s>>>(G, yin, out, yn, acc, st);
+    }
     return cudaGetLastError();
 }
 

@@ -105,6 +105,7 @@ __global__ void __launch_bounds__(NA_THREADS) k_na_ham(GridK G, const double* __
         P.st[0] = 1;
         P.st[1] = G.n0;
         P.st[2] = (long)G.n0 * G.n1;
+        P.ox = 0;
         P.g = make_geo<FAM>(G, p0, p1, p2);
         const double h = ham_core<FAM>(P);
         if (H) H[idx] = h;
@@ -204,6 +205,7 @@ extern "C" int nr_hamiltonian_noalloc(int coords, const int Nxx[3], const nr_par
     K.N2 = Nxx[2];
     K.NG = NG;
     K.fam = fam;
+    K.ax = -1;
     K.T = T;
     double lo[3], hi[3], dx[3];
     if (fam == FAM_CYL) {

@@ -1,16 +1,25 @@
 // nr_server.cu -- served mode: continuous batching of evolution requests.
 //
 // Requests (one grid + Brill-Lindquist data + a final time each) are queued
-// by nr_server_submit.  nr_server_advance admits queued requests in arrival
-// order while the summed device bytes stay within the HBM budget and a slot
-// is free, then advances every running request together as one nr_batch
-// (one persistent launch per RK4 substage for all of them).  Membership
+// by nr_server_submit.  nr_server_advance makes queued requests resident
+// (grid allocated, initial data set) while the summed device bytes stay
+// within the HBM budget and a slot is free, then advances a selection of the
+// resident requests together, as one nr_batch per kind of grid (coordinate
+// family x azimuth kind; one persistent launch per RK4 substage for each).
+// The policy orders both steps:
+//   FIFO: arrival order;
+//   SRPT: least remaining work first (remaining steps x interior points),
+//         preemptive at chunk boundaries -- a resident request that is not
+//         selected keeps its state in HBM and resumes later.
+// The selection is the longest prefix of that order whose interior points sum
+// to at most max_batch_points (at least one request; 0 = no cap).  Membership
 // changes only at step boundaries: a request that reaches its final time is
 // retired (its Hamiltonian-constraint norms recorded, optionally its final
 // state copied to the host, its device memory released) and the freed budget
 // admits the next queued requests.  Each request advances with its own CFL
 // step; since every point runs the single-grid arithmetic, a request's result
-// does not depend on which other requests shared the GPU with it.
+// does not depend on which other requests shared the GPU with it, nor on when
+// it was paused.
 #include <math.h>
 #include <string.h>
 
@@ -36,6 +45,8 @@ struct Request {
     double t_final = 0.0;
     int keep_state = 0;
     size_t bytes = 0;
+    int64_t interior = 0;      // interior points
+    int64_t steps_est = 0;     // steps to t_final at the CFL step, known at submission
     // progress
     int status = 0;          // 0 queued, 1 running, 2 done, 3 failed
     nr_grid* grid = nullptr;
@@ -61,22 +72,58 @@ struct nr_server {
     void* stream = nullptr;
     int64_t next_id = 1;
     std::deque<Request*> queue;
-    std::vector<Request*> running;
+    std::vector<Request*> running;   // resident: grid allocated, not finished
+    std::vector<Request*> active;    // the running requests the batches advance
     std::map<int64_t, Request*> all;
-    nr_batch* batch = nullptr;
+    // one batch per kind of grid among the active requests (coordinate family x azimuth kind)
+    std::vector<nr_batch*> batches;
+    std::vector<std::vector<Request*>> groups;
     bool batch_dirty = true;
     size_t used = 0;
     int tile_x = 0, tile_y = 0;   // 0: autotune on every rebuild
+    int policy = NR_SERVE_FIFO;
+    int64_t max_points = 0;       // 0: no cap on the interior points advanced together
+    // at most one chunk queued behind the running one, so that a new arrival
+    // is scheduled within about a chunk of GPU time
+    cudaEvent_t chunk_done[2] = {nullptr, nullptr};
+    bool chunk_pending[2] = {false, false};
+    int chunk_slot = 0;
 };
 
 namespace {
 
 void drop_batch(nr_server* s)
 {
-    if (s->batch) nr_batch_destroy(s->batch);
-    s->batch = nullptr;
+    for (nr_batch* b : s->batches) nr_batch_destroy(b);
+    s->batches.clear();
+    s->groups.clear();
     s->batch_dirty = true;
 }
+
+// After a chunk has been enqueued: mark its end, then wait for the chunk
+// before it, which bounds the work queued ahead of the scheduler.
+int chunk_fence(nr_server* s)
+{
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(s->device);
+    cudaError_t e = cudaSuccess;
+    for (int q = 0; q < 2 && e == cudaSuccess; q++)
+        if (!s->chunk_done[q]) e = cudaEventCreateWithFlags(&s->chunk_done[q], cudaEventDisableTiming);
+    const int me = s->chunk_slot, other = 1 - s->chunk_slot;
+    if (e == cudaSuccess) e = cudaEventRecord(s->chunk_done[me], (cudaStream_t)s->stream);
+    if (e == cudaSuccess) s->chunk_pending[me] = true;
+    if (e == cudaSuccess && s->chunk_pending[other]) {
+        e = cudaEventSynchronize(s->chunk_done[other]);
+        s->chunk_pending[other] = false;
+    }
+    s->chunk_slot = other;
+    cudaSetDevice(prev);
+    return e == cudaSuccess ? NR_OK : nrk_fail(NR_ECUDA, "server chunk fence: %s", cudaGetErrorString(e));
+}
+
+// grids that can share one batch: same coordinate family and azimuth kind
+int grid_kind(const nr_grid* g) { return 2 * g->K.fam + (g->K.ax >= 0 ? 1 : 0); }
 
 int start_request(nr_server* s, Request* r)
 {
@@ -114,22 +161,45 @@ int finish_request(nr_server* s, Request* r)
     return NR_OK;
 }
 
-// admit queued requests in arrival order while budget and slots allow
+// work left, in point-steps; ties broken by arrival (id)
+bool srpt_before(const Request* a, const Request* b)
+{
+    const int64_t wa = (a->steps_total - a->steps_done) * a->interior;
+    const int64_t wb = (b->steps_total - b->steps_done) * b->interior;
+    return wa != wb ? wa < wb : a->id < b->id;
+}
+
+// position in the queue of the request the policy admits next
+size_t next_queued(const nr_server* s)
+{
+    if (s->policy != NR_SERVE_SRPT) return 0;
+    size_t best = 0;
+    for (size_t q = 1; q < s->queue.size(); q++) {
+        const Request* a = s->queue[q];
+        const Request* b = s->queue[best];
+        const int64_t wa = a->steps_est * a->interior, wb = b->steps_est * b->interior;
+        if (wa < wb || (wa == wb && a->id < b->id)) best = q;
+    }
+    return best;
+}
+
+// make queued requests resident, in policy order, while budget and slots allow
 int admit(nr_server* s)
 {
     while (!s->queue.empty()) {
-        Request* r = s->queue.front();
+        const size_t pos = next_queued(s);
+        Request* r = s->queue[pos];
         if ((int)s->running.size() >= s->max_slots) break;
         if (s->used + r->bytes > s->budget) {
             if (s->running.empty())  // can never fit
             {
                 r->status = 3;
-                s->queue.pop_front();
+                s->queue.erase(s->queue.begin() + pos);
                 continue;
             }
             break;
         }
-        s->queue.pop_front();
+        s->queue.erase(s->queue.begin() + pos);
         if (start_request(s, r) != NR_OK) {
             r->status = 3;
             continue;
@@ -141,23 +211,59 @@ int admit(nr_server* s)
     return NR_OK;
 }
 
+// the running requests the next chunk advances: the longest prefix of the
+// policy order within the points cap (never empty while any request runs)
+void select_active(nr_server* s)
+{
+    std::vector<Request*> order = s->running;
+    if (s->policy == NR_SERVE_SRPT)
+        std::sort(order.begin(), order.end(), srpt_before);
+    else
+        std::sort(order.begin(), order.end(), [](const Request* a, const Request* b) { return a->id < b->id; });
+    std::vector<Request*> sel;
+    int64_t pts = 0;
+    for (Request* r : order) {
+        if (!sel.empty() && s->max_points > 0 && pts + r->interior > s->max_points) break;
+        sel.push_back(r);
+        pts += r->interior;
+    }
+    if (sel != s->active) {
+        s->active = sel;
+        s->batch_dirty = true;
+    }
+}
+
 int rebuild_batch(nr_server* s)
 {
     drop_batch(s);
-    if (s->running.empty()) return NR_OK;
-    std::vector<nr_grid*> g;
-    std::vector<double> dts;
-    for (Request* r : s->running) {
-        g.push_back(r->grid);
-        dts.push_back(r->dt);
+    if (s->active.empty()) return NR_OK;
+    std::map<int, size_t> slot;
+    for (Request* r : s->active) {
+        const int k = grid_kind(r->grid);
+        auto it = slot.find(k);
+        if (it == slot.end()) {
+            it = slot.emplace(k, s->groups.size()).first;
+            s->groups.emplace_back();
+        }
+        s->groups[it->second].push_back(r);
     }
-    int rc = nr_batch_create(g.data(), (int)g.size(), &s->batch);
-    if (rc) return rc;
-    if (s->tile_x > 0)
-        rc = nr_batch_set_tile(s->batch, s->tile_x, s->tile_y);
-    else
-        rc = nr_batch_autotune(s->batch, dts.data(), nullptr, nullptr, nullptr);
-    if (rc) return rc;
+    for (const auto& grp : s->groups) {
+        std::vector<nr_grid*> g;
+        std::vector<double> dts;
+        for (Request* r : grp) {
+            g.push_back(r->grid);
+            dts.push_back(r->dt);
+        }
+        nr_batch* b = nullptr;
+        int rc = nr_batch_create(g.data(), (int)g.size(), &b);
+        if (rc) return rc;
+        s->batches.push_back(b);
+        if (s->tile_x > 0)
+            rc = nr_batch_set_tile(b, s->tile_x, s->tile_y);
+        else
+            rc = nr_batch_autotune(b, dts.data(), nullptr, nullptr, nullptr);
+        if (rc) return rc;
+    }
     s->batch_dirty = false;
     return NR_OK;
 }
@@ -182,6 +288,8 @@ void nr_server_destroy(nr_server* s)
 {
     if (!s) return;
     drop_batch(s);
+    for (int q = 0; q < 2; q++)
+        if (s->chunk_done[q]) cudaEventDestroy(s->chunk_done[q]);
     for (auto& kv : s->all) {
         if (kv.second->grid) nr_grid_destroy(kv.second->grid);
         delete kv.second;
@@ -218,9 +326,27 @@ int nr_server_submit(nr_server* s, int coords, const int Nxx[3], const nr_params
     r->t_final = t_final;
     r->keep_state = keep_state;
     r->bytes = grid_bytes_estimate(Nxx);
+    r->interior = (int64_t)Nxx[0] * Nxx[1] * Nxx[2];
+    double dt = 0.0;
+    if (nr_dt_cfl(coords, Nxx, params, &dt) != NR_OK || !(dt > 0.0)) {
+        delete r;
+        s->next_id--;
+        return nrk_fail(NR_EINVAL, "request grid has no valid CFL step");
+    }
+    r->steps_est = std::max<int64_t>(1, (int64_t)ceil(t_final / dt - 1e-9));
     s->queue.push_back(r);
     s->all[r->id] = r;
     if (id_out) *id_out = r->id;
+    return NR_OK;
+}
+
+int nr_server_set_policy(nr_server* s, int policy, int64_t max_batch_points)
+{
+    if (!s) return nrk_fail(NR_EINVAL, "server is NULL");
+    if ((policy != NR_SERVE_FIFO && policy != NR_SERVE_SRPT) || max_batch_points < 0)
+        return nrk_fail(NR_EINVAL, "bad nr_server_set_policy arguments");
+    s->policy = policy;
+    s->max_points = max_batch_points;
     return NR_OK;
 }
 
@@ -230,15 +356,19 @@ int nr_server_advance(nr_server* s, int nsteps, int* n_running, int* n_queued)
     int rc = admit(s);
     int left = nsteps;
     while (left > 0 && !s->running.empty()) {
+        select_active(s);
         if (s->batch_dirty && (rc = rebuild_batch(s))) return rc;
         int64_t k = left;
-        for (Request* r : s->running) k = std::min(k, r->steps_total - r->steps_done);
-        std::vector<double> dts;
-        for (Request* r : s->running) dts.push_back(r->dt);
-        if ((rc = nr_batch_rk4_step(s->batch, dts.data(), (int)k))) return rc;
+        for (Request* r : s->active) k = std::min(k, r->steps_total - r->steps_done);
+        for (size_t q = 0; q < s->batches.size(); q++) {
+            std::vector<double> dts;
+            for (Request* r : s->groups[q]) dts.push_back(r->dt);
+            if ((rc = nr_batch_rk4_step(s->batches[q], dts.data(), (int)k))) return rc;
+        }
+        if ((rc = chunk_fence(s))) return rc;
         left -= (int)k;
         bool retired = false;
-        for (Request* r : s->running) r->steps_done += k;
+        for (Request* r : s->active) r->steps_done += k;
         for (size_t q = 0; q < s->running.size();) {
             Request* r = s->running[q];
             if (r->steps_done >= r->steps_total) {
@@ -253,6 +383,7 @@ int nr_server_advance(nr_server* s, int nsteps, int* n_running, int* n_queued)
             }
         }
         if (retired) {
+            s->active.clear();
             s->batch_dirty = true;
             admit(s);
         }

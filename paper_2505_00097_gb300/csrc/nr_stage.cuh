@@ -80,8 +80,9 @@ __device__ __forceinline__ int gf_type(int g)
 }
 
 // one interior point (interior-relative i in [0,N0), j = i1 + N1 i2 in [0, N1 N2)) of an RK stage:
-// right-hand side, upwinded advection, dissipation and the stage epilogue
-template <int FAM>
+// right-hand side, upwinded advection, dissipation and the stage epilogue.  AX: the azimuthal axis
+// when it holds two points (G.ax), else -1
+template <int FAM, int AX>
 __device__ __forceinline__ void rhs_point_stage(const GridK& G, const double* __restrict__ yin, double* out,
                                                 const double* yn, double* acc, const Stage& st, int i, int j)
 {
@@ -93,10 +94,13 @@ __device__ __forceinline__ void rhs_point_stage(const GridK& G, const double* __
     P.st[0] = 1;
     P.st[1] = G.n0;
     P.st[2] = (long)G.n0 * G.n1;
+    if constexpr (AX == 1) P.ox = p1 == G.NG ? P.st[1] : -P.st[1];
+    else if constexpr (AX == 2) P.ox = p2 == G.NG ? P.st[2] : -P.st[2];
+    else P.ox = 0;
     P.g = make_geo<FAM>(G, p0, p1, p2);
     double k[NGF];
-    rhs_core<FAM>(P, G.eta, k);
-    add_adv_ko(P.y, G.T, P.st, P.g.D, G.sigma, k);
+    rhs_core<FAM, AX>(P, G.eta, k);
+    add_adv_ko<AX>(P.y, G.T, P.st, P.ox, P.g.D, G.sigma_metric, G.sigma_gauge, k);
     stage_store(st, G.T, idx, k, yn, out, acc);
 }
 

@@ -36,11 +36,21 @@ def _cyl_runs():
     return runs
 
 
-def _sph_runs():
+def _sph_runs(three_d=False):
     runs = []
-    for k, N in enumerate([(20, 8, 2), (13, 6, 4), (30, 10, 2)]):
+    shapes = [(13, 6, 4), (11, 8, 6), (9, 5, 8)] if three_d else [(20, 8, 2), (13, 6, 2), (30, 10, 2)]
+    for k, N in enumerate(shapes):
         s = W.sinh_spherical(N)
         s.update(masses=(1.0,), positions=((0, 0, 0.01 * k),), perturb=1e-8 * (k + 1))
+        runs.append(s)
+    return runs
+
+
+def _cyl3d_runs():
+    runs = []
+    for k, (nr, nphi) in enumerate([(12, 4), (17, 6), (9, 8)]):
+        s = W.sinh_cylindrical((nr, nphi, 2 * nr + k), rho_max=30.0, z_max=30.0)
+        s.update(masses=(0.6, 0.4), positions=((0.1, 0, 0.4), (0, 0.05, -0.6)))
         runs.append(s)
     return runs
 
@@ -84,11 +94,22 @@ def test_batched_cylindrical_bitwise_equals_single_grid(tile):
 
 
 @pytest.mark.parametrize("tile", [(32, 4), (16, 8), (32, 1)], ids=["32x4", "16x8", "32x1"])
-def test_batched_spherical_bitwise_equals_single_grid(tile):
-    runs = _sph_runs()
+@pytest.mark.parametrize("three_d", [False, True], ids=["nphi2", "3d"])
+def test_batched_spherical_bitwise_equals_single_grid(tile, three_d):
+    runs = _sph_runs(three_d)
     ref, _ = _states(runs, 5, batched=False)
     got, _ = _states(runs, 5, batched=True, tile=tile)
     for a, b in zip(got, ref):
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("tile", [(32, 4), (64, 1)], ids=["32x4", "64x1"])
+def test_batched_cylindrical_3d_bitwise_equals_single_grid(tile):
+    runs = _cyl3d_runs()
+    ref, _ = _states(runs, 4, batched=False)
+    got, _ = _states(runs, 4, batched=True, tile=tile)
+    for a, b in zip(got, ref):
+        assert np.all(np.isfinite(a))
         assert np.array_equal(a, b)
 
 
@@ -115,3 +136,6 @@ def test_mixed_families_rejected():
         B.Batch([g1, g2])
     with pytest.raises(B.NrError):
         B.Batch([g1, g1])
+    g3 = B.Grid(W.sinh_cylindrical((8, 4, 16), rho_max=10.0, z_max=10.0))   # four-point azimuth
+    with pytest.raises(B.NrError, match="azimuth"):
+        B.Batch([g1, g3])

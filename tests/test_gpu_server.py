@@ -91,3 +91,76 @@ def test_autotuned_server_and_oversized_request():
     ref, n, T = _alone(reqs[0], 0.5)
     assert np.array_equal(srv.fetch_state(rid, 24 * T), ref)
     srv.close()
+
+
+def _run_until_done(srv, rid, step=1):
+    for _ in range(10000):
+        srv.advance(step)
+        if srv.poll(rid)["status"] in (2, 3):
+            return
+    raise AssertionError("request did not finish")
+
+
+def test_srpt_preempts_a_long_request_and_keeps_results():
+    long_spec, short_spec = _requests()[3], _requests()[0]   # 24x2x48 two punctures, 12x2x24 one
+    t_final = 0.8
+    srv = B.Server(int(80 * 2 ** 30), 8)
+    srv.set_tile(32, 4)
+    srv.set_policy("srpt", 1)          # one request at a time, least remaining work first
+    a = srv.submit(long_spec, t_final, keep_state=True)
+    srv.advance(2)
+    assert srv.poll(a)["steps_done"] == 2
+    b = srv.submit(short_spec, t_final, keep_state=True)
+    _run_until_done(srv, b)
+    assert srv.poll(b)["status"] == 2
+    assert srv.poll(a)["steps_done"] == 2      # paused while the shorter request ran
+    _run_until_done(srv, a, step=7)
+    for rid, spec in ((a, long_spec), (b, short_spec)):
+        ref, n, T = _alone(spec, t_final)
+        assert srv.poll(rid)["steps_done"] == n
+        assert np.array_equal(srv.fetch_state(rid, 24 * T), ref)
+    srv.close()
+
+
+def test_fifo_with_a_points_cap_runs_in_arrival_order():
+    first, second = _requests()[0], _requests()[3]
+    t_final = 0.8
+    srv = B.Server(int(80 * 2 ** 30), 8)
+    srv.set_tile(32, 4)
+    nfirst = first["N"][0] * first["N"][1] * first["N"][2]
+    srv.set_policy("fifo", nfirst)     # room for the first request only
+    a = srv.submit(first, t_final, keep_state=True)
+    b = srv.submit(second, t_final, keep_state=True)
+    srv.advance(1)
+    assert srv.poll(b)["status"] == 1 and srv.poll(b)["steps_done"] == 0   # resident, not advanced
+    _run_until_done(srv, a)
+    assert srv.poll(b)["steps_done"] == 0
+    _run_until_done(srv, b, step=5)
+    for rid, spec in ((a, first), (b, second)):
+        ref, n, T = _alone(spec, t_final)
+        assert np.array_equal(srv.fetch_state(rid, 24 * T), ref)
+    srv.close()
+
+
+def test_requests_of_every_kind_share_one_server():
+    """Cylindrical grids with a two-point and with a wider azimuth and a spherical grid run in one
+    server (one batch per kind of grid); each result is bitwise its result alone."""
+    a = W.sinh_cylindrical((14, 2, 28), rho_max=30.0, z_max=30.0)
+    a.update(masses=(1.0,), positions=((0, 0, 0),))
+    b = W.sinh_cylindrical((10, 4, 20), rho_max=30.0, z_max=30.0)
+    b.update(masses=(0.5, 0.5), positions=((0, 0.1, 0.5), (0, 0, -0.5)))
+    c = W.sinh_spherical((16, 8, 2))
+    c.update(masses=(1.0,), positions=((0, 0, 0),))
+    t_final = 0.3
+    srv = B.Server(int(80 * 2 ** 30), 8)
+    srv.set_tile(32, 4)
+    ids = [srv.submit(spec, t_final, keep_state=True) for spec in (a, b, c)]
+    for _ in range(1000):
+        nrun, nq = srv.advance(4)
+        if nrun == 0 and nq == 0:
+            break
+    for rid, spec in zip(ids, (a, b, c)):
+        assert srv.poll(rid)["status"] == 2
+        ref, n, T = _alone(spec, t_final)
+        assert np.array_equal(srv.fetch_state(rid, 24 * T), ref)
+    srv.close()

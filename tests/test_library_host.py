@@ -84,3 +84,31 @@ def test_maps_bit_exact_vs_oracle(spec):
                                   W.sinh_spherical((24, 12, 8))], ids=["c1", "c2", "sph", "sph3d"])
 def test_dt_cfl_vs_oracle(spec):
     assert B.dt_cfl(spec) == pytest.approx(Oracle(spec).dt(), rel=1e-15)
+
+
+def test_server_queue_and_policy_arguments_on_the_host():
+    srv = B.Server(2 ** 30, 4)
+    with pytest.raises(B.NrError):
+        srv.set_policy("lifo")
+    assert B.lib().nr_server_set_policy(srv.h, 1, -1) == 1
+    srv.set_policy("srpt", 10 ** 6)
+    spec = W.sinh_cylindrical((12, 2, 24), rho_max=30.0, z_max=30.0)
+    spec.update(masses=(1.0,), positions=((0, 0, 0),))
+    rid = srv.submit(spec, 0.5)
+    info = srv.poll(rid)
+    assert info["status"] == 0 and info["steps_done"] == 0   # queued: no device work until advance
+    bad = dict(spec, N=(12, 2, 0))
+    with pytest.raises(B.NrError):
+        srv.submit(bad, 0.5)
+    srv.close()
+
+
+def test_dissipation_strengths_must_split_metric_and_gauge():
+    ok = W.sinh_cylindrical((8, 2, 16), rho_max=10.0, z_max=10.0, ko_sigma=[0.3] * 17 + [0.99] * 7)
+    dt = B.dt_cfl(ok)
+    assert dt > 0.0
+    bad = dict(ok, ko_sigma=[0.3] * 16 + [0.5] + [0.99] * 7)
+    with pytest.raises(B.NrError, match="ko_sigma"):
+        B.dt_cfl(bad)
+    with pytest.raises(B.NrError, match="ko_sigma"):
+        B.Grid(bad)
