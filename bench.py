@@ -40,13 +40,16 @@ from paper_2505_00097_gb300 import workloads as W  # noqa: E402
 METRIC = "BSSN FP64 point-updates/s (RK4 substeps)"
 UNIT = "point-updates/s"
 
-# FP64 operations (FMA = 2) per interior point of one k_rhs launch, by
-# workload (the kernel variant it runs), counted from the kernel's
-# DADD/DMUL/DFMA thread-instruction counts in one ncu capture:
-# (DADD + DMUL + 2 DFMA) / interior points.  Head-on 256x2x512
-# (k_rhs<cylindrical, two-point azimuth>, profiles/k_rhs_headon_256x2x512.md):
-# 417 + 372 + 2 x 1295.  A workload without a capture reports no FLOP rate.
-F_ALG = {"headon": 3379.0}
+# FP64 operations (FMA = 2) per interior point of one plain-RHS k_rhs launch,
+# by workload (the kernel variant it runs), from the kernel's DADD/DMUL/DFMA
+# thread-instruction counts in one ncu capture: (DADD + DMUL + 2 DFMA) /
+# interior points (profiles/k_rhs_headon_256x2x512.md,
+# profiles/k_rhs_general_3d.md).  Head-on 256x2x512 (cylindrical, two-point
+# azimuth): 418 + 372 + 2 x 1295.  Large 3D (spherical, general kernel):
+# 687 + 472 + 2 x 1838.  A workload without a capture reports no FLOP rate.
+F_ALG = {"headon": 3380.0, "large3d": 4835.0}
+# DRAM bytes (read + write) of that launch in the same capture, or None
+TRAFFIC = {"headon": 58760448 + 312345856}
 # FP64 pipe of one SM: 2 DFMA per clock (ncu peak_sustained of
 # sm__sass_thread_inst_executed_op_dfma_pred_on), i.e. 4 FLOP per clock
 FP64_FLOP_PER_CLK_SM = 4.0
@@ -285,7 +288,7 @@ def run_ours(args, spec, world, rank, local):
         launches = 0
         for s in range(n):
             g.rk4_step(dt, 1)
-            launches += 12
+            launches += g.info.launches_per_step
             if h_every and (start + s + 1) % h_every == 0:
                 g.hamiltonian()
                 launches += 2
@@ -342,7 +345,8 @@ def run_ours(args, spec, world, rank, local):
     roof = {"bound": "alu", "kernel": "k_rhs (FP64 BSSN RHS + KO + upwind)", "unit": "TFLOP/s",
             "peak": peak / 1e12,
             "peak_source": f"derived: 2 DFMA/clk/SM x {n_sm} SMs x {mhz:.0f} MHz (median SM clock in the timed region)",
-            "probe_tflops": probe / 1e12, "launch_ms": rhs_ms, "points_per_launch": pts, "traffic": None}
+            "probe_tflops": probe / 1e12, "launch_ms": rhs_ms, "points_per_launch": pts,
+            "traffic": TRAFFIC.get(args.workload)}
     f_alg = F_ALG.get(args.workload)
     if f_alg:
         ach = f_alg * pts / (rhs_ms * 1e-3)

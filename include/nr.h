@@ -102,6 +102,10 @@ typedef struct {
     int64_t n_inner;   /* inner ghost points (parity copies) */
     double dt_cfl;     /* cfl * min over interior points and axes of |S_d| dxx_d */
     size_t device_bytes; /* device memory held by the grid */
+    int64_t n_inner_stencil; /* inner ghosts the RK stages before the last copy (all, unless the
+                                azimuth holds two points: then its ghosts are copied in stage 4 only) */
+    int launches_per_step;   /* kernel launches of one nr_rk4_step */
+    int pad_;
 } nr_grid_info;
 
 /* Defaults: ko_sigma 0.3, eta 2, cfl 0.5, wavespeed 1, f_inf 1 for W and alpha

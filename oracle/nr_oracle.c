@@ -623,7 +623,7 @@ void orc_outer_bc(const orc_params* p, const double* gfs, double* rhs)
 /* Unrescaled coordinate-basis fields at one interior point. */
 typedef struct {
     double eps[3][3], deps[3][3][3], ddeps[3][3][3][3], adv_eps[3][3];
-    double A[3][3], adv_A[3][3];
+    double A[3][3], dA[3][3][3], adv_A[3][3];   /* dA[i][j][k] = d_k Abar_ij */
     double W, dW[3], ddW[3][3], adv_W;
     double K, dK[3], adv_K;
     double Lam[3], dLam[3][3], adv_Lam[3];   /* dLam[i][k] = d_k Lambda^i */
@@ -706,6 +706,7 @@ static void load_point(const orc_params* p, const int n[3], long T, const double
             F->A[a][b] = X[G_ADD + s];
             F->adv_A[a][b] = adv[G_ADD + s];
             for (int k = 0; k < 3; k++) {
+                F->dA[a][b][k] = dX[G_ADD + s][k];
                 F->deps[a][b][k] = dX[G_HDD + s][k];
                 for (int l = 0; l < 3; l++) F->ddeps[a][b][k][l] = ddX[G_HDD + s][k][l];
             }
@@ -1211,6 +1212,115 @@ void orc_hamiltonian(const orc_params* p, const double* gfs, double* H, double r
                 if (fabs(H[idx]) > mx) mx = fabs(H[idx]);
                 cnt++;
             }
+    if (l2) *l2 = cnt ? sqrt(s2 / cnt) : 0.0;
+    if (linf) *linf = mx;
+    if (count) *count = cnt;
+}
+
+/* Eq. Mconstraint:
+ *   M^i = e^{-4 phi} (Dhat_j Abar^{ij} + 2 Abar^{k(i} Delta^{j)}_{jk} + 6 Abar^{ij} d_j phi
+ *                     - 2/3 gammabar^{ij} d_j K),
+ * the symmetrisation taken over the free index i and the upper index j of
+ * Delta^j_{jk} before the contraction: 2 Abar^{k(i} Delta^{j)}_{jk} =
+ * Abar^{ki} Delta^j_{jk} + Abar^{kj} Delta^i_{jk}.  Dhat_j Abar^{ij} =
+ * d_j Abar^{ij} + Gammahat^i_{jm} Abar^{mj} + Gammahat^j_{jm} Abar^{im}, with
+ * d_j Abar^{ij} from the product rule on gammabar^{ik} gammabar^{jl} Abar_kl
+ * and d gammabar^{-1} = -gammabar^{-1} (d gammabar) gammabar^{-1}.
+ * Outputs (any may be NULL): M (3*T) the rescaled components S_i M^i at
+ * interior points (ghosts 0), Mnorm (T) |M| = sqrt(gamma_ij M^i M^j) with the
+ * physical metric gamma_ij = e^{4 phi} gammabar_ij, and the L2 / Linf norms of
+ * |M| over interior points with Cartesian radius in [rmin, rmax]. */
+void orc_momentum(const orc_params* p, const double* gfs, double* Mout, double* Mnorm, double rmin, double rmax,
+                  double* l2, double* linf, long* count)
+{
+    int n[3];
+    long T = orc_sizes(p, n);
+    int NG = p->NG;
+    double* mag = (double*)calloc((size_t)T, sizeof(double));
+    if (Mout)
+        for (long q = 0; q < 3 * T; q++) Mout[q] = 0.0;
+    int nt = p->nthreads;
+#ifdef _OPENMP
+    if (nt <= 0) nt = omp_get_max_threads();
+#pragma omp parallel for collapse(2) schedule(static) num_threads(nt)
+#endif
+    for (int k = 0; k < p->N[2]; k++)
+        for (int j = 0; j < p->N[1]; j++)
+            for (int i = 0; i < p->N[0]; i++) {
+                int ii[3] = {i + NG, j + NG, k + NG};
+                long idx = ii[0] + (long)n[0] * (ii[1] + (long)n[1] * ii[2]);
+                double xx[3] = {orc_xx(p, 0, ii[0]), orc_xx(p, 1, ii[1]), orc_xx(p, 2, ii[2])};
+                rfm_pt R;
+                refmet M;
+                pt_fields F;
+                geom_pt G;
+                rfm_eval(p, xx, &R);
+                refmet_from(&R, &M);
+                load_point(p, n, T, gfs, idx, &R, &F);
+                geometry(&M, &F, &G);
+                /* d_m gammabar^{ab} */
+                double dgi[3][3][3];
+                for (int a = 0; a < 3; a++)
+                    for (int b = 0; b < 3; b++)
+                        for (int m = 0; m < 3; m++) {
+                            double t = 0.0;
+                            for (int c = 0; c < 3; c++)
+                                for (int d = 0; d < 3; d++)
+                                    t += G.gbinv[a][c] * (M.dg[c][d][m] + F.deps[c][d][m]) * G.gbinv[d][b];
+                            dgi[a][b][m] = -t;
+                        }
+                double Mv[3];
+                for (int a = 0; a < 3; a++) {
+                    /* Dhat_j Abar^{aj} */
+                    double div = 0.0;
+                    for (int b = 0; b < 3; b++) {
+                        double dAuu = 0.0; /* d_b Abar^{ab} */
+                        for (int c = 0; c < 3; c++)
+                            for (int d = 0; d < 3; d++)
+                                dAuu += dgi[a][c][b] * G.gbinv[b][d] * F.A[c][d] +
+                                        G.gbinv[a][c] * dgi[b][d][b] * F.A[c][d] +
+                                        G.gbinv[a][c] * G.gbinv[b][d] * F.dA[c][d][b];
+                        div += dAuu;
+                        for (int m = 0; m < 3; m++)
+                            div += M.Gam[a][b][m] * G.Auu[m][b] + M.Gam[b][b][m] * G.Auu[a][m];
+                    }
+                    /* Abar^{ka} Delta^j_{jk} + Abar^{kj} Delta^a_{jk} */
+                    double dterm = 0.0;
+                    for (int b = 0; b < 3; b++)
+                        for (int c = 0; c < 3; c++)
+                            dterm += G.Auu[c][a] * G.Dup[b][b][c] + G.Auu[c][b] * G.Dup[a][b][c];
+                    double ph = 0.0, kk = 0.0;
+                    for (int b = 0; b < 3; b++) {
+                        ph += G.Auu[a][b] * G.dphi[b];
+                        kk += G.gbinv[a][b] * F.dK[b];
+                    }
+                    Mv[a] = F.W * F.W * (div + dterm + 6.0 * ph - (2.0 / 3.0) * kk);
+                }
+                double q = 0.0;
+                for (int a = 0; a < 3; a++)
+                    for (int b = 0; b < 3; b++) q += G.gb[a][b] * Mv[a] * Mv[b];
+                mag[idx] = sqrt(q) / F.W;
+                if (Mout)
+                    for (int a = 0; a < 3; a++) Mout[a * T + idx] = Mv[a] * R.S[a];
+            }
+    (void)nt;
+    double s2 = 0.0, mx = 0.0;
+    long cnt = 0;
+    for (int k = 0; k < p->N[2]; k++)
+        for (int j = 0; j < p->N[1]; j++)
+            for (int i = 0; i < p->N[0]; i++) {
+                long idx = (i + NG) + (long)n[0] * ((j + NG) + (long)n[1] * (k + NG));
+                double x[3];
+                orc_cart(p, idx, x);
+                double r = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+                if (r < rmin || r > rmax) continue;
+                s2 += mag[idx] * mag[idx];
+                if (mag[idx] > mx) mx = mag[idx];
+                cnt++;
+            }
+    if (Mnorm)
+        for (long q = 0; q < T; q++) Mnorm[q] = mag[q];
+    free(mag);
     if (l2) *l2 = cnt ? sqrt(s2 / cnt) : 0.0;
     if (linf) *linf = mx;
     if (count) *count = cnt;

@@ -87,6 +87,11 @@ int orc_rk4_step(const orc_params* p, double* gfs, double dt, int nsteps);
  * Linf over interior points with Cartesian radius in [rmin, rmax]. */
 void orc_hamiltonian(const orc_params* p, const double* gfs, double* H, double rmin, double rmax,
                      double* l2, double* linf, long* count);
+/* Momentum constraint, Eq. Mconstraint (see nr_oracle.c): rescaled S_i M^i
+ * (3*T, interior points; may be NULL), |M| with the physical metric (T; may be
+ * NULL) and its L2 / Linf norms over the radius band [rmin, rmax]. */
+void orc_momentum(const orc_params* p, const double* gfs, double* M, double* Mnorm, double rmin, double rmax,
+                  double* l2, double* linf, long* count);
 
 /* Generic classic RK4 (used by orc_rk4_step; exported for its pin). */
 typedef void (*orc_rhs_fn)(void* ctx, const double* y, double* k);

@@ -95,6 +95,8 @@ def lib() -> ctypes.CDLL:
         L.orc_rk4_step.restype = ctypes.c_int
         L.orc_hamiltonian.argtypes = [P, dp, dp, ctypes.c_double, ctypes.c_double, dp, dp,
                                       ctypes.POINTER(ctypes.c_long)]
+        L.orc_momentum.argtypes = [P, dp, dp, dp, ctypes.c_double, ctypes.c_double, dp, dp,
+                                   ctypes.POINTER(ctypes.c_long)]
         L.orc_rk4_generic.argtypes = [ctypes.c_long, dp, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]
         for name in ("orc_d1", "orc_d2", "orc_ko6"):
             getattr(L, name).restype = ctypes.c_double
@@ -235,6 +237,15 @@ class Oracle:
         self.L.orc_hamiltonian(ctypes.byref(self.p), _dp(y), _dp(H), float(rmin), float(rmax),
                                ctypes.byref(l2), ctypes.byref(linf), ctypes.byref(cnt))
         return H, l2.value, linf.value, cnt.value
+
+    def momentum(self, y: np.ndarray, rmin: float = 0.0, rmax: float = 1e300):
+        """Eq. Mconstraint: rescaled S_i M^i (3, T), |M| (T), and the L2 / Linf norms of |M| over the band."""
+        M = np.zeros(3 * self.T)
+        mag = np.zeros(self.T)
+        l2 = ctypes.c_double(); linf = ctypes.c_double(); cnt = ctypes.c_long()
+        self.L.orc_momentum(ctypes.byref(self.p), _dp(y), _dp(M), _dp(mag), float(rmin), float(rmax),
+                            ctypes.byref(l2), ctypes.byref(linf), ctypes.byref(cnt))
+        return M.reshape(3, self.T), mag, l2.value, linf.value, cnt.value
 
     def interior_mask(self) -> np.ndarray:
         NG = self.NG

@@ -67,6 +67,9 @@ class NrGridInfo(ctypes.Structure):
         ("n_inner", ctypes.c_int64),
         ("dt_cfl", ctypes.c_double),
         ("device_bytes", ctypes.c_size_t),
+        ("n_inner_stencil", ctypes.c_int64),
+        ("launches_per_step", ctypes.c_int),
+        ("pad_", ctypes.c_int),
     ]
 
 

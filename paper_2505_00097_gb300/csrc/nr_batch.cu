@@ -45,6 +45,7 @@ struct nr_batch {
     BGrid* d_grids = nullptr;
     BInner* d_inner = nullptr;
     int n_inner = 0;
+    int n_inner_stencil = 0;   // the entries the stages before the last copy
     int* d_counter = nullptr;
     std::vector<double> dts;   // dts of the current table
     bool table_ok = false;
@@ -116,9 +117,10 @@ cudaError_t enqueue_step(nr_batch* b, cudaStream_t s)
     cudaError_t e = cudaMemsetAsync(b->d_counter, 0, 4 * sizeof(int), s);
     for (int stage = 0; stage < 4 && e == cudaSuccess; stage++) {
         e = enqueue_stage_launch(b, stage, s);
-        if (e == cudaSuccess && b->n_inner) {
-            dim3 grd((b->n_inner + 255) / 256, NR_NGF);
-            k_batch_inner<<<grd, 256, 0, s>>>(b->d_grids, b->d_inner, b->n_inner, stage);
+        const int ninner = stage == 3 ? b->n_inner : b->n_inner_stencil;
+        if (e == cudaSuccess && ninner) {
+            dim3 grd((ninner + 255) / 256, NR_NGF);
+            k_batch_inner<<<grd, 256, 0, s>>>(b->d_grids, b->d_inner, ninner, stage);
             e = cudaGetLastError();
         }
     }
@@ -165,17 +167,29 @@ int nr_batch_create(nr_grid* const* grids, int ngrids, nr_batch** out)
     b->device = grids[0]->device;
     b->stream = grids[0]->stream;
     DevGuard dg(b->device);
-    std::vector<BInner> inner;
+    // parity copies of all grids: those the RK-stage stencils read first (every
+    // ghost, unless the azimuth holds two points), then the azimuthal ghosts,
+    // which only the last stage copies -- the same split as the single-grid path
+    std::vector<BInner> inner, rest;
     for (int q = 0; q < ngrids; q++) {
         const nr_grid* g = grids[q];
+        const int ax = g->K.ax, n0 = g->K.n0, n1 = g->K.n1;
         for (long idx = 0; idx < g->geo.T; idx++) {
             if (g->cls[idx] != 2) continue;
             int m = 0;
             for (int t = 0; t < 10; t++)
                 if (g->par[10 * idx + t] < 0) m |= 1 << t;
-            inner.push_back(BInner{q, (int)idx, g->src[idx], m});
+            const BInner e{q, (int)idx, g->src[idx], m};
+            bool read = true;
+            if (ax >= 0) {
+                const int ia = ax == 1 ? (int)((idx / n0) % n1) : (int)(idx / ((long)n0 * n1));
+                read = ia >= g->K.NG && ia < g->K.NG + (ax == 1 ? g->K.N1 : g->K.N2);
+            }
+            (read ? inner : rest).push_back(e);
         }
     }
+    b->n_inner_stencil = (int)inner.size();
+    inner.insert(inner.end(), rest.begin(), rest.end());
     b->n_inner = (int)inner.size();
     cudaError_t e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_grids, sizeof(BGrid) * ngrids);

@@ -254,6 +254,14 @@ double dt_cfl_host(const HostGeom& G, const nr_params& p)
     return p.cfl * std::min(m0, std::min(m1, m2));
 }
 
+// the azimuthal axis when it holds two points (1 cylindrical-like, 2 spherical-like), else -1
+int two_point_axis(const HostGeom& G)
+{
+    if (G.fam == FAM_CYL && G.N[1] == 2) return 1;
+    if (G.fam == FAM_SPH && G.N[2] == 2) return 2;
+    return -1;
+}
+
 int check_args(int coords, const int Nxx[3], const nr_params* p)
 {
     if (coords != NR_SINH_SPHERICAL && coords != NR_SINH_CYLINDRICAL && coords != NR_SPHERICAL)
@@ -328,12 +336,18 @@ struct DeviceGuard {
     ~DeviceGuard() { cudaSetDevice(prev); }
 };
 
+// one RK stage: interior right-hand side and radiation condition in one launch,
+// then the parity copies (ninner: the first entries of the inner list)
 int enqueue_stage(nr_grid* g, cudaStream_t s, const double* yin, double* out, const double* yn, double* acc,
-                  Stage st)
+                  Stage st, int ninner)
 {
-    CUDA_OR_FAIL(launch_rhs(g->K, yin, out, yn, acc, st, s));
-    CUDA_OR_FAIL(launch_outer(g->K, g->outer, g->n_outer, yin, out, yn, acc, g->finf, g->wspeed, st, s));
-    CUDA_OR_FAIL(launch_inner(g->K, g->inner, g->n_inner, out, s));
+    OuterArgs oa;
+    oa.pts = g->outer;
+    oa.npts = g->n_outer;
+    oa.finf = g->finf;
+    oa.wspeed = g->wspeed;
+    CUDA_OR_FAIL(launch_rhs(g->K, yin, out, yn, acc, st, s, oa));
+    CUDA_OR_FAIL(launch_inner(g->K, g->inner, ninner, out, s));
     return NR_OK;
 }
 
@@ -347,10 +361,12 @@ int enqueue_rk4(nr_grid* g, cudaStream_t s, double dt)
     Stage s3{MODE_STAGE23, enf, dt, dt / 3.0};
     Stage s4{MODE_STAGE4, enf, 0.0, dt / 6.0};
     int rc;
-    if ((rc = enqueue_stage(g, s, g->y, g->ya, g->y, g->acc, s1))) return rc;
-    if ((rc = enqueue_stage(g, s, g->ya, g->yb, g->y, g->acc, s2))) return rc;
-    if ((rc = enqueue_stage(g, s, g->yb, g->ya, g->y, g->acc, s3))) return rc;
-    if ((rc = enqueue_stage(g, s, g->ya, g->y, nullptr, g->acc, s4))) return rc;
+    // the intermediate states need only the ghosts the stencils read; y_{n+1} gets all
+    const int ns = g->n_inner_stencil;
+    if ((rc = enqueue_stage(g, s, g->y, g->ya, g->y, g->acc, s1, ns))) return rc;
+    if ((rc = enqueue_stage(g, s, g->ya, g->yb, g->y, g->acc, s2, ns))) return rc;
+    if ((rc = enqueue_stage(g, s, g->yb, g->ya, g->y, g->acc, s3, ns))) return rc;
+    if ((rc = enqueue_stage(g, s, g->ya, g->y, nullptr, g->acc, s4, g->n_inner))) return rc;
     return NR_OK;
 }
 
@@ -479,6 +495,17 @@ int nr_grid_create(int coords, const int Nxx[3], const nr_params* params, nr_gri
             inner.push_back(q);
         }
     }
+    // ghosts the RK-stage stencils read first: with a two-point azimuth (GridK::ax) the
+    // stencils of interior and pure-outer points never reach an azimuthal ghost
+    const int ax = two_point_axis(G);
+    auto read_by_stencils = [&](const InnerPt& q) {
+        if (ax < 0) return true;
+        const long idx = q.dst;
+        const int ia = ax == 1 ? (int)((idx / n0) % n1) : (int)(idx / ((long)n0 * n1));
+        return ia >= G.NG && ia < G.NG + G.N[ax];
+    };
+    std::stable_partition(inner.begin(), inner.end(), read_by_stencils);
+    g->n_inner_stencil = (int)std::count_if(inner.begin(), inner.end(), read_by_stencils);
     g->n_outer = (int)outer.size();
     g->n_inner = (int)inner.size();
     g->n_canon = (long)canon.size();
@@ -513,7 +540,7 @@ int nr_grid_create(int coords, const int Nxx[3], const nr_params* params, nr_gri
     K.N0 = G.N[0]; K.N1 = G.N[1]; K.N2 = G.N[2];
     K.NG = G.NG;
     K.fam = G.fam;
-    K.ax = (G.fam == FAM_CYL && G.N[1] == 2) ? 1 : (G.fam == FAM_SPH && G.N[2] == 2) ? 2 : -1;
+    K.ax = two_point_axis(G);
     K.T = G.T;
     for (int d = 0; d < 3; d++) {
         K.inv12dx[d] = 1.0 / (12.0 * G.dxx[d]);
@@ -574,6 +601,10 @@ int nr_query(const nr_grid* g, nr_grid_info* info)
     info->n_inner = g->n_inner;
     info->dt_cfl = g->dt_cfl;
     info->device_bytes = g->bytes;
+    info->n_inner_stencil = g->n_inner_stencil;
+    // per stage: k_rhs (interior + pure-outer points), then k_inner if it has entries
+    info->launches_per_step = 4 + 3 * (g->n_inner_stencil > 0) + (g->n_inner > 0);
+    info->pad_ = 0;
     return NR_OK;
 }
 

@@ -63,9 +63,19 @@ struct Stage {
     double cacc;        // acc (=|+=) cacc * k; stage 4: y_n = acc + cacc * k
 };
 
+// Pure-outer points whose radiation condition runs inside the k_rhs launch
+// of an RK stage (extra blocks ahead of the interior tiles).
+struct OuterArgs {
+    const OuterPt* pts = nullptr;
+    int npts = 0;
+    int nblocks = 0;    // set by launch_rhs
+    const double* finf = nullptr;
+    const double* wspeed = nullptr;
+};
+
 // kernel launchers (nr_kernels.cu)
 cudaError_t launch_rhs(const GridK& G, const double* yin, double* out, const double* yn, double* acc, Stage st,
-                       cudaStream_t s);
+                       cudaStream_t s, OuterArgs oa = OuterArgs());
 cudaError_t launch_outer(const GridK& G, const OuterPt* pts, int npts, const double* yin, double* out,
                          const double* yn, double* acc, const double* finf, const double* wspeed, Stage st,
                          cudaStream_t s);
@@ -114,6 +124,10 @@ struct nr_grid {
     int* flag = nullptr;
     double* mxyz = nullptr;
     int n_outer = 0, n_inner = 0, nparts = 0;
+    // inner ghosts read by the stencils of an RK stage: the first n_inner_stencil
+    // entries of inner (all of them unless the azimuth holds two points; then the
+    // azimuthal ghosts, read by nothing within a step, are copied in stage 4 only)
+    int n_inner_stencil = 0;
     long n_canon = 0;
     size_t bytes = 0;
     double dt_cfl = 0.0;

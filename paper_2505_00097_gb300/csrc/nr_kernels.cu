@@ -2,8 +2,10 @@
 //
 //   k_rhs     interior right-hand side (Sec. 2.1 equations, upwinded advection,
 //             Kreiss-Oliger dissipation) with the RK4 stage update and the
-//             det(gammabar) enforcement fused into its epilogue
-//   k_outer   radiation condition at pure-outer ghosts (Sec. 3), same epilogue
+//             det(gammabar) enforcement fused into its epilogue; in an RK
+//             stage its first blocks also run the radiation condition at the
+//             pure-outer ghosts (Sec. 3) with the same epilogue
+//   k_outer   the radiation condition alone (nr_apply_bcs)
 //   k_inner   parity copies at inner ghosts (Sec. 3), one warp-coalesced gather
 //             per gridfunction
 //   k_bl      Brill-Lindquist data + SplitMix64 perturbation
@@ -23,12 +25,19 @@ constexpr int RHS_BX = 32, RHS_BY = 4;
 
 template <int FAM, int AX>
 __global__ void __launch_bounds__(RHS_BX* RHS_BY) k_rhs(GridK G, const double* __restrict__ yin, double* out,
-                                                        const double* yn, double* acc, Stage st)
+                                                        const double* yn, double* acc, Stage st, OuterArgs oa)
 {
-    // blocks tile (i0, j = i1 + N1 i2) in 32 x 4 points, flattened into blockIdx.x
+    // the first oa.nblocks blocks take the pure-outer points, 128 per block
+    if ((int)blockIdx.x < oa.nblocks) {
+        const int t = (int)blockIdx.x * (RHS_BX * RHS_BY) + threadIdx.y * RHS_BX + threadIdx.x;
+        if (t < oa.npts) outer_point_stage<FAM>(G, oa.pts[t], yin, out, yn, acc, oa.finf, oa.wspeed, st);
+        return;
+    }
+    // the others tile (i0, j = i1 + N1 i2) in 32 x 4 points, flattened into the block index
+    const int b = (int)blockIdx.x - oa.nblocks;
     const int nbx = (G.N0 + RHS_BX - 1) / RHS_BX;
-    const int i = (int)(blockIdx.x % nbx) * RHS_BX + threadIdx.x;
-    const int j = (int)(blockIdx.x / nbx) * RHS_BY + threadIdx.y;
+    const int i = (b % nbx) * RHS_BX + threadIdx.x;
+    const int j = (b / nbx) * RHS_BY + threadIdx.y;
     if (i >= G.N0 || j >= G.N1 * G.N2) return;
     rhs_point_stage<FAM, AX>(G, yin, out, yn, acc, st, i, j);
 }
@@ -203,17 +212,18 @@ cudaError_t launch_fp64_probe(int blocks, int iters, double* sink, cudaStream_t 
 // ------------------------------------------------------------ launchers
 
 cudaError_t launch_rhs(const GridK& G, const double* yin, double* out, const double* yn, double* acc, Stage st,
-                       cudaStream_t s)
+                       cudaStream_t s, OuterArgs oa)
 {
     dim3 blk(RHS_BX, RHS_BY);
-    const long nb = (long)((G.N0 + RHS_BX - 1) / RHS_BX) * ((G.N1 * G.N2 + RHS_BY - 1) / RHS_BY);
+    oa.nblocks = (oa.npts + RHS_BX * RHS_BY - 1) / (RHS_BX * RHS_BY);
+    const long nb = (long)((G.N0 + RHS_BX - 1) / RHS_BX) * ((G.N1 * G.N2 + RHS_BY - 1) / RHS_BY) + oa.nblocks;
     dim3 grd((unsigned)nb);
     if (G.fam == FAM_SPH) {
-        if (G.ax == 2) k_rhs<FAM_SPH, 2><<<grd, blk, 0, s>>>(G, yin, out, yn, acc, st);
-        else k_rhs<FAM_SPH, -1><<<grd, blk, 0, s>>>(G, yin, out, yn, acc, st);
+        if (G.ax == 2) k_rhs<FAM_SPH, 2><<<grd, blk, 0, s>>>(G, yin, out, yn, acc, st, oa);
+        else k_rhs<FAM_SPH, -1><<<grd, blk, 0, s>>>(G, yin, out, yn, acc, st, oa);
     } else {
-        if (G.ax == 1) k_rhs<FAM_CYL, 1><<<grd, blk, 0, s>>>(G, yin, out, yn, acc, st);
-        else k_rhs<FAM_CYL, -1><<<grd, blk, 0, s>>>(G, yin, out, yn, acc, st);
+        if (G.ax == 1) k_rhs<FAM_CYL, 1><<<grd, blk, 0, s>>>(G, yin, out, yn, acc, st, oa);
+        else k_rhs<FAM_CYL, -1><<<grd, blk, 0, s>>>(G, yin, out, yn, acc, st, oa);
     }
     return cudaGetLastError();
 }
