@@ -335,6 +335,124 @@ double orc_d11(const double* f, long sa, long sb, double ha, double hb)
     return s / (144.0 * ha * hb);
 }
 
+/* Finite differences of order N_FD = 2 (NG - 1) for NG other than 3 (the
+ * production scheme of Sec. 4.1 uses N_FD = 8, NG = 5).  The weights come from
+ * Fornberg's recursion (B. Fornberg, Math. Comp. 51 (1988) 699-706) on the
+ * offsets each stencil uses:
+ *   centred first and second derivatives: -m..m (m = N_FD/2);
+ *   upwind first derivative: -(m-1)..m+1 for vet > 0, the mirror otherwise
+ *     (the centred window shifted one point upwind; N_G = m+1, Sec. 3);
+ *   one-sided first derivatives at outer ghosts: the 2m+1 window a..a+2m with
+ *     a = clamp(-m, -i, n-1-i-2m) (the centred one where it fits);
+ *   Kreiss-Oliger: the difference of order 2r = N_FD + 2 (binomial weights). */
+static void fd_weights(double x0, const double* x, int n, int mord, double* c)
+{
+    memset(c, 0, sizeof(double) * (size_t)(mord + 1) * n);
+    double c1 = 1.0, c4 = x[0] - x0;
+    c[0] = 1.0;
+    for (int i = 1; i < n; i++) {
+        int mn = i < mord ? i : mord;
+        double c2 = 1.0, c5 = c4;
+        c4 = x[i] - x0;
+        for (int j = 0; j < i; j++) {
+            double c3 = x[i] - x[j];
+            c2 *= c3;
+            if (j == i - 1) {
+                for (int k = mn; k >= 1; k--) c[k * n + i] = c1 * (k * c[(k - 1) * n + i - 1] - c5 * c[k * n + i - 1]) / c2;
+                c[i] = -c1 * c5 * c[i - 1] / c2;
+            }
+            for (int k = mn; k >= 1; k--) c[k * n + j] = (c4 * c[k * n + j] - k * c[(k - 1) * n + j]) / c3;
+            c[j] = c4 * c[j] / c3;
+        }
+        c1 = c2;
+    }
+}
+
+/* The weights are rational; each set is kept as integers over the smallest
+ * common denominator found from the recursion's doubles, so that the stencils
+ * of a constant are exactly zero (a flat metric stays exactly flat). */
+#define FD_MAXW 17
+typedef struct {
+    int m;                    /* N_FD / 2 */
+    double d1[FD_MAXW];       /* offsets -m..m: integer weights over den1, times h */
+    double d2[FD_MAXW];       /* offsets -m..m, over den2, times h^2 */
+    double up[FD_MAXW];       /* offsets -(m-1)..m+1, over denu, times h */
+    double ko[FD_MAXW + 2];   /* offsets -(m+1)..m+1 (integers) */
+    double os[FD_MAXW][FD_MAXW]; /* os[-a]: offsets a..a+2m, over deno[-a], times h */
+    double den1, den2, denu, deno[FD_MAXW];
+} fdw;
+
+/* smallest D <= 10^7 with every w D within 1e-7 of an integer; w <- round(w D) */
+static double integerise(double* w, int n)
+{
+    for (long D = 1; D <= 10000000; D++) {
+        int ok = 1;
+        for (int i = 0; i < n && ok; i++) ok = fabs(w[i] * D - nearbyint(w[i] * D)) < 1e-7;
+        if (ok) {
+            for (int i = 0; i < n; i++) w[i] = nearbyint(w[i] * D);
+            return (double)D;
+        }
+    }
+    return 0.0;
+}
+
+static double binom(int n, int k)
+{
+    double r = 1.0;
+    for (int i = 1; i <= k; i++) r = r * (n - k + i) / i;
+    return r;
+}
+
+static void fdw_make(int NG, fdw* W)
+{
+    int m = NG - 1, n = 2 * m + 1;
+    double x[FD_MAXW], c[3 * FD_MAXW];
+    memset(W, 0, sizeof *W);
+    W->m = m;
+    for (int i = 0; i < n; i++) x[i] = i - m;
+    fd_weights(0.0, x, n, 2, c);
+    for (int i = 0; i < n; i++) { W->d1[i] = c[n + i]; W->d2[i] = c[2 * n + i]; }
+    W->den1 = integerise(W->d1, n);
+    W->den2 = integerise(W->d2, n);
+    for (int i = 0; i < n; i++) x[i] = i - (m - 1);
+    fd_weights(0.0, x, n, 1, c);
+    for (int i = 0; i < n; i++) W->up[i] = c[n + i];
+    W->denu = integerise(W->up, n);
+    for (int a = 0; a <= 2 * m; a++) {
+        for (int i = 0; i < n; i++) x[i] = i - a;
+        fd_weights(0.0, x, n, 1, c);
+        for (int i = 0; i < n; i++) W->os[a][i] = c[n + i];
+        W->deno[a] = integerise(W->os[a], n);
+    }
+    int r = m + 1;
+    /* (E^(1/2) - E^(-1/2))^(2r): (-1)^(r+k) C(2r, r+k) at offset k */
+    for (int k = -r; k <= r; k++) W->ko[k + r] = (((k + r) % 2) ? -1.0 : 1.0) * binom(2 * r, k + r);
+}
+
+/* weights of the order-(2(NG-1)) stencils, for the pins: which 0 centred first
+ * derivative, 1 centred second, 2 upwind (forward), 3 Kreiss-Oliger difference,
+ * 4 one-sided with window start a; returns the number of weights */
+int orc_fd_weights(int NG, int which, int a, double* w)
+{
+    fdw W;
+    if (NG < 2 || 2 * (NG - 1) + 3 > FD_MAXW) return 0;
+    fdw_make(NG, &W);
+    int n = 2 * W.m + 1;
+    if (which == 4 && (a > 0 || a < -2 * W.m)) return 0;
+    const double* src = which == 0 ? W.d1 : which == 1 ? W.d2 : which == 2 ? W.up : which == 3 ? W.ko : W.os[-a];
+    const double den = which == 0 ? W.den1 : which == 1 ? W.den2 : which == 2 ? W.denu : which == 3 ? 1.0 : W.deno[-a];
+    if (which == 3) n += 2;
+    for (int i = 0; i < n; i++) w[i] = src[i] / den;
+    return n;
+}
+
+static double sten(const double* f, long st, const double* w, int lo, int hi)
+{
+    double s = 0.0;
+    for (int k = lo; k <= hi; k++) s += w[k - lo] * f[k * st];
+    return s;
+}
+
 /* upwind-biased first derivative: offsets -1..+3 (forward) or -3..+1 */
 double orc_dup(const double* f, long st, double h, int forward)
 {
@@ -585,6 +703,8 @@ static void outer_bc_with(const orc_params* p, const bmap* m, const double* gfs,
     long T = orc_sizes(p, n);
     long st[3] = {1, n[0], (long)n[0] * n[1]};
     double h[3] = {dxx_of(p, 0), dxx_of(p, 1), dxx_of(p, 2)};
+    fdw Wd;
+    fdw_make(p->NG, &Wd);
     for (long idx = 0; idx < T; idx++) {
         if (m->cls[idx] != 1) continue;
         int ii[3];
@@ -599,7 +719,16 @@ static void outer_bc_with(const orc_params* p, const bmap* m, const double* gfs,
         for (int gf = 0; gf < NGF; gf++) {
             const double* f = &gfs[gf * T + idx];
             double dl[3], radial = 0.0;
-            for (int d = 0; d < 3; d++) dl[d] = orc_d1_onesided(f, st[d], h[d], kind[d]);
+            for (int d = 0; d < 3; d++) {
+                if (p->NG == 3) {
+                    dl[d] = orc_d1_onesided(f, st[d], h[d], kind[d]);
+                } else {
+                    int mm = Wd.m, a = -mm;
+                    if (a < -ii[d]) a = -ii[d];
+                    if (a > n[d] - 1 - ii[d] - 2 * mm) a = n[d] - 1 - ii[d] - 2 * mm;
+                    dl[d] = sten(f, st[d], Wd.os[-a], a, a + 2 * mm) / (Wd.deno[-a] * h[d]);
+                }
+            }
             for (int a = 0; a < 3; a++) {
                 double dfa = 0.0;
                 for (int d = 0; d < 3; d++) dfa += Jinv[d][a] * dl[d];
@@ -664,7 +793,7 @@ static void rescale_factor(const rfm_pt* R, int type, double* Rv, double Rd[3], 
 }
 
 static void load_point(const orc_params* p, const int n[3], long T, const double* gfs, long idx,
-                       const rfm_pt* R, pt_fields* F)
+                       const rfm_pt* R, pt_fields* F, const fdw* Wd)
 {
     long st[3] = {1, n[0], (long)n[0] * n[1]};
     double h[3] = {dxx_of(p, 0), dxx_of(p, 1), dxx_of(p, 2)};
@@ -680,10 +809,27 @@ static void load_point(const orc_params* p, const int n[3], long T, const double
         const double* f = &gfs[gf * T + idx];
         double v = f[0], d1[3], d2[3][3], up[3];
         for (int k = 0; k < 3; k++) {
-            d1[k] = orc_d1(f, st[k], h[k]);
-            up[k] = orc_dup(f, st[k], h[k], fwd[k]);
-            for (int l = 0; l < 3; l++)
-                d2[k][l] = (k == l) ? orc_d2(f, st[k], h[k]) : orc_d11(f, st[k], st[l], h[k], h[l]);
+            if (p->NG == 3) {
+                d1[k] = orc_d1(f, st[k], h[k]);
+                up[k] = orc_dup(f, st[k], h[k], fwd[k]);
+                for (int l = 0; l < 3; l++)
+                    d2[k][l] = (k == l) ? orc_d2(f, st[k], h[k]) : orc_d11(f, st[k], st[l], h[k], h[l]);
+                continue;
+            }
+            int m = Wd->m;
+            d1[k] = sten(f, st[k], Wd->d1, -m, m) / (Wd->den1 * h[k]);
+            /* the backward stencil is the mirror image: weight -w(-o) at offset o */
+            up[k] = (fwd[k] ? sten(f, st[k], Wd->up, -(m - 1), m + 1) : -sten(f, -st[k], Wd->up, -(m - 1), m + 1)) /
+                    (Wd->denu * h[k]);
+            for (int l = 0; l < 3; l++) {
+                if (k == l) {
+                    d2[k][l] = sten(f, st[k], Wd->d2, -m, m) / (Wd->den2 * h[k] * h[k]);
+                } else {
+                    double s2 = 0.0;
+                    for (int b = -m; b <= m; b++) s2 += Wd->d1[b + m] * sten(f + b * st[l], st[k], Wd->d1, -m, m);
+                    d2[k][l] = s2 / (Wd->den1 * Wd->den1 * h[k] * h[l]);
+                }
+            }
         }
         double Rv, Rd[3], Rdd[3][3];
         rescale_factor(R, gf_type(gf), &Rv, Rd, Rdd);
@@ -1025,6 +1171,8 @@ void orc_rhs(const orc_params* p, const double* gfs, double* rhs, int k_lo, int 
     double h[3] = {dxx_of(p, 0), dxx_of(p, 1), dxx_of(p, 2)};
     if (k_lo < 0) k_lo = 0;
     if (k_hi > p->N[2]) k_hi = p->N[2];
+    fdw Wd;
+    fdw_make(p->NG, &Wd);
     int nt = p->nthreads;
 #ifdef _OPENMP
     if (nt <= 0) nt = omp_get_max_threads();
@@ -1042,13 +1190,21 @@ void orc_rhs(const orc_params* p, const double* gfs, double* rhs, int k_lo, int 
                 double out[NGF];
                 rfm_eval(p, xx, &R);
                 refmet_from(&R, &M);
-                load_point(p, n, T, gfs, idx, &R, &F);
+                load_point(p, n, T, gfs, idx, &R, &F, &Wd);
                 rhs_at_point(p, &R, &M, &F, out);
-                /* Kreiss-Oliger dissipation (reading R-KO): physical spacing S_d dxx_d */
+                /* Kreiss-Oliger dissipation (reading R-KO): sigma / (2^(2r) S_d dxx_d) times the
+                 * difference of order 2r = N_FD + 2 along each axis, physical spacing S_d dxx_d */
                 for (int gf = 0; gf < NGF; gf++) {
                     double ko = 0.0;
-                    for (int d = 0; d < 3; d++)
-                        ko += p->ko_sigma[gf] / (64.0 * h[d] * R.S[d]) * orc_ko6(&gfs[gf * T + idx], st[d]);
+                    for (int d = 0; d < 3; d++) {
+                        const double* f = &gfs[gf * T + idx];
+                        if (p->NG == 3) {
+                            ko += p->ko_sigma[gf] / (64.0 * h[d] * R.S[d]) * orc_ko6(f, st[d]);
+                        } else {
+                            int r = Wd.m + 1;
+                            ko += p->ko_sigma[gf] / (ldexp(1.0, 2 * r) * h[d] * R.S[d]) * sten(f, st[d], Wd.ko, -r, r);
+                        }
+                    }
                     rhs[gf * T + idx] = out[gf] + ko;
                 }
             }
@@ -1107,6 +1263,52 @@ void orc_enforce_detgb(const orc_params* p, double* gfs)
 /* ------------------------------------------------------------------ RK4 */
 
 /* classic RK4 (Sec. 4.2.1 footnote: the performance runs use RK4) */
+/* SSPRK3 (Gottlieb, Shu & Tadmor 2001; named in Sec. 3 and Sec. 4.1):
+ *   y1 = y + dt f(y),  y2 = 3/4 y + 1/4 (y1 + dt f(y1)),  y' = 1/3 y + 2/3 (y2 + dt f(y2)),
+ * boundary conditions on each right-hand side, det(gammabar) enforced after each
+ * substage update. */
+int orc_ssprk3_step(const orc_params* p, double* gfs, double dt, int nsteps)
+{
+    bmap m;
+    int bad = bmap_make(p, &m);
+    long n = (long)NGF * m.T;
+    double* k = (double*)malloc(sizeof(double) * n);
+    double* y1 = (double*)malloc(sizeof(double) * n);
+    double* y2 = (double*)malloc(sizeof(double) * n);
+    for (int step = 0; step < nsteps; step++) {
+        full_rhs_with(p, &m, gfs, k);
+        for (long i = 0; i < n; i++) y1[i] = gfs[i] + dt * k[i];
+        if (p->enforce_detgb) orc_enforce_detgb(p, y1);
+        full_rhs_with(p, &m, y1, k);
+        for (long i = 0; i < n; i++) y2[i] = 0.75 * gfs[i] + 0.25 * (y1[i] + dt * k[i]);
+        if (p->enforce_detgb) orc_enforce_detgb(p, y2);
+        full_rhs_with(p, &m, y2, k);
+        for (long i = 0; i < n; i++) gfs[i] = (1.0 / 3.0) * gfs[i] + (2.0 / 3.0) * (y2[i] + dt * k[i]);
+        if (p->enforce_detgb) orc_enforce_detgb(p, gfs);
+    }
+    free(k);
+    free(y1);
+    free(y2);
+    bmap_free(&m);
+    return bad;
+}
+
+void orc_ssprk3_generic(long n, double* y, double dt, orc_rhs_fn f, void* ctx)
+{
+    double* k = (double*)malloc(sizeof(double) * n);
+    double* y1 = (double*)malloc(sizeof(double) * n);
+    double* y2 = (double*)malloc(sizeof(double) * n);
+    f(ctx, y, k);
+    for (long i = 0; i < n; i++) y1[i] = y[i] + dt * k[i];
+    f(ctx, y1, k);
+    for (long i = 0; i < n; i++) y2[i] = 0.75 * y[i] + 0.25 * (y1[i] + dt * k[i]);
+    f(ctx, y2, k);
+    for (long i = 0; i < n; i++) y[i] = (1.0 / 3.0) * y[i] + (2.0 / 3.0) * (y2[i] + dt * k[i]);
+    free(k);
+    free(y1);
+    free(y2);
+}
+
 void orc_rk4_generic(long n, double* y, double dt, orc_rhs_fn f, void* ctx)
 {
     double* k1 = (double*)malloc(sizeof(double) * n);
@@ -1169,6 +1371,8 @@ void orc_hamiltonian(const orc_params* p, const double* gfs, double* H, double r
     long T = orc_sizes(p, n);
     int NG = p->NG;
     for (long idx = 0; idx < T; idx++) H[idx] = 0.0;
+    fdw Wd;
+    fdw_make(p->NG, &Wd);
     int nt = p->nthreads;
 #ifdef _OPENMP
     if (nt <= 0) nt = omp_get_max_threads();
@@ -1186,7 +1390,7 @@ void orc_hamiltonian(const orc_params* p, const double* gfs, double* H, double r
                 geom_pt G;
                 rfm_eval(p, xx, &R);
                 refmet_from(&R, &M);
-                load_point(p, n, T, gfs, idx, &R, &F);
+                load_point(p, n, T, gfs, idx, &R, &F, &Wd);
                 geometry(&M, &F, &G);
                 double Rs = 0.0, gp = 0.0, lp = 0.0;
                 for (int a = 0; a < 3; a++)
@@ -1239,6 +1443,8 @@ void orc_momentum(const orc_params* p, const double* gfs, double* Mout, double* 
     double* mag = (double*)calloc((size_t)T, sizeof(double));
     if (Mout)
         for (long q = 0; q < 3 * T; q++) Mout[q] = 0.0;
+    fdw Wd;
+    fdw_make(p->NG, &Wd);
     int nt = p->nthreads;
 #ifdef _OPENMP
     if (nt <= 0) nt = omp_get_max_threads();
@@ -1256,7 +1462,7 @@ void orc_momentum(const orc_params* p, const double* gfs, double* Mout, double* 
                 geom_pt G;
                 rfm_eval(p, xx, &R);
                 refmet_from(&R, &M);
-                load_point(p, n, T, gfs, idx, &R, &F);
+                load_point(p, n, T, gfs, idx, &R, &F, &Wd);
                 geometry(&M, &F, &G);
                 /* d_m gammabar^{ab} */
                 double dgi[3][3][3];

@@ -96,6 +96,15 @@ void orc_momentum(const orc_params* p, const double* gfs, double* M, double* Mno
 /* Generic classic RK4 (used by orc_rk4_step; exported for its pin). */
 typedef void (*orc_rhs_fn)(void* ctx, const double* y, double* k);
 void orc_rk4_generic(long n, double* y, double dt, orc_rhs_fn f, void* ctx);
+/* SSPRK3 (Gottlieb-Shu-Tadmor) on the 24 gridfunctions, as orc_rk4_step; and on a
+ * plain vector for the pins */
+int orc_ssprk3_step(const orc_params* p, double* gfs, double dt, int nsteps);
+void orc_ssprk3_generic(long n, double* y, double dt, orc_rhs_fn f, void* ctx);
+/* weights of the order-2(NG-1) stencils (NG != 3 paths): which 0 centred first
+ * derivative, 1 centred second, 2 upwind forward (offsets -(NG-2)..NG), 3 the
+ * Kreiss-Oliger difference of order 2 NG, 4 one-sided with window start a;
+ * returns their number */
+int orc_fd_weights(int NG, int which, int a, double* w);
 
 /* Stencil helpers on a strided line (exported for their pins).  f points at
  * the centre value. */

@@ -98,6 +98,11 @@ def lib() -> ctypes.CDLL:
         L.orc_momentum.argtypes = [P, dp, dp, dp, ctypes.c_double, ctypes.c_double, dp, dp,
                                    ctypes.POINTER(ctypes.c_long)]
         L.orc_rk4_generic.argtypes = [ctypes.c_long, dp, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]
+        L.orc_ssprk3_generic.argtypes = [ctypes.c_long, dp, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]
+        L.orc_ssprk3_step.argtypes = [P, dp, ctypes.c_double, ctypes.c_int]
+        L.orc_ssprk3_step.restype = ctypes.c_int
+        L.orc_fd_weights.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp]
+        L.orc_fd_weights.restype = ctypes.c_int
         for name in ("orc_d1", "orc_d2", "orc_ko6"):
             getattr(L, name).restype = ctypes.c_double
         L.orc_d1.argtypes = [dp, ctypes.c_long, ctypes.c_double]
@@ -231,6 +236,10 @@ class Oracle:
         if self.L.orc_rk4_step(ctypes.byref(self.p), _dp(y), float(dt), int(nsteps)):
             raise ValueError("inner boundary map failed")
 
+    def ssprk3(self, y: np.ndarray, dt: float, nsteps: int) -> None:
+        if self.L.orc_ssprk3_step(ctypes.byref(self.p), _dp(y), float(dt), int(nsteps)):
+            raise ValueError("inner boundary map failed")
+
     def hamiltonian(self, y: np.ndarray, rmin: float = 0.0, rmax: float = 1e300):
         H = np.zeros(self.T)
         l2 = ctypes.c_double(); linf = ctypes.c_double(); cnt = ctypes.c_long()
@@ -268,6 +277,28 @@ def rk4_generic(y: np.ndarray, dt: float, f) -> None:
 
     fn = RHS_FN(cb)
     lib().orc_rk4_generic(n, _dp(y), float(dt), ctypes.cast(fn, ctypes.c_void_p), None)
+
+
+def ssprk3_generic(y: np.ndarray, dt: float, f) -> None:
+    """Run one SSPRK3 step of the oracle's integrator on y' = f(y)."""
+    n = y.size
+
+    def cb(_ctx, yp, kp):
+        yy = np.ctypeslib.as_array(yp, shape=(n,))
+        kk = np.ctypeslib.as_array(kp, shape=(n,))
+        kk[:] = f(yy.copy())
+
+    fn = RHS_FN(cb)
+    lib().orc_ssprk3_generic(n, _dp(y), float(dt), ctypes.cast(fn, ctypes.c_void_p), None)
+
+
+def fd_weights(NG: int, which: int, a: int = 0) -> np.ndarray:
+    """Weights of the oracle's order-2(NG-1) stencils (see orc_fd_weights)."""
+    w = np.zeros(32)
+    n = lib().orc_fd_weights(int(NG), int(which), int(a), _dp(w))
+    if n == 0:
+        raise ValueError("no such stencil")
+    return w[:n].copy()
 
 
 def threads_used(spec: dict) -> int:
