@@ -40,16 +40,18 @@ from paper_2505_00097_gb300 import workloads as W  # noqa: E402
 METRIC = "BSSN FP64 point-updates/s (RK4 substeps)"
 UNIT = "point-updates/s"
 
-# FP64 operations (FMA = 2) per interior point of one plain-RHS k_rhs launch,
-# by workload (the kernel variant it runs), from the kernel's DADD/DMUL/DFMA
-# thread-instruction counts in one ncu capture: (DADD + DMUL + 2 DFMA) /
-# interior points (profiles/k_rhs_headon_256x2x512.md,
+# FP64 operations (FMA = 2) per interior point of one RHS evaluation (nr_rhs:
+# the k_d1 pre-pass and k_rhs), by workload (the kernel variant it runs), from
+# the kernels' DADD/DMUL/DFMA thread-instruction counts in one ncu capture:
+# (DADD + DMUL + 2 DFMA) / interior points (profiles/k_rhs_headon_256x2x512.md,
 # profiles/k_rhs_general_3d.md).  Head-on 256x2x512 (cylindrical, two-point
-# azimuth): 418 + 372 + 2 x 1295.  Large 3D (spherical, general kernel):
-# 687 + 472 + 2 x 1838.  A workload without a capture reports no FLOP rate.
-F_ALG = {"headon": 3380.0, "large3d": 4835.0}
-# DRAM bytes (read + write) of that launch in the same capture, or None
-TRAFFIC = {"headon": 58760448 + 312345856}
+# azimuth): k_rhs 308 + 376 + 2 x 1242 = 3168, k_d1 44.3.  Large 3D
+# (spherical, general): k_rhs 382 + 479 + 2 x 1684 = 4229, k_d1 89.9 (4 FLOP per
+# stored difference, 22 differences per point over the 1.03x larger region).
+# A workload without a capture reports no FLOP rate.
+F_ALG = {"headon": 3212.3, "large3d": 4318.9}
+# DRAM bytes (read + write) of the same two launches in that capture, or None
+TRAFFIC = {"headon": 24016640 + 91136 + 81816832 + 249576960}
 # FP64 pipe of one SM: 2 DFMA per clock (ncu peak_sustained of
 # sm__sass_thread_inst_executed_op_dfma_pred_on), i.e. 4 FLOP per clock
 FP64_FLOP_PER_CLK_SM = 4.0
@@ -321,7 +323,7 @@ def run_ours(args, spec, world, rank, local):
     g.check_finite()
     value = world * pts * 4 * args.steps / (ms_max * 1e-3)
 
-    # dominant kernel: k_rhs, timed alone with CUDA events on the same stream
+    # dominant kernels: one RHS evaluation (k_d1 + k_rhs), timed alone with CUDA events on the same stream
     T = g.T
     ybuf = torch.empty(24 * T, dtype=torch.float64, device=dev)
     obuf = torch.empty_like(ybuf)
@@ -342,7 +344,8 @@ def run_ours(args, spec, world, rank, local):
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
     mhz = (ck or {}).get("sm_mhz") or (ck or {}).get("sm_max_mhz") or 2070.0
     peak = FP64_FLOP_PER_CLK_SM * n_sm * mhz * 1e6
-    roof = {"bound": "alu", "kernel": "k_rhs (FP64 BSSN RHS + KO + upwind)", "unit": "TFLOP/s",
+    roof = {"bound": "alu", "kernel": "k_d1 + k_rhs (one FP64 BSSN RHS evaluation + KO + upwind, nr_rhs)",
+            "unit": "TFLOP/s",
             "peak": peak / 1e12,
             "peak_source": f"derived: 2 DFMA/clk/SM x {n_sm} SMs x {mhz:.0f} MHz (median SM clock in the timed region)",
             "probe_tflops": probe / 1e12, "launch_ms": rhs_ms, "points_per_launch": pts,
@@ -402,7 +405,7 @@ def run_ours(args, spec, world, rank, local):
 
 def run_batch(args, world, rank, local):
     """64 uneven head-on runs (the batched workload): plain one-grid-at-a-time nr_rk4_step versus
-    one nr_batch (one persistent launch per substage for all grids, autotuned tile), same steps."""
+    one nr_batch (one launch per substage over the tiles of all grids, autotuned tile), same steps."""
     import torch
 
     from paper_2505_00097_gb300 import binding as B

@@ -153,9 +153,9 @@ int nr_apply_inner_bcs(nr_grid* grid, double* gfs_dev);
 /* Advance the grid-owned state by nsteps classic RK4 steps of size dt (Sec.
  * 4.2.1): per substage, the interior RHS with the RK update fused into its
  * epilogue, the radiation condition at outer ghosts, parity copies at inner
- * ghosts, and (enforce_detgb) det(gammabar) enforcement.  The 12 launches of
- * one step are captured once in a CUDA graph (re-captured when dt changes)
- * and replayed.  dt > 0, nsteps >= 0. */
+ * ghosts, and (enforce_detgb) det(gammabar) enforcement.  The launches of
+ * one step (nr_grid_info.launches_per_step) are captured once in a CUDA graph
+ * (re-captured when dt changes) and replayed.  dt > 0, nsteps >= 0. */
 int nr_rk4_step(nr_grid* grid, double dt, int nsteps);
 
 /* Hamiltonian constraint (Eq. Hconstraint) at interior points of y_dev (NULL:
@@ -165,6 +165,19 @@ int nr_rk4_step(nr_grid* grid, double dt, int nsteps);
  * norms are reduced on the device in a fixed order and copied to the host:
  * this call synchronises params.stream when l2_out or linf_out is given. */
 int nr_hamiltonian(nr_grid* grid, const double* y_dev, double* H_dev, double* l2_out, double* linf_out);
+
+/* Momentum constraint (Eq. Mconstraint) at interior points of y_dev (NULL:
+ * the grid-owned state),
+ *   M^i = e^{-4 phi} (Dhat_j Abar^ij + 2 Abar^k(i Delta^j)_jk + 6 Abar^ij d_j phi
+ *                     - 2/3 gammabar^ij d_j K).
+ * M_dev (NULL allowed): caller-owned 3*T doubles, the rescaled components
+ * (S_i M^i, the layout of lambdaU) at interior points, ghost points set to 0.
+ * l2_out / linf_out: sqrt(mean |M|^2) and max |M| over interior points with
+ * Cartesian radius in [h_rmin, h_rmax], |M| = sqrt(gamma_ij M^i M^j) with the
+ * physical metric gamma_ij = e^{4 phi} gammabar_ij; either may be NULL.
+ * Reduced on the device in a fixed order; synchronises params.stream when a
+ * norm is asked for. */
+int nr_momentum(nr_grid* grid, const double* y_dev, double* M_dev, double* l2_out, double* linf_out);
 
 /* Copy the grid-owned state (24*T doubles) to / from dst / src.  to_host /
  * from_host = 1: dst/src is host memory (pinned or pageable) and the call
@@ -192,10 +205,10 @@ int nr_dt_cfl(int coords, const int Nxx[3], const nr_params* params, double* dt_
  * scaling tests run many times over): many grids of uneven sizes, all of one
  * coordinate family (spherical-like or cylindrical-like), one azimuth kind
  * (two points, or more: the right-hand-side kernel is specialised for a
- * two-point azimuth) and one device, advanced together.  Each RK4 substage is one persistent launch in which
- * thread blocks take work items -- a tile of one grid's interior points or a
- * chunk of its pure-outer ghost points -- from an atomic counter until the
- * list is exhausted, followed by one parity-copy launch for all grids; one
+ * two-point azimuth) and one device, advanced together.  Each RK4 substage
+ * is one launch over the work items of all grids -- a tile of one grid's
+ * interior points or a chunk of its pure-outer ghost points, one thread block
+ * each -- followed by one parity-copy launch for all grids; one
  * step is captured in a CUDA graph (re-captured when the step sizes or the
  * tile shape change) and replayed.  Every point runs the same arithmetic as
  * nr_rk4_step, so each grid's state is bitwise what nr_rk4_step would give,
@@ -229,7 +242,7 @@ int nr_batch_rk4_step(nr_batch* batch, const double* dts, int nsteps);
  *   nr_server_advance: makes queued requests resident (running) in policy
  *     order while the budget and the slots allow, then advances the selected
  *     running requests together -- one nr_batch per kind of grid (coordinate
- *     family x azimuth kind), one persistent launch per RK4 substage for each
+ *     family x azimuth kind), one launch per RK4 substage for each
  *     -- by up to nsteps steps.  Membership changes only at step boundaries:
  *     a request reaching t_final is retired (Hamiltonian-constraint norms
  *     recorded, state kept if asked, device memory released) and queued

@@ -23,7 +23,8 @@ COORDS = {"sinh_spherical": 0, "sinh_cylindrical": 1, "spherical": 2}
 # every entry point declared in include/nr.h
 EXPORTS = (
     "nr_params_default", "nr_grid_create", "nr_grid_destroy", "nr_query", "nr_set_brill_lindquist", "nr_rhs",
-    "nr_apply_bcs", "nr_apply_inner_bcs", "nr_rk4_step", "nr_hamiltonian", "nr_get_state", "nr_set_state",
+    "nr_apply_bcs", "nr_apply_inner_bcs", "nr_rk4_step", "nr_hamiltonian", "nr_momentum", "nr_get_state",
+    "nr_set_state",
     "nr_sync", "nr_check_finite", "nr_build_maps", "nr_dt_cfl", "nr_fp64_peak", "nr_hamiltonian_noalloc",
     "nr_batch_create", "nr_batch_destroy", "nr_batch_set_tile", "nr_batch_autotune", "nr_batch_rk4_step",
     "nr_server_create", "nr_server_destroy", "nr_server_set_tile", "nr_server_set_policy", "nr_server_submit",
@@ -102,6 +103,7 @@ def lib() -> ctypes.CDLL:
     L.nr_apply_inner_bcs.argtypes = [vp, vp]
     L.nr_rk4_step.argtypes = [vp, ctypes.c_double, ctypes.c_int]
     L.nr_hamiltonian.argtypes = [vp, vp, vp, dp, dp]
+    L.nr_momentum.argtypes = [vp, vp, vp, dp, dp]
     L.nr_get_state.argtypes = [vp, vp, ctypes.c_int]
     L.nr_set_state.argtypes = [vp, vp, ctypes.c_int]
     L.nr_sync.argtypes = [vp]
@@ -268,6 +270,12 @@ class Grid:
         l2, linf = ctypes.c_double(), ctypes.c_double()
         _check(lib().nr_hamiltonian(self.h, None if y is None else _ptr(y), None if H is None else _ptr(H),
                                     ctypes.byref(l2), ctypes.byref(linf)))
+        return l2.value, linf.value
+
+    def momentum(self, y=None, M=None):
+        l2, linf = ctypes.c_double(), ctypes.c_double()
+        _check(lib().nr_momentum(self.h, None if y is None else _ptr(y), None if M is None else _ptr(M),
+                                 ctypes.byref(l2), ctypes.byref(linf)))
         return l2.value, linf.value
 
     def get_state(self, dst, to_host: bool) -> None:

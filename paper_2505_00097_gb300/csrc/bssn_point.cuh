@@ -98,12 +98,18 @@ __host__ __device__ constexpr bool ax_ok()
 // a Hessian component known to vanish: a mixed pair that involves the axis
 __host__ __device__ constexpr bool hzero(int AX, int kl) { return AX >= 0 && offd(kl) && (spi(kl) == AX || spj(kl) == AX); }
 
-// e_k f (zero along the two-point axis)
-template <int AX>
-__device__ __forceinline__ double e1(const double* f, const long st[3], const double D[3], int k)
+// Gridfunctions with second derivatives (h, W, alpha, vet) have their raw first
+// differences along axis 0 (and, for a general grid, axis 1) stored by a
+// pre-pass (k_d1).  A mixed second difference is the first difference of
+// those along the other axis -- the same expression mixraw evaluates -- so the
+// stored path gives bitwise the result of the inline one.
+constexpr int N_D1 = 11;
+__host__ __device__ constexpr int d1slot(int gf)
 {
-    return k == AX ? 0.0 : D[k] * d1raw(f, st[k]);
+    return gf < 6 ? gf : gf == G_CF ? 6 : gf == G_ALPHA ? 7 : (gf >= G_VET && gf < G_VET + 3) ? 8 + gf - G_VET : -1;
 }
+__host__ __device__ constexpr int d1gf(int q) { return q < 6 ? q : q == 6 ? G_CF : q == 7 ? G_ALPHA : G_VET + q - 8; }
+
 // sum_k a_k x_k, skipping k = AX where x vanishes (AX is never 0)
 template <int AX>
 __device__ __forceinline__ double dot3(double a0, double a1, double a2, const double x[3])
@@ -117,23 +123,27 @@ __device__ __forceinline__ double dot3(double a0, double a1, double a2, const do
 // ---- frame Hessian of a component function:
 // H_kl f = e_k e_l f - omega^m_kl e_m f  (symmetric in kl); ox is the offset of
 // the other slice of the two-point axis
-template <int FAM, int KL, int AX>
-__device__ __forceinline__ double hess(const double* f, const long st[3], long ox, const Geo& g, const double df[3])
+// fx, fy: stored first differences of f along axes 0 and 1 (S = true)
+template <int FAM, int KL, int AX, bool S>
+__device__ __forceinline__ double hess(const double* f, const double* fx, const double* fy, const long st[3], long ox,
+                                       const Geo& g, const double df[3])
 {
     if constexpr (hzero(AX, KL)) return 0.0;
     if constexpr (KL == 0) return fma(g.D2[0], d2raw(f, st[0]), -g.d00 * df[0]);
-    if constexpr (KL == 1) return fma(g.DD[0], mixraw(f, st[0], st[1]), -g.a * df[1]);
+    if constexpr (KL == 1) return fma(g.DD[0], S ? d1raw(fx, st[1]) : mixraw(f, st[0], st[1]), -g.a * df[1]);
     if constexpr (KL == 2) {
-        if constexpr (FAM == FAM_SPH) return fma(g.DD[1], mixraw(f, st[0], st[2]), -g.b * df[2]);
-        else return g.DD[1] * mixraw(f, st[0], st[2]);
+        const double m = S ? d1raw(fx, st[2]) : mixraw(f, st[0], st[2]);
+        if constexpr (FAM == FAM_SPH) return fma(g.DD[1], m, -g.b * df[2]);
+        else return g.DD[1] * m;
     }
     if constexpr (KL == 3) {
         if constexpr (AX == 1) return fma(32.0 * g.D2[1], ld(f + ox) - ld(f), g.a * df[0]);
         else return fma(g.D2[1], d2raw(f, st[1]), g.a * df[0]);
     }
     if constexpr (KL == 4) {
-        if constexpr (FAM == FAM_SPH) return fma(g.DD[2], mixraw(f, st[1], st[2]), -g.c * df[2]);
-        else return g.DD[2] * mixraw(f, st[1], st[2]);
+        const double m = (S && AX < 0) ? d1raw(fy, st[2]) : mixraw(f, st[1], st[2]);
+        if constexpr (FAM == FAM_SPH) return fma(g.DD[2], m, -g.c * df[2]);
+        else return g.DD[2] * m;
     }
     if constexpr (KL == 5) {
         if constexpr (FAM == FAM_SPH) {
@@ -146,16 +156,16 @@ __device__ __forceinline__ double hess(const double* f, const long st[3], long o
     return 0.0;
 }
 
-template <int FAM, int AX>
-__device__ __forceinline__ void hess6(const double* f, const long st[3], long ox, const Geo& g, const double df[3],
-                                      double H[6])
+template <int FAM, int AX, bool S>
+__device__ __forceinline__ void hess6(const double* f, const double* fx, const double* fy, const long st[3], long ox,
+                                      const Geo& g, const double df[3], double H[6])
 {
-    H[0] = hess<FAM, 0, AX>(f, st, ox, g, df);
-    H[1] = hess<FAM, 1, AX>(f, st, ox, g, df);
-    H[2] = hess<FAM, 2, AX>(f, st, ox, g, df);
-    H[3] = hess<FAM, 3, AX>(f, st, ox, g, df);
-    H[4] = hess<FAM, 4, AX>(f, st, ox, g, df);
-    H[5] = hess<FAM, 5, AX>(f, st, ox, g, df);
+    H[0] = hess<FAM, 0, AX, S>(f, fx, fy, st, ox, g, df);
+    H[1] = hess<FAM, 1, AX, S>(f, fx, fy, st, ox, g, df);
+    H[2] = hess<FAM, 2, AX, S>(f, fx, fy, st, ox, g, df);
+    H[3] = hess<FAM, 3, AX, S>(f, fx, fy, st, ox, g, df);
+    H[4] = hess<FAM, 4, AX, S>(f, fx, fy, st, ox, g, df);
+    H[5] = hess<FAM, 5, AX, S>(f, fx, fy, st, ox, g, df);
 }
 // gammabar^kl H_kl (gw: off-diagonal entries doubled), skipping vanishing components
 template <int AX>
@@ -223,8 +233,35 @@ struct PointIn {
     long T;
     long st[3];
     long ox;          // offset of the other slice of a two-point azimuthal axis (unused otherwise)
+    // stored raw first differences d1raw along axis 0 (dx) and axis 1 (dy) of the
+    // gridfunctions with second derivatives, at this point (slot q at dx[q*T]);
+    // NULL where the kernel differences inline
+    const double* dx;
+    const double* dy;
     Geo g;
 };
+
+// e_k of gridfunction gf: zero along the two-point axis, from the stored first
+// differences where the point has them (S), else inline
+template <int AX, bool S>
+__device__ __forceinline__ double der1(const PointIn& P, int gf, int k)
+{
+    if (k == AX) return 0.0;
+    const int q = d1slot(gf);
+    if (S && q >= 0 && k == 0) return P.g.D[0] * ld(P.dx + (long)q * P.T);
+    if (S && AX < 0 && q >= 0 && k == 1) return P.g.D[1] * ld(P.dy + (long)q * P.T);
+    return P.g.D[k] * d1raw(P.y + (long)gf * P.T, P.st[k]);
+}
+template <bool S>
+__device__ __forceinline__ const double* dxp(const PointIn& P, int gf)
+{
+    return S ? P.dx + (long)d1slot(gf) * P.T : nullptr;
+}
+template <int AX, bool S>
+__device__ __forceinline__ const double* dyp(const PointIn& P, int gf)
+{
+    return (S && AX < 0) ? P.dy + (long)d1slot(gf) * P.T : nullptr;
+}
 
 // Metric-sector quantities shared by the right-hand side and the
 // Hamiltonian constraint.
@@ -240,8 +277,11 @@ struct MetricPart {
     double W, iW, dphi[3], DDphi[6];
 };
 
-template <int FAM, bool NEED_GH, int AX>
-__device__ __forceinline__ void metric_part(const PointIn& P, MetricPart& M)
+// The conformal metric and its inverse, first frame derivatives of h, and
+// Delta (lowered, raised, its trace Delta^k and Delta^k_km): shared by the
+// right-hand side and both constraints.
+template <int FAM, int AX, bool S>
+__device__ __forceinline__ void metric_first(const PointIn& P, MetricPart& M)
 {
     static_assert(ax_ok<FAM, AX>(), "two-point axis must be the azimuth");
     const double* y = P.y;
@@ -279,25 +319,7 @@ __device__ __forceinline__ void metric_part(const PointIn& P, MetricPart& M)
 #pragma unroll
     for (int k = 0; k < 3; k++)
 #pragma unroll
-        for (int s = 0; s < 6; s++) dh[k][s] = e1<AX>(F(G_HDD + s), st, g.D, k);
-
-    // ---------------- Hessians of h contracted two ways:
-    // Lh_ij = gammabar^kl H_kl h_ij,  GH_kl = gammabar^ij H_kl h_ij
-    double Lh[6];
-#pragma unroll
-    for (int s = 0; s < 6; s++) {
-        double df[3] = {dh[0][s], dh[1][s], dh[2][s]};
-        double H[6];
-        hess6<FAM, AX>(F(G_HDD + s), st, P.ox, g, df, H);
-        Lh[s] = contract6<AX>(gw, H);
-        if constexpr (NEED_GH) {
-#pragma unroll
-            for (int kl = 0; kl < 6; kl++) {
-                if (hzero(AX, kl)) M.GH[kl] = 0.0;
-                else M.GH[kl] = s == 0 ? gw[0] * H[kl] : fma(gw[s], H[kl], M.GH[kl]);
-            }
-        }
-    }
+        for (int s = 0; s < 6; s++) dh[k][s] = der1<AX, S>(P, G_HDD + s, k);
 
     // ---------------- Dhat_k h_ij, Delta_kij (first index lowered), Delta^k_ij, Delta^k
     double Dh[3][6];
@@ -334,6 +356,42 @@ __device__ __forceinline__ void metric_part(const PointIn& P, MetricPart& M)
 #pragma unroll
         for (int s = 1; s < 6; s++) t = fma(gw[s], dh[m][s], t);
         M.Dtr[m] = m == AX ? 0.0 : 0.5 * t;
+    }
+}
+
+template <int FAM, bool NEED_GH, int AX, bool S>
+__device__ __forceinline__ void metric_part(const PointIn& P, MetricPart& M)
+{
+    metric_first<FAM, AX, S>(P, M);
+    const double* y = P.y;
+    const long T = P.T;
+    const Geo& g = P.g;
+    const long* st = P.st;
+    auto F = [&](int gf) { return y + (long)gf * T; };
+    const double* h = M.h;
+    const double* gi = M.gi;
+    const double* gw = M.gw;
+    const double (*dh)[6] = M.dh;
+    const double (*Dl)[6] = M.Dl;
+    const double (*Dup)[6] = M.Dup;
+    const double* Dvec = M.Dvec;
+
+    // ---------------- Hessians of h contracted two ways:
+    // Lh_ij = gammabar^kl H_kl h_ij,  GH_kl = gammabar^ij H_kl h_ij
+    double Lh[6];
+#pragma unroll
+    for (int s = 0; s < 6; s++) {
+        double df[3] = {dh[0][s], dh[1][s], dh[2][s]};
+        double H[6];
+        hess6<FAM, AX, S>(F(G_HDD + s), dxp<S>(P, G_HDD + s), dyp<AX, S>(P, G_HDD + s), st, P.ox, g, df, H);
+        Lh[s] = contract6<AX>(gw, H);
+        if constexpr (NEED_GH) {
+#pragma unroll
+            for (int kl = 0; kl < 6; kl++) {
+                if (hzero(AX, kl)) M.GH[kl] = 0.0;
+                else M.GH[kl] = s == 0 ? gw[0] * H[kl] : fma(gw[s], H[kl], M.GH[kl]);
+            }
+        }
     }
 
     // ---------------- Ricci tensor
@@ -385,7 +443,7 @@ __device__ __forceinline__ void metric_part(const PointIn& P, MetricPart& M)
 #pragma unroll
     for (int j = 0; j < 3; j++)
 #pragma unroll
-        for (int k = 0; k < 3; k++) Dlam[j][k] = e1<AX>(F(G_LAM + k), st, g.D, j);
+        for (int k = 0; k < 3; k++) Dlam[j][k] = der1<AX, S>(P, G_LAM + k, j);
     omv<FAM, 1>(g, 1.0, lam, Dlam[1]);
     omv<FAM, 2>(g, 1.0, lam, Dlam[2]);
     // Y[j][m][k] = gammabar^kl Delta_jml
@@ -435,13 +493,13 @@ __device__ __forceinline__ void metric_part(const PointIn& P, MetricPart& M)
     // ---------------- conformal factor: phi = -1/2 ln W
     double dW[3];
 #pragma unroll
-    for (int k = 0; k < 3; k++) dW[k] = e1<AX>(F(G_CF), st, g.D, k);
+    for (int k = 0; k < 3; k++) dW[k] = der1<AX, S>(P, G_CF, k);
     const double mhiW = -0.5 * M.iW;
 #pragma unroll
     for (int k = 0; k < 3; k++) M.dphi[k] = k == AX ? 0.0 : mhiW * dW[k];
     {
         double HW[6];
-        hess6<FAM, AX>(F(G_CF), st, P.ox, g, dW, HW);
+        hess6<FAM, AX, S>(F(G_CF), dxp<S>(P, G_CF), dyp<AX, S>(P, G_CF), st, P.ox, g, dW, HW);
 #pragma unroll
         for (int s = 0; s < 6; s++) {
             const int i = spi(s), j = spj(s);
@@ -453,7 +511,7 @@ __device__ __forceinline__ void metric_part(const PointIn& P, MetricPart& M)
 
 // Output: the 24 right-hand sides without the beta^k d_k advection and
 // without Kreiss-Oliger dissipation (added by the caller, see adv_ko()).
-template <int FAM, int AX>
+template <int FAM, int AX, bool S>
 __device__ __forceinline__ void rhs_core(const PointIn& P, double eta, double out[NGF])
 {
     const double* y = P.y;
@@ -463,7 +521,7 @@ __device__ __forceinline__ void rhs_core(const PointIn& P, double eta, double ou
     auto F = [&](int gf) { return y + (long)gf * T; };
 
     MetricPart M;
-    metric_part<FAM, true, AX>(P, M);
+    metric_part<FAM, true, AX, S>(P, M);
     const double* h = M.h;
     const double* gi = M.gi;
     const double* gw = M.gw;
@@ -486,15 +544,15 @@ __device__ __forceinline__ void rhs_core(const PointIn& P, double eta, double ou
     double dK[3], dal[3], dvet[3][3];
 #pragma unroll
     for (int k = 0; k < 3; k++) {
-        dK[k] = e1<AX>(F(G_TRK), st, g.D, k);
-        dal[k] = e1<AX>(F(G_ALPHA), st, g.D, k);
+        dK[k] = der1<AX, S>(P, G_TRK, k);
+        dal[k] = der1<AX, S>(P, G_ALPHA, k);
 #pragma unroll
-        for (int i = 0; i < 3; i++) dvet[k][i] = e1<AX>(F(G_VET + i), st, g.D, k);
+        for (int i = 0; i < 3; i++) dvet[k][i] = der1<AX, S>(P, G_VET + i, k);
     }
     double DDal[6];
     {
         double Hal[6];
-        hess6<FAM, AX>(F(G_ALPHA), st, P.ox, g, dal, Hal);
+        hess6<FAM, AX, S>(F(G_ALPHA), dxp<S>(P, G_ALPHA), dyp<AX, S>(P, G_ALPHA), st, P.ox, g, dal, Hal);
 #pragma unroll
         for (int s = 0; s < 6; s++) DDal[s] = Hal[s] - dot3<AX>(Dup[0][s], Dup[1][s], Dup[2][s], dal);
     }
@@ -539,7 +597,8 @@ __device__ __forceinline__ void rhs_core(const PointIn& P, double eta, double ou
 #pragma unroll
         for (int i = 0; i < 3; i++) {
             double df[3] = {dvet[0][i], dvet[1][i], dvet[2][i]};
-            hess6<FAM, AX>(F(G_VET + i), st, P.ox, g, df, Hv[i]);
+            hess6<FAM, AX, S>(F(G_VET + i), dxp<S>(P, G_VET + i), dyp<AX, S>(P, G_VET + i), st, P.ox, g, df,
+                              Hv[i]);
         }
 #pragma unroll
         for (int kl = 0; kl < 6; kl++)
@@ -780,7 +839,7 @@ template <int FAM>
 __device__ __forceinline__ double ham_core(const PointIn& P)
 {
     MetricPart M;
-    metric_part<FAM, false, -1>(P, M);
+    metric_part<FAM, false, -1, false>(P, M);
     const double* gi = M.gi;
     const double* gw = M.gw;
     double a[6];
@@ -805,6 +864,84 @@ __device__ __forceinline__ double ham_core(const PointIn& P)
         lp = fma(gw[s], M.DDphi[s], lp);
     }
     return fma((2.0 / 3.0) * K, K, fma(M.W * M.W, fma(-8.0, gp + lp, R), -AA));
+}
+
+// Momentum constraint, Eq. Mconstraint.  Its first two terms are Dbar_j Abar^ij
+// (Dhat_j Abar^ij + Delta^i_jk Abar^kj + Delta^j_jk Abar^ik), evaluated here
+// with metric compatibility as gammabar^ik gammabar^jl Dbar_j Abar_kl and
+// Dbar_j Abar_kl = Dhat_j Abar_kl - Delta^m_jk Abar_ml - Delta^m_jl Abar_km:
+//   M^i = W^2 (gammabar^ik V_k + 6 Abar^ij e_j phi - 2/3 gammabar^ij e_j K),
+//   V_k = gammabar^jl Dhat_j a_kl - Delta^m_jk Abar^j_m - a_km Delta^m.
+// Writes the frame (rescaled) components M^i; returns |M| = sqrt(gamma_ij M^i M^j)
+// with the physical metric gamma_ij = gammabar_ij / W^2.
+template <int FAM>
+__device__ __forceinline__ double mom_core(const PointIn& P, double Mv[3])
+{
+    MetricPart M;
+    metric_first<FAM, -1, false>(P, M);
+    const double* y = P.y;
+    const long T = P.T;
+    const Geo& g = P.g;
+    const long* st = P.st;
+    auto F = [&](int gf) { return y + (long)gf * T; };
+    const double* gi = M.gi;
+    const double (*Dup)[6] = M.Dup;
+    const double W = M.W;
+    double a[6], Da[3][6], dK[3], dphi[3];
+#pragma unroll
+    for (int s = 0; s < 6; s++) a[s] = ld(F(G_ADD + s));
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+#pragma unroll
+        for (int s = 0; s < 6; s++) Da[k][s] = g.D[k] * d1raw(F(G_ADD + s), st[k]);
+        dK[k] = g.D[k] * d1raw(F(G_TRK), st[k]);
+        dphi[k] = (-0.5 * M.iW) * (g.D[k] * d1raw(F(G_CF), st[k]));
+    }
+    oms<FAM, 1>(g, 1.0, a, Da[1]);   // Dhat_k a_ij
+    oms<FAM, 2>(g, 1.0, a, Da[2]);
+    double Aud[3][3];  // Abar^k_j
+#pragma unroll
+    for (int k = 0; k < 3; k++)
+#pragma unroll
+        for (int j = 0; j < 3; j++)
+            Aud[k][j] = fma(gsym(gi, k, 2), a[sp(2, j)], fma(gsym(gi, k, 1), a[sp(1, j)], gsym(gi, k, 0) * a[sp(0, j)]));
+    double V[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        double t = 0.0;
+#pragma unroll
+        for (int j = 0; j < 3; j++)
+#pragma unroll
+            for (int l = 0; l < 3; l++) t = fma(gsym(gi, j, l), Da[j][sp(k, l)], t);
+#pragma unroll
+        for (int j = 0; j < 3; j++)
+#pragma unroll
+            for (int m = 0; m < 3; m++) t = fma(-Dup[m][sp(j, k)], Aud[j][m], t);
+#pragma unroll
+        for (int m = 0; m < 3; m++) t = fma(-a[sp(k, m)], M.Dvec[m], t);
+        V[k] = t;
+    }
+    const double W2 = W * W;
+    double q = 0.0;
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        double t = 0.0;
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            // Abar^ij = Abar^i_k gammabar^kj
+            const double Auu = fma(Aud[i][2], gsym(gi, 2, j), fma(Aud[i][1], gsym(gi, 1, j), Aud[i][0] * gsym(gi, 0, j)));
+            t = fma(gsym(gi, i, j), fma((-2.0 / 3.0), dK[j], V[j]), fma(6.0 * Auu, dphi[j], t));
+        }
+        Mv[i] = W2 * t;
+    }
+    // gamma_ij M^i M^j = (M.M + h_ij M^i M^j) / W^2
+#pragma unroll
+    for (int s = 0; s < 6; s++) {
+        const int i = spi(s), j = spj(s);
+        const double hm = (offd(s) ? 2.0 : 1.0) * M.h[s] * Mv[i] * Mv[j];
+        q += (i == j) ? fma(Mv[i], Mv[i], hm) : hm;
+    }
+    return sqrt(q) * M.iW;
 }
 
 // beta^k d_k f, upwinded, and the Kreiss-Oliger dissipation of f, evaluated as

@@ -1,8 +1,9 @@
 // nr_batch.cu -- batched mode: many grids of uneven sizes advanced together,
-// one persistent launch per RK4 substage plus one parity-copy launch, the
-// whole step captured in a CUDA graph; the tile shape is chosen by timing.
+// one launch per RK4 substage over the work items of all grids plus one
+// parity-copy launch, the whole step captured in a CUDA graph; the tile shape
+// is chosen by timing.
 //
-// The persistent kernel and its work items: nr_batch_kernels.cuh.
+// The per-substage kernel and its work items: nr_batch_kernels.cuh.
 #include <string.h>
 
 #include <algorithm>
@@ -36,17 +37,15 @@ struct nr_batch {
     int fam = FAM_SPH;
     bool two_point = false;   // the grids' azimuth holds two points
     int device = 0;
-    int sms = 0;
     cudaStream_t stream = nullptr;
     cudaStream_t cap = nullptr;
     int tile = 0;
-    int blocks = 0;
     int total = 0;
+    int total_d1 = 0;          // items of the first-difference pass
     BGrid* d_grids = nullptr;
     BInner* d_inner = nullptr;
     int n_inner = 0;
     int n_inner_stencil = 0;   // the entries the stages before the last copy
-    int* d_counter = nullptr;
     std::vector<double> dts;   // dts of the current table
     bool table_ok = false;
     cudaGraphExec_t exec = nullptr;
@@ -75,6 +74,8 @@ int build_table(nr_batch* b, const double* dts)
         B.ya = g->ya;
         B.yb = g->yb;
         B.acc = g->acc;
+        B.d1x = g->d1x;
+        B.d1y = g->d1y;
         B.outer = g->outer;
         B.finf = g->finf;
         B.wspeed = g->wspeed;
@@ -94,11 +95,15 @@ int build_table(nr_batch* b, const double* dts)
         B.st[3] = Stage{MODE_STAGE4, enf, 0.0, dt / 6.0};
     }
     b->total = w;
+    int w1 = 0;
+    for (size_t q = 0; q < b->grids.size(); q++) {
+        h[q].d1_begin = w1;
+        w1 += (int)((d1_points(h[q].K) + 255) / 256);
+        h[q].d1_end = w1;
+    }
+    b->total_d1 = w1;
     cudaError_t e = cudaMemcpy(b->d_grids, h.data(), sizeof(BGrid) * h.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return nrk_fail(NR_ECUDA, "batch table upload: %s", cudaGetErrorString(e));
-    b->blocks = b->fam == FAM_SPH ? batch_occupancy_sph(b->two_point, b->tile, b->sms)
-                                  : batch_occupancy_cyl(b->two_point, b->tile, b->sms);
-    if (b->blocks <= 0) return nrk_fail(NR_ECUDA, "occupancy query failed");
     b->dts.assign(dts, dts + b->grids.size());
     b->table_ok = true;
     return NR_OK;
@@ -106,15 +111,18 @@ int build_table(nr_batch* b, const double* dts)
 
 cudaError_t enqueue_stage_launch(nr_batch* b, int stage, cudaStream_t s)
 {
-    return b->fam == FAM_SPH ? batch_stage_launch_sph(b->two_point, b->tile, b->d_grids, (int)b->grids.size(),
-                                                      b->total, b->d_counter + stage, stage, b->blocks, s)
-                             : batch_stage_launch_cyl(b->two_point, b->tile, b->d_grids, (int)b->grids.size(),
-                                                      b->total, b->d_counter + stage, stage, b->blocks, s);
+    cudaError_t e = b->fam == FAM_SPH
+                        ? batch_d1_launch_sph(b->two_point, b->d_grids, (int)b->grids.size(), b->total_d1, stage, s)
+                        : batch_d1_launch_cyl(b->two_point, b->d_grids, (int)b->grids.size(), b->total_d1, stage, s);
+    if (e != cudaSuccess) return e;
+    return b->fam == FAM_SPH
+               ? batch_stage_launch_sph(b->two_point, b->tile, b->d_grids, (int)b->grids.size(), b->total, stage, s)
+               : batch_stage_launch_cyl(b->two_point, b->tile, b->d_grids, (int)b->grids.size(), b->total, stage, s);
 }
 
 cudaError_t enqueue_step(nr_batch* b, cudaStream_t s)
 {
-    cudaError_t e = cudaMemsetAsync(b->d_counter, 0, 4 * sizeof(int), s);
+    cudaError_t e = cudaSuccess;
     for (int stage = 0; stage < 4 && e == cudaSuccess; stage++) {
         e = enqueue_stage_launch(b, stage, s);
         const int ninner = stage == 3 ? b->n_inner : b->n_inner_stencil;
@@ -191,10 +199,8 @@ int nr_batch_create(nr_grid* const* grids, int ngrids, nr_batch** out)
     b->n_inner_stencil = (int)inner.size();
     inner.insert(inner.end(), rest.begin(), rest.end());
     b->n_inner = (int)inner.size();
-    cudaError_t e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_grids, sizeof(BGrid) * ngrids);
+    cudaError_t e = cudaMalloc(&b->d_grids, sizeof(BGrid) * ngrids);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_inner, sizeof(BInner) * std::max<size_t>(inner.size(), 1));
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, 4 * sizeof(int));
     if (e == cudaSuccess && !inner.empty())
         e = cudaMemcpy(b->d_inner, inner.data(), sizeof(BInner) * inner.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
@@ -214,7 +220,6 @@ void nr_batch_destroy(nr_batch* b)
     drop_graph(b);
     if (b->d_grids) cudaFree(b->d_grids);
     if (b->d_inner) cudaFree(b->d_inner);
-    if (b->d_counter) cudaFree(b->d_counter);
     if (b->cap) cudaStreamDestroy(b->cap);
     delete b;
 }
@@ -250,7 +255,6 @@ int nr_batch_autotune(nr_batch* b, const double* dts, int* tile_x, int* tile_y, 
         // stage 1 writes only the stage buffer and the accumulator: the state is untouched
         float tt = 0.f;
         for (int rep = 0; rep < 4; rep++) {
-            cudaMemsetAsync(b->d_counter, 0, sizeof(int), b->stream);
             cudaEventRecord(e0, b->stream);
             cudaError_t e = enqueue_stage_launch(b, 0, b->stream);
             cudaEventRecord(e1, b->stream);

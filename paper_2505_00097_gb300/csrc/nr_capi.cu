@@ -321,7 +321,7 @@ void free_grid(nr_grid* g)
     cudaGetDevice(&prev);
     cudaSetDevice(g->device);
     if (g->exec) cudaGraphExecDestroy(g->exec);
-    void* ptrs[] = {g->y, g->ya, g->yb, g->acc, g->ax0, g->ax1, g->ax2, g->outer, g->inner, g->canon,
+    void* ptrs[] = {g->y, g->ya, g->yb, g->acc, g->d1x, g->d1y, g->ax0, g->ax1, g->ax2, g->outer, g->inner, g->canon,
                     g->finf, g->wspeed, g->partials, g->hres, g->flag, g->mxyz};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -346,7 +346,7 @@ int enqueue_stage(nr_grid* g, cudaStream_t s, const double* yin, double* out, co
     oa.npts = g->n_outer;
     oa.finf = g->finf;
     oa.wspeed = g->wspeed;
-    CUDA_OR_FAIL(launch_rhs(g->K, yin, out, yn, acc, st, s, oa));
+    CUDA_OR_FAIL(launch_rhs(g->K, yin, g->d1x, g->d1y, out, yn, acc, st, s, oa));
     CUDA_OR_FAIL(launch_inner(g->K, g->inner, ninner, out, s));
     return NR_OK;
 }
@@ -551,7 +551,8 @@ int nr_grid_create(int coords, const int Nxx[3], const nr_params* params, nr_gri
     K.eta = P.eta;
     g->nparts = ham_partials_needed(K);
     if ((rc = dmalloc(g, &g->y, set)) || (rc = dmalloc(g, &g->ya, set)) || (rc = dmalloc(g, &g->yb, set)) ||
-        (rc = dmalloc(g, &g->acc, set)) || (rc = dmalloc(g, &g->ax0, a0.size())) ||
+        (rc = dmalloc(g, &g->acc, set)) || (rc = dmalloc(g, &g->d1x, (size_t)N_D1 * G.T)) ||
+        (rc = dmalloc(g, &g->d1y, K.ax < 0 ? (size_t)N_D1 * G.T : 1)) || (rc = dmalloc(g, &g->ax0, a0.size())) ||
         (rc = dmalloc(g, &g->ax1, a1.size())) || (rc = dmalloc(g, &g->ax2, a2.size())) ||
         (rc = dmalloc(g, &g->outer, outer.size())) || (rc = dmalloc(g, &g->inner, inner.size())) ||
         (rc = dmalloc(g, &g->canon, canon.size())) || (rc = dmalloc(g, &g->finf, NR_NGF)) ||
@@ -602,8 +603,8 @@ int nr_query(const nr_grid* g, nr_grid_info* info)
     info->dt_cfl = g->dt_cfl;
     info->device_bytes = g->bytes;
     info->n_inner_stencil = g->n_inner_stencil;
-    // per stage: k_rhs (interior + pure-outer points), then k_inner if it has entries
-    info->launches_per_step = 4 + 3 * (g->n_inner_stencil > 0) + (g->n_inner > 0);
+    // per stage: k_d1, k_rhs (interior + pure-outer points), then k_inner if it has entries
+    info->launches_per_step = 8 + 3 * (g->n_inner_stencil > 0) + (g->n_inner > 0);
     info->pad_ = 0;
     return NR_OK;
 }
@@ -642,7 +643,7 @@ int nr_rhs(nr_grid* g, const double* y_dev, double* rhs_dev)
     if (!g || !y_dev || !rhs_dev || y_dev == rhs_dev) return fail(NR_EINVAL, "bad nr_rhs arguments");
     DeviceGuard dg(g->device);
     Stage st{MODE_RHS, 0, 0.0, 0.0};
-    CUDA_OR_FAIL(launch_rhs(g->K, y_dev, rhs_dev, nullptr, nullptr, st, g->stream));
+    CUDA_OR_FAIL(launch_rhs(g->K, y_dev, g->d1x, g->d1y, rhs_dev, nullptr, nullptr, st, g->stream));
     return NR_OK;
 }
 
@@ -697,6 +698,23 @@ int nr_hamiltonian(nr_grid* g, const double* y_dev, double* H_dev, double* l2_ou
     const double* y = y_dev ? y_dev : g->y;
     if (H_dev) CUDA_OR_FAIL(cudaMemsetAsync(H_dev, 0, sizeof(double) * g->geo.T, g->stream));
     CUDA_OR_FAIL(launch_ham(g->K, y, H_dev, g->P.h_rmin, g->P.h_rmax, g->partials, g->nparts, g->hres, g->stream));
+    if (l2_out || linf_out) {
+        double r[3];
+        CUDA_OR_FAIL(cudaMemcpyAsync(r, g->hres, sizeof r, cudaMemcpyDeviceToHost, g->stream));
+        CUDA_OR_FAIL(cudaStreamSynchronize(g->stream));
+        if (l2_out) *l2_out = r[0];
+        if (linf_out) *linf_out = r[1];
+    }
+    return NR_OK;
+}
+
+int nr_momentum(nr_grid* g, const double* y_dev, double* M_dev, double* l2_out, double* linf_out)
+{
+    if (!g) return fail(NR_EINVAL, "grid is NULL");
+    DeviceGuard dg(g->device);
+    const double* y = y_dev ? y_dev : g->y;
+    if (M_dev) CUDA_OR_FAIL(cudaMemsetAsync(M_dev, 0, sizeof(double) * 3 * g->geo.T, g->stream));
+    CUDA_OR_FAIL(launch_mom(g->K, y, M_dev, g->P.h_rmin, g->P.h_rmax, g->partials, g->nparts, g->hres, g->stream));
     if (l2_out || linf_out) {
         double r[3];
         CUDA_OR_FAIL(cudaMemcpyAsync(r, g->hres, sizeof r, cudaMemcpyDeviceToHost, g->stream));

@@ -74,8 +74,10 @@ struct OuterArgs {
 };
 
 // kernel launchers (nr_kernels.cu)
-cudaError_t launch_rhs(const GridK& G, const double* yin, double* out, const double* yn, double* acc, Stage st,
-                       cudaStream_t s, OuterArgs oa = OuterArgs());
+// k_d1 on yin into d1x / d1y (N_D1 sets of T doubles each; d1y used on general
+// grids only), then k_rhs
+cudaError_t launch_rhs(const GridK& G, const double* yin, double* d1x, double* d1y, double* out, const double* yn,
+                       double* acc, Stage st, cudaStream_t s, OuterArgs oa = OuterArgs());
 cudaError_t launch_outer(const GridK& G, const OuterPt* pts, int npts, const double* yin, double* out,
                          const double* yn, double* acc, const double* finf, const double* wspeed, Stage st,
                          cudaStream_t s);
@@ -83,6 +85,8 @@ cudaError_t launch_inner(const GridK& G, const InnerPt* pts, int npts, double* y
 cudaError_t launch_bl(const GridK& G, const int* canon_idx, long ncanon, int np, const double* mxyz, double amp,
                       uint64_t seed, double* y, cudaStream_t s);
 cudaError_t launch_ham(const GridK& G, const double* y, double* H, double rmin, double rmax, double* partials,
+                       int nparts, double* result, cudaStream_t s);
+cudaError_t launch_mom(const GridK& G, const double* y, double* M, double rmin, double rmax, double* partials,
                        int nparts, double* result, cudaStream_t s);
 int ham_partials_needed(const GridK& G);
 cudaError_t launch_finite(const GridK& G, const double* y, int* flag, cudaStream_t s);
@@ -114,6 +118,7 @@ struct nr_grid {
     // device buffers
     double *y = nullptr, *ya = nullptr, *yb = nullptr, *acc = nullptr;
     double *ax0 = nullptr, *ax1 = nullptr, *ax2 = nullptr;
+    double *d1x = nullptr, *d1y = nullptr;   // stored first differences (k_d1), N_D1 sets each
     nrk::OuterPt* outer = nullptr;
     nrk::InnerPt* inner = nullptr;
     int* canon = nullptr;

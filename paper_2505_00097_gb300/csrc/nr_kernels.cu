@@ -1,5 +1,7 @@
 // nr_kernels.cu -- sm_103a FP64 kernels of the BSSN hot path.
 //
+//   k_d1      raw first differences along axes 0 (and 1) of the gridfunctions
+//             with second derivatives, read by k_rhs for its mixed derivatives
 //   k_rhs     interior right-hand side (Sec. 2.1 equations, upwinded advection,
 //             Kreiss-Oliger dissipation) with the RK4 stage update and the
 //             det(gammabar) enforcement fused into its epilogue; in an RK
@@ -10,7 +12,8 @@
 //             per gridfunction
 //   k_bl      Brill-Lindquist data + SplitMix64 perturbation
 //   k_ham     Hamiltonian constraint (Eq. Hconstraint) + per-block norm partials
-//   k_ham_reduce  fixed-order reduction of the partials
+//   k_mom     momentum constraint (Eq. Mconstraint) + per-block norm partials
+//   k_ham_reduce  fixed-order reduction of the partials (both constraints)
 //   k_finite  NaN/Inf guard on alpha and W
 #include <math.h>
 
@@ -23,9 +26,22 @@ namespace nrk {
 
 constexpr int RHS_BX = 32, RHS_BY = 4;
 
+// Raw first differences along axis 0 (and, on a general grid, axis 1) of the N_D1
+// gridfunctions with second derivatives, at interior i0 and every row a mixed
+// stencil of an interior point reads: i1 and i2 within two points of the interior,
+// except along a two-point azimuth (no mixed derivatives there); the axis-1 set at
+// interior i1 only.
+template <int AX>
+__global__ void __launch_bounds__(256) k_d1(GridK G, const double* __restrict__ y, double* d1x, double* d1y)
+{
+    d1_point<AX>(G, y, d1x, d1y, (long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 template <int FAM, int AX>
-__global__ void __launch_bounds__(RHS_BX* RHS_BY) k_rhs(GridK G, const double* __restrict__ yin, double* out,
-                                                        const double* yn, double* acc, Stage st, OuterArgs oa)
+__global__ void __launch_bounds__(RHS_BX* RHS_BY) k_rhs(GridK G, const double* __restrict__ yin,
+                                                        const double* __restrict__ d1x, const double* __restrict__ d1y,
+                                                        double* out, const double* yn, double* acc, Stage st,
+                                                        OuterArgs oa)
 {
     // the first oa.nblocks blocks take the pure-outer points, 128 per block
     if ((int)blockIdx.x < oa.nblocks) {
@@ -39,7 +55,7 @@ __global__ void __launch_bounds__(RHS_BX* RHS_BY) k_rhs(GridK G, const double* _
     const int i = (b % nbx) * RHS_BX + threadIdx.x;
     const int j = (b / nbx) * RHS_BY + threadIdx.y;
     if (i >= G.N0 || j >= G.N1 * G.N2) return;
-    rhs_point_stage<FAM, AX>(G, yin, out, yn, acc, st, i, j);
+    rhs_point_stage<FAM, AX, true>(G, yin, d1x, d1y, out, yn, acc, st, i, j);
 }
 
 template <int FAM>
@@ -97,36 +113,9 @@ __global__ void k_bl(GridK G, const int* __restrict__ canon, long ncanon, int np
 
 constexpr int HAM_THREADS = 128;
 
-template <int FAM>
-__global__ void __launch_bounds__(HAM_THREADS) k_ham(GridK G, const double* __restrict__ y, double* H, double rmin,
-                                                      double rmax, double* partials)
+// per-block partial norms (sum of squares, max, count) of a constraint, in a fixed order
+__device__ __forceinline__ void block_partials(double s2, double mx, double cnt, double* partials)
 {
-    const long t = (long)blockIdx.x * HAM_THREADS + threadIdx.x;
-    const long nint = (long)G.N0 * G.N1 * G.N2;
-    double s2 = 0.0, mx = 0.0, cnt = 0.0;
-    if (t < nint) {
-        const int i = (int)(t % G.N0), j = (int)(t / G.N0);
-        const int p0 = i + G.NG, p1 = j % G.N1 + G.NG, p2 = j / G.N1 + G.NG;
-        const long idx = p0 + (long)G.n0 * (p1 + (long)G.n1 * p2);
-        PointIn P;
-        P.y = y + idx;
-        P.T = G.T;
-        P.st[0] = 1;
-        P.st[1] = G.n0;
-        P.st[2] = (long)G.n0 * G.n1;
-        P.ox = 0;
-        P.g = make_geo<FAM>(G, p0, p1, p2);
-        const double h = ham_core<FAM>(P);
-        if (H) H[idx] = h;
-        double x[3];
-        cart_of(G, p0, p1, p2, x);
-        const double r = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
-        if (r >= rmin && r <= rmax) {
-            s2 = h * h;
-            mx = fabs(h);
-            cnt = 1.0;
-        }
-    }
     __shared__ double sh[3][HAM_THREADS];
     sh[0][threadIdx.x] = s2;
     sh[1][threadIdx.x] = mx;
@@ -145,6 +134,83 @@ __global__ void __launch_bounds__(HAM_THREADS) k_ham(GridK G, const double* __re
         partials[3 * blockIdx.x + 1] = sh[1][0];
         partials[3 * blockIdx.x + 2] = sh[2][0];
     }
+}
+
+template <int FAM>
+__global__ void __launch_bounds__(HAM_THREADS) k_ham(GridK G, const double* __restrict__ y, double* H, double rmin,
+                                                      double rmax, double* partials)
+{
+    const long t = (long)blockIdx.x * HAM_THREADS + threadIdx.x;
+    const long nint = (long)G.N0 * G.N1 * G.N2;
+    double s2 = 0.0, mx = 0.0, cnt = 0.0;
+    if (t < nint) {
+        const int i = (int)(t % G.N0), j = (int)(t / G.N0);
+        const int p0 = i + G.NG, p1 = j % G.N1 + G.NG, p2 = j / G.N1 + G.NG;
+        const long idx = p0 + (long)G.n0 * (p1 + (long)G.n1 * p2);
+        PointIn P;
+        P.y = y + idx;
+        P.T = G.T;
+        P.st[0] = 1;
+        P.st[1] = G.n0;
+        P.st[2] = (long)G.n0 * G.n1;
+        P.ox = 0;
+        P.dx = nullptr;
+        P.dy = nullptr;
+        P.g = make_geo<FAM>(G, p0, p1, p2);
+        const double h = ham_core<FAM>(P);
+        if (H) H[idx] = h;
+        double x[3];
+        cart_of(G, p0, p1, p2, x);
+        const double r = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+        if (r >= rmin && r <= rmax) {
+            s2 = h * h;
+            mx = fabs(h);
+            cnt = 1.0;
+        }
+    }
+    block_partials(s2, mx, cnt, partials);
+}
+
+// momentum constraint (Eq. Mconstraint): rescaled M^i at interior points (M: 3 gridfunctions, or
+// NULL) and per-block partial norms of |M|
+template <int FAM>
+__global__ void __launch_bounds__(HAM_THREADS) k_mom(GridK G, const double* __restrict__ y, double* Mout, double rmin,
+                                                      double rmax, double* partials)
+{
+    const long t = (long)blockIdx.x * HAM_THREADS + threadIdx.x;
+    const long nint = (long)G.N0 * G.N1 * G.N2;
+    double s2 = 0.0, mx = 0.0, cnt = 0.0;
+    if (t < nint) {
+        const int i = (int)(t % G.N0), j = (int)(t / G.N0);
+        const int p0 = i + G.NG, p1 = j % G.N1 + G.NG, p2 = j / G.N1 + G.NG;
+        const long idx = p0 + (long)G.n0 * (p1 + (long)G.n1 * p2);
+        PointIn P;
+        P.y = y + idx;
+        P.T = G.T;
+        P.st[0] = 1;
+        P.st[1] = G.n0;
+        P.st[2] = (long)G.n0 * G.n1;
+        P.ox = 0;
+        P.dx = nullptr;
+        P.dy = nullptr;
+        P.g = make_geo<FAM>(G, p0, p1, p2);
+        double Mv[3];
+        const double m = mom_core<FAM>(P, Mv);
+        if (Mout) {
+            Mout[idx] = Mv[0];
+            Mout[G.T + idx] = Mv[1];
+            Mout[2 * G.T + idx] = Mv[2];
+        }
+        double x[3];
+        cart_of(G, p0, p1, p2, x);
+        const double r = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+        if (r >= rmin && r <= rmax) {
+            s2 = m * m;
+            mx = m;
+            cnt = 1.0;
+        }
+    }
+    block_partials(s2, mx, cnt, partials);
 }
 
 // one block; fixed order: thread t sums partials t, t+256, ..., then a tree
@@ -211,19 +277,28 @@ cudaError_t launch_fp64_probe(int blocks, int iters, double* sink, cudaStream_t 
 
 // ------------------------------------------------------------ launchers
 
-cudaError_t launch_rhs(const GridK& G, const double* yin, double* out, const double* yn, double* acc, Stage st,
-                       cudaStream_t s, OuterArgs oa)
+cudaError_t launch_rhs(const GridK& G, const double* yin, double* d1x, double* d1y, double* out, const double* yn,
+                       double* acc, Stage st, cudaStream_t s, OuterArgs oa)
 {
+    // the stored first differences of yin
+    {
+        const unsigned b = (unsigned)((d1_points(G) + 255) / 256);
+        if (G.ax == 1) k_d1<1><<<b, 256, 0, s>>>(G, yin, d1x, d1y);
+        else if (G.ax == 2) k_d1<2><<<b, 256, 0, s>>>(G, yin, d1x, d1y);
+        else k_d1<-1><<<b, 256, 0, s>>>(G, yin, d1x, d1y);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     dim3 blk(RHS_BX, RHS_BY);
     oa.nblocks = (oa.npts + RHS_BX * RHS_BY - 1) / (RHS_BX * RHS_BY);
     const long nb = (long)((G.N0 + RHS_BX - 1) / RHS_BX) * ((G.N1 * G.N2 + RHS_BY - 1) / RHS_BY) + oa.nblocks;
     dim3 grd((unsigned)nb);
     if (G.fam == FAM_SPH) {
-        if (G.ax == 2) k_rhs<FAM_SPH, 2><<<grd, blk, 0, s>>>(G, yin, out, yn, acc, st, oa);
-        else k_rhs<FAM_SPH, -1><<<grd, blk, 0, s>>>(G, yin, out, yn, acc, st, oa);
+        if (G.ax == 2) k_rhs<FAM_SPH, 2><<<grd, blk, 0, s>>>(G, yin, d1x, d1y, out, yn, acc, st, oa);
+        else k_rhs<FAM_SPH, -1><<<grd, blk, 0, s>>>(G, yin, d1x, d1y, out, yn, acc, st, oa);
     } else {
-        if (G.ax == 1) k_rhs<FAM_CYL, 1><<<grd, blk, 0, s>>>(G, yin, out, yn, acc, st, oa);
-        else k_rhs<FAM_CYL, -1><<<grd, blk, 0, s>>>(G, yin, out, yn, acc, st, oa);
+        if (G.ax == 1) k_rhs<FAM_CYL, 1><<<grd, blk, 0, s>>>(G, yin, d1x, d1y, out, yn, acc, st, oa);
+        else k_rhs<FAM_CYL, -1><<<grd, blk, 0, s>>>(G, yin, d1x, d1y, out, yn, acc, st, oa);
     }
     return cudaGetLastError();
 }
@@ -271,6 +346,19 @@ cudaError_t launch_ham(const GridK& G, const double* y, double* H, double rmin, 
         k_ham<FAM_SPH><<<nparts, HAM_THREADS, 0, s>>>(G, y, H, rmin, rmax, partials);
     else
         k_ham<FAM_CYL><<<nparts, HAM_THREADS, 0, s>>>(G, y, H, rmin, rmax, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_ham_reduce<<<1, 256, 0, s>>>(partials, nparts, result);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mom(const GridK& G, const double* y, double* M, double rmin, double rmax, double* partials,
+                       int nparts, double* result, cudaStream_t s)
+{
+    if (G.fam == FAM_SPH)
+        k_mom<FAM_SPH><<<nparts, HAM_THREADS, 0, s>>>(G, y, M, rmin, rmax, partials);
+    else
+        k_mom<FAM_CYL><<<nparts, HAM_THREADS, 0, s>>>(G, y, M, rmin, rmax, partials);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_ham_reduce<<<1, 256, 0, s>>>(partials, nparts, result);

@@ -106,6 +106,8 @@ __global__ void __launch_bounds__(NA_THREADS) k_na_ham(GridK G, const double* __
         P.st[1] = G.n0;
         P.st[2] = (long)G.n0 * G.n1;
         P.ox = 0;
+        P.dx = nullptr;
+        P.dy = nullptr;
         P.g = make_geo<FAM>(G, p0, p1, p2);
         const double h = ham_core<FAM>(P);
         if (H) H[idx] = h;

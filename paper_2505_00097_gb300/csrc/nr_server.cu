@@ -5,7 +5,7 @@
 // (grid allocated, initial data set) while the summed device bytes stay
 // within the HBM budget and a slot is free, then advances a selection of the
 // resident requests together, as one nr_batch per kind of grid (coordinate
-// family x azimuth kind; one persistent launch per RK4 substage for each).
+// family x azimuth kind; one launch per RK4 substage for each).
 // The policy orders both steps:
 //   FIFO: arrival order;
 //   SRPT: least remaining work first (remaining steps x interior points),
@@ -59,8 +59,9 @@ struct Request {
 size_t grid_bytes_estimate(const int N[3])
 {
     const size_t T = (size_t)(N[0] + 6) * (N[1] + 6) * (N[2] + 6);
-    // four 24-gridfunction sets + maps/lists (generous per-point allowance)
-    return T * (4 * 24 * sizeof(double) + 64);
+    // four 24-gridfunction sets, two sets of stored first differences (11 gridfunctions
+    // each), maps and lists (generous per-point allowance)
+    return T * (4 * 24 * sizeof(double) + 2 * 11 * sizeof(double) + 64);
 }
 
 }  // namespace

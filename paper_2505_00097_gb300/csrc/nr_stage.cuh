@@ -1,5 +1,5 @@
 // nr_stage.cuh -- per-point bodies of the RK4-stage kernels, shared by the
-// single-grid kernels (nr_kernels.cu) and the batched persistent kernel
+// single-grid kernels (nr_kernels.cu) and the batched kernel
 // (nr_batch.cu) so that both run bit-identical arithmetic per point.
 #pragma once
 
@@ -81,10 +81,14 @@ __device__ __forceinline__ int gf_type(int g)
 
 // one interior point (interior-relative i in [0,N0), j = i1 + N1 i2 in [0, N1 N2)) of an RK stage:
 // right-hand side, upwinded advection, dissipation and the stage epilogue.  AX: the azimuthal axis
-// when it holds two points (G.ax), else -1
-template <int FAM, int AX>
-__device__ __forceinline__ void rhs_point_stage(const GridK& G, const double* __restrict__ yin, double* out,
-                                                const double* yn, double* acc, const Stage& st, int i, int j)
+// when it holds two points (G.ax), else -1.  S: the raw first differences along axes 0 and 1 of the
+// gridfunctions with second derivatives are read from d1x, d1y (N_D1 sets of T doubles; d1y only
+// for AX = -1), as k_d1 stored them from yin; the result is bitwise the same either way.
+template <int FAM, int AX, bool S>
+__device__ __forceinline__ void rhs_point_stage(const GridK& G, const double* __restrict__ yin,
+                                                const double* __restrict__ d1x, const double* __restrict__ d1y,
+                                                double* out, const double* yn, double* acc, const Stage& st, int i,
+                                                int j)
 {
     const int p0 = i + G.NG, p1 = j % G.N1 + G.NG, p2 = j / G.N1 + G.NG;
     const long idx = p0 + (long)G.n0 * (p1 + (long)G.n1 * p2);
@@ -97,11 +101,43 @@ __device__ __forceinline__ void rhs_point_stage(const GridK& G, const double* __
     if constexpr (AX == 1) P.ox = p1 == G.NG ? P.st[1] : -P.st[1];
     else if constexpr (AX == 2) P.ox = p2 == G.NG ? P.st[2] : -P.st[2];
     else P.ox = 0;
+    P.dx = S ? d1x + idx : nullptr;
+    P.dy = (S && AX < 0) ? d1y + idx : nullptr;
     P.g = make_geo<FAM>(G, p0, p1, p2);
     double k[NGF];
-    rhs_core<FAM, AX>(P, G.eta, k);
+    rhs_core<FAM, AX, S>(P, G.eta, k);
     add_adv_ko<AX>(P.y, G.T, P.st, P.ox, P.g.D, G.sigma_metric, G.sigma_gauge, k);
     stage_store(st, G.T, idx, k, yn, out, acc);
+}
+
+// Points of the stored first differences (k_d1): interior i0, and i1 and i2 within
+// two points of the interior except along a two-point azimuth, which has no mixed
+// derivatives; the axis-1 set is taken at interior i1 only (general grids).
+__host__ __device__ inline long d1_points(const GridK& G)
+{
+    const int E1 = G.ax == 1 ? 0 : 2, E2 = G.ax == 2 ? 0 : 2;
+    return (long)G.N0 * (G.N1 + 2 * E1) * (G.N2 + 2 * E2);
+}
+
+// point t of that region: raw first differences along axis 0 (and 1) of the N_D1
+// gridfunctions with second derivatives
+template <int AX>
+__device__ __forceinline__ void d1_point(const GridK& G, const double* __restrict__ y, double* d1x, double* d1y, long t)
+{
+    constexpr int E1 = AX == 1 ? 0 : 2, E2 = AX == 2 ? 0 : 2;
+    const int L1 = G.N1 + 2 * E1;
+    if (t >= d1_points(G)) return;
+    const int i = (int)(t % G.N0);
+    const long r = t / G.N0;
+    const int p0 = i + G.NG, p1 = (int)(r % L1) - E1 + G.NG, p2 = (int)(r / L1) - E2 + G.NG;
+    const long idx = p0 + (long)G.n0 * (p1 + (long)G.n1 * p2);
+    const bool ycol = AX < 0 && p1 >= G.NG && p1 < G.NG + G.N1;
+#pragma unroll
+    for (int q = 0; q < N_D1; q++) {
+        const double* f = y + (long)d1gf(q) * G.T + idx;
+        d1x[(long)q * G.T + idx] = d1raw(f, 1);
+        if (ycol) d1y[(long)q * G.T + idx] = d1raw(f, G.n0);
+    }
 }
 
 // one pure-outer ghost point of an RK stage: radiation condition and the stage epilogue

@@ -1,4 +1,4 @@
-"""Batched mode: many uneven grids advanced by one persistent launch per RK4 substage.
+"""Batched mode: many uneven grids advanced by one launch per RK4 substage over all their tiles.
 
 Each grid's state after n batched steps must be bitwise the state after n
 single-grid steps (nr_rk4_step) from the same initial data -- for every tile
