@@ -66,7 +66,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["headon", "single_puncture", "large3d", "batch", "served"],
+    ap.add_argument("--workload", choices=["headon", "headon8", "single_puncture", "large3d", "batch", "served"],
                     default="headon")
     ap.add_argument("--batch-runs", type=int, default=64)
     ap.add_argument("--served-requests", type=int, default=24)
@@ -82,7 +82,7 @@ def parse():
 
 def workload(name: str) -> dict:
     return {"headon": W.config_headon, "single_puncture": W.config_single_puncture,
-            "large3d": W.config_large3d}[name]()
+            "large3d": W.config_large3d, "headon8": W.config_headon8}[name]()
 
 
 def config_of(spec: dict, extra: dict | None = None) -> dict:
@@ -93,10 +93,11 @@ def config_of(spec: dict, extra: dict | None = None) -> dict:
         "ghost_zones": spec["NG"],
         "steps_in_config": spec["steps"],
         "h_every": spec["h_every"],
-        "fd_order": 4,
-        "ko_sigma": spec["ko_sigma"],
+        "fd_order": 2 * (spec["NG"] - 1),
+        "ko_sigma": spec["ko_sigma"] if not isinstance(spec["ko_sigma"], (list, tuple)) or len(set(spec["ko_sigma"])) > 2
+        else {"metric": spec["ko_sigma"][0], "gauge": spec["ko_sigma"][17]},
         "cfl": spec["cfl"],
-        "integrator": "RK4",
+        "integrator": "SSPRK3" if spec.get("integrator", "rk4") == "ssprk3" else "RK4",
         "l2_policy": "inputs larger than L2 (4 resident 24-gridfunction sets)",
     }
     if extra:
@@ -213,23 +214,25 @@ def oracle_threads() -> int:
 
 
 def cpu_baseline(spec: dict, seconds: float) -> dict:
-    """The oracle as it stands, on the host cores: RK4 steps of the workload until `seconds` pass."""
+    """The oracle as it stands, on the host cores: time steps of the workload (its integrator) until
+    `seconds` pass."""
     from oracle.oracle import Oracle
 
     o = Oracle(dict(spec, nthreads=0))
     y = o.brill_lindquist(spec["masses"], spec["positions"], spec["perturb_amp"], spec["seed"])
     dt = o.dt()
+    ssp = spec.get("integrator", "rk4") == "ssprk3"
     steps = 0
     t0 = time.perf_counter()
     while True:
-        o.rk4(y, dt, 1)
+        (o.ssprk3 if ssp else o.rk4)(y, dt, 1)
         steps += 1
         if time.perf_counter() - t0 >= seconds:
             break
     el = time.perf_counter() - t0
     pts = math.prod(spec["N"])
-    return {"value": pts * 4 * steps / el, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
-            "sample": f"first {steps} RK4 steps of {spec['name']} (full grid), {el:.1f} s"}
+    return {"value": pts * (3 if ssp else 4) * steps / el, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
+            "sample": f"first {steps} {'SSPRK3' if ssp else 'RK4'} steps of {spec['name']} (full grid), {el:.1f} s"}
 
 
 def run_reference(args, spec):
@@ -285,12 +288,16 @@ def run_ours(args, spec, world, rank, local):
     pts = g.interior
     h_every = int(spec["h_every"])
     stream = torch.cuda.current_stream(dev)   # the library's stream is the legacy stream of this device
+    ssp = spec.get("integrator", "rk4") == "ssprk3"
+    substeps = 3 if ssp else 4
+    step = g.ssprk3_step if ssp else g.rk4_step
+    per_step = g.info.launches_per_ssprk3_step if ssp else g.info.launches_per_step
 
     def run_steps(n, start):
         launches = 0
         for s in range(n):
-            g.rk4_step(dt, 1)
-            launches += g.info.launches_per_step
+            step(dt, 1)
+            launches += per_step
             if h_every and (start + s + 1) % h_every == 0:
                 g.hamiltonian()
                 launches += 2
@@ -321,7 +328,7 @@ def run_ours(args, spec, world, rank, local):
         dist.barrier()
     ms_max = reduce_max(dist, ms, dev)
     g.check_finite()
-    value = world * pts * 4 * args.steps / (ms_max * 1e-3)
+    value = world * pts * substeps * args.steps / (ms_max * 1e-3)
 
     # dominant kernels: one RHS evaluation (k_d1 + k_rhs), timed alone with CUDA events on the same stream
     T = g.T
@@ -376,9 +383,10 @@ def run_ours(args, spec, world, rank, local):
         torch.cuda.synchronize()
         el = reduce_max(dist, time.perf_counter() - t0, dev)
         nbytes = 24 * T * 8
-        e2e = {"value": world * pts * 4 * n_e2e / el, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+        e2e = {"value": world * pts * substeps * n_e2e / el, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes, "steps": n_e2e,
-               "path": "nr_set_state(pinned host) + nr_rk4_step + nr_get_state(pinned host) per step"}
+               "path": f"nr_set_state(pinned host) + {'nr_ssprk3_step' if ssp else 'nr_rk4_step'} + "
+                       "nr_get_state(pinned host) per step"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

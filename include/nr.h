@@ -71,8 +71,14 @@ enum { NR_NGF = 24 };
  *   eta: Gamma-driver damping; cfl: CFL factor.
  *   wavespeed, f_inf: radiation condition d_t f = -v [(x^j/r) d_j f + (f - f_inf)/r].
  *   h_rmin, h_rmax: radius band of the Hamiltonian-constraint norms.
- *   NG must be 3.  enforce_detgb: rescale h so det(gammabar)=det(gammahat)
- *   after every RK substage (the Lagrangian choice of Sec. 2.1).
+ *   NG: ghost layers, N_G = N_FD/2 + 1 (Sec. 3): 3 selects the 4th-order
+ *     scheme (6th-difference dissipation over 64 S dxx), 5 the 8th-order
+ *     production scheme of Sec. 4.1 (10th-difference dissipation over
+ *     1024 S dxx, 8th-order one-sided derivatives in the radiation condition);
+ *     any other value is NR_EINVAL.  Batched and served modes and
+ *     nr_hamiltonian_noalloc take NG = 3 only.
+ *   enforce_detgb: rescale h so det(gammabar)=det(gammahat) after every RK
+ *     substage (the Lagrangian choice of Sec. 2.1).
  *   stream: cudaStream_t used for all device work of the grid (NULL: legacy stream). */
 typedef struct {
     double ampl[3];
@@ -105,7 +111,7 @@ typedef struct {
     int64_t n_inner_stencil; /* inner ghosts the RK stages before the last copy (all, unless the
                                 azimuth holds two points: then its ghosts are copied in stage 4 only) */
     int launches_per_step;   /* kernel launches of one nr_rk4_step */
-    int pad_;
+    int launches_per_ssprk3_step; /* kernel launches of one nr_ssprk3_step */
 } nr_grid_info;
 
 /* Defaults: ko_sigma 0.3, eta 2, cfl 0.5, wavespeed 1, f_inf 1 for W and alpha
@@ -157,6 +163,15 @@ int nr_apply_inner_bcs(nr_grid* grid, double* gfs_dev);
  * one step (nr_grid_info.launches_per_step) are captured once in a CUDA graph
  * (re-captured when dt changes) and replayed.  dt > 0, nsteps >= 0. */
 int nr_rk4_step(nr_grid* grid, double dt, int nsteps);
+
+/* nsteps steps of SSPRK3 (Gottlieb-Shu-Tadmor; the integrator of the paper's
+ * production runs, Sec. 4.1) on the grid-owned state:
+ *   y1 = y + dt k(y),  y2 = 3/4 y + 1/4 (y1 + dt k(y1)),
+ *   y_{n+1} = 1/3 y + 2/3 (y2 + dt k(y2)),
+ * each k with the boundary conditions of Sec. 3 and each stage followed by
+ * det(gammabar) enforcement when enforce_detgb is set.  Three RHS evaluations
+ * per step, captured in a CUDA graph like nr_rk4_step.  dt > 0, nsteps >= 0. */
+int nr_ssprk3_step(nr_grid* grid, double dt, int nsteps);
 
 /* Hamiltonian constraint (Eq. Hconstraint) at interior points of y_dev (NULL:
  * the grid-owned state).  H_dev (NULL allowed): caller-owned T doubles, ghost

@@ -23,7 +23,8 @@ COORDS = {"sinh_spherical": 0, "sinh_cylindrical": 1, "spherical": 2}
 # every entry point declared in include/nr.h
 EXPORTS = (
     "nr_params_default", "nr_grid_create", "nr_grid_destroy", "nr_query", "nr_set_brill_lindquist", "nr_rhs",
-    "nr_apply_bcs", "nr_apply_inner_bcs", "nr_rk4_step", "nr_hamiltonian", "nr_momentum", "nr_get_state",
+    "nr_apply_bcs", "nr_apply_inner_bcs", "nr_rk4_step", "nr_ssprk3_step", "nr_hamiltonian", "nr_momentum",
+    "nr_get_state",
     "nr_set_state",
     "nr_sync", "nr_check_finite", "nr_build_maps", "nr_dt_cfl", "nr_fp64_peak", "nr_hamiltonian_noalloc",
     "nr_batch_create", "nr_batch_destroy", "nr_batch_set_tile", "nr_batch_autotune", "nr_batch_rk4_step",
@@ -70,7 +71,7 @@ class NrGridInfo(ctypes.Structure):
         ("device_bytes", ctypes.c_size_t),
         ("n_inner_stencil", ctypes.c_int64),
         ("launches_per_step", ctypes.c_int),
-        ("pad_", ctypes.c_int),
+        ("launches_per_ssprk3_step", ctypes.c_int),
     ]
 
 
@@ -102,6 +103,7 @@ def lib() -> ctypes.CDLL:
     L.nr_apply_bcs.argtypes = [vp, vp, vp]
     L.nr_apply_inner_bcs.argtypes = [vp, vp]
     L.nr_rk4_step.argtypes = [vp, ctypes.c_double, ctypes.c_int]
+    L.nr_ssprk3_step.argtypes = [vp, ctypes.c_double, ctypes.c_int]
     L.nr_hamiltonian.argtypes = [vp, vp, vp, dp, dp]
     L.nr_momentum.argtypes = [vp, vp, vp, dp, dp]
     L.nr_get_state.argtypes = [vp, vp, ctypes.c_int]
@@ -265,6 +267,9 @@ class Grid:
 
     def rk4_step(self, dt: float, nsteps: int = 1) -> None:
         _check(lib().nr_rk4_step(self.h, float(dt), int(nsteps)))
+
+    def ssprk3_step(self, dt: float, nsteps: int = 1) -> None:
+        _check(lib().nr_ssprk3_step(self.h, float(dt), int(nsteps)))
 
     def hamiltonian(self, y=None, H=None):
         l2, linf = ctypes.c_double(), ctypes.c_double()

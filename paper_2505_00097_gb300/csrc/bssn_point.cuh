@@ -83,13 +83,81 @@ __device__ __forceinline__ double koraw(const double* f, long s)
     return fma(15.0, ld(f - s) + ld(f + s), fma(-6.0, ld(f - 2 * s) + ld(f + 2 * s), ld(f - 3 * s) + ld(f + 3 * s)));
 }
 
+// ---- 8th-order stencils (the production scheme of Sec. 4.1, N_G = 5), integer
+// weights: first derivative over 840 h, second over 5040 h^2 (the scale factors
+// are in Geo); a mixed derivative is the first-derivative stencil applied to the
+// first differences of the neighbouring rows.
+__device__ __forceinline__ double d1w8(double m4, double m3, double m2, double m1, double p1, double p2, double p3,
+                                       double p4)
+{
+    double t = fma(-3.0, p4 - m4, 32.0 * (p3 - m3));
+    t = fma(-168.0, p2 - m2, t);
+    return fma(672.0, p1 - m1, t);
+}
+__device__ __forceinline__ double d1raw8(const double* f, long s)
+{
+    return d1w8(ld(f - 4 * s), ld(f - 3 * s), ld(f - 2 * s), ld(f - s), ld(f + s), ld(f + 2 * s), ld(f + 3 * s),
+                ld(f + 4 * s));
+}
+__device__ __forceinline__ double d2raw8(const double* f, long s)
+{
+    double t = fma(-9.0, ld(f + 4 * s) + ld(f - 4 * s), 128.0 * (ld(f + 3 * s) + ld(f - 3 * s)));
+    t = fma(-1008.0, ld(f + 2 * s) + ld(f - 2 * s), t);
+    t = fma(8064.0, ld(f + s) + ld(f - s), t);
+    return fma(-14350.0, ld(f), t);
+}
+__device__ __forceinline__ double mixraw8(const double* f, long sa, long sb)
+{
+    return d1w8(d1raw8(f - 4 * sb, sa), d1raw8(f - 3 * sb, sa), d1raw8(f - 2 * sb, sa), d1raw8(f - sb, sa),
+                d1raw8(f + sb, sa), d1raw8(f + 2 * sb, sa), d1raw8(f + 3 * sb, sa), d1raw8(f + 4 * sb, sa));
+}
+
+// Finite-difference families: order ORD = N_FD with N_G = ORD/2 + 1 ghost layers
+// (Sec. 3).  den1, den2: denominators of the integer first- and second-derivative
+// weights (Geo: D = 1/(den1 dxx S), D2 = 1/(den2 dxx^2 S^2)); ko_den = 2^(2r) of
+// the Kreiss-Oliger difference of order 2r = ORD + 2; ax_*: the second, upwind and
+// dissipation differences along a two-point azimuth as multiples of f_other - f.
+template <int ORD>
+struct FD;
+template <>
+struct FD<4> {
+    static constexpr int M = 2;
+    static constexpr double den1 = 12.0, den2 = 12.0, ko_den = 64.0;
+    static constexpr double ax_d2 = 32.0, ax_up = 16.0, ax_ko = 32.0;
+};
+template <>
+struct FD<8> {
+    static constexpr int M = 4;
+    static constexpr double den1 = 840.0, den2 = 5040.0, ko_den = 1024.0;
+    static constexpr double ax_d2 = 16384.0, ax_up = 768.0, ax_ko = 512.0;
+};
+template <int ORD>
+__device__ __forceinline__ double d1r(const double* f, long s)
+{
+    if constexpr (ORD == 4) return d1raw(f, s);
+    else return d1raw8(f, s);
+}
+template <int ORD>
+__device__ __forceinline__ double d2r(const double* f, long s)
+{
+    if constexpr (ORD == 4) return d2raw(f, s);
+    else return d2raw8(f, s);
+}
+template <int ORD>
+__device__ __forceinline__ double mixr(const double* f, long sa, long sb)
+{
+    if constexpr (ORD == 4) return mixraw(f, sa, sb);
+    else return mixraw8(f, sa, sb);
+}
+
 // ---- a periodic azimuthal axis that holds two points (AX = 1 for
 // cylindrical-like, AX = 2 for spherical-like coordinates; AX = -1: none).
 // Along it the neighbours at offsets +-1 and +-3 are the other slice and those
 // at +-2 the point itself, so the centred first difference and every mixed
 // difference that involves the axis vanish identically, and the second,
-// upwind and sixth differences are 32, 16 and 32 times f_other - f.  The
-// kernels then skip those stencils; the result is the same discrete operator.
+// upwind and sixth differences are 32, 16 and 32 times f_other - f (8th order:
+// 16384, 768 and 512 for the second, upwind and tenth differences).  The kernels
+// then skip those stencils; the result is the same discrete operator.
 template <int FAM, int AX>
 __host__ __device__ constexpr bool ax_ok()
 {
@@ -124,48 +192,48 @@ __device__ __forceinline__ double dot3(double a0, double a1, double a2, const do
 // H_kl f = e_k e_l f - omega^m_kl e_m f  (symmetric in kl); ox is the offset of
 // the other slice of the two-point axis
 // fx, fy: stored first differences of f along axes 0 and 1 (S = true)
-template <int FAM, int KL, int AX, bool S>
+template <int FAM, int KL, int AX, bool S, int ORD>
 __device__ __forceinline__ double hess(const double* f, const double* fx, const double* fy, const long st[3], long ox,
                                        const Geo& g, const double df[3])
 {
     if constexpr (hzero(AX, KL)) return 0.0;
-    if constexpr (KL == 0) return fma(g.D2[0], d2raw(f, st[0]), -g.d00 * df[0]);
-    if constexpr (KL == 1) return fma(g.DD[0], S ? d1raw(fx, st[1]) : mixraw(f, st[0], st[1]), -g.a * df[1]);
+    if constexpr (KL == 0) return fma(g.D2[0], d2r<ORD>(f, st[0]), -g.d00 * df[0]);
+    if constexpr (KL == 1) return fma(g.DD[0], S ? d1r<ORD>(fx, st[1]) : mixr<ORD>(f, st[0], st[1]), -g.a * df[1]);
     if constexpr (KL == 2) {
-        const double m = S ? d1raw(fx, st[2]) : mixraw(f, st[0], st[2]);
+        const double m = S ? d1r<ORD>(fx, st[2]) : mixr<ORD>(f, st[0], st[2]);
         if constexpr (FAM == FAM_SPH) return fma(g.DD[1], m, -g.b * df[2]);
         else return g.DD[1] * m;
     }
     if constexpr (KL == 3) {
-        if constexpr (AX == 1) return fma(32.0 * g.D2[1], ld(f + ox) - ld(f), g.a * df[0]);
-        else return fma(g.D2[1], d2raw(f, st[1]), g.a * df[0]);
+        if constexpr (AX == 1) return fma(FD<ORD>::ax_d2 * g.D2[1], ld(f + ox) - ld(f), g.a * df[0]);
+        else return fma(g.D2[1], d2r<ORD>(f, st[1]), g.a * df[0]);
     }
     if constexpr (KL == 4) {
-        const double m = (S && AX < 0) ? d1raw(fy, st[2]) : mixraw(f, st[1], st[2]);
+        const double m = (S && AX < 0) ? d1r<ORD>(fy, st[2]) : mixr<ORD>(f, st[1], st[2]);
         if constexpr (FAM == FAM_SPH) return fma(g.DD[2], m, -g.c * df[2]);
         else return g.DD[2] * m;
     }
     if constexpr (KL == 5) {
         if constexpr (FAM == FAM_SPH) {
-            if constexpr (AX == 2) return fma(32.0 * g.D2[2], ld(f + ox) - ld(f), fma(g.b, df[0], g.c * df[1]));
-            else return fma(g.D2[2], d2raw(f, st[2]), fma(g.b, df[0], g.c * df[1]));
+            if constexpr (AX == 2) return fma(FD<ORD>::ax_d2 * g.D2[2], ld(f + ox) - ld(f), fma(g.b, df[0], g.c * df[1]));
+            else return fma(g.D2[2], d2r<ORD>(f, st[2]), fma(g.b, df[0], g.c * df[1]));
         } else {
-            return fma(g.D2[2], d2raw(f, st[2]), -g.d22 * df[2]);
+            return fma(g.D2[2], d2r<ORD>(f, st[2]), -g.d22 * df[2]);
         }
     }
     return 0.0;
 }
 
-template <int FAM, int AX, bool S>
+template <int FAM, int AX, bool S, int ORD>
 __device__ __forceinline__ void hess6(const double* f, const double* fx, const double* fy, const long st[3], long ox,
                                       const Geo& g, const double df[3], double H[6])
 {
-    H[0] = hess<FAM, 0, AX, S>(f, fx, fy, st, ox, g, df);
-    H[1] = hess<FAM, 1, AX, S>(f, fx, fy, st, ox, g, df);
-    H[2] = hess<FAM, 2, AX, S>(f, fx, fy, st, ox, g, df);
-    H[3] = hess<FAM, 3, AX, S>(f, fx, fy, st, ox, g, df);
-    H[4] = hess<FAM, 4, AX, S>(f, fx, fy, st, ox, g, df);
-    H[5] = hess<FAM, 5, AX, S>(f, fx, fy, st, ox, g, df);
+    H[0] = hess<FAM, 0, AX, S, ORD>(f, fx, fy, st, ox, g, df);
+    H[1] = hess<FAM, 1, AX, S, ORD>(f, fx, fy, st, ox, g, df);
+    H[2] = hess<FAM, 2, AX, S, ORD>(f, fx, fy, st, ox, g, df);
+    H[3] = hess<FAM, 3, AX, S, ORD>(f, fx, fy, st, ox, g, df);
+    H[4] = hess<FAM, 4, AX, S, ORD>(f, fx, fy, st, ox, g, df);
+    H[5] = hess<FAM, 5, AX, S, ORD>(f, fx, fy, st, ox, g, df);
 }
 // gammabar^kl H_kl (gw: off-diagonal entries doubled), skipping vanishing components
 template <int AX>
@@ -243,14 +311,14 @@ struct PointIn {
 
 // e_k of gridfunction gf: zero along the two-point axis, from the stored first
 // differences where the point has them (S), else inline
-template <int AX, bool S>
+template <int AX, bool S, int ORD>
 __device__ __forceinline__ double der1(const PointIn& P, int gf, int k)
 {
     if (k == AX) return 0.0;
     const int q = d1slot(gf);
     if (S && q >= 0 && k == 0) return P.g.D[0] * ld(P.dx + (long)q * P.T);
     if (S && AX < 0 && q >= 0 && k == 1) return P.g.D[1] * ld(P.dy + (long)q * P.T);
-    return P.g.D[k] * d1raw(P.y + (long)gf * P.T, P.st[k]);
+    return P.g.D[k] * d1r<ORD>(P.y + (long)gf * P.T, P.st[k]);
 }
 template <bool S>
 __device__ __forceinline__ const double* dxp(const PointIn& P, int gf)
@@ -280,7 +348,7 @@ struct MetricPart {
 // The conformal metric and its inverse, first frame derivatives of h, and
 // Delta (lowered, raised, its trace Delta^k and Delta^k_km): shared by the
 // right-hand side and both constraints.
-template <int FAM, int AX, bool S>
+template <int FAM, int AX, bool S, int ORD>
 __device__ __forceinline__ void metric_first(const PointIn& P, MetricPart& M)
 {
     static_assert(ax_ok<FAM, AX>(), "two-point axis must be the azimuth");
@@ -319,7 +387,7 @@ __device__ __forceinline__ void metric_first(const PointIn& P, MetricPart& M)
 #pragma unroll
     for (int k = 0; k < 3; k++)
 #pragma unroll
-        for (int s = 0; s < 6; s++) dh[k][s] = der1<AX, S>(P, G_HDD + s, k);
+        for (int s = 0; s < 6; s++) dh[k][s] = der1<AX, S, ORD>(P, G_HDD + s, k);
 
     // ---------------- Dhat_k h_ij, Delta_kij (first index lowered), Delta^k_ij, Delta^k
     double Dh[3][6];
@@ -359,10 +427,10 @@ __device__ __forceinline__ void metric_first(const PointIn& P, MetricPart& M)
     }
 }
 
-template <int FAM, bool NEED_GH, int AX, bool S>
+template <int FAM, bool NEED_GH, int AX, bool S, int ORD>
 __device__ __forceinline__ void metric_part(const PointIn& P, MetricPart& M)
 {
-    metric_first<FAM, AX, S>(P, M);
+    metric_first<FAM, AX, S, ORD>(P, M);
     const double* y = P.y;
     const long T = P.T;
     const Geo& g = P.g;
@@ -383,7 +451,7 @@ __device__ __forceinline__ void metric_part(const PointIn& P, MetricPart& M)
     for (int s = 0; s < 6; s++) {
         double df[3] = {dh[0][s], dh[1][s], dh[2][s]};
         double H[6];
-        hess6<FAM, AX, S>(F(G_HDD + s), dxp<S>(P, G_HDD + s), dyp<AX, S>(P, G_HDD + s), st, P.ox, g, df, H);
+        hess6<FAM, AX, S, ORD>(F(G_HDD + s), dxp<S>(P, G_HDD + s), dyp<AX, S>(P, G_HDD + s), st, P.ox, g, df, H);
         Lh[s] = contract6<AX>(gw, H);
         if constexpr (NEED_GH) {
 #pragma unroll
@@ -443,7 +511,7 @@ __device__ __forceinline__ void metric_part(const PointIn& P, MetricPart& M)
 #pragma unroll
     for (int j = 0; j < 3; j++)
 #pragma unroll
-        for (int k = 0; k < 3; k++) Dlam[j][k] = der1<AX, S>(P, G_LAM + k, j);
+        for (int k = 0; k < 3; k++) Dlam[j][k] = der1<AX, S, ORD>(P, G_LAM + k, j);
     omv<FAM, 1>(g, 1.0, lam, Dlam[1]);
     omv<FAM, 2>(g, 1.0, lam, Dlam[2]);
     // Y[j][m][k] = gammabar^kl Delta_jml
@@ -493,13 +561,13 @@ __device__ __forceinline__ void metric_part(const PointIn& P, MetricPart& M)
     // ---------------- conformal factor: phi = -1/2 ln W
     double dW[3];
 #pragma unroll
-    for (int k = 0; k < 3; k++) dW[k] = der1<AX, S>(P, G_CF, k);
+    for (int k = 0; k < 3; k++) dW[k] = der1<AX, S, ORD>(P, G_CF, k);
     const double mhiW = -0.5 * M.iW;
 #pragma unroll
     for (int k = 0; k < 3; k++) M.dphi[k] = k == AX ? 0.0 : mhiW * dW[k];
     {
         double HW[6];
-        hess6<FAM, AX, S>(F(G_CF), dxp<S>(P, G_CF), dyp<AX, S>(P, G_CF), st, P.ox, g, dW, HW);
+        hess6<FAM, AX, S, ORD>(F(G_CF), dxp<S>(P, G_CF), dyp<AX, S>(P, G_CF), st, P.ox, g, dW, HW);
 #pragma unroll
         for (int s = 0; s < 6; s++) {
             const int i = spi(s), j = spj(s);
@@ -511,7 +579,7 @@ __device__ __forceinline__ void metric_part(const PointIn& P, MetricPart& M)
 
 // Output: the 24 right-hand sides without the beta^k d_k advection and
 // without Kreiss-Oliger dissipation (added by the caller, see adv_ko()).
-template <int FAM, int AX, bool S>
+template <int FAM, int AX, bool S, int ORD>
 __device__ __forceinline__ void rhs_core(const PointIn& P, double eta, double out[NGF])
 {
     const double* y = P.y;
@@ -521,7 +589,7 @@ __device__ __forceinline__ void rhs_core(const PointIn& P, double eta, double ou
     auto F = [&](int gf) { return y + (long)gf * T; };
 
     MetricPart M;
-    metric_part<FAM, true, AX, S>(P, M);
+    metric_part<FAM, true, AX, S, ORD>(P, M);
     const double* h = M.h;
     const double* gi = M.gi;
     const double* gw = M.gw;
@@ -544,15 +612,15 @@ __device__ __forceinline__ void rhs_core(const PointIn& P, double eta, double ou
     double dK[3], dal[3], dvet[3][3];
 #pragma unroll
     for (int k = 0; k < 3; k++) {
-        dK[k] = der1<AX, S>(P, G_TRK, k);
-        dal[k] = der1<AX, S>(P, G_ALPHA, k);
+        dK[k] = der1<AX, S, ORD>(P, G_TRK, k);
+        dal[k] = der1<AX, S, ORD>(P, G_ALPHA, k);
 #pragma unroll
-        for (int i = 0; i < 3; i++) dvet[k][i] = der1<AX, S>(P, G_VET + i, k);
+        for (int i = 0; i < 3; i++) dvet[k][i] = der1<AX, S, ORD>(P, G_VET + i, k);
     }
     double DDal[6];
     {
         double Hal[6];
-        hess6<FAM, AX, S>(F(G_ALPHA), dxp<S>(P, G_ALPHA), dyp<AX, S>(P, G_ALPHA), st, P.ox, g, dal, Hal);
+        hess6<FAM, AX, S, ORD>(F(G_ALPHA), dxp<S>(P, G_ALPHA), dyp<AX, S>(P, G_ALPHA), st, P.ox, g, dal, Hal);
 #pragma unroll
         for (int s = 0; s < 6; s++) DDal[s] = Hal[s] - dot3<AX>(Dup[0][s], Dup[1][s], Dup[2][s], dal);
     }
@@ -597,7 +665,7 @@ __device__ __forceinline__ void rhs_core(const PointIn& P, double eta, double ou
 #pragma unroll
         for (int i = 0; i < 3; i++) {
             double df[3] = {dvet[0][i], dvet[1][i], dvet[2][i]};
-            hess6<FAM, AX, S>(F(G_VET + i), dxp<S>(P, G_VET + i), dyp<AX, S>(P, G_VET + i), st, P.ox, g, df,
+            hess6<FAM, AX, S, ORD>(F(G_VET + i), dxp<S>(P, G_VET + i), dyp<AX, S>(P, G_VET + i), st, P.ox, g, df,
                               Hv[i]);
         }
 #pragma unroll
@@ -835,11 +903,11 @@ __device__ __forceinline__ void rhs_core(const PointIn& P, double eta, double ou
 
 // Hamiltonian constraint, Eq. Hconstraint:
 // H = 2/3 K^2 - Abar_ij Abar^ij + W^2 (Rbar - 8 gammabar^ij d_i phi d_j phi - 8 gammabar^ij Dbar_i Dbar_j phi)
-template <int FAM>
+template <int FAM, int ORD>
 __device__ __forceinline__ double ham_core(const PointIn& P)
 {
     MetricPart M;
-    metric_part<FAM, false, -1, false>(P, M);
+    metric_part<FAM, false, -1, false, ORD>(P, M);
     const double* gi = M.gi;
     const double* gw = M.gw;
     double a[6];
@@ -874,11 +942,11 @@ __device__ __forceinline__ double ham_core(const PointIn& P)
 //   V_k = gammabar^jl Dhat_j a_kl - Delta^m_jk Abar^j_m - a_km Delta^m.
 // Writes the frame (rescaled) components M^i; returns |M| = sqrt(gamma_ij M^i M^j)
 // with the physical metric gamma_ij = gammabar_ij / W^2.
-template <int FAM>
+template <int FAM, int ORD>
 __device__ __forceinline__ double mom_core(const PointIn& P, double Mv[3])
 {
     MetricPart M;
-    metric_first<FAM, -1, false>(P, M);
+    metric_first<FAM, -1, false, ORD>(P, M);
     const double* y = P.y;
     const long T = P.T;
     const Geo& g = P.g;
@@ -893,9 +961,9 @@ __device__ __forceinline__ double mom_core(const PointIn& P, double Mv[3])
 #pragma unroll
     for (int k = 0; k < 3; k++) {
 #pragma unroll
-        for (int s = 0; s < 6; s++) Da[k][s] = g.D[k] * d1raw(F(G_ADD + s), st[k]);
-        dK[k] = g.D[k] * d1raw(F(G_TRK), st[k]);
-        dphi[k] = (-0.5 * M.iW) * (g.D[k] * d1raw(F(G_CF), st[k]));
+        for (int s = 0; s < 6; s++) Da[k][s] = g.D[k] * d1r<ORD>(F(G_ADD + s), st[k]);
+        dK[k] = g.D[k] * d1r<ORD>(F(G_TRK), st[k]);
+        dphi[k] = (-0.5 * M.iW) * (g.D[k] * d1r<ORD>(F(G_CF), st[k]));
     }
     oms<FAM, 1>(g, 1.0, a, Da[1]);   // Dhat_k a_ij
     oms<FAM, 2>(g, 1.0, a, Da[2]);
@@ -1006,13 +1074,94 @@ __device__ __forceinline__ double advko_apply(const double* f, const long st[3],
     return k;
 }
 
+// 8th order: upwind weights on offsets -3..+5 (over 840; the backward stencil
+// uses them mirrored) and the tenth difference on -5..+5, as one 11-point
+// stencil per axis.  Along a two-point azimuth the sum is
+// (768 u + 512 kap)(f_other - f), kap = sigma/(1024 S_k dxx_k) = (840/1024) sigma D_k.
+__host__ __device__ constexpr double up8(int o)
+{
+    return o == -3 ? -5.0 : o == -2 ? 60.0 : o == -1 ? -420.0 : o == 0 ? -378.0 : o == 1 ? 1050.0
+         : o == 2 ? -420.0 : o == 3 ? 140.0 : o == 4 ? -30.0 : o == 5 ? 3.0 : 0.0;
+}
+__host__ __device__ constexpr double ko10(int o)
+{
+    return o == 0 ? -252.0 : (o == 1 || o == -1) ? 210.0 : (o == 2 || o == -2) ? -120.0
+         : (o == 3 || o == -3) ? 45.0 : (o == 4 || o == -4) ? -10.0 : (o == 5 || o == -5) ? 1.0 : 0.0;
+}
+__host__ __device__ constexpr int off10(int j) { return j < 5 ? j - 5 : j - 4; }   // offsets -5..-1, 1..5
+
+struct AdvKoW8 {
+    double w[3][10];   // per axis, offsets off10(j)
+    double c0;         // centre weight summed over the axes
+    double cax;        // two-point axis: weight of f_other - f
+};
+
+template <int AX>
+__device__ __forceinline__ void advko_weights8(const double u[3], const bool fwd[3], const double D[3], double sigma,
+                                               AdvKoW8& W)
+{
+    double c0 = 0.0;
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        const double kap = (0.8203125 * sigma) * D[d];
+        if (d == AX) {
+            W.cax = fma(768.0, u[d], 512.0 * kap);
+            continue;
+        }
+        const double p = fwd[d] ? u[d] : 0.0, q = fwd[d] ? 0.0 : u[d];
+#pragma unroll
+        for (int j = 0; j < 10; j++) {
+            const int o = off10(j);
+            double w = ko10(o) * kap;
+            if (up8(o) != 0.0) w = fma(p, up8(o), w);
+            if (up8(-o) != 0.0) w = fma(q, up8(-o), w);
+            W.w[d][j] = w;
+        }
+        const double c = fma(-378.0, u[d], -252.0 * kap);   // p + q = u
+        c0 = d == 0 ? c : c0 + c;
+    }
+    W.c0 = c0;
+}
+
+template <int AX>
+__device__ __forceinline__ double advko_apply8(const double* f, const long st[3], long ox, const AdvKoW8& W, double k)
+{
+    k = fma(W.c0, ld(f), k);
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        if (d == AX) {
+            k = fma(W.cax, ld(f + ox) - ld(f), k);
+            continue;
+        }
+#pragma unroll
+        for (int j = 0; j < 10; j++) k = fma(W.w[d][j], ld(f + off10(j) * st[d]), k);
+    }
+    return k;
+}
+
 // Adds the upwinded advection and the dissipation to the 24 right-hand sides
 // of rhs_core: sigma_metric on the 17 metric gridfunctions (h, a, W, K,
 // lambda), sigma_gauge on the 7 gauge gridfunctions (vet, bet, alpha).
-template <int AX>
+template <int AX, int ORD>
 __device__ __forceinline__ void add_adv_ko(const double* y, long T, const long st[3], long ox, const double D[3],
                                            double sigma_metric, double sigma_gauge, double k[NGF])
 {
+    if constexpr (ORD == 8) {
+        double u[3];
+        bool fwd[3];
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            const double v = ld(y + (long)(G_VET + d) * T);
+            u[d] = fabs(v) * D[d];
+            fwd[d] = v > 0.0;
+        }
+        AdvKoW8 Wm, Wg;
+        advko_weights8<AX>(u, fwd, D, sigma_metric, Wm);
+        advko_weights8<AX>(u, fwd, D, sigma_gauge, Wg);
+#pragma unroll
+        for (int g = 0; g < NGF; g++) k[g] = advko_apply8<AX>(y + (long)g * T, st, ox, g < G_VET ? Wm : Wg, k[g]);
+        return;
+    }
     double u[3];
     bool fwd[3];
 #pragma unroll

@@ -160,6 +160,7 @@ int nr_batch_create(nr_grid* const* grids, int ngrids, nr_batch** out)
     for (int q = 0; q < ngrids; q++) {
         if (!grids[q]) return nrk_fail(NR_EINVAL, "grid %d is NULL", q);
         if (grids[q]->device != grids[0]->device) return nrk_fail(NR_EINVAL, "grids on different devices");
+        if (grids[q]->K.ord != 4) return nrk_fail(NR_EINVAL, "batched mode runs the 4th-order scheme (NG = 3) only");
         if (grids[q]->geo.fam != grids[0]->geo.fam)
             return nrk_fail(NR_EINVAL, "grids of spherical-like and cylindrical-like coordinates cannot share a batch");
         if ((grids[q]->K.ax >= 0) != (grids[0]->K.ax >= 0))

@@ -81,11 +81,11 @@ __global__ void __launch_bounds__(TX* TY) k_batch_stage(const BGrid* __restrict_
         const int i = (t % B.tiles_x) * TX + tid % TX;
         const int j = (t / B.tiles_x) * TY + tid / TX;
         if (i < B.K.N0 && j < B.K.N1 * B.K.N2)
-            rhs_point_stage<FAM, AX, true>(B.K, yin, B.d1x, B.d1y, out, yn, B.acc, B.st[stage], i, j);
+            rhs_point_stage<FAM, AX, true, 4>(B.K, yin, B.d1x, B.d1y, out, yn, B.acc, B.st[stage], i, j);
     } else {
         const int p = (w - B.w_rhs_end) * (TX * TY) + tid;
         if (p < B.n_outer)
-            outer_point_stage<FAM>(B.K, B.outer[p], yin, out, yn, B.acc, B.finf, B.wspeed, B.st[stage]);
+            outer_point_stage<FAM, 4>(B.K, B.outer[p], yin, out, yn, B.acc, B.finf, B.wspeed, B.st[stage]);
     }
 }
 
@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(256) k_batch_d1(const BGrid* __restrict__ grid
     const double* yn;
     double* out;
     stage_buffers(B, stage, yin, out, yn);
-    d1_point<AX>(B.K, yin, B.d1x, B.d1y, (long)(w - B.d1_begin) * 256 + threadIdx.x);
+    d1_point<AX, 4>(B.K, yin, B.d1x, B.d1y, (long)(w - B.d1_begin) * 256 + threadIdx.x);
 }
 
 // tile shapes the autotuner tries (threads per block = TX * TY)

@@ -221,6 +221,15 @@ int onesided_kind(int i, int n)
     return (i - 1 >= 0) ? 3 : 4;
 }
 
+// 8th order: the 9-point window a..a+8 nearest to centred that fits, as w = -a
+int onesided_window8(int i, int n)
+{
+    int a = -4;
+    if (a < -i) a = -i;
+    if (a > n - 1 - i - 8) a = n - 1 - i - 8;
+    return -a;
+}
+
 double dt_cfl_host(const HostGeom& G, const nr_params& p)
 {
     const int NG = G.NG;
@@ -267,7 +276,8 @@ int check_args(int coords, const int Nxx[3], const nr_params* p)
     if (coords != NR_SINH_SPHERICAL && coords != NR_SINH_CYLINDRICAL && coords != NR_SPHERICAL)
         return fail(NR_EINVAL, "unknown coordinate system %d", coords);
     if (!Nxx) return fail(NR_EINVAL, "Nxx is NULL");
-    if (p && p->NG != 3) return fail(NR_EINVAL, "NG must be 3 (4th-order FD with upwinding), got %d", p->NG);
+    if (p && p->NG != 3 && p->NG != 5)
+        return fail(NR_EINVAL, "NG must be 3 (4th-order FD) or 5 (8th-order FD), with upwinding; got %d", p->NG);
     if (p) {
         for (int g = 1; g < NR_NGF; g++) {
             const int first = g < 17 ? 0 : 17;
@@ -321,6 +331,7 @@ void free_grid(nr_grid* g)
     cudaGetDevice(&prev);
     cudaSetDevice(g->device);
     if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->exec_ssp) cudaGraphExecDestroy(g->exec_ssp);
     void* ptrs[] = {g->y, g->ya, g->yb, g->acc, g->d1x, g->d1y, g->ax0, g->ax1, g->ax2, g->outer, g->inner, g->canon,
                     g->finf, g->wspeed, g->partials, g->hres, g->flag, g->mxyz};
     for (void* p : ptrs)
@@ -367,6 +378,22 @@ int enqueue_rk4(nr_grid* g, cudaStream_t s, double dt)
     if ((rc = enqueue_stage(g, s, g->ya, g->yb, g->y, g->acc, s2, ns))) return rc;
     if ((rc = enqueue_stage(g, s, g->yb, g->ya, g->y, g->acc, s3, ns))) return rc;
     if ((rc = enqueue_stage(g, s, g->ya, g->y, nullptr, g->acc, s4, g->n_inner))) return rc;
+    return NR_OK;
+}
+
+// one SSPRK3 step (Gottlieb-Shu-Tadmor): y1 = y + dt k(y), y2 = 3/4 y + 1/4 (y1 + dt k(y1)),
+// y_{n+1} = 1/3 y + 2/3 (y2 + dt k(y2)), the last stage in place
+int enqueue_ssprk3(nr_grid* g, cudaStream_t s, double dt)
+{
+    const int enf = g->P.enforce_detgb;
+    Stage s1{MODE_SSP, enf, dt, 1.0, 0.0};
+    Stage s2{MODE_SSP, enf, dt, 0.25, 0.75};
+    Stage s3{MODE_SSP, enf, dt, 2.0 / 3.0, 1.0 / 3.0};
+    int rc;
+    const int ns = g->n_inner_stencil;
+    if ((rc = enqueue_stage(g, s, g->y, g->ya, g->y, nullptr, s1, ns))) return rc;
+    if ((rc = enqueue_stage(g, s, g->ya, g->yb, g->y, nullptr, s2, ns))) return rc;
+    if ((rc = enqueue_stage(g, s, g->yb, g->y, g->y, nullptr, s3, g->n_inner))) return rc;
     return NR_OK;
 }
 
@@ -466,10 +493,14 @@ int nr_grid_create(int coords, const int Nxx[3], const nr_params* params, nr_gri
             OuterPt o{};
             o.idx = (int)idx;
             double f[4];
+            // stencil kind per axis and the denominator of its integer weights
+            const bool o8 = G.NG == 5;
+            const double den = o8 ? 840.0 : 12.0;
+            auto kind = [&](int i, int n) { return o8 ? onesided_window8(i, n) : onesided_kind(i, n); };
             if (G.fam == FAM_SPH) {
                 axis0_map(G, P, G.xx(0, i0), f);
-                o.kind = onesided_kind(i0, G.n[0]);
-                o.w0 = (1.0 / f[1]) / (12.0 * G.dxx[0]);
+                o.kind = kind(i0, G.n[0]);
+                o.w0 = (1.0 / f[1]) / (den * G.dxx[0]);
                 o.w2 = 0.0;
                 o.invr = 1.0 / f[0];
             } else {
@@ -477,9 +508,9 @@ int nr_grid_create(int coords, const int Nxx[3], const nr_params* params, nr_gri
                 radial(P.ampl[0], P.sinhw[0], 1, G.xx(0, i0), f);
                 radial(P.ampl[2], P.sinhw[2], 1, G.xx(2, i2), z);
                 const double r = sqrt(f[0] * f[0] + z[0] * z[0]);
-                o.kind = onesided_kind(i0, G.n[0]) | (onesided_kind(i2, G.n[2]) << 8);
-                o.w0 = (f[0] / r) * (1.0 / f[1]) / (12.0 * G.dxx[0]);
-                o.w2 = (z[0] / r) * (1.0 / z[1]) / (12.0 * G.dxx[2]);
+                o.kind = kind(i0, G.n[0]) | (kind(i2, G.n[2]) << 8);
+                o.w0 = (f[0] / r) * (1.0 / f[1]) / (den * G.dxx[0]);
+                o.w2 = (z[0] / r) * (1.0 / z[1]) / (den * G.dxx[2]);
                 o.invr = 1.0 / r;
             }
             (void)i1;
@@ -541,10 +572,12 @@ int nr_grid_create(int coords, const int Nxx[3], const nr_params* params, nr_gri
     K.NG = G.NG;
     K.fam = G.fam;
     K.ax = two_point_axis(G);
+    K.ord = 2 * (G.NG - 1);
     K.T = G.T;
     for (int d = 0; d < 3; d++) {
-        K.inv12dx[d] = 1.0 / (12.0 * G.dxx[d]);
-        K.inv12dx2[d] = 1.0 / (12.0 * G.dxx[d] * G.dxx[d]);
+        // the denominators of the integer stencil weights (bssn_point.cuh, FD<ORD>)
+        K.inv_d1[d] = 1.0 / ((K.ord == 8 ? 840.0 : 12.0) * G.dxx[d]);
+        K.inv_d2[d] = 1.0 / ((K.ord == 8 ? 5040.0 : 12.0) * G.dxx[d] * G.dxx[d]);
     }
     K.sigma_metric = P.ko_sigma[0];
     K.sigma_gauge = P.ko_sigma[17];
@@ -605,7 +638,7 @@ int nr_query(const nr_grid* g, nr_grid_info* info)
     info->n_inner_stencil = g->n_inner_stencil;
     // per stage: k_d1, k_rhs (interior + pure-outer points), then k_inner if it has entries
     info->launches_per_step = 8 + 3 * (g->n_inner_stencil > 0) + (g->n_inner > 0);
-    info->pad_ = 0;
+    info->launches_per_ssprk3_step = 6 + 2 * (g->n_inner_stencil > 0) + (g->n_inner > 0);
     return NR_OK;
 }
 
@@ -688,6 +721,31 @@ int nr_rk4_step(nr_grid* g, double dt, int nsteps)
         g->graph_dt = dt;
     }
     for (int n = 0; n < nsteps; n++) CUDA_OR_FAIL(cudaGraphLaunch(g->exec, g->stream));
+    return NR_OK;
+}
+
+int nr_ssprk3_step(nr_grid* g, double dt, int nsteps)
+{
+    if (!g || !(dt > 0.0) || nsteps < 0) return fail(NR_EINVAL, "bad nr_ssprk3_step arguments");
+    if (nsteps == 0) return NR_OK;
+    DeviceGuard dg(g->device);
+    if (!g->exec_ssp || g->graph_dt_ssp != dt) {
+        if (g->exec_ssp) {
+            cudaGraphExecDestroy(g->exec_ssp);
+            g->exec_ssp = nullptr;
+        }
+        cudaGraph_t graph;
+        CUDA_OR_FAIL(cudaStreamBeginCapture(g->cap, cudaStreamCaptureModeThreadLocal));
+        int rc = enqueue_ssprk3(g, g->cap, dt);
+        cudaError_t e = cudaStreamEndCapture(g->cap, &graph);
+        if (rc) return rc;
+        if (e != cudaSuccess) return fail(NR_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&g->exec_ssp, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return fail(NR_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+        g->graph_dt_ssp = dt;
+    }
+    for (int n = 0; n < nsteps; n++) CUDA_OR_FAIL(cudaGraphLaunch(g->exec_ssp, g->stream));
     return NR_OK;
 }
 

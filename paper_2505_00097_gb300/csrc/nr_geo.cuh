@@ -36,12 +36,12 @@ __device__ __forceinline__ Geo make_geo(const GridK& G, int i0, int i1, int i2)
         g.e0c = 0.0;
         g.e1c = 0.0;
     }
-    g.D[0] = s0 * G.inv12dx[0];
-    g.D[1] = a * G.inv12dx[1];
-    g.D[2] = s2 * G.inv12dx[2];
-    g.D2[0] = s0 * s0 * G.inv12dx2[0];
-    g.D2[1] = a * a * G.inv12dx2[1];
-    g.D2[2] = s2 * s2 * G.inv12dx2[2];
+    g.D[0] = s0 * G.inv_d1[0];
+    g.D[1] = a * G.inv_d1[1];
+    g.D[2] = s2 * G.inv_d1[2];
+    g.D2[0] = s0 * s0 * G.inv_d2[0];
+    g.D2[1] = a * a * G.inv_d2[1];
+    g.D2[2] = s2 * s2 * G.inv_d2[2];
     g.DD[0] = g.D[0] * g.D[1];
     g.DD[1] = g.D[0] * g.D[2];
     g.DD[2] = g.D[1] * g.D[2];

@@ -29,9 +29,10 @@ struct GridK {
     int NG;
     int fam;            // FAM_SPH / FAM_CYL
     int ax;             // azimuthal axis when it holds two points (1 cylindrical-like, 2 spherical-like), else -1
+    int ord;            // finite-difference order N_FD = 2 (NG - 1): 4 or 8
     long T;
-    double inv12dx[3];  // 1/(12 dxx_k)
-    double inv12dx2[3]; // 1/(12 dxx_k^2)
+    double inv_d1[3];   // 1/(den1 dxx_k): 1/12 (4th order) or 1/840 (8th order) over the spacing
+    double inv_d2[3];   // 1/(den2 dxx_k^2): den2 = 12 or 5040
     double sigma_metric;  // Kreiss-Oliger strength on gridfunctions 0-16 (h, a, W, K, lambda)
     double sigma_gauge;   // and on 17-23 (vet, bet, alpha)
     double eta;
@@ -53,14 +54,17 @@ struct InnerPt {
     int pad;
 };
 
-enum { MODE_RHS = 0, MODE_STAGE1 = 1, MODE_STAGE23 = 2, MODE_STAGE4 = 3 };
+enum { MODE_RHS = 0, MODE_STAGE1 = 1, MODE_STAGE23 = 2, MODE_STAGE4 = 3, MODE_SSP = 4 };
 
-// RK4 stage description for the fused epilogues.
+// Stage description for the fused epilogues.  RK4: stages 1-3 y_next = y_n +
+// cnext k and acc (=|+=) cacc k; stage 4 y_n = acc + cacc k.  SSPRK3 (MODE_SSP):
+// y_next = cyn y_n + cacc (y_in + cnext k), cnext = dt.
 struct Stage {
     int mode;
     int enforce;
-    double cnext;       // y_next = y_n + cnext * k          (stages 1-3)
-    double cacc;        // acc (=|+=) cacc * k; stage 4: y_n = acc + cacc * k
+    double cnext;
+    double cacc;
+    double cyn;
 };
 
 // Pure-outer points whose radiation condition runs inside the k_rhs launch
@@ -143,5 +147,7 @@ struct nr_grid {
     // graph
     cudaGraphExec_t exec = nullptr;
     double graph_dt = 0.0;
+    cudaGraphExec_t exec_ssp = nullptr;   // SSPRK3 step
+    double graph_dt_ssp = 0.0;
 };
 

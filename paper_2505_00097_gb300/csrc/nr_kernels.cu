@@ -31,13 +31,13 @@ constexpr int RHS_BX = 32, RHS_BY = 4;
 // stencil of an interior point reads: i1 and i2 within two points of the interior,
 // except along a two-point azimuth (no mixed derivatives there); the axis-1 set at
 // interior i1 only.
-template <int AX>
+template <int AX, int ORD>
 __global__ void __launch_bounds__(256) k_d1(GridK G, const double* __restrict__ y, double* d1x, double* d1y)
 {
-    d1_point<AX>(G, y, d1x, d1y, (long)blockIdx.x * blockDim.x + threadIdx.x);
+    d1_point<AX, ORD>(G, y, d1x, d1y, (long)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
-template <int FAM, int AX>
+template <int FAM, int AX, int ORD>
 __global__ void __launch_bounds__(RHS_BX* RHS_BY) k_rhs(GridK G, const double* __restrict__ yin,
                                                         const double* __restrict__ d1x, const double* __restrict__ d1y,
                                                         double* out, const double* yn, double* acc, Stage st,
@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(RHS_BX* RHS_BY) k_rhs(GridK G, const double* _
     // the first oa.nblocks blocks take the pure-outer points, 128 per block
     if ((int)blockIdx.x < oa.nblocks) {
         const int t = (int)blockIdx.x * (RHS_BX * RHS_BY) + threadIdx.y * RHS_BX + threadIdx.x;
-        if (t < oa.npts) outer_point_stage<FAM>(G, oa.pts[t], yin, out, yn, acc, oa.finf, oa.wspeed, st);
+        if (t < oa.npts) outer_point_stage<FAM, ORD>(G, oa.pts[t], yin, out, yn, acc, oa.finf, oa.wspeed, st);
         return;
     }
     // the others tile (i0, j = i1 + N1 i2) in 32 x 4 points, flattened into the block index
@@ -55,10 +55,10 @@ __global__ void __launch_bounds__(RHS_BX* RHS_BY) k_rhs(GridK G, const double* _
     const int i = (b % nbx) * RHS_BX + threadIdx.x;
     const int j = (b / nbx) * RHS_BY + threadIdx.y;
     if (i >= G.N0 || j >= G.N1 * G.N2) return;
-    rhs_point_stage<FAM, AX, true>(G, yin, d1x, d1y, out, yn, acc, st, i, j);
+    rhs_point_stage<FAM, AX, true, ORD>(G, yin, d1x, d1y, out, yn, acc, st, i, j);
 }
 
-template <int FAM>
+template <int FAM, int ORD>
 __global__ void __launch_bounds__(128) k_outer(GridK G, const OuterPt* __restrict__ pts, int npts,
                                                const double* __restrict__ yin, double* out, const double* yn,
                                                double* acc, const double* __restrict__ finf,
@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(128) k_outer(GridK G, const OuterPt* __restric
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= npts) return;
-    outer_point_stage<FAM>(G, pts[t], yin, out, yn, acc, finf, wspeed, st);
+    outer_point_stage<FAM, ORD>(G, pts[t], yin, out, yn, acc, finf, wspeed, st);
 }
 
 __global__ void __launch_bounds__(256) k_inner(long T, const InnerPt* __restrict__ pts, int npts, double* y)
@@ -136,7 +136,7 @@ __device__ __forceinline__ void block_partials(double s2, double mx, double cnt,
     }
 }
 
-template <int FAM>
+template <int FAM, int ORD>
 __global__ void __launch_bounds__(HAM_THREADS) k_ham(GridK G, const double* __restrict__ y, double* H, double rmin,
                                                       double rmax, double* partials)
 {
@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(HAM_THREADS) k_ham(GridK G, const double* __re
         P.dx = nullptr;
         P.dy = nullptr;
         P.g = make_geo<FAM>(G, p0, p1, p2);
-        const double h = ham_core<FAM>(P);
+        const double h = ham_core<FAM, ORD>(P);
         if (H) H[idx] = h;
         double x[3];
         cart_of(G, p0, p1, p2, x);
@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(HAM_THREADS) k_ham(GridK G, const double* __re
 
 // momentum constraint (Eq. Mconstraint): rescaled M^i at interior points (M: 3 gridfunctions, or
 // NULL) and per-block partial norms of |M|
-template <int FAM>
+template <int FAM, int ORD>
 __global__ void __launch_bounds__(HAM_THREADS) k_mom(GridK G, const double* __restrict__ y, double* Mout, double rmin,
                                                       double rmax, double* partials)
 {
@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(HAM_THREADS) k_mom(GridK G, const double* __re
         P.dy = nullptr;
         P.g = make_geo<FAM>(G, p0, p1, p2);
         double Mv[3];
-        const double m = mom_core<FAM>(P, Mv);
+        const double m = mom_core<FAM, ORD>(P, Mv);
         if (Mout) {
             Mout[idx] = Mv[0];
             Mout[G.T + idx] = Mv[1];
@@ -277,15 +277,16 @@ cudaError_t launch_fp64_probe(int blocks, int iters, double* sink, cudaStream_t 
 
 // ------------------------------------------------------------ launchers
 
-cudaError_t launch_rhs(const GridK& G, const double* yin, double* d1x, double* d1y, double* out, const double* yn,
-                       double* acc, Stage st, cudaStream_t s, OuterArgs oa)
+template <int ORD>
+cudaError_t launch_rhs_ord(const GridK& G, const double* yin, double* d1x, double* d1y, double* out,
+                           const double* yn, double* acc, Stage st, cudaStream_t s, OuterArgs oa)
 {
     // the stored first differences of yin
     {
         const unsigned b = (unsigned)((d1_points(G) + 255) / 256);
-        if (G.ax == 1) k_d1<1><<<b, 256, 0, s>>>(G, yin, d1x, d1y);
-        else if (G.ax == 2) k_d1<2><<<b, 256, 0, s>>>(G, yin, d1x, d1y);
-        else k_d1<-1><<<b, 256, 0, s>>>(G, yin, d1x, d1y);
+        if (G.ax == 1) k_d1<1, ORD><<<b, 256, 0, s>>>(G, yin, d1x, d1y);
+        else if (G.ax == 2) k_d1<2, ORD><<<b, 256, 0, s>>>(G, yin, d1x, d1y);
+        else k_d1<-1, ORD><<<b, 256, 0, s>>>(G, yin, d1x, d1y);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -294,13 +295,20 @@ cudaError_t launch_rhs(const GridK& G, const double* yin, double* d1x, double* d
     const long nb = (long)((G.N0 + RHS_BX - 1) / RHS_BX) * ((G.N1 * G.N2 + RHS_BY - 1) / RHS_BY) + oa.nblocks;
     dim3 grd((unsigned)nb);
     if (G.fam == FAM_SPH) {
-        if (G.ax == 2) k_rhs<FAM_SPH, 2><<<grd, blk, 0, s>>>(G, yin, d1x, d1y, out, yn, acc, st, oa);
-        else k_rhs<FAM_SPH, -1><<<grd, blk, 0, s>>>(G, yin, d1x, d1y, out, yn, acc, st, oa);
+        if (G.ax == 2) k_rhs<FAM_SPH, 2, ORD><<<grd, blk, 0, s>>>(G, yin, d1x, d1y, out, yn, acc, st, oa);
+        else k_rhs<FAM_SPH, -1, ORD><<<grd, blk, 0, s>>>(G, yin, d1x, d1y, out, yn, acc, st, oa);
     } else {
-        if (G.ax == 1) k_rhs<FAM_CYL, 1><<<grd, blk, 0, s>>>(G, yin, d1x, d1y, out, yn, acc, st, oa);
-        else k_rhs<FAM_CYL, -1><<<grd, blk, 0, s>>>(G, yin, d1x, d1y, out, yn, acc, st, oa);
+        if (G.ax == 1) k_rhs<FAM_CYL, 1, ORD><<<grd, blk, 0, s>>>(G, yin, d1x, d1y, out, yn, acc, st, oa);
+        else k_rhs<FAM_CYL, -1, ORD><<<grd, blk, 0, s>>>(G, yin, d1x, d1y, out, yn, acc, st, oa);
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_rhs(const GridK& G, const double* yin, double* d1x, double* d1y, double* out, const double* yn,
+                       double* acc, Stage st, cudaStream_t s, OuterArgs oa)
+{
+    return G.ord == 8 ? launch_rhs_ord<8>(G, yin, d1x, d1y, out, yn, acc, st, s, oa)
+                      : launch_rhs_ord<4>(G, yin, d1x, d1y, out, yn, acc, st, s, oa);
 }
 
 cudaError_t launch_outer(const GridK& G, const OuterPt* pts, int npts, const double* yin, double* out,
@@ -309,10 +317,13 @@ cudaError_t launch_outer(const GridK& G, const OuterPt* pts, int npts, const dou
 {
     if (npts == 0) return cudaSuccess;
     const int b = 128, n = (npts + b - 1) / b;
-    if (G.fam == FAM_SPH)
-        k_outer<FAM_SPH><<<n, b, 0, s>>>(G, pts, npts, yin, out, yn, acc, finf, wspeed, st);
-    else
-        k_outer<FAM_CYL><<<n, b, 0, s>>>(G, pts, npts, yin, out, yn, acc, finf, wspeed, st);
+    if (G.fam == FAM_SPH) {
+        if (G.ord == 8) k_outer<FAM_SPH, 8><<<n, b, 0, s>>>(G, pts, npts, yin, out, yn, acc, finf, wspeed, st);
+        else k_outer<FAM_SPH, 4><<<n, b, 0, s>>>(G, pts, npts, yin, out, yn, acc, finf, wspeed, st);
+    } else {
+        if (G.ord == 8) k_outer<FAM_CYL, 8><<<n, b, 0, s>>>(G, pts, npts, yin, out, yn, acc, finf, wspeed, st);
+        else k_outer<FAM_CYL, 4><<<n, b, 0, s>>>(G, pts, npts, yin, out, yn, acc, finf, wspeed, st);
+    }
     return cudaGetLastError();
 }
 
@@ -342,10 +353,13 @@ int ham_partials_needed(const GridK& G)
 cudaError_t launch_ham(const GridK& G, const double* y, double* H, double rmin, double rmax, double* partials,
                        int nparts, double* result, cudaStream_t s)
 {
-    if (G.fam == FAM_SPH)
-        k_ham<FAM_SPH><<<nparts, HAM_THREADS, 0, s>>>(G, y, H, rmin, rmax, partials);
-    else
-        k_ham<FAM_CYL><<<nparts, HAM_THREADS, 0, s>>>(G, y, H, rmin, rmax, partials);
+    if (G.fam == FAM_SPH) {
+        if (G.ord == 8) k_ham<FAM_SPH, 8><<<nparts, HAM_THREADS, 0, s>>>(G, y, H, rmin, rmax, partials);
+        else k_ham<FAM_SPH, 4><<<nparts, HAM_THREADS, 0, s>>>(G, y, H, rmin, rmax, partials);
+    } else {
+        if (G.ord == 8) k_ham<FAM_CYL, 8><<<nparts, HAM_THREADS, 0, s>>>(G, y, H, rmin, rmax, partials);
+        else k_ham<FAM_CYL, 4><<<nparts, HAM_THREADS, 0, s>>>(G, y, H, rmin, rmax, partials);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_ham_reduce<<<1, 256, 0, s>>>(partials, nparts, result);
@@ -355,10 +369,13 @@ cudaError_t launch_ham(const GridK& G, const double* y, double* H, double rmin, 
 cudaError_t launch_mom(const GridK& G, const double* y, double* M, double rmin, double rmax, double* partials,
                        int nparts, double* result, cudaStream_t s)
 {
-    if (G.fam == FAM_SPH)
-        k_mom<FAM_SPH><<<nparts, HAM_THREADS, 0, s>>>(G, y, M, rmin, rmax, partials);
-    else
-        k_mom<FAM_CYL><<<nparts, HAM_THREADS, 0, s>>>(G, y, M, rmin, rmax, partials);
+    if (G.fam == FAM_SPH) {
+        if (G.ord == 8) k_mom<FAM_SPH, 8><<<nparts, HAM_THREADS, 0, s>>>(G, y, M, rmin, rmax, partials);
+        else k_mom<FAM_SPH, 4><<<nparts, HAM_THREADS, 0, s>>>(G, y, M, rmin, rmax, partials);
+    } else {
+        if (G.ord == 8) k_mom<FAM_CYL, 8><<<nparts, HAM_THREADS, 0, s>>>(G, y, M, rmin, rmax, partials);
+        else k_mom<FAM_CYL, 4><<<nparts, HAM_THREADS, 0, s>>>(G, y, M, rmin, rmax, partials);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_ham_reduce<<<1, 256, 0, s>>>(partials, nparts, result);

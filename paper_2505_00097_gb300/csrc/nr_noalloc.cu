@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(NA_THREADS) k_na_ham(GridK G, const double* __
         P.dx = nullptr;
         P.dy = nullptr;
         P.g = make_geo<FAM>(G, p0, p1, p2);
-        const double h = ham_core<FAM>(P);
+        const double h = ham_core<FAM, 4>(P);
         if (H) H[idx] = h;
         double x[3];
         cart_of(G, p0, p1, p2, x);
@@ -208,6 +208,7 @@ extern "C" int nr_hamiltonian_noalloc(int coords, const int Nxx[3], const nr_par
     K.NG = NG;
     K.fam = fam;
     K.ax = -1;
+    K.ord = 4;
     K.T = T;
     double lo[3], hi[3], dx[3];
     if (fam == FAM_CYL) {
@@ -221,8 +222,8 @@ extern "C" int nr_hamiltonian_noalloc(int coords, const int Nxx[3], const nr_par
     }
     for (int d = 0; d < 3; d++) {
         dx[d] = (hi[d] - lo[d]) / Nxx[d];
-        K.inv12dx[d] = 1.0 / (12.0 * dx[d]);
-        K.inv12dx2[d] = 1.0 / (12.0 * dx[d] * dx[d]);
+        K.inv_d1[d] = 1.0 / (12.0 * dx[d]);
+        K.inv_d2[d] = 1.0 / (12.0 * dx[d] * dx[d]);
     }
     double* ax0 = scratch + NA_AXES;
     double* ax1 = ax0 + 4L * n[0];

@@ -312,6 +312,7 @@ int nr_server_submit(nr_server* s, int coords, const int Nxx[3], const nr_params
 {
     if (!s || !Nxx || !params || npunct < 0 || npunct > 16 || (npunct && (!mass || !xyz)) || !(t_final > 0.0))
         return nrk_fail(NR_EINVAL, "bad nr_server_submit arguments");
+    if (params->NG != 3) return nrk_fail(NR_EINVAL, "served mode runs the 4th-order scheme (NG = 3) only");
     if (s->running.size() + s->queue.size() > 0 && s->all.size() > 1000000)
         return nrk_fail(NR_EINVAL, "too many requests");
     Request* r = new Request();

@@ -30,9 +30,11 @@ __device__ __forceinline__ void enforce_det(double* v)
     v[5] = fma(f1, v[5], v[5] + f1);
 }
 
-// RK4 stage epilogue for one point: k -> (y_next, acc) or the plain RHS.
+// Stage epilogue for one point: k -> (y_next, acc), or the plain RHS.  yin: the
+// stage input (read by MODE_SSP at this point).  yn may equal out (the last
+// SSPRK3 stage updates y_n in place: each point reads its own values first).
 __device__ __forceinline__ void stage_store(const Stage& st, long T, long idx, const double k[NGF],
-                                            const double* __restrict__ yn, double* __restrict__ out,
+                                            const double* yin, const double* yn, double* out,
                                             double* __restrict__ acc)
 {
     if (st.mode == MODE_RHS) {
@@ -41,7 +43,10 @@ __device__ __forceinline__ void stage_store(const Stage& st, long T, long idx, c
         return;
     }
     double v[NGF];
-    if (st.mode == MODE_STAGE4) {
+    if (st.mode == MODE_SSP) {
+#pragma unroll
+        for (int g = 0; g < NGF; g++) v[g] = fma(st.cyn, yn[g * T + idx], st.cacc * fma(st.cnext, k[g], yin[g * T + idx]));
+    } else if (st.mode == MODE_STAGE4) {
 #pragma unroll
         for (int g = 0; g < NGF; g++) v[g] = fma(st.cacc, k[g], acc[g * T + idx]);
     } else {
@@ -69,6 +74,37 @@ __device__ __forceinline__ double osraw(const double* f, long s, int kind)
     }
 }
 
+// 8th-order one-sided first derivative on the window a..a+8, a = -w (w = 0..8),
+// integer weights over 840 h; w = 4 is the centred stencil
+__host__ __device__ constexpr double os8(int w, int i)
+{
+    constexpr double t[9][9] = {
+        {-2283, 6720, -11760, 15680, -14700, 9408, -3920, 960, -105},
+        {-105, -1338, 2940, -2940, 2450, -1470, 588, -140, 15},
+        {15, -240, -798, 1680, -1050, 560, -210, 48, -5},
+        {-5, 60, -420, -378, 1050, -420, 140, -30, 3},
+        {3, -32, 168, -672, 0, 672, -168, 32, -3},
+        {-3, 30, -140, 420, -1050, 378, 420, -60, 5},
+        {5, -48, 210, -560, 1050, -1680, 798, 240, -15},
+        {-15, 140, -588, 1470, -2450, 2940, -2940, 1338, 105},
+        {105, -960, 3920, -9408, 14700, -15680, 11760, -6720, 2283}};
+    return t[w][i];
+}
+__device__ __forceinline__ double osraw8(const double* f, long s, int w)
+{
+    double t = 0.0;
+    switch (w) {
+#define OS8_CASE(W)                                                                         \
+    case W:                                                                                 \
+        _Pragma("unroll") for (int i = 0; i < 9; i++) t = fma(os8(W, i), ld(f + (i - W) * s), t); \
+        return t;
+        OS8_CASE(0) OS8_CASE(1) OS8_CASE(2) OS8_CASE(3) OS8_CASE(4) OS8_CASE(5) OS8_CASE(6) OS8_CASE(7)
+        OS8_CASE(8)
+#undef OS8_CASE
+    default: return 0.0;
+    }
+}
+
 __device__ __forceinline__ int gf_type(int g)
 {
     if (g < 6) return 4 + g;
@@ -84,7 +120,7 @@ __device__ __forceinline__ int gf_type(int g)
 // when it holds two points (G.ax), else -1.  S: the raw first differences along axes 0 and 1 of the
 // gridfunctions with second derivatives are read from d1x, d1y (N_D1 sets of T doubles; d1y only
 // for AX = -1), as k_d1 stored them from yin; the result is bitwise the same either way.
-template <int FAM, int AX, bool S>
+template <int FAM, int AX, bool S, int ORD>
 __device__ __forceinline__ void rhs_point_stage(const GridK& G, const double* __restrict__ yin,
                                                 const double* __restrict__ d1x, const double* __restrict__ d1y,
                                                 double* out, const double* yn, double* acc, const Stage& st, int i,
@@ -105,9 +141,9 @@ __device__ __forceinline__ void rhs_point_stage(const GridK& G, const double* __
     P.dy = (S && AX < 0) ? d1y + idx : nullptr;
     P.g = make_geo<FAM>(G, p0, p1, p2);
     double k[NGF];
-    rhs_core<FAM, AX, S>(P, G.eta, k);
-    add_adv_ko<AX>(P.y, G.T, P.st, P.ox, P.g.D, G.sigma_metric, G.sigma_gauge, k);
-    stage_store(st, G.T, idx, k, yn, out, acc);
+    rhs_core<FAM, AX, S, ORD>(P, G.eta, k);
+    add_adv_ko<AX, ORD>(P.y, G.T, P.st, P.ox, P.g.D, G.sigma_metric, G.sigma_gauge, k);
+    stage_store(st, G.T, idx, k, yin, yn, out, acc);
 }
 
 // Points of the stored first differences (k_d1): interior i0, and i1 and i2 within
@@ -115,16 +151,16 @@ __device__ __forceinline__ void rhs_point_stage(const GridK& G, const double* __
 // derivatives; the axis-1 set is taken at interior i1 only (general grids).
 __host__ __device__ inline long d1_points(const GridK& G)
 {
-    const int E1 = G.ax == 1 ? 0 : 2, E2 = G.ax == 2 ? 0 : 2;
+    const int E = G.ord / 2, E1 = G.ax == 1 ? 0 : E, E2 = G.ax == 2 ? 0 : E;
     return (long)G.N0 * (G.N1 + 2 * E1) * (G.N2 + 2 * E2);
 }
 
 // point t of that region: raw first differences along axis 0 (and 1) of the N_D1
 // gridfunctions with second derivatives
-template <int AX>
+template <int AX, int ORD>
 __device__ __forceinline__ void d1_point(const GridK& G, const double* __restrict__ y, double* d1x, double* d1y, long t)
 {
-    constexpr int E1 = AX == 1 ? 0 : 2, E2 = AX == 2 ? 0 : 2;
+    constexpr int E1 = AX == 1 ? 0 : ORD / 2, E2 = AX == 2 ? 0 : ORD / 2;
     const int L1 = G.N1 + 2 * E1;
     if (t >= d1_points(G)) return;
     const int i = (int)(t % G.N0);
@@ -135,13 +171,13 @@ __device__ __forceinline__ void d1_point(const GridK& G, const double* __restric
 #pragma unroll
     for (int q = 0; q < N_D1; q++) {
         const double* f = y + (long)d1gf(q) * G.T + idx;
-        d1x[(long)q * G.T + idx] = d1raw(f, 1);
-        if (ycol) d1y[(long)q * G.T + idx] = d1raw(f, G.n0);
+        d1x[(long)q * G.T + idx] = d1r<ORD>(f, 1);
+        if (ycol) d1y[(long)q * G.T + idx] = d1r<ORD>(f, G.n0);
     }
 }
 
 // one pure-outer ghost point of an RK stage: radiation condition and the stage epilogue
-template <int FAM>
+template <int FAM, int ORD>
 __device__ __forceinline__ void outer_point_stage(const GridK& G, const OuterPt p, const double* __restrict__ yin,
                                                   double* out, const double* yn, double* acc,
                                                   const double* __restrict__ finf, const double* __restrict__ wspeed,
@@ -154,11 +190,17 @@ __device__ __forceinline__ void outer_point_stage(const GridK& G, const OuterPt 
 #pragma unroll
     for (int g = 0; g < NGF; g++) {
         const double* f = yin + (long)g * G.T + idx;
-        double rad = p.w0 * osraw(f, 1, k0);
-        if constexpr (FAM == FAM_CYL) rad = fma(p.w2, osraw(f, s2, k2), rad);
+        double rad;
+        if constexpr (ORD == 8) {
+            rad = p.w0 * osraw8(f, 1, k0);
+            if constexpr (FAM == FAM_CYL) rad = fma(p.w2, osraw8(f, s2, k2), rad);
+        } else {
+            rad = p.w0 * osraw(f, 1, k0);
+            if constexpr (FAM == FAM_CYL) rad = fma(p.w2, osraw(f, s2, k2), rad);
+        }
         k[g] = -ld(wspeed + g) * fma(ld(f) - ld(finf + g), p.invr, rad);
     }
-    stage_store(st, G.T, idx, k, yn, out, acc);
+    stage_store(st, G.T, idx, k, yin, yn, out, acc);
 }
 
 // y[ghost] = p * y[source] for gridfunction g; the sign is applied to the bit pattern (exact)

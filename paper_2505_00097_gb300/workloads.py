@@ -67,6 +67,14 @@ def config_headon() -> dict:
     return s
 
 
+def config_headon8() -> dict:
+    """The head-on configuration with the production scheme of Sec. 4.1: 8th-order finite differences
+    (NG = 5), SSPRK3, Kreiss-Oliger 0.3 on the metric and 0.99 on the gauge gridfunctions."""
+    s = config_headon()
+    s.update(name="headon8_sinhcyl_256x2x512", NG=5, ko_sigma=[0.3] * 17 + [0.99] * 7, integrator="ssprk3")
+    return s
+
+
 def config_large3d() -> dict:
     """Single BL puncture + 1e-10 SplitMix64 perturbation of hDD, SinhSpherical 384x192x384, 200 RK4 steps."""
     s = sinh_spherical((384, 192, 384))

@@ -1,0 +1,144 @@
+"""The production scheme of Sec. 4.1 on the GPU, through the C ABI, against the oracle:
+8th-order finite differences (NG = 5), 10th-difference dissipation with the paper's
+strengths (0.3 metric, 0.99 gauge), 8th-order one-sided derivatives in the radiation
+condition and SSPRK3 time integration.
+
+* one RHS evaluation: 1e-12 relative per tensor (grids with a two-point azimuth run
+  the specialised kernels, the others the general ones);
+* boundary conditions: radiation RHS 1e-12, parity copies bit-exact;
+* 30 SSPRK3 steps of Brill-Lindquist data: 1e-10 relative, inner ghosts exact parity
+  copies;
+* Hamiltonian and momentum constraints: 1e-12 pointwise, norms 1e-10.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle.oracle import Oracle  # noqa: E402
+from paper_2505_00097_gb300 import binding as B  # noqa: E402
+from paper_2505_00097_gb300 import build as BUILD  # noqa: E402
+from paper_2505_00097_gb300 import workloads as W  # noqa: E402
+from tests._common import assert_close  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+KO = [0.3] * 17 + [0.99] * 7
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    BUILD.build()
+    B.lib()
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def _host(t):
+    return t.detach().cpu().numpy()
+
+
+def _o8(spec):
+    return dict(spec, NG=5, ko_sigma=KO)
+
+
+SPECS = [
+    _o8(W.sinh_spherical((64, 16, 2))),                                   # two-point azimuth
+    _o8(W.sinh_spherical((37, 11, 10))),                                  # general, ragged tails
+    _o8(W.sinh_cylindrical((33, 2, 70), rho_max=20.0, z_max=20.0)),       # two-point azimuth
+    _o8(W.sinh_cylindrical((20, 6, 19), rho_max=5.0, z_max=5.0, w=0.4)),  # general
+]
+IDS = ["sph2", "sph3d", "cyl2", "cyl3d"]
+
+
+@pytest.mark.parametrize("smooth", [False, True], ids=["noise", "smooth"])
+@pytest.mark.parametrize("spec", SPECS, ids=IDS)
+def test_rhs_parity_8th_order(spec, smooth):
+    o = Oracle(spec)
+    g = B.Grid(spec)
+    assert g.n == tuple(N + 10 for N in spec["N"])
+    y = W.random_state(o.n, seed=31 + int(smooth), smooth=smooth)
+    o.inner_bc(y)
+    ref = o.rhs(y)
+    yd = _dev(y)
+    out = torch.full_like(yd, float("nan"))
+    g.rhs(yd, out)
+    torch.cuda.synchronize()
+    got = _host(out)
+    assert np.all(np.isnan(got[~np.tile(o.interior_mask(), 24)]))
+    assert_close(got, ref, o.T, 1e-12, mask=o.interior_mask(), what="8th-order rhs")
+
+
+@pytest.mark.parametrize("spec", SPECS, ids=IDS)
+def test_boundary_conditions_parity_8th_order(spec):
+    o = Oracle(spec)
+    g = B.Grid(spec)
+    y = W.random_state(o.n, seed=6, smooth=True)
+    o.inner_bc(y)
+    ref = o.full_rhs(y)
+    yd = _dev(y)
+    out = torch.zeros_like(yd)
+    g.rhs(yd, out)
+    g.apply_bcs(yd, out)
+    torch.cuda.synchronize()
+    assert_close(_host(out), ref, o.T, 1e-12, what="8th-order full rhs incl. boundaries")
+    src, par, cls = B.build_maps(spec["coords"], spec["N"], 5)
+    osrc, opar, ocls = o.build_map()[1:]
+    assert np.array_equal(src, osrc) and np.array_equal(par, opar.reshape(-1, 10)) and np.array_equal(cls, ocls)
+
+
+@pytest.mark.parametrize("spec", [SPECS[1], SPECS[2]], ids=["sph3d", "cyl2"])
+def test_ssprk3_steps_parity(spec):
+    o = Oracle(spec)
+    masses, pos = (0.6, 0.4), ((0.0, 0.0, 0.45), (0.0, 0.0, -0.55))
+    y = o.brill_lindquist(masses, pos, 1e-8, seed=5)
+    g = B.Grid(spec)
+    g.set_state(y, True)
+    dt = o.dt()
+    assert g.dt_cfl == pytest.approx(dt, rel=1e-15)
+    o.ssprk3(y, dt, 30)
+    g.ssprk3_step(dt, 30)
+    got = np.empty_like(y)
+    g.get_state(got, True)
+    assert np.all(np.isfinite(got))
+    assert_close(got, y, o.T, 1e-10, what="30 SSPRK3 steps, 8th order")
+    src, par, cls = B.build_maps(spec["coords"], spec["N"], 5)
+    gh = np.nonzero(cls == 2)[0]
+    types = [4, 5, 6, 7, 8, 9, 4, 5, 6, 7, 8, 9, 0, 0, 1, 2, 3, 1, 2, 3, 1, 2, 3, 0]
+    T = o.T
+    for gf in range(24):
+        v = got[gf * T:(gf + 1) * T]
+        assert np.array_equal(v[gh], par[gh, types[gf]] * v[src[gh]])
+    assert g.info.launches_per_ssprk3_step == 9
+
+
+@pytest.mark.parametrize("spec", [SPECS[1], SPECS[3]], ids=["sph3d", "cyl3d"])
+def test_constraints_parity_8th_order(spec):
+    o = Oracle(spec)
+    g = B.Grid(dict(spec, h_rmin=0.3, h_rmax=4.0))
+    y = W.random_state(o.n, seed=17, smooth=True)
+    o.inner_bc(y)
+    yd = _dev(y)
+    H = torch.zeros(o.T, dtype=torch.float64, device=DEV)
+    l2g, linfg = g.hamiltonian(yd, H)
+    Href, l2, linf, _ = o.hamiltonian(y, 0.3, 4.0)
+    m = o.interior_mask()
+    assert np.abs(_host(H)[m] - Href[m]).max() <= 1e-12 * np.abs(Href[m]).max()
+    assert l2g == pytest.approx(l2, rel=1e-10) and linfg == pytest.approx(linf, rel=1e-10)
+    Md = torch.zeros(3 * o.T, dtype=torch.float64, device=DEV)
+    ml2g, mlinfg = g.momentum(yd, Md)
+    M, _, ml2, mlinf, _ = o.momentum(y, 0.3, 4.0)
+    got = _host(Md).reshape(3, o.T)
+    assert np.abs(got[:, m] - M[:, m]).max() <= 1e-12 * np.abs(M[:, m]).max()
+    assert ml2g == pytest.approx(ml2, rel=1e-10) and mlinfg == pytest.approx(mlinf, rel=1e-10)
+
+
+def test_batched_mode_takes_the_4th_order_scheme_only():
+    g = B.Grid(SPECS[2])
+    with pytest.raises(B.NrError, match="4th-order"):
+        B.Batch([g])

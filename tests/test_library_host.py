@@ -66,15 +66,19 @@ MAP_SPECS = [
     W.sinh_spherical((64, 16, 2)), W.sinh_spherical((6, 4, 2)), W.sinh_spherical((5, 3, 4)), W.spherical((4, 5, 6)),
     W.sinh_spherical((12, 8, 10)), W.sinh_cylindrical((16, 2, 32)), W.sinh_cylindrical((6, 2, 5)),
     W.sinh_cylindrical((4, 6, 4), w=0.4), W.sinh_cylindrical((7, 8, 3)),
+    # five ghost layers (8th-order scheme)
+    dict(W.sinh_spherical((12, 8, 2)), NG=5), dict(W.sinh_spherical((7, 5, 6)), NG=5),
+    dict(W.sinh_cylindrical((9, 2, 11)), NG=5), dict(W.sinh_cylindrical((6, 6, 4), w=0.4), NG=5),
 ]
 
 
-@pytest.mark.parametrize("spec", MAP_SPECS, ids=[f"{s['coords']}-{'x'.join(map(str, s['N']))}" for s in MAP_SPECS])
+@pytest.mark.parametrize("spec", MAP_SPECS,
+                         ids=[f"{s['coords']}-{'x'.join(map(str, s['N']))}-ng{s['NG']}" for s in MAP_SPECS])
 def test_maps_bit_exact_vs_oracle(spec):
     o = Oracle(spec)
     rc, s1, p1, c1 = o.build_map()
     assert rc == 0
-    s2, p2, c2 = B.build_maps(spec["coords"], spec["N"])
+    s2, p2, c2 = B.build_maps(spec["coords"], spec["N"], spec["NG"])
     np.testing.assert_array_equal(c2, c1)
     np.testing.assert_array_equal(s2, s1)
     np.testing.assert_array_equal(p2, p1)
@@ -112,3 +116,18 @@ def test_dissipation_strengths_must_split_metric_and_gauge():
         B.dt_cfl(bad)
     with pytest.raises(B.NrError, match="ko_sigma"):
         B.Grid(bad)
+
+
+def test_ghost_layers_select_the_scheme():
+    for NG, ok in ((3, True), (5, True), (4, False), (2, False)):
+        spec = dict(W.sinh_cylindrical((8, 2, 16), rho_max=10.0, z_max=10.0), NG=NG)
+        if ok:
+            assert B.dt_cfl(spec) > 0.0
+        else:
+            with pytest.raises(B.NrError, match="NG"):
+                B.dt_cfl(spec)
+    srv = B.Server(2 ** 30, 2)
+    spec = dict(W.sinh_cylindrical((8, 2, 16), rho_max=10.0, z_max=10.0), NG=5, masses=(1.0,), positions=((0, 0, 0),))
+    with pytest.raises(B.NrError, match="4th-order"):
+        srv.submit(spec, 1.0)
+    srv.close()
