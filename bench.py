@@ -48,10 +48,13 @@ UNIT = "point-updates/s"
 # azimuth): k_rhs 308 + 376 + 2 x 1242 = 3168, k_d1 44.3.  Large 3D
 # (spherical, general): k_rhs 382 + 479 + 2 x 1684 = 4229, k_d1 89.9 (4 FLOP per
 # stored difference, 22 differences per point over the 1.03x larger region).
+# Head-on with the 8th-order scheme (headon8): k_rhs 403 + 432 + 2 x 1586 =
+# 4007, k_d1 122.9 (profiles/k_rhs_headon8_256x2x512.md).
 # A workload without a capture reports no FLOP rate.
-F_ALG = {"headon": 3212.3, "large3d": 4318.9}
+F_ALG = {"headon": 3212.3, "large3d": 4318.9, "headon8": 4129.9}
 # DRAM bytes (read + write) of the same two launches in that capture, or None
-TRAFFIC = {"headon": 24016640 + 91136 + 81816832 + 249576960}
+TRAFFIC = {"headon": 24016640 + 91136 + 81816832 + 249576960,
+           "headon8": 24951552 + 130048 + 87611136 + 331784192}
 # FP64 pipe of one SM: 2 DFMA per clock (ncu peak_sustained of
 # sm__sass_thread_inst_executed_op_dfma_pred_on), i.e. 4 FLOP per clock
 FP64_FLOP_PER_CLK_SM = 4.0

@@ -69,9 +69,12 @@ def config_headon() -> dict:
 
 def config_headon8() -> dict:
     """The head-on configuration with the production scheme of Sec. 4.1: 8th-order finite differences
-    (NG = 5), SSPRK3, Kreiss-Oliger 0.3 on the metric and 0.99 on the gauge gridfunctions."""
+    (NG = 5), SSPRK3, Kreiss-Oliger 0.3 on the metric and 0.99 on the gauge gridfunctions.  CFL 0.35:
+    on this grid SSPRK3 at CFL 0.5 goes unstable near the rho axis (measured at both orders; RK4,
+    whose stability interval on the imaginary axis is wider, is stable at 0.5)."""
     s = config_headon()
-    s.update(name="headon8_sinhcyl_256x2x512", NG=5, ko_sigma=[0.3] * 17 + [0.99] * 7, integrator="ssprk3")
+    s.update(name="headon8_sinhcyl_256x2x512", NG=5, ko_sigma=[0.3] * 17 + [0.99] * 7, integrator="ssprk3",
+             cfl=0.35)
     return s
 
 
