@@ -227,6 +227,19 @@ void orc_cart_all(const orc_params* p, double* out)
 }
 
 /* generic 3x3 inverse by cofactors; returns the determinant */
+static double det3(const double m[3][3])
+{
+    return m[0][0] * (m[1][1] * m[2][2] - m[1][2] * m[2][1]) - m[0][1] * (m[1][0] * m[2][2] - m[1][2] * m[2][0]) +
+           m[0][2] * (m[1][0] * m[2][1] - m[1][1] * m[2][0]);
+}
+
+/* Levi-Civita symbol [ijk] */
+static int levi(int i, int j, int k)
+{
+    if (i == j || j == k || i == k) return 0;
+    return ((i == 0 && j == 1) || (i == 1 && j == 2) || (i == 2 && j == 0)) ? 1 : -1;
+}
+
 static double inv3(const double m[3][3], double inv[3][3])
 {
     double c00 = m[1][1] * m[2][2] - m[1][2] * m[2][1];
@@ -1530,6 +1543,293 @@ void orc_momentum(const orc_params* p, const double* gfs, double* Mout, double* 
     if (l2) *l2 = cnt ? sqrt(s2 / cnt) : 0.0;
     if (linf) *linf = mx;
     if (count) *count = cnt;
+}
+
+/* ---------------------------------------------------------- Weyl scalar psi4 */
+/* The paper decomposes the Weyl scalar psi4 into spin-weight -2 harmonics
+ * (Sec. 4.1) without printing its definition; the oracle takes the textbook
+ * 3+1 form (vacuum):
+ *   E_ij = R_ij - K_ik K^k_j + K K_ij,   B_ij = eps_(i|^kl D_k K_l|j),
+ *   psi4 = -(E_ij - i B_ij) mbar^i mbar^j,
+ * with R_ij = Rbar_ij + R^phi_ij (Rbar_ij of the evolution equations),
+ * R^phi_ij = -2 Dbar_i Dbar_j phi - 2 gammabar_ij Dbar^2 phi + 4 d_i phi d_j phi
+ *            - 4 gammabar_ij |d phi|^2,
+ * K_ij = e^{4 phi} (Abar_ij + gammabar_ij K / 3), eps^{mkl} = [mkl] / sqrt(det gamma)
+ * in the (positively oriented) coordinate basis, and m = (u_theta + i u_phi)/sqrt 2
+ * from Gram-Schmidt, in the physical metric, of the radial, theta and phi
+ * directions of the point's Cartesian position.  For a linearised outgoing wave
+ * this gives psi4 = d_t^2 h_+ - i d_t^2 h_x, h_+ = (h_thth - h_phph)/2, h_x = h_thph. */
+static void weyl_point(const orc_params* p, const rfm_pt* R, const refmet* M, const pt_fields* F, double Et[3][3],
+                       double Bt[3][3])
+{
+    geom_pt G;
+    geometry(M, F, &G);
+    const double W = F->W, iW2 = 1.0 / (W * W);
+    double gam[3][3], gami[3][3], dgam[3][3][3], Kd[3][3], dK[3][3][3], Ric[3][3];
+    double lap = 0.0, gp = 0.0;
+    for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++) {
+            lap += G.gbinv[a][b] * G.DDphi[a][b];
+            gp += G.gbinv[a][b] * G.dphi[a] * G.dphi[b];
+        }
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) {
+            gam[i][j] = G.gb[i][j] * iW2;
+            gami[i][j] = G.gbinv[i][j] * W * W;
+            Kd[i][j] = (F->A[i][j] + G.gb[i][j] * F->K / 3.0) * iW2;
+            Ric[i][j] = G.Ric[i][j] - 2.0 * G.DDphi[i][j] - 2.0 * G.gb[i][j] * lap + 4.0 * G.dphi[i] * G.dphi[j] -
+                        4.0 * G.gb[i][j] * gp;
+            for (int k = 0; k < 3; k++) {
+                const double dgb = M->dg[i][j][k] + F->deps[i][j][k];
+                dgam[i][j][k] = dgb * iW2 - 2.0 * G.gb[i][j] * iW2 / W * F->dW[k];
+                dK[i][j][k] = (F->dA[i][j][k] + dgb * F->K / 3.0 + G.gb[i][j] * F->dK[k] / 3.0) * iW2 -
+                              2.0 * (F->A[i][j] + G.gb[i][j] * F->K / 3.0) * iW2 / W * F->dW[k];
+            }
+        }
+    (void)p;
+    /* physical Christoffel symbols Gam[k][i][j] */
+    double Gp[3][3][3];
+    for (int k = 0; k < 3; k++)
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) {
+                double t = 0.0;
+                for (int l = 0; l < 3; l++) t += gami[k][l] * (dgam[j][l][i] + dgam[i][l][j] - dgam[i][j][l]);
+                Gp[k][i][j] = 0.5 * t;
+            }
+    double DK[3][3][3]; /* DK[k][i][j] = D_k K_ij */
+    for (int k = 0; k < 3; k++)
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) {
+                double t = dK[i][j][k];
+                for (int m = 0; m < 3; m++) t -= Gp[m][k][i] * Kd[m][j] + Gp[m][k][j] * Kd[i][m];
+                DK[k][i][j] = t;
+            }
+    double E[3][3], Bm[3][3];
+    const double sq = sqrt(det3(gam));
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) {
+            double kk = 0.0;
+            for (int k = 0; k < 3; k++)
+                for (int l = 0; l < 3; l++) kk += Kd[i][k] * gami[k][l] * Kd[l][j];
+            E[i][j] = Ric[i][j] - kk + F->K * Kd[i][j];
+            /* eps_i^{kl} D_k K_lj = gamma_im [mkl] / sqrt(gamma) D_k K_lj */
+            double b = 0.0;
+            for (int m = 0; m < 3; m++)
+                for (int k = 0; k < 3; k++)
+                    for (int l = 0; l < 3; l++) {
+                        const int e = levi(m, k, l);
+                        if (e) b += gam[i][m] * e * DK[k][l][j];
+                    }
+            Bm[i][j] = b / sq;
+        }
+    /* tetrad: Gram-Schmidt of the radial, theta, phi directions of the Cartesian position */
+    double Jinv[3][3];
+    inv3(R->J, Jinv);
+    const double x = R->cart[0], y = R->cart[1], z = R->cart[2];
+    const double rr = sqrt(x * x + y * y + z * z), th = acos(z / rr), ph = atan2(y, x);
+    const double vc[3][3] = {{x / rr, y / rr, z / rr},
+                             {cos(th) * cos(ph), cos(th) * sin(ph), -sin(th)},
+                             {-sin(ph), cos(ph), 0.0}};
+    double u[3][3];
+    for (int a = 0; a < 3; a++) {
+        for (int d = 0; d < 3; d++) {
+            double t = 0.0;
+            for (int c = 0; c < 3; c++) t += Jinv[d][c] * vc[a][c];
+            u[a][d] = t;
+        }
+        for (int b = 0; b < a; b++) {
+            double dot = 0.0;
+            for (int i = 0; i < 3; i++)
+                for (int j = 0; j < 3; j++) dot += gam[i][j] * u[a][i] * u[b][j];
+            for (int d = 0; d < 3; d++) u[a][d] -= dot * u[b][d];
+        }
+        double nn = 0.0;
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) nn += gam[i][j] * u[a][i] * u[a][j];
+        for (int d = 0; d < 3; d++) u[a][d] /= sqrt(nn);
+    }
+    for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++) {
+            double e = 0.0, bb = 0.0;
+            for (int i = 0; i < 3; i++)
+                for (int j = 0; j < 3; j++) {
+                    e += E[i][j] * u[a][i] * u[b][j];
+                    bb += 0.5 * (Bm[i][j] + Bm[j][i]) * u[a][i] * u[b][j];
+                }
+            Et[a][b] = e;
+            Bt[a][b] = bb;
+        }
+}
+
+/* E and B in the tetrad (u_r, u_theta, u_phi) at interior points: Eout, Bout
+ * (6*T each, symmetric pairs rr, rt, rp, tt, tp, pp; either may be NULL), and
+ * psi4 (2*T: real, imaginary; may be NULL).  Ghost points are set to 0. */
+void orc_psi4(const orc_params* p, const double* gfs, double* psi4, double* Eout, double* Bout)
+{
+    int n[3];
+    long T = orc_sizes(p, n);
+    int NG = p->NG;
+    if (psi4)
+        for (long q = 0; q < 2 * T; q++) psi4[q] = 0.0;
+    if (Eout)
+        for (long q = 0; q < 6 * T; q++) Eout[q] = 0.0;
+    if (Bout)
+        for (long q = 0; q < 6 * T; q++) Bout[q] = 0.0;
+    fdw Wd;
+    fdw_make(p->NG, &Wd);
+    int nt = p->nthreads;
+#ifdef _OPENMP
+    if (nt <= 0) nt = omp_get_max_threads();
+#pragma omp parallel for collapse(2) schedule(static) num_threads(nt)
+#endif
+    for (int k = 0; k < p->N[2]; k++)
+        for (int j = 0; j < p->N[1]; j++)
+            for (int i = 0; i < p->N[0]; i++) {
+                int ii[3] = {i + NG, j + NG, k + NG};
+                long idx = ii[0] + (long)n[0] * (ii[1] + (long)n[1] * ii[2]);
+                double xx[3] = {orc_xx(p, 0, ii[0]), orc_xx(p, 1, ii[1]), orc_xx(p, 2, ii[2])};
+                rfm_pt R;
+                refmet M;
+                pt_fields F;
+                rfm_eval(p, xx, &R);
+                refmet_from(&R, &M);
+                load_point(p, n, T, gfs, idx, &R, &F, &Wd);
+                double Et[3][3], Bt[3][3];
+                weyl_point(p, &R, &M, &F, Et, Bt);
+                if (psi4) {
+                    psi4[idx] = -0.5 * (Et[1][1] - Et[2][2]) + Bt[1][2];
+                    psi4[T + idx] = Et[1][2] + 0.5 * (Bt[1][1] - Bt[2][2]);
+                }
+                for (int s = 0; s < 6; s++) {
+                    if (Eout) Eout[s * T + idx] = Et[SYM_I[s]][SYM_J[s]];
+                    if (Bout) Bout[s * T + idx] = Bt[SYM_I[s]][SYM_J[s]];
+                }
+            }
+    (void)nt;
+}
+
+/* spin-weighted spherical harmonic sY_lm (Goldberg et al. 1967 closed form):
+ * (-1)^m sqrt[(l+m)!(l-m)!(2l+1) / (4 pi (l+s)!(l-s)!)] sin^{2l}(th/2)
+ *   sum_r C(l-s, r) C(l+s, r+s-m) (-1)^{l-r-s} e^{i m ph} cot^{2r+s-m}(th/2) */
+static double fact(int n)
+{
+    double r = 1.0;
+    for (int i = 2; i <= n; i++) r *= i;
+    return r;
+}
+void orc_sylm(int s, int l, int m, double th, double ph, double* re, double* im)
+{
+    double pre = ((m % 2) ? -1.0 : 1.0) *
+                 sqrt(fact(l + m) * fact(l - m) * (2 * l + 1) / (4.0 * M_PI * fact(l + s) * fact(l - s)));
+    double sh = sin(0.5 * th), ch = cos(0.5 * th), sum = 0.0;
+    for (int r = 0; r <= l - s; r++) {
+        int k2 = r + s - m;
+        if (k2 < 0 || k2 > l + s) continue;
+        int pw = 2 * r + s - m; /* power of cot(th/2) = ch/sh; combined with sh^{2l}: ch^pw sh^{2l-pw} */
+        double term = binom(l - s, r) * binom(l + s, k2) * (((l - r - s) % 2) ? -1.0 : 1.0);
+        term *= pow(ch, pw) * pow(sh, 2 * l - pw);
+        sum += term;
+    }
+    *re = pre * sum * cos(m * ph);
+    *im = pre * sum * sin(m * ph);
+}
+
+/* Gauss-Legendre nodes and weights on [-1, 1] (Newton iteration on P_n) */
+static void gauss_legendre(int n, double* x, double* w)
+{
+    for (int i = 0; i < n; i++) {
+        double z = cos(M_PI * (i + 0.75) / (n + 0.5)), dp = 0.0;
+        for (int it = 0; it < 100; it++) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; k++) {
+                double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            if (n == 1) { p1 = z; p0 = 1.0; }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            double dz = p1 / dp;
+            z -= dz;
+            if (fabs(dz) < 1e-16) break;
+        }
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+/* Modes C_lm = integral of psi4 conj(-2Y_lm) over the sphere of radius Rext,
+ * l = 2..lmax, m = -l..l in that order (2 doubles each: re, im).  psi4 (2*T)
+ * holds the field at interior points; inner ghosts are filled here by the
+ * parity map (psi4 is a scalar: the same physical point); the sphere must keep
+ * two cells from the outer boundary.  Quadrature: ntheta Gauss-Legendre nodes
+ * in cos(theta) times nphi uniform nodes in phi; psi4 at each node by cubic
+ * Lagrange interpolation in the logical coordinates. */
+int orc_psi4_modes(const orc_params* p, const double* psi4, double Rext, int ntheta, int nphi, int lmax, double* out)
+{
+    int n[3];
+    long T = orc_sizes(p, n);
+    bmap m;
+    int bad = bmap_make(p, &m);
+    double* f = (double*)malloc(sizeof(double) * 2 * T);
+    memcpy(f, psi4, sizeof(double) * 2 * T);
+    for (long idx = 0; idx < T; idx++)
+        if (m.cls[idx] == 2) {
+            f[idx] = f[m.src[idx]];
+            f[T + idx] = f[T + m.src[idx]];
+        }
+    double lo[3], hi[3];
+    domain(p, lo, hi);
+    double* x = (double*)malloc(sizeof(double) * ntheta);
+    double* w = (double*)malloc(sizeof(double) * ntheta);
+    gauss_legendre(ntheta, x, w);
+    int nm = 0;
+    for (int l = 2; l <= lmax; l++) nm += 2 * l + 1;
+    for (int q = 0; q < 2 * nm; q++) out[q] = 0.0;
+    for (int it = 0; it < ntheta; it++)
+        for (int jp = 0; jp < nphi; jp++) {
+            const double th = acos(x[it]), ph = -M_PI + 2.0 * M_PI * (jp + 0.5) / nphi;
+            const double c[3] = {Rext * sin(th) * cos(ph), Rext * sin(th) * sin(ph), Rext * cos(th)};
+            double xx[3];
+            cart_to_xx(p, c, xx);
+            int base[3];
+            double L[3][4];
+            for (int d = 0; d < 3; d++) {
+                double fi = (xx[d] - lo[d]) / dxx_of(p, d) + p->NG - 0.5;
+                int i0 = (int)floor(fi);
+                double t = fi - i0;
+                base[d] = i0 - 1;
+                L[d][0] = -t * (t - 1.0) * (t - 2.0) / 6.0;
+                L[d][1] = (t + 1.0) * (t - 1.0) * (t - 2.0) / 2.0;
+                L[d][2] = -(t + 1.0) * t * (t - 2.0) / 2.0;
+                L[d][3] = (t + 1.0) * t * (t - 1.0) / 6.0;
+                if (base[d] < 0 || base[d] + 3 >= n[d]) bad = 1;
+            }
+            if (bad) continue;
+            double vr = 0.0, vi = 0.0;
+            for (int a = 0; a < 4; a++)
+                for (int b = 0; b < 4; b++)
+                    for (int cc = 0; cc < 4; cc++) {
+                        long idx = (base[0] + a) + (long)n[0] * ((base[1] + b) + (long)n[1] * (base[2] + cc));
+                        double wt = L[0][a] * L[1][b] * L[2][cc];
+                        vr += wt * f[idx];
+                        vi += wt * f[T + idx];
+                    }
+            const double dw = w[it] * 2.0 * M_PI / nphi;
+            int q = 0;
+            for (int l = 2; l <= lmax; l++)
+                for (int mm = -l; mm <= l; mm++, q++) {
+                    double yr, yi;
+                    orc_sylm(-2, l, mm, th, ph, &yr, &yi);
+                    /* psi4 conj(Y) */
+                    out[2 * q] += dw * (vr * yr + vi * yi);
+                    out[2 * q + 1] += dw * (vi * yr - vr * yi);
+                }
+        }
+    free(x);
+    free(w);
+    free(f);
+    bmap_free(&m);
+    return bad;
 }
 
 /* -------------------------------------------------------- initial data */

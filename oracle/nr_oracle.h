@@ -92,6 +92,14 @@ void orc_hamiltonian(const orc_params* p, const double* gfs, double* H, double r
  * NULL) and its L2 / Linf norms over the radius band [rmin, rmax]. */
 void orc_momentum(const orc_params* p, const double* gfs, double* M, double* Mnorm, double rmin, double rmax,
                   double* l2, double* linf, long* count);
+/* Weyl scalar psi4 (see nr_oracle.c) at interior points: psi4 (2*T: re, im),
+ * E and B in the tetrad (6*T each: rr rt rp tt tp pp); any may be NULL */
+void orc_psi4(const orc_params* p, const double* gfs, double* psi4, double* E, double* B);
+/* spin-weighted spherical harmonic sY_lm(theta, phi) */
+void orc_sylm(int s, int l, int m, double th, double ph, double* re, double* im);
+/* modes of psi4 (2*T) on the sphere of radius Rext, l = 2..lmax, m = -l..l:
+ * out[2q], out[2q+1] = re, im; nonzero return: a stencil left the grid */
+int orc_psi4_modes(const orc_params* p, const double* psi4, double Rext, int ntheta, int nphi, int lmax, double* out);
 
 /* Generic classic RK4 (used by orc_rk4_step; exported for its pin). */
 typedef void (*orc_rhs_fn)(void* ctx, const double* y, double* k);

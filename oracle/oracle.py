@@ -97,6 +97,10 @@ def lib() -> ctypes.CDLL:
                                       ctypes.POINTER(ctypes.c_long)]
         L.orc_momentum.argtypes = [P, dp, dp, dp, ctypes.c_double, ctypes.c_double, dp, dp,
                                    ctypes.POINTER(ctypes.c_long)]
+        L.orc_psi4.argtypes = [P, dp, dp, dp, dp]
+        L.orc_sylm.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp, dp]
+        L.orc_psi4_modes.argtypes = [P, dp, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp]
+        L.orc_psi4_modes.restype = ctypes.c_int
         L.orc_rk4_generic.argtypes = [ctypes.c_long, dp, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]
         L.orc_ssprk3_generic.argtypes = [ctypes.c_long, dp, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]
         L.orc_ssprk3_step.argtypes = [P, dp, ctypes.c_double, ctypes.c_int]
@@ -256,6 +260,23 @@ class Oracle:
                             ctypes.byref(l2), ctypes.byref(linf), ctypes.byref(cnt))
         return M.reshape(3, self.T), mag, l2.value, linf.value, cnt.value
 
+    def psi4(self, y: np.ndarray):
+        """Weyl scalar psi4 (2, T) and E, B in the tetrad (6, T each) at interior points."""
+        out = np.zeros(2 * self.T)
+        E = np.zeros(6 * self.T)
+        Bm = np.zeros(6 * self.T)
+        self.L.orc_psi4(ctypes.byref(self.p), _dp(y), _dp(out), _dp(E), _dp(Bm))
+        return out.reshape(2, self.T), E.reshape(6, self.T), Bm.reshape(6, self.T)
+
+    def psi4_modes(self, psi4: np.ndarray, Rext: float, ntheta: int = 24, nphi: int = 48, lmax: int = 8):
+        """Complex modes C_lm, l = 2..lmax, m = -l..l, of a psi4 field (2, T) on the sphere Rext."""
+        nm = sum(2 * l + 1 for l in range(2, lmax + 1))
+        out = np.zeros(2 * nm)
+        f = np.ascontiguousarray(psi4, dtype=np.float64).reshape(-1)
+        if self.L.orc_psi4_modes(ctypes.byref(self.p), _dp(f), float(Rext), int(ntheta), int(nphi), int(lmax), _dp(out)):
+            raise ValueError("sphere outside the grid or map failed")
+        return out[0::2] + 1j * out[1::2]
+
     def interior_mask(self) -> np.ndarray:
         NG = self.NG
         m = np.zeros(self.n[::-1], dtype=bool)
@@ -299,6 +320,12 @@ def fd_weights(NG: int, which: int, a: int = 0) -> np.ndarray:
     if n == 0:
         raise ValueError("no such stencil")
     return w[:n].copy()
+
+
+def sylm(s: int, l: int, m: int, th: float, ph: float) -> complex:
+    re, im = ctypes.c_double(), ctypes.c_double()
+    lib().orc_sylm(int(s), int(l), int(m), float(th), float(ph), ctypes.byref(re), ctypes.byref(im))
+    return complex(re.value, im.value)
 
 
 def threads_used(spec: dict) -> int:
