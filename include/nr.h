@@ -194,6 +194,26 @@ int nr_hamiltonian(nr_grid* grid, const double* y_dev, double* H_dev, double* l2
  * norm is asked for. */
 int nr_momentum(nr_grid* grid, const double* y_dev, double* M_dev, double* l2_out, double* linf_out);
 
+/* Weyl scalar psi4 (the waveform of Sec. 4.1; the paper prints no formula):
+ *   psi4 = -(E_ij - i B_ij) mbar^i mbar^j,  E_ij = R_ij - K_ik K^k_j + K K_ij,
+ *   B_ij = eps_(i|^kl D_k K_l|j),  R_ij = Rbar_ij (as in the evolution) + R^phi_ij,
+ * m = (u_theta + i u_phi)/sqrt 2, u from Gram-Schmidt in the physical metric of
+ * the spherical directions of the point's Cartesian position; a linearised
+ * outgoing wave gives psi4 = d_t^2 h_+ - i d_t^2 h_x.  At interior points of
+ * y_dev (NULL: the grid-owned state) into psi4_dev (caller-owned 2*T doubles:
+ * real part, imaginary part); inner ghosts take the value of the point they map
+ * to (psi4 is a scalar), outer ghosts are 0.  Stream-ordered, no sync. */
+int nr_psi4(nr_grid* grid, const double* y_dev, double* psi4_dev);
+
+/* Spin-weight -2 modes C_lm = integral over the sphere of radius Rext of
+ * psi4 conj(-2Y_lm), l = 2..lmax (lmax <= 16), m = -l..l in that order,
+ * written to modes_out (host, 2 doubles per mode: re, im).  psi4 of y_dev (NULL:
+ * the grid-owned state) is sampled at ntheta Gauss-Legendre nodes in cos(theta)
+ * times nphi uniform nodes in phi by cubic Lagrange interpolation in the logical
+ * coordinates.  NR_EINVAL if a node's stencil reaches the outer boundary.
+ * Allocates its scratch and synchronises params.stream. */
+int nr_psi4_modes(nr_grid* grid, const double* y_dev, double Rext, int ntheta, int nphi, int lmax, double* modes_out);
+
 /* Copy the grid-owned state (24*T doubles) to / from dst / src.  to_host /
  * from_host = 1: dst/src is host memory (pinned or pageable) and the call
  * synchronises; 0: device memory, stream-ordered. */

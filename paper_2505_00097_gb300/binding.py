@@ -24,7 +24,7 @@ COORDS = {"sinh_spherical": 0, "sinh_cylindrical": 1, "spherical": 2}
 EXPORTS = (
     "nr_params_default", "nr_grid_create", "nr_grid_destroy", "nr_query", "nr_set_brill_lindquist", "nr_rhs",
     "nr_apply_bcs", "nr_apply_inner_bcs", "nr_rk4_step", "nr_ssprk3_step", "nr_hamiltonian", "nr_momentum",
-    "nr_get_state",
+    "nr_psi4", "nr_psi4_modes", "nr_get_state",
     "nr_set_state",
     "nr_sync", "nr_check_finite", "nr_build_maps", "nr_dt_cfl", "nr_fp64_peak", "nr_hamiltonian_noalloc",
     "nr_batch_create", "nr_batch_destroy", "nr_batch_set_tile", "nr_batch_autotune", "nr_batch_rk4_step",
@@ -106,6 +106,8 @@ def lib() -> ctypes.CDLL:
     L.nr_ssprk3_step.argtypes = [vp, ctypes.c_double, ctypes.c_int]
     L.nr_hamiltonian.argtypes = [vp, vp, vp, dp, dp]
     L.nr_momentum.argtypes = [vp, vp, vp, dp, dp]
+    L.nr_psi4.argtypes = [vp, vp, vp]
+    L.nr_psi4_modes.argtypes = [vp, vp, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp]
     L.nr_get_state.argtypes = [vp, vp, ctypes.c_int]
     L.nr_set_state.argtypes = [vp, vp, ctypes.c_int]
     L.nr_sync.argtypes = [vp]
@@ -276,6 +278,18 @@ class Grid:
         _check(lib().nr_hamiltonian(self.h, None if y is None else _ptr(y), None if H is None else _ptr(H),
                                     ctypes.byref(l2), ctypes.byref(linf)))
         return l2.value, linf.value
+
+    def psi4(self, out, y=None) -> None:
+        """psi4 (2*T doubles on the device: re, im) of y (default: the grid-owned state)."""
+        _check(lib().nr_psi4(self.h, None if y is None else _ptr(y), _ptr(out)))
+
+    def psi4_modes(self, Rext: float, ntheta: int = 24, nphi: int = 48, lmax: int = 8, y=None) -> np.ndarray:
+        """Complex C_lm, l = 2..lmax, m = -l..l."""
+        nm = sum(2 * l + 1 for l in range(2, lmax + 1))
+        out = np.zeros(2 * nm)
+        _check(lib().nr_psi4_modes(self.h, None if y is None else _ptr(y), float(Rext), int(ntheta), int(nphi),
+                                   int(lmax), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return out[0::2] + 1j * out[1::2]
 
     def momentum(self, y=None, M=None):
         l2, linf = ctypes.c_double(), ctypes.c_double()
