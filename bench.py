@@ -55,6 +55,13 @@ F_ALG = {"headon": 3212.3, "large3d": 4318.9, "headon8": 4129.9}
 # DRAM bytes (read + write) of the same two launches in that capture, or None
 TRAFFIC = {"headon": 24016640 + 91136 + 81816832 + 249576960,
            "headon8": 24951552 + 130048 + 87611136 + 331784192}
+# The same for the diagnostics (Hamiltonian and momentum constraints, psi4), per interior
+# point of one call, from one ncu capture of those kernels, by workload (head-on: k_ham 416 /
+# 258 / 651 DADD / DMUL / DFMA, k_mom 137 / 162 / 269, k_psi4 551 / 505 / 1103; the reductions
+# and ghost copies add < 0.1; profiles/diagnostics_headon_256x2x512.md); absent: not captured
+DIAG_FLOPS = {"headon": {"hamiltonian": 1976.0, "momentum": 837.0, "psi4": 3262.0}}
+# psi4 modes on the workload's extraction sphere: l <= 8, Gauss-Legendre x uniform nodes
+PSI4_LMAX, PSI4_NTHETA, PSI4_NPHI = 8, 24, 48
 # FP64 pipe of one SM: 2 DFMA per clock (ncu peak_sustained of
 # sm__sass_thread_inst_executed_op_dfma_pred_on), i.e. 4 FLOP per clock
 FP64_FLOP_PER_CLK_SM = 4.0
@@ -79,6 +86,8 @@ def parse():
                     help="interior points advanced together by the served arm (0: no cap)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-diagnostics", action="store_true")
+    ap.add_argument("--diag-reps", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     return ap.parse_args()
 
@@ -350,6 +359,7 @@ def run_ours(args, spec, world, rank, local):
     torch.cuda.synchronize()
     rhs_ms = r0.elapsed_time(r1) / nrep
     del ybuf, obuf
+    diag = None if args.no_diagnostics else diagnostics(g, spec, stream, args.workload, args.diag_reps)
     probe = B.fp64_peak(local)
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
     mhz = (ck or {}).get("sm_mhz") or (ck or {}).get("sm_max_mhz") or 2070.0
@@ -368,28 +378,38 @@ def run_ours(args, spec, world, rank, local):
         roof.update(achieved=None, frac=None, flops_per_point=None)
 
     # end to end through the C ABI with host buffers: every step uploads the state from
-    # pinned host memory, advances it, and reads the new state back
+    # pinned host memory, advances it, and reads the new state back.  The headline uses the
+    # compact state (interior + pure outer points; inner ghosts are parity copies rebuilt on
+    # upload); the full padded array is timed too.
     e2e = None
     if not args.no_e2e:
         n_e2e = min(args.steps, 100)
-        host_in = torch.empty(24 * T, dtype=torch.float64).pin_memory()
-        host_out = torch.empty(24 * T, dtype=torch.float64).pin_memory()
-        g.get_state(host_in.data_ptr(), True)
-        if dist is not None:
-            dist.barrier()
-        t0 = time.perf_counter()
-        for s in range(n_e2e):
-            g.set_state(host_in.data_ptr(), True)
-            run_steps(1, args.warmup + args.steps + s)
-            g.get_state(host_out.data_ptr(), True)
-            host_in, host_out = host_out, host_in
-        torch.cuda.synchronize()
-        el = reduce_max(dist, time.perf_counter() - t0, dev)
-        nbytes = 24 * T * 8
-        e2e = {"value": world * pts * substeps * n_e2e / el, "unit": UNIT, "h2d_bytes_per_step": nbytes,
-               "d2h_bytes_per_step": nbytes, "steps": n_e2e,
-               "path": f"nr_set_state(pinned host) + {'nr_ssprk3_step' if ssp else 'nr_rk4_step'} + "
-                       "nr_get_state(pinned host) per step"}
+
+        def e2e_run(npts, put, get, start):
+            host_in = torch.empty(24 * npts, dtype=torch.float64).pin_memory()
+            host_out = torch.empty(24 * npts, dtype=torch.float64).pin_memory()
+            get(host_in.data_ptr(), True)
+            if dist is not None:
+                dist.barrier()
+            t0 = time.perf_counter()
+            for s in range(n_e2e):
+                put(host_in.data_ptr(), True)
+                run_steps(1, start + s)
+                get(host_out.data_ptr(), True)
+                host_in, host_out = host_out, host_in
+            torch.cuda.synchronize()
+            el = reduce_max(dist, time.perf_counter() - t0, dev)
+            return world * pts * substeps * n_e2e / el, 24 * npts * 8
+
+        nc = g.info.n_state_points
+        stepper = "nr_ssprk3_step" if ssp else "nr_rk4_step"
+        v, nbytes = e2e_run(nc, g.set_state_compact, g.get_state_compact, args.warmup + args.steps)
+        vf, fbytes = e2e_run(T, g.set_state, g.get_state, args.warmup + args.steps + n_e2e)
+        e2e = {"value": v, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "steps": n_e2e,
+               "path": f"nr_set_state_compact(pinned host) + {stepper} + nr_get_state_compact(pinned host) per step "
+                       f"({nc} interior + pure outer points of {T})",
+               "full_state": {"value": vf, "h2d_bytes_per_step": fbytes, "d2h_bytes_per_step": fbytes,
+                              "path": f"nr_set_state(pinned host) + {stepper} + nr_get_state(pinned host) per step"}}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -404,11 +424,57 @@ def run_ours(args, spec, world, rank, local):
                                        "dt": dt}),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": ck,
         }
+        if diag is not None:
+            line["diagnostics"] = diag
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
     g.close()
+
+
+def diagnostics(g, spec, stream, wl: str, nrep: int) -> dict:
+    """Device time per call of the constraint and waveform diagnostics on the evolved state
+    (CUDA events on the library's stream, no norm read-back), and the wall time of one
+    psi4 mode decomposition (host set-up, sampling, reduction, copy back)."""
+    import torch
+
+    T, pts = g.T, g.interior
+    dev = torch.device("cuda", torch.cuda.current_device())
+    H = torch.empty(T, dtype=torch.float64, device=dev)
+    M = torch.empty(3 * T, dtype=torch.float64, device=dev)
+    P4 = torch.empty(2 * T, dtype=torch.float64, device=dev)
+    calls = {"hamiltonian": (lambda: g.hamiltonian(None, H, norms=False), "nr_hamiltonian: k_ham + k_ham_reduce"),
+             "momentum": (lambda: g.momentum(None, M, norms=False), "nr_momentum: k_mom + k_ham_reduce"),
+             "psi4": (lambda: g.psi4(P4), "nr_psi4: k_psi4 + k_psi4_ghosts")}
+    out = {}
+    for name, (fn, what) in calls.items():
+        fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(nrep):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / nrep
+        d = {"launches": what, "device_ms": ms, "points_per_s": pts / (ms * 1e-3)}
+        f = DIAG_FLOPS.get(wl, {}).get(name)
+        if f:
+            d.update(flops_per_point=f, achieved_tflops=f * pts / (ms * 1e-3) / 1e12)
+        out[name] = d
+    R = spec.get("psi4_radius")
+    if R:
+        g.psi4_modes(R, PSI4_NTHETA, PSI4_NPHI, PSI4_LMAX)
+        t0 = time.perf_counter()
+        for _ in range(nrep):
+            c = g.psi4_modes(R, PSI4_NTHETA, PSI4_NPHI, PSI4_LMAX)
+        out["psi4_modes"] = {"launches": "nr_psi4_modes: k_psi4 + k_psi4_ghosts + k_sphere_sample + k_sphere_modes",
+                             "wall_ms": (time.perf_counter() - t0) * 1e3 / nrep, "radius": R, "lmax": PSI4_LMAX,
+                             "nodes": [PSI4_NTHETA, PSI4_NPHI], "abs_C2m": [float(abs(v)) for v in c[:5]]}
+    del H, M, P4
+    return out
 
 
 # ------------------------------------------------------- batched / served

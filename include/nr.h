@@ -112,6 +112,7 @@ typedef struct {
                                 azimuth holds two points: then its ghosts are copied in stage 4 only) */
     int launches_per_step;   /* kernel launches of one nr_rk4_step */
     int launches_per_ssprk3_step; /* kernel launches of one nr_ssprk3_step */
+    int64_t n_state_points;  /* interior + pure outer ghost points: the points of a compact state */
 } nr_grid_info;
 
 /* Defaults: ko_sigma 0.3, eta 2, cfl 0.5, wavespeed 1, f_inf 1 for W and alpha
@@ -219,6 +220,19 @@ int nr_psi4_modes(nr_grid* grid, const double* y_dev, double Rext, int ntheta, i
  * synchronises; 0: device memory, stream-ordered. */
 int nr_get_state(nr_grid* grid, double* dst, int to_host);
 int nr_set_state(nr_grid* grid, const double* src, int from_host);
+
+/* Compact state: the 24 gridfunctions at the n_state_points canonical points only
+ * (interior and pure outer ghosts, flat-index order; layout [gf][t], 24 *
+ * n_state_points doubles).  Inner ghost points hold parity copies of canonical
+ * points (Sec. 3), so the compact state determines the full one:
+ * nr_set_state_compact scatters it and then applies the inner boundary
+ * condition, which leaves the same state, bit for bit, as nr_set_state of the
+ * full array it came from.  to_host / from_host = 1: host memory (pinned or
+ * pageable), staged through a grid-owned device buffer allocated on first use
+ * (NR_ENOMEM / NR_ECUDA if that fails); the call synchronises.  0: device
+ * memory, stream-ordered. */
+int nr_get_state_compact(nr_grid* grid, double* dst, int to_host);
+int nr_set_state_compact(nr_grid* grid, const double* src, int from_host);
 
 /* Wait for all work of the grid's stream. */
 int nr_sync(nr_grid* grid);

@@ -24,7 +24,7 @@ COORDS = {"sinh_spherical": 0, "sinh_cylindrical": 1, "spherical": 2}
 EXPORTS = (
     "nr_params_default", "nr_grid_create", "nr_grid_destroy", "nr_query", "nr_set_brill_lindquist", "nr_rhs",
     "nr_apply_bcs", "nr_apply_inner_bcs", "nr_rk4_step", "nr_ssprk3_step", "nr_hamiltonian", "nr_momentum",
-    "nr_psi4", "nr_psi4_modes", "nr_get_state",
+    "nr_psi4", "nr_psi4_modes", "nr_get_state", "nr_get_state_compact", "nr_set_state_compact",
     "nr_set_state",
     "nr_sync", "nr_check_finite", "nr_build_maps", "nr_dt_cfl", "nr_fp64_peak", "nr_hamiltonian_noalloc",
     "nr_batch_create", "nr_batch_destroy", "nr_batch_set_tile", "nr_batch_autotune", "nr_batch_rk4_step",
@@ -72,6 +72,7 @@ class NrGridInfo(ctypes.Structure):
         ("n_inner_stencil", ctypes.c_int64),
         ("launches_per_step", ctypes.c_int),
         ("launches_per_ssprk3_step", ctypes.c_int),
+        ("n_state_points", ctypes.c_int64),
     ]
 
 
@@ -110,6 +111,8 @@ def lib() -> ctypes.CDLL:
     L.nr_psi4_modes.argtypes = [vp, vp, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp]
     L.nr_get_state.argtypes = [vp, vp, ctypes.c_int]
     L.nr_set_state.argtypes = [vp, vp, ctypes.c_int]
+    L.nr_get_state_compact.argtypes = [vp, vp, ctypes.c_int]
+    L.nr_set_state_compact.argtypes = [vp, vp, ctypes.c_int]
     L.nr_sync.argtypes = [vp]
     L.nr_check_finite.argtypes = [vp]
     L.nr_build_maps.argtypes = [ctypes.c_int, ip, ctypes.c_int, ctypes.POINTER(ctypes.c_int32),
@@ -273,11 +276,12 @@ class Grid:
     def ssprk3_step(self, dt: float, nsteps: int = 1) -> None:
         _check(lib().nr_ssprk3_step(self.h, float(dt), int(nsteps)))
 
-    def hamiltonian(self, y=None, H=None):
+    def hamiltonian(self, y=None, H=None, norms: bool = True):
+        """(l2, linf) of H; norms=False skips the norms' device-to-host read (no synchronisation)."""
         l2, linf = ctypes.c_double(), ctypes.c_double()
         _check(lib().nr_hamiltonian(self.h, None if y is None else _ptr(y), None if H is None else _ptr(H),
-                                    ctypes.byref(l2), ctypes.byref(linf)))
-        return l2.value, linf.value
+                                    ctypes.byref(l2) if norms else None, ctypes.byref(linf) if norms else None))
+        return (l2.value, linf.value) if norms else None
 
     def psi4(self, out, y=None) -> None:
         """psi4 (2*T doubles on the device: re, im) of y (default: the grid-owned state)."""
@@ -291,11 +295,12 @@ class Grid:
                                    int(lmax), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
         return out[0::2] + 1j * out[1::2]
 
-    def momentum(self, y=None, M=None):
+    def momentum(self, y=None, M=None, norms: bool = True):
+        """(l2, linf) of |M|; norms=False skips the norms' device-to-host read (no synchronisation)."""
         l2, linf = ctypes.c_double(), ctypes.c_double()
         _check(lib().nr_momentum(self.h, None if y is None else _ptr(y), None if M is None else _ptr(M),
-                                 ctypes.byref(l2), ctypes.byref(linf)))
-        return l2.value, linf.value
+                                 ctypes.byref(l2) if norms else None, ctypes.byref(linf) if norms else None))
+        return (l2.value, linf.value) if norms else None
 
     def get_state(self, dst, to_host: bool) -> None:
         addr = dst.ctypes.data if isinstance(dst, np.ndarray) else (dst.data_ptr() if not isinstance(dst, int) else dst)
@@ -304,6 +309,15 @@ class Grid:
     def set_state(self, src, from_host: bool) -> None:
         addr = src.ctypes.data if isinstance(src, np.ndarray) else (src.data_ptr() if not isinstance(src, int) else src)
         _check(lib().nr_set_state(self.h, addr, int(bool(from_host))))
+
+    def get_state_compact(self, dst, to_host: bool) -> None:
+        """24 x info.n_state_points doubles: the state at the interior and pure outer points."""
+        addr = dst.ctypes.data if isinstance(dst, np.ndarray) else (dst.data_ptr() if not isinstance(dst, int) else dst)
+        _check(lib().nr_get_state_compact(self.h, addr, int(bool(to_host))))
+
+    def set_state_compact(self, src, from_host: bool) -> None:
+        addr = src.ctypes.data if isinstance(src, np.ndarray) else (src.data_ptr() if not isinstance(src, int) else src)
+        _check(lib().nr_set_state_compact(self.h, addr, int(bool(from_host))))
 
     def sync(self) -> None:
         _check(lib().nr_sync(self.h))

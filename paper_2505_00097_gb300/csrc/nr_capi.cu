@@ -333,7 +333,7 @@ void free_grid(nr_grid* g)
     if (g->exec) cudaGraphExecDestroy(g->exec);
     if (g->exec_ssp) cudaGraphExecDestroy(g->exec_ssp);
     void* ptrs[] = {g->y, g->ya, g->yb, g->acc, g->d1x, g->d1y, g->ax0, g->ax1, g->ax2, g->outer, g->inner, g->canon,
-                    g->finf, g->wspeed, g->partials, g->hres, g->flag, g->mxyz};
+                    g->finf, g->wspeed, g->partials, g->hres, g->flag, g->mxyz, g->stage};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (g->cap) cudaStreamDestroy(g->cap);
@@ -639,6 +639,7 @@ int nr_query(const nr_grid* g, nr_grid_info* info)
     // per stage: k_d1, k_rhs (interior + pure-outer points), then k_inner if it has entries
     info->launches_per_step = 8 + 3 * (g->n_inner_stencil > 0) + (g->n_inner > 0);
     info->launches_per_ssprk3_step = 6 + 2 * (g->n_inner_stencil > 0) + (g->n_inner > 0);
+    info->n_state_points = g->n_canon;
     return NR_OK;
 }
 
@@ -799,6 +800,41 @@ int nr_set_state(nr_grid* g, const double* src, int from_host)
     DeviceGuard dg(g->device);
     const size_t b = sizeof(double) * NR_NGF * g->geo.T;
     CUDA_OR_FAIL(cudaMemcpyAsync(g->y, src, b, from_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, g->stream));
+    if (from_host) CUDA_OR_FAIL(cudaStreamSynchronize(g->stream));
+    return NR_OK;
+}
+
+int nr_get_state_compact(nr_grid* g, double* dst, int to_host)
+{
+    if (!g || !dst) return fail(NR_EINVAL, "bad nr_get_state_compact arguments");
+    DeviceGuard dg(g->device);
+    const long nc = g->n_canon;
+    const size_t b = sizeof(double) * NR_NGF * nc;
+    if (!to_host) {
+        CUDA_OR_FAIL(launch_compact(g->K, g->canon, nc, g->y, dst, true, g->stream));
+        return NR_OK;
+    }
+    if (!g->stage) CUDA_OR_FAIL(cudaMalloc(&g->stage, b));
+    CUDA_OR_FAIL(launch_compact(g->K, g->canon, nc, g->y, g->stage, true, g->stream));
+    CUDA_OR_FAIL(cudaMemcpyAsync(dst, g->stage, b, cudaMemcpyDeviceToHost, g->stream));
+    CUDA_OR_FAIL(cudaStreamSynchronize(g->stream));
+    return NR_OK;
+}
+
+int nr_set_state_compact(nr_grid* g, const double* src, int from_host)
+{
+    if (!g || !src) return fail(NR_EINVAL, "bad nr_set_state_compact arguments");
+    DeviceGuard dg(g->device);
+    const long nc = g->n_canon;
+    const size_t b = sizeof(double) * NR_NGF * nc;
+    const double* from = src;
+    if (from_host) {
+        if (!g->stage) CUDA_OR_FAIL(cudaMalloc(&g->stage, b));
+        CUDA_OR_FAIL(cudaMemcpyAsync(g->stage, src, b, cudaMemcpyHostToDevice, g->stream));
+        from = g->stage;
+    }
+    CUDA_OR_FAIL(launch_compact(g->K, g->canon, nc, from, g->y, false, g->stream));
+    CUDA_OR_FAIL(launch_inner(g->K, g->inner, g->n_inner, g->y, g->stream));
     if (from_host) CUDA_OR_FAIL(cudaStreamSynchronize(g->stream));
     return NR_OK;
 }

@@ -86,6 +86,9 @@ cudaError_t launch_outer(const GridK& G, const OuterPt* pts, int npts, const dou
                          const double* yn, double* acc, const double* finf, const double* wspeed, Stage st,
                          cudaStream_t s);
 cudaError_t launch_inner(const GridK& G, const InnerPt* pts, int npts, double* y, cudaStream_t s);
+// gather (src: 24-gf set, dst: compact [gf][t]) or scatter (the reverse) over the canonical points
+cudaError_t launch_compact(const GridK& G, const int* canon, long nc, const double* src, double* dst, bool gather,
+                           cudaStream_t s);
 cudaError_t launch_bl(const GridK& G, const int* canon_idx, long ncanon, int np, const double* mxyz, double amp,
                       uint64_t seed, double* y, cudaStream_t s);
 cudaError_t launch_ham(const GridK& G, const double* y, double* H, double rmin, double rmax, double* partials,
@@ -132,6 +135,7 @@ struct nr_grid {
     double* hres = nullptr;
     int* flag = nullptr;
     double* mxyz = nullptr;
+    double* stage = nullptr;   // compact-state staging for host transfers (allocated on first use)
     int n_outer = 0, n_inner = 0, nparts = 0;
     // inner ghosts read by the stencils of an RK stage: the first n_inner_stencil
     // entries of inner (all of them unless the azimuth holds two points; then the

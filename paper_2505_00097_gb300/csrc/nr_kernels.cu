@@ -17,6 +17,8 @@
 //   k_finite  NaN/Inf guard on alpha and W
 #include <math.h>
 
+#include <algorithm>
+
 #include "bssn_point.cuh"
 #include "nr_geo.cuh"
 #include "nr_internal.h"
@@ -332,6 +334,35 @@ cudaError_t launch_inner(const GridK& G, const InnerPt* pts, int npts, double* y
     if (npts == 0) return cudaSuccess;
     dim3 grd((npts + 255) / 256, NGF);
     k_inner<<<grd, 256, 0, s>>>(G.T, pts, npts, y);
+    return cudaGetLastError();
+}
+
+// compact state: the 24 gridfunctions at the canonical points (interior and pure outer),
+// layout [gf][t]; one grid row per gridfunction
+__global__ void __launch_bounds__(256) k_gather(long T, const int* __restrict__ canon, long nc,
+                                                const double* __restrict__ y, double* __restrict__ out)
+{
+    const double* src = y + (long)blockIdx.y * T;
+    double* dst = out + (long)blockIdx.y * nc;
+    for (long t = (long)blockIdx.x * 256 + threadIdx.x; t < nc; t += (long)gridDim.x * 256) dst[t] = src[canon[t]];
+}
+
+__global__ void __launch_bounds__(256) k_scatter(long T, const int* __restrict__ canon, long nc,
+                                                 const double* __restrict__ in, double* __restrict__ y)
+{
+    const double* src = in + (long)blockIdx.y * nc;
+    double* dst = y + (long)blockIdx.y * T;
+    for (long t = (long)blockIdx.x * 256 + threadIdx.x; t < nc; t += (long)gridDim.x * 256) dst[canon[t]] = src[t];
+}
+
+cudaError_t launch_compact(const GridK& G, const int* canon, long nc, const double* src, double* dst, bool gather,
+                           cudaStream_t s)
+{
+    if (nc == 0) return cudaSuccess;
+    const long bx = std::min<long>((nc + 255) / 256, 4L * 152);
+    const dim3 grd((unsigned)bx, NGF);
+    if (gather) k_gather<<<grd, 256, 0, s>>>(G.T, canon, nc, src, dst);
+    else k_scatter<<<grd, 256, 0, s>>>(G.T, canon, nc, src, dst);
     return cudaGetLastError();
 }
 

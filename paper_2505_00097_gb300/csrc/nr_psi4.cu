@@ -396,6 +396,15 @@ int nr_psi4_modes(nr_grid* g, const double* y_dev, double Rext, int ntheta, int 
     for (int l = 2; l <= lmax; l++) nmodes += 2 * l + 1;
     std::vector<SpherePt> pts(nq);
     std::vector<double> wy(2L * nmodes * nq);
+    // w_q sqrt((2l+1)/4pi) d^l_{m,2}(theta) depends on the theta node only
+    std::vector<double> amp((size_t)ntheta * nmodes);
+    for (int it = 0; it < ntheta; it++) {
+        const double th = acos(x[it]), dw = w[it] * 2.0 * M_PI / nphi;
+        int md = 0;
+        for (int l = 2; l <= lmax; l++)
+            for (int m = -l; m <= l; m++, md++)
+                amp[(size_t)it * nmodes + md] = sqrt((2.0 * l + 1.0) / (4.0 * M_PI)) * wigner_d(l, m, 2, th) * dw;
+    }
     for (int it = 0; it < ntheta; it++)
         for (int jp = 0; jp < nphi; jp++) {
             const int q = it * nphi + jp;
@@ -424,13 +433,12 @@ int nr_psi4_modes(nr_grid* g, const double* y_dev, double Rext, int ntheta, int 
                 stride *= G.n[d];
             }
             pts[q].base = base;
-            const double dw = w[it] * 2.0 * M_PI / nphi;
             int md = 0;
             for (int l = 2; l <= lmax; l++)
                 for (int m = -l; m <= l; m++, md++) {
-                    const double amp = sqrt((2.0 * l + 1.0) / (4.0 * M_PI)) * wigner_d(l, m, 2, th) * dw;
-                    wy[2L * (md * (long)nq + q)] = amp * cos(m * ph);
-                    wy[2L * (md * (long)nq + q) + 1] = amp * sin(m * ph);
+                    const double a = amp[(size_t)it * nmodes + md];
+                    wy[2L * (md * (long)nq + q)] = a * cos(m * ph);
+                    wy[2L * (md * (long)nq + q) + 1] = a * sin(m * ph);
                 }
         }
     DevGuard dg(g->device);

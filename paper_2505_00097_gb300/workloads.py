@@ -55,7 +55,7 @@ def config_single_puncture() -> dict:
     """Single BL puncture M=1 at the origin, SinhSpherical AMPL=10 w=0.2, 64x16x2, 20 RK4 steps."""
     s = sinh_spherical((64, 16, 2))
     s.update(name="single_puncture_sinhsph_64x16x2", masses=(1.0,), positions=((0.0, 0.0, 0.0),),
-             perturb_amp=0.0, seed=0, steps=20, h_every=0)
+             perturb_amp=0.0, seed=0, steps=20, h_every=0, psi4_radius=5.0)
     return s
 
 
@@ -63,7 +63,7 @@ def config_headon() -> dict:
     """Head-on BL binary m=0.5+0.5 at z=+-0.5, SinhCylindrical rho,z in 300, 256x2x512, 2000 RK4 steps."""
     s = sinh_cylindrical((256, 2, 512))
     s.update(name="headon_sinhcyl_256x2x512", masses=(0.5, 0.5), positions=((0.0, 0.0, 0.5), (0.0, 0.0, -0.5)),
-             perturb_amp=0.0, seed=0, steps=2000, h_every=100)
+             perturb_amp=0.0, seed=0, steps=2000, h_every=100, psi4_radius=100.0)
     return s
 
 
@@ -82,7 +82,7 @@ def config_large3d() -> dict:
     """Single BL puncture + 1e-10 SplitMix64 perturbation of hDD, SinhSpherical 384x192x384, 200 RK4 steps."""
     s = sinh_spherical((384, 192, 384))
     s.update(name="vacuum3d_sinhsph_384x192x384", masses=(1.0,), positions=((0.0, 0.0, 0.0),),
-             perturb_amp=1e-10, seed=MASTER_SEED + 3, steps=200, h_every=0)
+             perturb_amp=1e-10, seed=MASTER_SEED + 3, steps=200, h_every=0, psi4_radius=5.0)
     return s
 
 

@@ -1,0 +1,106 @@
+"""Compact state transfer through the C ABI (nr_get_state_compact / nr_set_state_compact).
+
+Inner ghost points hold parity copies of canonical points (Sec. 3), so the state at
+the interior and pure outer points determines the whole padded array:
+* the compact array equals the full state at the canonical points, in flat order,
+  bit for bit (host and device variants);
+* uploading it into a fresh grid reproduces the full state bit for bit, and both
+  grids then evolve identically;
+* for arbitrary ghost values, the upload leaves the oracle's inner boundary
+  condition applied to the same canonical values.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle.oracle import Oracle  # noqa: E402
+from paper_2505_00097_gb300 import binding as B  # noqa: E402
+from paper_2505_00097_gb300 import build as BUILD  # noqa: E402
+from paper_2505_00097_gb300 import workloads as W  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    BUILD.build()
+    B.lib()
+
+
+SPECS = [
+    W.sinh_cylindrical((48, 2, 96), rho_max=20.0, z_max=20.0),
+    W.sinh_spherical((37, 11, 10)),
+    dict(W.sinh_cylindrical((33, 2, 70), rho_max=20.0, z_max=20.0), NG=5, ko_sigma=[0.3] * 17 + [0.99] * 7),
+]
+IDS = ["cyl2", "sph3d", "cyl2-o8"]
+
+
+def _canon(spec):
+    cls = B.build_maps(spec["coords"], spec["N"], spec.get("NG", 3))[2]
+    return np.nonzero(cls != 2)[0]
+
+
+@pytest.mark.parametrize("spec", SPECS, ids=IDS)
+def test_compact_round_trip_is_bit_exact(spec):
+    masses, pos = (0.6, 0.4), ((0.0, 0.0, 0.45), (0.0, 0.0, -0.55))
+    g = B.Grid(spec)
+    g.set_brill_lindquist(masses, pos, 1e-8, 5)
+    g.rk4_step(g.dt_cfl, 2)
+    T = g.T
+    canon = _canon(spec)
+    nc = g.info.n_state_points
+    assert nc == canon.size == g.interior + g.info.n_outer
+    full = np.empty(24 * T)
+    g.get_state(full, True)
+    comp = np.empty(24 * nc)
+    g.get_state_compact(comp, True)
+    assert np.array_equal(comp.reshape(24, nc), full.reshape(24, T)[:, canon])
+    dcomp = torch.empty(24 * nc, dtype=torch.float64, device=DEV)
+    g.get_state_compact(dcomp, False)
+    torch.cuda.synchronize()
+    assert np.array_equal(dcomp.cpu().numpy(), comp)
+
+    for from_host, src in ((True, comp), (False, dcomp)):
+        g2 = B.Grid(spec)
+        g2.set_state_compact(src, from_host)
+        back = np.empty(24 * T)
+        g2.get_state(back, True)
+        assert np.array_equal(back.view(np.uint64), full.view(np.uint64))
+        dt = g.dt_cfl
+        ga = B.Grid(spec)
+        ga.set_state(full, True)
+        ga.rk4_step(dt, 3)
+        g2.rk4_step(dt, 3)
+        a = np.empty(24 * T)
+        b = np.empty(24 * T)
+        ga.get_state(a, True)
+        g2.get_state(b, True)
+        assert np.array_equal(a.view(np.uint64), b.view(np.uint64))
+
+
+@pytest.mark.parametrize("spec", SPECS, ids=IDS)
+def test_upload_rebuilds_inner_ghosts_as_the_oracle(spec):
+    o = Oracle(spec)
+    y = W.random_state(o.n, seed=12, smooth=False)
+    canon = _canon(spec)
+    comp = np.ascontiguousarray(y.reshape(24, o.T)[:, canon]).reshape(-1)
+    o.inner_bc(y)
+    g = B.Grid(spec)
+    g.set_state_compact(comp, True)
+    got = np.empty(24 * o.T)
+    g.get_state(got, True)
+    assert np.array_equal(got, y)
+
+
+def test_compact_state_is_the_canonical_fraction_of_the_headon_grid():
+    spec = W.config_headon()
+    g = B.Grid(spec)
+    info = g.info
+    assert info.n_state_points == info.interior + info.n_outer
+    # 256 x 2 x 512 interior points with three ghost layers: a quarter of the padded array
+    assert 0.24 < info.n_state_points / info.T < 0.26
