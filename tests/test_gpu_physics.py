@@ -1,0 +1,82 @@
+"""Physics of the head-on collision of Sec. 4.1 through the whole GPU pipeline.
+
+The production scheme (8th order, SSPRK3, KO 0.3/0.99) evolves the head-on
+Brill-Lindquist data (bare masses 0.5 + 0.5, ADM mass M = 1) on the 256x2x512
+SinhCylindrical grid; nr_psi4_modes extracts C_20 on spheres of radius 30M and 40M.
+* The system is axisymmetric and has no twist, so psi4 is real: C_20 has no imaginary
+  part and the m != 0 and l = 3 modes are at round-off level.
+* psi4 falls off as 1/R: R |C_20| peaks at the same value on both spheres.
+* After the burst, the signal rings down at the fundamental l = 2 quasinormal mode of
+  the Schwarzschild remnant, M omega = 0.37367 - 0.08896 i (Leaver 1985).  A damped
+  sinusoid fitted over retarded times 40M..90M at R = 40M gives omega 0.366 and decay
+  rate 0.081 on this grid (measured). The tolerances (5 % and 20 %) leave room for
+  the grid's resolution and catch a wrong sign, factor or mode in the pipeline.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+scipy_opt = pytest.importorskip("scipy.optimize")
+
+from paper_2505_00097_gb300 import binding as B  # noqa: E402
+from paper_2505_00097_gb300 import build as BUILD  # noqa: E402
+from paper_2505_00097_gb300 import workloads as W  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+QNM_OMEGA, QNM_GAMMA = 0.37367, 0.08896
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    BUILD.build()
+    B.lib()
+
+
+def test_headon_ringdown_at_the_fundamental_quasinormal_mode():
+    spec = W.config_headon8()
+    g = B.Grid(spec)
+    g.set_brill_lindquist(spec["masses"], spec["positions"], 0.0, 0)
+    dt = g.dt_cfl
+    radii = (30.0, 40.0)
+    every = max(1, int(round(0.25 / dt)))
+    t_end = radii[-1] + 90.0
+    ts, modes = [], {R: [] for R in radii}
+    n = 0
+    while n * dt <= t_end:
+        t = n * dt
+        if n % every == 0 and t >= 25.0:
+            ts.append(t)
+            for R in radii:
+                modes[R].append(g.psi4_modes(R, 24, 48, 3))
+        g.ssprk3_step(dt, 1)
+        n += 1
+    g.check_finite()
+    ts = np.array(ts)
+    C = {R: np.array(v) for R, v in modes.items()}   # l = 2 (m = -2..2), l = 3 (m = -3..3)
+
+    for R in radii:
+        c20 = C[R][:, 2]
+        assert np.all(c20.imag == 0.0)
+        others = np.delete(C[R], [2], axis=1)
+        assert np.abs(others).max() <= 1e-8 * np.abs(c20).max()
+    peaks = [R * np.abs(C[R][:, 2]).max() for R in radii]
+    assert peaks[0] == pytest.approx(peaks[1], rel=0.05)
+
+    R = radii[-1]
+    u = ts - R
+    y = R * C[R][:, 2].real
+    m = (u >= 40.0) & (u <= 90.0)
+    assert m.sum() > 100
+
+    def ring(x, A, gam, om, ph):
+        return A * np.exp(-gam * (x - 40.0)) * np.cos(om * (x - 40.0) + ph)
+
+    p, _ = scipy_opt.curve_fit(ring, u[m], y[m], p0=[np.abs(y[m]).max(), 0.09, 0.37, 0.0], maxfev=20000)
+    omega, gamma = abs(p[2]), p[1]
+    resid = np.sqrt(np.mean((ring(u[m], *p) - y[m]) ** 2)) / np.abs(y[m]).max()
+    assert resid < 0.05, (omega, gamma, resid)
+    assert omega == pytest.approx(QNM_OMEGA, rel=0.05), (omega, gamma)
+    assert gamma == pytest.approx(QNM_GAMMA, rel=0.20), (omega, gamma)
