@@ -243,8 +243,23 @@ def cpu_baseline(spec: dict, seconds: float) -> dict:
             break
     el = time.perf_counter() - t0
     pts = math.prod(spec["N"])
-    return {"value": pts * (3 if ssp else 4) * steps / el, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
-            "sample": f"first {steps} {'SSPRK3' if ssp else 'RK4'} steps of {spec['name']} (full grid), {el:.1f} s"}
+    out = {"value": pts * (3 if ssp else 4) * steps / el, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
+           "sample": f"first {steps} {'SSPRK3' if ssp else 'RK4'} steps of {spec['name']} (full grid), {el:.1f} s"}
+    if pts <= 4_000_000:
+        # the diagnostics on the evolved state, one call each (wall ms on the same cores)
+        diag = {}
+        for name, fn in (("hamiltonian", lambda: o.hamiltonian(y)), ("momentum", lambda: o.momentum(y)),
+                         ("psi4", lambda: o.psi4(y))):
+            t0 = time.perf_counter()
+            r = fn()
+            diag[name + "_ms"] = 1e3 * (time.perf_counter() - t0)
+        R = spec.get("psi4_radius")
+        if R:
+            t0 = time.perf_counter()
+            o.psi4_modes(r[0], R, PSI4_NTHETA, PSI4_NPHI, PSI4_LMAX)
+            diag["psi4_modes_ms"] = 1e3 * (time.perf_counter() - t0)
+        out["diagnostics"] = diag
+    return out
 
 
 def run_reference(args, spec):
