@@ -355,7 +355,6 @@ __device__ __forceinline__ void metric_first(const PointIn& P, MetricPart& M)
     const double* y = P.y;
     const long T = P.T;
     const Geo& g = P.g;
-    const long* st = P.st;
     auto F = [&](int gf) { return y + (long)gf * T; };
     double* h = M.h;
     double* gi = M.gi;
@@ -1146,22 +1145,6 @@ template <int AX, int ORD>
 __device__ __forceinline__ void add_adv_ko(const double* y, long T, const long st[3], long ox, const double D[3],
                                            double sigma_metric, double sigma_gauge, double k[NGF])
 {
-    if constexpr (ORD == 8) {
-        double u[3];
-        bool fwd[3];
-#pragma unroll
-        for (int d = 0; d < 3; d++) {
-            const double v = ld(y + (long)(G_VET + d) * T);
-            u[d] = fabs(v) * D[d];
-            fwd[d] = v > 0.0;
-        }
-        AdvKoW8 Wm, Wg;
-        advko_weights8<AX>(u, fwd, D, sigma_metric, Wm);
-        advko_weights8<AX>(u, fwd, D, sigma_gauge, Wg);
-#pragma unroll
-        for (int g = 0; g < NGF; g++) k[g] = advko_apply8<AX>(y + (long)g * T, st, ox, g < G_VET ? Wm : Wg, k[g]);
-        return;
-    }
     double u[3];
     bool fwd[3];
 #pragma unroll
@@ -1170,11 +1153,19 @@ __device__ __forceinline__ void add_adv_ko(const double* y, long T, const long s
         u[d] = fabs(v) * D[d];
         fwd[d] = v > 0.0;
     }
-    AdvKoW Wm, Wg;
-    advko_weights<AX>(u, fwd, D, sigma_metric, Wm);
-    advko_weights<AX>(u, fwd, D, sigma_gauge, Wg);
+    if constexpr (ORD == 8) {
+        AdvKoW8 Wm, Wg;
+        advko_weights8<AX>(u, fwd, D, sigma_metric, Wm);
+        advko_weights8<AX>(u, fwd, D, sigma_gauge, Wg);
 #pragma unroll
-    for (int g = 0; g < NGF; g++) k[g] = advko_apply<AX>(y + (long)g * T, st, ox, g < G_VET ? Wm : Wg, k[g]);
+        for (int g = 0; g < NGF; g++) k[g] = advko_apply8<AX>(y + (long)g * T, st, ox, g < G_VET ? Wm : Wg, k[g]);
+    } else {
+        AdvKoW Wm, Wg;
+        advko_weights<AX>(u, fwd, D, sigma_metric, Wm);
+        advko_weights<AX>(u, fwd, D, sigma_gauge, Wg);
+#pragma unroll
+        for (int g = 0; g < NGF; g++) k[g] = advko_apply<AX>(y + (long)g * T, st, ox, g < G_VET ? Wm : Wg, k[g]);
+    }
 }
 
 }  // namespace nrk
