@@ -167,7 +167,9 @@ int build_maps_host(const HostGeom& G, std::vector<int32_t>& src, std::vector<in
                         p[0] = -p[0];
                         p[2] = -p[2];
                     }
-                    if (j1 < NG || j1 >= NG + G.N[1]) {  // th < 0 or th > pi: reflect, ph + pi
+                    // th < 0 or th > pi: reflect, ph + pi; repeated while the ghost layers are
+                    // deeper than N_th (each pair of reflections is a shift by 2 N_th, i.e. 2 pi)
+                    while (j1 < NG || j1 >= NG + G.N[1]) {
                         j1 = (j1 < NG) ? 2 * NG - 1 - j1 : 2 * (NG + G.N[1]) - 1 - j1;
                         j2 += Nph / 2;
                         half_turn = true;
@@ -288,10 +290,11 @@ int check_args(int coords, const int Nxx[3], const nr_params* p)
         if (!(p->ko_sigma[0] >= 0.0) || !(p->ko_sigma[17] >= 0.0))
             return fail(NR_EINVAL, "ko_sigma must be non-negative");
     }
+    const int pad = 2 * (p ? p->NG : 3);
     long T = 1;
     for (int d = 0; d < 3; d++) {
         if (Nxx[d] < 1 || Nxx[d] > (1 << 20)) return fail(NR_EINVAL, "Nxx[%d] = %d out of range", d, Nxx[d]);
-        T *= Nxx[d] + 6;
+        T *= Nxx[d] + pad;
     }
     if (T * 24 >= (1L << 40) || T >= (1L << 31)) return fail(NR_EINVAL, "grid too large (%ld points)", T);
     return NR_OK;

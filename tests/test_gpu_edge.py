@@ -1,0 +1,92 @@
+"""Degenerate grids and calls through the C ABI, against the oracle.
+
+* Grids with one to three cells along an axis, where the ghost layers are deeper than
+  the grid and the parity map wraps several times (Sec. 3): the right-hand side with
+  both boundary conditions (1e-12 per tensor) and a few steps of the integrator
+  (1e-10), at both orders, on the two-point-azimuth and the general kernels.
+* A step count of zero leaves the state untouched, bit for bit.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle.oracle import Oracle  # noqa: E402
+from paper_2505_00097_gb300 import binding as B  # noqa: E402
+from paper_2505_00097_gb300 import build as BUILD  # noqa: E402
+from paper_2505_00097_gb300 import workloads as W  # noqa: E402
+from tests._common import assert_close  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+KO8 = [0.3] * 17 + [0.99] * 7
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    BUILD.build()
+    B.lib()
+
+
+TINY = [
+    W.sinh_spherical((1, 2, 2)),                                          # two-point azimuth
+    W.sinh_spherical((3, 1, 4)),                                          # general, one theta cell
+    W.spherical((2, 3, 2)),
+    W.sinh_cylindrical((1, 2, 1), rho_max=3.0, z_max=3.0),                # one cell in rho and z
+    W.sinh_cylindrical((2, 4, 3), rho_max=3.0, z_max=3.0),                # general
+    dict(W.sinh_spherical((3, 3, 4)), NG=5, ko_sigma=KO8),
+    dict(W.sinh_spherical((1, 2, 2)), NG=5, ko_sigma=KO8),
+    dict(W.sinh_cylindrical((1, 2, 1), rho_max=3.0, z_max=3.0), NG=5, ko_sigma=KO8),
+]
+IDS = ["sph122", "sph314", "plain232", "cyl121", "cyl243", "sph334-o8", "sph122-o8", "cyl121-o8"]
+
+
+@pytest.mark.parametrize("spec", TINY, ids=IDS)
+def test_rhs_and_boundaries_on_tiny_grids(spec):
+    o = Oracle(spec)
+    g = B.Grid(spec)
+    y = W.random_state(o.n, seed=21, smooth=True)
+    o.inner_bc(y)
+    ref = o.full_rhs(y)
+    yd = torch.from_numpy(y).to(DEV)
+    out = torch.zeros_like(yd)
+    g.rhs(yd, out)
+    g.apply_bcs(yd, out)
+    torch.cuda.synchronize()
+    assert_close(out.cpu().numpy(), ref, o.T, 1e-12, what="tiny-grid rhs with boundaries")
+
+
+@pytest.mark.parametrize("spec", TINY, ids=IDS)
+def test_steps_on_tiny_grids(spec):
+    o = Oracle(spec)
+    masses, pos = (0.6, 0.4), ((0.0, 0.0, 0.45), (0.0, 0.0, -0.55))
+    y = o.brill_lindquist(masses, pos, 1e-8, seed=4)
+    g = B.Grid(spec)
+    g.set_state(y, True)
+    dt = o.dt()
+    if spec["NG"] == 5:
+        o.ssprk3(y, dt, 5)
+        g.ssprk3_step(dt, 5)
+    else:
+        o.rk4(y, dt, 5)
+        g.rk4_step(dt, 5)
+    got = np.empty_like(y)
+    g.get_state(got, True)
+    assert np.all(np.isfinite(got))
+    assert_close(got, y, o.T, 1e-10, what="tiny-grid steps")
+
+
+def test_zero_steps_leave_the_state_untouched():
+    spec = W.sinh_cylindrical((16, 2, 24), rho_max=20.0, z_max=20.0)
+    g = B.Grid(spec)
+    g.set_brill_lindquist((1.0,), ((0.0, 0.0, 0.0),), 1e-8, 3)
+    a = np.empty(24 * g.T)
+    g.get_state(a, True)
+    g.rk4_step(g.dt_cfl, 0)
+    g.ssprk3_step(g.dt_cfl, 0)
+    b = np.empty_like(a)
+    g.get_state(b, True)
+    assert np.array_equal(a.view(np.uint64), b.view(np.uint64))

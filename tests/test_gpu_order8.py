@@ -138,6 +138,33 @@ def test_constraints_parity_8th_order(spec):
     assert ml2g == pytest.approx(ml2, rel=1e-10) and mlinfg == pytest.approx(mlinf, rel=1e-10)
 
 
+def test_headon8_full_size_parity_in_bench_configuration():
+    """The production-scheme head-on workload at full size (256x2x512, NG = 5): one RHS
+    evaluation of a seeded random state (1e-12), then 5 SSPRK3 steps of its Brill-Lindquist data
+    in the launch configuration the benchmark times (graph-replayed nr_ssprk3_step), compared
+    with the oracle at every point (1e-10)."""
+    spec = W.config_headon8()
+    o = Oracle(spec)
+    g = B.Grid(spec)
+    yr = W.random_state(o.n, seed=321, smooth=True)
+    o.inner_bc(yr)
+    yd = _dev(yr)
+    out = torch.zeros_like(yd)
+    g.rhs(yd, out)
+    torch.cuda.synchronize()
+    assert_close(_host(out), o.rhs(yr), o.T, 1e-12, mask=o.interior_mask(), what="head-on 8th-order RHS")
+    del yd, out
+    y = o.brill_lindquist(spec["masses"], spec["positions"])
+    g.set_brill_lindquist(spec["masses"], spec["positions"])
+    dt = o.dt()
+    assert g.dt_cfl == pytest.approx(dt, rel=1e-15)
+    o.ssprk3(y, dt, 5)
+    g.ssprk3_step(dt, 5)
+    got = np.empty_like(y)
+    g.get_state(got, True)
+    assert_close(got, y, o.T, 1e-10, what="head-on 256x2x512 after 5 SSPRK3 steps, 8th order")
+
+
 def test_batched_mode_takes_the_4th_order_scheme_only():
     g = B.Grid(SPECS[2])
     with pytest.raises(B.NrError, match="4th-order"):

@@ -69,6 +69,10 @@ MAP_SPECS = [
     # five ghost layers (8th-order scheme)
     dict(W.sinh_spherical((12, 8, 2)), NG=5), dict(W.sinh_spherical((7, 5, 6)), NG=5),
     dict(W.sinh_cylindrical((9, 2, 11)), NG=5), dict(W.sinh_cylindrical((6, 6, 4), w=0.4), NG=5),
+    # fewer theta cells than ghost layers: the deepest theta ghosts need repeated reflections
+    W.sinh_spherical((1, 2, 2)), W.sinh_spherical((3, 1, 4)), W.spherical((2, 3, 2)),
+    dict(W.sinh_spherical((3, 3, 4)), NG=5), dict(W.sinh_spherical((1, 1, 2)), NG=5),
+    W.sinh_cylindrical((1, 2, 1)), dict(W.sinh_cylindrical((1, 4, 1)), NG=5),
 ]
 
 

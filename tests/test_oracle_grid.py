@@ -101,6 +101,10 @@ TINY = [
     W.spherical((4, 5, 6)),
     W.sinh_cylindrical((6, 2, 5), rho_max=3.0, z_max=3.0),
     W.sinh_cylindrical((4, 6, 4), rho_max=3.0, z_max=2.0, w=0.4),
+    # one or two cells per axis: ghost layers deeper than the grid wrap several times
+    W.sinh_spherical((1, 2, 2)),
+    W.sinh_spherical((3, 1, 4)),
+    W.sinh_cylindrical((1, 2, 1), rho_max=3.0, z_max=3.0),
 ]
 
 
