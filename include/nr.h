@@ -8,14 +8,16 @@
  *     Abar_RHS_orig_final, W_RHS_orig_final, K_RHS_orig_final,
  *     Lambda_RHS_orig_final), the conformal Ricci tensor, 1+log slicing and
  *     the Gamma-driver shift (Eqs. gauge_eqns, damping_eta_final), the
- *     Hamiltonian constraint (Eq. Hconstraint);
+ *     Hamiltonian and momentum constraints (Eqs. Hconstraint, Mconstraint);
  *   - Sec. 2.2: tensor rescaling by the scale factors S_i;
- *   - Sec. 3: cell-centred logically rectangular grids, 4th-order centred
- *     finite differences with upwinded shift advection and N_G = 3 ghost
- *     layers, outer (radiation) and inner (parity) boundary points, and the
- *     boundary order outer -> inner after every time-integrator substage;
+ *   - Sec. 3: cell-centred logically rectangular grids, centred finite
+ *     differences of order N_FD with upwinded shift advection and
+ *     N_G = N_FD/2 + 1 ghost layers (N_FD = 4: N_G = 3; N_FD = 8: N_G = 5),
+ *     outer (radiation) and inner (parity) boundary points, and the boundary
+ *     order outer -> inner after every time-integrator substage;
  *   - Sec. 4.1: the sinh coordinate map x'(x) = x_max sinh(x/w)/sinh(1/w),
- *     Kreiss-Oliger dissipation and the CFL factor;
+ *     Kreiss-Oliger dissipation, the CFL factor, the production scheme
+ *     (8th order, SSPRK3) and the psi4 waveforms;
  *   - Sec. 4.2.1: method-of-lines RK4.
  *
  * Conventions (all entry points):

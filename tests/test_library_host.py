@@ -135,3 +135,48 @@ def test_ghost_layers_select_the_scheme():
     with pytest.raises(B.NrError, match="4th-order"):
         srv.submit(spec, 1.0)
     srv.close()
+
+
+# the C example of the user guide: create a grid, set Brill-Lindquist data, step, read H
+C_EXAMPLE = r"""
+#include <stdio.h>
+#include "nr.h"
+
+int main(void)
+{
+    nr_params p;
+    nr_grid* g = NULL;
+    const int N[3] = {256, 2, 512};
+    const double mass[2] = {0.5, 0.5}, xyz[6] = {0.0, 0.0, 0.5, 0.0, 0.0, -0.5};
+    nr_grid_info info;
+    double l2 = 0.0, linf = 0.0;
+    if (nr_params_default(NR_SINH_CYLINDRICAL, &p) != NR_OK) return 1;
+    if (nr_grid_create(NR_SINH_CYLINDRICAL, N, &p, &g) != NR_OK) {
+        fprintf(stderr, "%s\n", nr_last_error());
+        return 1;
+    }
+    nr_query(g, &info);
+    nr_set_brill_lindquist(g, 2, mass, xyz, 0.0, 0);
+    nr_rk4_step(g, info.dt_cfl, 100);
+    nr_hamiltonian(g, NULL, NULL, &l2, &linf);
+    printf("t = %g  |H|_2 = %g\n", 100 * info.dt_cfl, l2);
+    nr_grid_destroy(g);
+    return 0;
+}
+"""
+
+
+def test_header_is_plain_c_and_the_example_links(tmp_path):
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not found")
+    src = tmp_path / "example.c"
+    src.write_text(C_EXAMPLE)
+    inc = os.path.join(ROOT, "include")
+    lib = B.library_path()
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", inc, str(src),
+                        "-o", str(tmp_path / "example"), lib, "-Wl,-rpath," + os.path.dirname(lib)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
