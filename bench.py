@@ -319,6 +319,8 @@ def run_ours(args, spec, world, rank, local):
     substeps = 3 if ssp else 4
     step = g.ssprk3_step if ssp else g.rk4_step
     per_step = g.info.launches_per_ssprk3_step if ssp else g.info.launches_per_step
+    # k_ham + k_ham_reduce, after a step also the azimuthal ghost refresh (if the grid has one)
+    per_h = 2 + int(g.info.n_inner > g.info.n_inner_stencil)
 
     def run_steps(n, start):
         launches = 0
@@ -327,7 +329,7 @@ def run_ours(args, spec, world, rank, local):
             launches += per_step
             if h_every and (start + s + 1) % h_every == 0:
                 g.hamiltonian()
-                launches += 2
+                launches += per_h
         return launches
 
     # warm-up (graph capture happens on the first step)

@@ -112,7 +112,8 @@ typedef struct {
     size_t device_bytes; /* device memory held by the grid */
     int64_t n_inner_stencil; /* inner ghosts the RK stages before the last copy (all, unless the
                                 azimuth holds two points: then its ghosts are copied in stage 4 only) */
-    int launches_per_step;   /* kernel launches of one nr_rk4_step */
+    int launches_per_step;   /* kernel launches of one nr_rk4_step (the on-demand ghost refresh
+                                described at nr_rk4_step is one more, outside the step) */
     int launches_per_ssprk3_step; /* kernel launches of one nr_ssprk3_step */
     int64_t n_state_points;  /* interior + pure outer ghost points: the points of a compact state */
 } nr_grid_info;
@@ -164,7 +165,13 @@ int nr_apply_inner_bcs(nr_grid* grid, double* gfs_dev);
  * epilogue, the radiation condition at outer ghosts, parity copies at inner
  * ghosts, and (enforce_detgb) det(gammabar) enforcement.  The launches of
  * one step (nr_grid_info.launches_per_step) are captured once in a CUDA graph
- * (re-captured when dt changes) and replayed.  dt > 0, nsteps >= 0. */
+ * (re-captured when dt changes) and replayed.  dt > 0, nsteps >= 0.
+ * With a two-point azimuth the steps copy only the inner ghosts the stencils
+ * read; the azimuthal ghost copies of the state are refreshed (one launch, on
+ * params.stream) by the next call that returns or reads them: nr_get_state,
+ * nr_check_finite, and nr_hamiltonian, nr_momentum, nr_psi4 and nr_psi4_modes
+ * on the grid-owned state.  Results are the same as if every step had copied
+ * them. */
 int nr_rk4_step(nr_grid* grid, double dt, int nsteps);
 
 /* nsteps steps of SSPRK3 (Gottlieb-Shu-Tadmor; the integrator of the paper's
@@ -173,7 +180,8 @@ int nr_rk4_step(nr_grid* grid, double dt, int nsteps);
  *   y_{n+1} = 1/3 y + 2/3 (y2 + dt k(y2)),
  * each k with the boundary conditions of Sec. 3 and each stage followed by
  * det(gammabar) enforcement when enforce_detgb is set.  Three RHS evaluations
- * per step, captured in a CUDA graph like nr_rk4_step.  dt > 0, nsteps >= 0. */
+ * per step, captured in a CUDA graph like nr_rk4_step, with the same
+ * on-demand refresh of azimuthal ghosts.  dt > 0, nsteps >= 0. */
 int nr_ssprk3_step(nr_grid* grid, double dt, int nsteps);
 
 /* Hamiltonian constraint (Eq. Hconstraint) at interior points of y_dev (NULL:

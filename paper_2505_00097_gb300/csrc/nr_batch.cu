@@ -313,6 +313,8 @@ int nr_batch_rk4_step(nr_batch* b, const double* dts, int nsteps)
         cudaError_t e = cudaGraphLaunch(b->exec, b->stream);
         if (e != cudaSuccess) return nrk_fail(NR_ECUDA, "graph launch: %s", cudaGetErrorString(e));
     }
+    // the last stage copies every inner ghost of every grid
+    for (nr_grid* g : b->grids) g->ghosts_stale = false;
     return NR_OK;
 }
 

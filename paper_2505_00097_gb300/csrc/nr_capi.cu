@@ -375,12 +375,13 @@ int enqueue_rk4(nr_grid* g, cudaStream_t s, double dt)
     Stage s3{MODE_STAGE23, enf, dt, dt / 3.0};
     Stage s4{MODE_STAGE4, enf, 0.0, dt / 6.0};
     int rc;
-    // the intermediate states need only the ghosts the stencils read; y_{n+1} gets all
+    // every stage copies only the ghosts the stencils read; the rest of y_{n+1}'s are
+    // refreshed on demand (refresh_ghosts)
     const int ns = g->n_inner_stencil;
     if ((rc = enqueue_stage(g, s, g->y, g->ya, g->y, g->acc, s1, ns))) return rc;
     if ((rc = enqueue_stage(g, s, g->ya, g->yb, g->y, g->acc, s2, ns))) return rc;
     if ((rc = enqueue_stage(g, s, g->yb, g->ya, g->y, g->acc, s3, ns))) return rc;
-    if ((rc = enqueue_stage(g, s, g->ya, g->y, nullptr, g->acc, s4, g->n_inner))) return rc;
+    if ((rc = enqueue_stage(g, s, g->ya, g->y, nullptr, g->acc, s4, ns))) return rc;
     return NR_OK;
 }
 
@@ -396,7 +397,7 @@ int enqueue_ssprk3(nr_grid* g, cudaStream_t s, double dt)
     const int ns = g->n_inner_stencil;
     if ((rc = enqueue_stage(g, s, g->y, g->ya, g->y, nullptr, s1, ns))) return rc;
     if ((rc = enqueue_stage(g, s, g->ya, g->yb, g->y, nullptr, s2, ns))) return rc;
-    if ((rc = enqueue_stage(g, s, g->yb, g->y, g->y, nullptr, s3, g->n_inner))) return rc;
+    if ((rc = enqueue_stage(g, s, g->yb, g->y, g->y, nullptr, s3, ns))) return rc;
     return NR_OK;
 }
 
@@ -639,9 +640,10 @@ int nr_query(const nr_grid* g, nr_grid_info* info)
     info->dt_cfl = g->dt_cfl;
     info->device_bytes = g->bytes;
     info->n_inner_stencil = g->n_inner_stencil;
-    // per stage: k_d1, k_rhs (interior + pure-outer points), then k_inner if it has entries
-    info->launches_per_step = 8 + 3 * (g->n_inner_stencil > 0) + (g->n_inner > 0);
-    info->launches_per_ssprk3_step = 6 + 2 * (g->n_inner_stencil > 0) + (g->n_inner > 0);
+    // per stage: k_d1, k_rhs (interior + pure-outer points), then k_inner over the ghosts the
+    // stencils read, if any (the rest are refreshed on demand, one launch)
+    info->launches_per_step = 8 + 4 * (g->n_inner_stencil > 0);
+    info->launches_per_ssprk3_step = 6 + 3 * (g->n_inner_stencil > 0);
     info->n_state_points = g->n_canon;
     return NR_OK;
 }
@@ -670,6 +672,7 @@ int nr_set_brill_lindquist(nr_grid* g, int npunct, const double* mass, const dou
     CUDA_OR_FAIL(cudaMemsetAsync(g->y, 0, sizeof(double) * NR_NGF * g->geo.T, g->stream));
     CUDA_OR_FAIL(launch_bl(g->K, g->canon, g->n_canon, npunct, g->mxyz, perturb_amp, seed, g->y, g->stream));
     CUDA_OR_FAIL(launch_inner(g->K, g->inner, g->n_inner, g->y, g->stream));
+    g->ghosts_stale = false;
     // the host array m must stay valid until the copy is done
     CUDA_OR_FAIL(cudaStreamSynchronize(g->stream));
     return NR_OK;
@@ -725,6 +728,7 @@ int nr_rk4_step(nr_grid* g, double dt, int nsteps)
         g->graph_dt = dt;
     }
     for (int n = 0; n < nsteps; n++) CUDA_OR_FAIL(cudaGraphLaunch(g->exec, g->stream));
+    g->ghosts_stale = g->n_inner > g->n_inner_stencil;
     return NR_OK;
 }
 
@@ -750,6 +754,7 @@ int nr_ssprk3_step(nr_grid* g, double dt, int nsteps)
         g->graph_dt_ssp = dt;
     }
     for (int n = 0; n < nsteps; n++) CUDA_OR_FAIL(cudaGraphLaunch(g->exec_ssp, g->stream));
+    g->ghosts_stale = g->n_inner > g->n_inner_stencil;
     return NR_OK;
 }
 
@@ -757,6 +762,7 @@ int nr_hamiltonian(nr_grid* g, const double* y_dev, double* H_dev, double* l2_ou
 {
     if (!g) return fail(NR_EINVAL, "grid is NULL");
     DeviceGuard dg(g->device);
+    if (!y_dev) CUDA_OR_FAIL(refresh_ghosts(g));
     const double* y = y_dev ? y_dev : g->y;
     if (H_dev) CUDA_OR_FAIL(cudaMemsetAsync(H_dev, 0, sizeof(double) * g->geo.T, g->stream));
     CUDA_OR_FAIL(launch_ham(g->K, y, H_dev, g->P.h_rmin, g->P.h_rmax, g->partials, g->nparts, g->hres, g->stream));
@@ -774,6 +780,7 @@ int nr_momentum(nr_grid* g, const double* y_dev, double* M_dev, double* l2_out, 
 {
     if (!g) return fail(NR_EINVAL, "grid is NULL");
     DeviceGuard dg(g->device);
+    if (!y_dev) CUDA_OR_FAIL(refresh_ghosts(g));
     const double* y = y_dev ? y_dev : g->y;
     if (M_dev) CUDA_OR_FAIL(cudaMemsetAsync(M_dev, 0, sizeof(double) * 3 * g->geo.T, g->stream));
     CUDA_OR_FAIL(launch_mom(g->K, y, M_dev, g->P.h_rmin, g->P.h_rmax, g->partials, g->nparts, g->hres, g->stream));
@@ -792,6 +799,7 @@ int nr_get_state(nr_grid* g, double* dst, int to_host)
     if (!g || !dst) return fail(NR_EINVAL, "bad nr_get_state arguments");
     DeviceGuard dg(g->device);
     const size_t b = sizeof(double) * NR_NGF * g->geo.T;
+    CUDA_OR_FAIL(refresh_ghosts(g));
     CUDA_OR_FAIL(cudaMemcpyAsync(dst, g->y, b, to_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, g->stream));
     if (to_host) CUDA_OR_FAIL(cudaStreamSynchronize(g->stream));
     return NR_OK;
@@ -802,6 +810,7 @@ int nr_set_state(nr_grid* g, const double* src, int from_host)
     if (!g || !src) return fail(NR_EINVAL, "bad nr_set_state arguments");
     DeviceGuard dg(g->device);
     const size_t b = sizeof(double) * NR_NGF * g->geo.T;
+    g->ghosts_stale = false;
     CUDA_OR_FAIL(cudaMemcpyAsync(g->y, src, b, from_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, g->stream));
     if (from_host) CUDA_OR_FAIL(cudaStreamSynchronize(g->stream));
     return NR_OK;
@@ -838,6 +847,7 @@ int nr_set_state_compact(nr_grid* g, const double* src, int from_host)
     }
     CUDA_OR_FAIL(launch_compact(g->K, g->canon, nc, from, g->y, false, g->stream));
     CUDA_OR_FAIL(launch_inner(g->K, g->inner, g->n_inner, g->y, g->stream));
+    g->ghosts_stale = false;
     if (from_host) CUDA_OR_FAIL(cudaStreamSynchronize(g->stream));
     return NR_OK;
 }
@@ -855,6 +865,7 @@ int nr_check_finite(nr_grid* g)
     if (!g) return fail(NR_EINVAL, "grid is NULL");
     DeviceGuard dg(g->device);
     int h = 0;
+    CUDA_OR_FAIL(refresh_ghosts(g));
     CUDA_OR_FAIL(cudaMemsetAsync(g->flag, 0, sizeof(int), g->stream));
     CUDA_OR_FAIL(launch_finite(g->K, g->y, g->flag, g->stream));
     CUDA_OR_FAIL(cudaMemcpyAsync(&h, g->flag, sizeof(int), cudaMemcpyDeviceToHost, g->stream));

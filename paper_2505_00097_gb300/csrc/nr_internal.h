@@ -141,6 +141,9 @@ struct nr_grid {
     // entries of inner (all of them unless the azimuth holds two points; then the
     // azimuthal ghosts, read by nothing within a step, are copied in stage 4 only)
     int n_inner_stencil = 0;
+    // the azimuthal ghosts of the grid-owned state (entries n_inner_stencil.. of inner) lag
+    // behind after nr_rk4_step / nr_ssprk3_step; refresh_ghosts copies them before any use
+    bool ghosts_stale = false;
     long n_canon = 0;
     size_t bytes = 0;
     double dt_cfl = 0.0;
@@ -154,4 +157,14 @@ struct nr_grid {
     cudaGraphExec_t exec_ssp = nullptr;   // SSPRK3 step
     double graph_dt_ssp = 0.0;
 };
+
+// the parity copies of the grid-owned state that the integrators leave stale (azimuthal
+// ghosts of a two-point azimuth, read by no stencil of a step); stream-ordered
+inline cudaError_t refresh_ghosts(nr_grid* g)
+{
+    if (!g->ghosts_stale) return cudaSuccess;
+    g->ghosts_stale = false;
+    return nrk::launch_inner(g->K, g->inner + g->n_inner_stencil, g->n_inner - g->n_inner_stencil, g->y, g->stream);
+}
+
 

@@ -377,6 +377,7 @@ int nr_psi4(nr_grid* g, const double* y_dev, double* psi4_dev)
 {
     if (!g || !psi4_dev) return nrk_fail(NR_EINVAL, "bad nr_psi4 arguments");
     DevGuard dg(g->device);
+    if (!y_dev) CUDA_TRY(refresh_ghosts(g));
     CUDA_TRY(cudaMemsetAsync(psi4_dev, 0, sizeof(double) * 2 * g->geo.T, g->stream));
     CUDA_TRY(launch_psi4(g, y_dev ? y_dev : g->y, psi4_dev, g->stream));
     return NR_OK;
@@ -442,6 +443,7 @@ int nr_psi4_modes(nr_grid* g, const double* y_dev, double Rext, int ntheta, int 
                 }
         }
     DevGuard dg(g->device);
+    if (!y_dev) CUDA_TRY(refresh_ghosts(g));
     double *psi4 = nullptr, *samples = nullptr, *dwy = nullptr, *dout = nullptr;
     SpherePt* dpts = nullptr;
     cudaError_t e = cudaMalloc(&psi4, sizeof(double) * 2 * G.T);

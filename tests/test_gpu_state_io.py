@@ -104,3 +104,38 @@ def test_compact_state_is_the_canonical_fraction_of_the_headon_grid():
     assert info.n_state_points == info.interior + info.n_outer
     # 256 x 2 x 512 interior points with three ghost layers: a quarter of the padded array
     assert 0.24 < info.n_state_points / info.T < 0.26
+
+
+def test_stale_azimuthal_ghosts_are_refreshed_before_use():
+    """With a two-point azimuth the integrators leave the azimuthal ghost copies of the state
+    stale; the constraints and psi4 of the grid-owned state, called right after the steps, must
+    see the refreshed copies -- the same values as the explicit full state."""
+    spec = W.sinh_cylindrical((48, 2, 96), rho_max=20.0, z_max=20.0)
+    g = B.Grid(spec)
+    assert g.info.n_inner > g.info.n_inner_stencil
+    g.set_brill_lindquist((0.6, 0.4), ((0.0, 0.0, 0.45), (0.0, 0.0, -0.55)), 1e-8, 5)
+    g.rk4_step(g.dt_cfl, 5)
+    T = g.T
+    H_own = torch.zeros(T, dtype=torch.float64, device=DEV)
+    n_own = g.hamiltonian(None, H_own)
+    M_own = torch.zeros(3 * T, dtype=torch.float64, device=DEV)
+    m_own = g.momentum(None, M_own)
+    p_own = torch.zeros(2 * T, dtype=torch.float64, device=DEV)
+    g.psi4(p_own)
+    y = torch.empty(24 * T, dtype=torch.float64, device=DEV)
+    g.get_state(y, False)
+    H = torch.zeros_like(H_own)
+    M = torch.zeros_like(M_own)
+    p = torch.zeros_like(p_own)
+    assert g.hamiltonian(y, H) == n_own
+    assert g.momentum(y, M) == m_own
+    g.psi4(p, y)
+    torch.cuda.synchronize()
+    assert torch.equal(H, H_own) and torch.equal(M, M_own) and torch.equal(p, p_own)
+    # the refreshed ghosts are exact parity copies
+    src, par, cls = B.build_maps(spec["coords"], spec["N"], 3)
+    yh = y.cpu().numpy().reshape(24, T)
+    gh = np.nonzero(cls == 2)[0]
+    types = [4, 5, 6, 7, 8, 9, 4, 5, 6, 7, 8, 9, 0, 0, 1, 2, 3, 1, 2, 3, 1, 2, 3, 0]
+    for gf in range(24):
+        assert np.array_equal(yh[gf, gh], par[gh, types[gf]] * yh[gf, src[gh]])
