@@ -11,8 +11,25 @@ namespace nrk {
 
 // det(delta_ij + h_ij) := 1 (Lagrangian choice of Sec. 2.1), in place, in
 // terms of the deviation h so that small h keeps its relative precision:
+// f(x) = (1 + x)^(-1/3) - 1.  After every substage |x| = |det - 1| is small: there the
+// binomial series to x^6 (C(-1/3, k): -1/3, 2/9, -14/81, 35/243, -91/729, 728/6561) in
+// Horner form; for |x| <= 2^-10 the first omitted term, |C(-1/3, 7)| x^7 ~ 0.1 x^7, is below
+// 3e-19 |f|, far under an ulp.  Elsewhere f = expm1(-log1p(x)/3).  f(0) = 0 exactly.
+__device__ __forceinline__ double rcbrt1p_m1(double x)
+{
+    if (fabs(x) <= 0x1p-10) {
+        double p = fma(728.0 / 6561.0, x, -91.0 / 729.0);
+        p = fma(p, x, 35.0 / 243.0);
+        p = fma(p, x, -14.0 / 81.0);
+        p = fma(p, x, 2.0 / 9.0);
+        p = fma(p, x, -1.0 / 3.0);
+        return p * x;
+    }
+    return expm1(log1p(x) * (-1.0 / 3.0));
+}
+
 // det(I + h) - 1 = tr h + (sum of principal 2x2 minors of h) + det h,
-// f1 = det^(-1/3) - 1 = expm1(-log1p(det - 1)/3), h <- h + f1 (delta + h).
+// f1 = det^(-1/3) - 1, h <- h + f1 (delta + h).
 __device__ __forceinline__ void enforce_det(double* v)
 {
     const double m2 = fma(v[0], v[3], fma(v[0], v[5], fma(v[3], v[5], -fma(v[1], v[1], fma(v[2], v[2], v[4] * v[4])))));
@@ -21,7 +38,7 @@ __device__ __forceinline__ void enforce_det(double* v)
     const double c2 = fma(v[1], v[4], -v[2] * v[3]);
     const double d3 = fma(v[0], c0, fma(v[1], c1, v[2] * c2));
     const double dm1 = (v[0] + v[3] + v[5]) + (m2 + d3);
-    const double f1 = expm1(log1p(dm1) * (-1.0 / 3.0));
+    const double f1 = rcbrt1p_m1(dm1);
     v[0] = fma(f1, v[0], v[0] + f1);
     v[1] = fma(f1, v[1], v[1]);
     v[2] = fma(f1, v[2], v[2]);

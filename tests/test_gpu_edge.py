@@ -90,3 +90,42 @@ def test_zero_steps_leave_the_state_untouched():
     b = np.empty_like(a)
     g.get_state(b, True)
     assert np.array_equal(a.view(np.uint64), b.view(np.uint64))
+
+
+def test_det_enforcement_isolated_by_a_vanishing_step():
+    """det(gammabar) = det(gammahat) enforcement (after every substage) on its own: with
+    dt = 1e-300 every stage input equals y bit for bit, so one RK4 step returns the enforced
+    state.  h is random with det(1 + h) - 1 from 1e-8 to 5e-3, covering both evaluations of
+    (1 + x)^(-1/3) - 1 in the kernel; the result agrees with the oracle's expm1/log1p form to
+    round-off and has det(1 + h) = 1 to round-off."""
+    spec = W.sinh_cylindrical((16, 2, 24), rho_max=20.0, z_max=20.0)
+    o = Oracle(spec)
+    T = o.T
+    rng = np.random.default_rng(77)
+    y = o.zeros()
+    eps = 10.0 ** rng.uniform(-8.0, -2.3, size=T)
+    for s in range(6):
+        y[s * T:(s + 1) * T] = eps * rng.uniform(-1.0, 1.0, size=T)
+    y[12 * T:13 * T] = 1.0
+    y[23 * T:24 * T] = 1.0
+    o.inner_bc(y)
+    g = B.Grid(spec)
+    g.set_state(y, True)
+    g.rk4_step(1e-300, 1)
+    got = np.empty_like(y)
+    g.get_state(got, True)
+    ref = y.copy()
+    o.enforce_detgb(ref)
+    m = o.interior_mask()
+    h = got[:6 * T].reshape(6, T)[:, m]
+    href = ref[:6 * T].reshape(6, T)[:, m]
+
+    def det(hh):
+        h00, h01, h02, h11, h12, h22 = hh
+        return ((1 + h00) * ((1 + h11) * (1 + h22) - h12 * h12) - h01 * (h01 * (1 + h22) - h12 * h02)
+                + h02 * (h01 * h12 - (1 + h11) * h02))
+
+    x = np.abs(det(y[:6 * T].reshape(6, T)[:, m]) - 1.0)
+    assert x.min() < 1e-6 and x.max() > 2.0 ** -10 and (x > 2.0 ** -10).sum() > 10   # both branches ran
+    assert np.abs(h - href).max() <= 4e-16 * np.abs(href).max()
+    assert np.abs(det(h) - 1.0).max() <= 1e-15
