@@ -77,10 +77,11 @@ enum { NR_NGF = 24 };
  *     scheme (6th-difference dissipation over 64 S dxx), 5 the 8th-order
  *     production scheme of Sec. 4.1 (10th-difference dissipation over
  *     1024 S dxx, 8th-order one-sided derivatives in the radiation condition);
- *     any other value is NR_EINVAL.  Batched and served modes and
- *     nr_hamiltonian_noalloc take NG = 3 only.
+ *     any other value is NR_EINVAL.  nr_hamiltonian_noalloc takes NG = 3 only.
  *   enforce_detgb: rescale h so det(gammabar)=det(gammahat) after every RK
  *     substage (the Lagrangian choice of Sec. 2.1).
+ *   integrator: the time integrator of a served request, NR_RK4 or NR_SSPRK3
+ *     (NR_EINVAL otherwise); the single-grid and batch calls name theirs.
  *   stream: cudaStream_t used for all device work of the grid (NULL: legacy stream). */
 typedef struct {
     double ampl[3];
@@ -95,9 +96,11 @@ typedef struct {
     int NG;
     int enforce_detgb;
     int device;
-    int reserved;
+    int integrator;
     void* stream;
 } nr_params;
+
+enum { NR_RK4 = 0, NR_SSPRK3 = 1 };
 
 typedef struct nr_grid nr_grid;
 
@@ -264,34 +267,39 @@ int nr_dt_cfl(int coords, const int Nxx[3], const nr_params* params, double* dt_
  * scaling tests run many times over): many grids of uneven sizes, all of one
  * coordinate family (spherical-like or cylindrical-like), one azimuth kind
  * (two points, or more: the right-hand-side kernel is specialised for a
- * two-point azimuth) and one device, advanced together.  Each RK4 substage
- * is one launch over the work items of all grids -- a tile of one grid's
- * interior points or a chunk of its pure-outer ghost points, one thread block
- * each -- followed by one parity-copy launch for all grids; one
- * step is captured in a CUDA graph (re-captured when the step sizes or the
- * tile shape change) and replayed.  Every point runs the same arithmetic as
- * nr_rk4_step, so each grid's state is bitwise what nr_rk4_step would give,
- * for any tile shape and any batch composition.
+ * two-point azimuth), one finite-difference order (NG), one device and one
+ * stream, advanced together.  Each RK4 or SSPRK3 substage is one launch over
+ * the work items of all grids -- a tile of one grid's interior points or a
+ * chunk of its pure-outer ghost points, one thread block each -- followed by
+ * one parity-copy launch for all grids; one step is captured in a CUDA graph
+ * (re-captured when the step sizes, the integrator or the tile shape change)
+ * and replayed.  Every point runs the same arithmetic as nr_rk4_step /
+ * nr_ssprk3_step, so each grid's state is bitwise what those would give, for
+ * any tile shape and any batch composition (azimuthal ghost copies are
+ * refreshed on demand, as described at nr_rk4_step).
  *   nr_batch_create: grids stay owned by the caller and must outlive the
  *     batch; their library-owned states are advanced in place.  Work is issued
- *     on the first grid's stream.  Errors: NR_EINVAL (mixed families or
- *     devices, mixed azimuth kinds, duplicates), NR_ENOMEM, NR_ECUDA.
+ *     on the grids' stream.  Errors: NR_EINVAL (mixed families, orders,
+ *     devices, streams or azimuth kinds, duplicates), NR_ENOMEM, NR_ECUDA.
  *   nr_batch_set_tile: tile shape tile_x x tile_y of interior points per work
  *     item, one of 32x4, 64x2, 128x1, 16x8, 32x2, 64x1, 32x1 (default 32x4).
  *   nr_batch_autotune: times one substage launch of each compiled tile shape
  *     on the batch (it writes only the RK work buffers, not the states), keeps
  *     the fastest and returns it (synchronises).
- *   nr_batch_rk4_step: dts[ngrids] per-grid step sizes (host), nsteps steps. */
+ *   nr_batch_rk4_step, nr_batch_ssprk3_step: dts[ngrids] per-grid step sizes
+ *     (host), nsteps steps of RK4 or SSPRK3. */
 typedef struct nr_batch nr_batch;
 int nr_batch_create(nr_grid* const* grids, int ngrids, nr_batch** out);
 void nr_batch_destroy(nr_batch* batch);
 int nr_batch_set_tile(nr_batch* batch, int tile_x, int tile_y);
 int nr_batch_autotune(nr_batch* batch, const double* dts, int* tile_x, int* tile_y, double* best_ms);
 int nr_batch_rk4_step(nr_batch* batch, const double* dts, int nsteps);
+int nr_batch_ssprk3_step(nr_batch* batch, const double* dts, int nsteps);
 
 /* Served mode: continuous batching of evolution requests on one device.
  * A request is one grid (coords, Nxx, params) with Brill-Lindquist data
- * (npunct masses at xyz) evolved by RK4 at its own CFL step until t_final.
+ * (npunct masses at xyz) evolved at its own CFL step until t_final by
+ * params->integrator (RK4 or SSPRK3), with the scheme params->NG selects.
  *   nr_server_create: hbm_budget_bytes caps the summed device bytes of the
  *     running requests; max_slots caps their number; work is issued on stream.
  *   nr_server_submit: queues a request and returns its id (no device work;
@@ -300,9 +308,9 @@ int nr_batch_rk4_step(nr_batch* batch, const double* dts, int nsteps);
  *     nr_server_fetch_state.
  *   nr_server_advance: makes queued requests resident (running) in policy
  *     order while the budget and the slots allow, then advances the selected
- *     running requests together -- one nr_batch per kind of grid (coordinate
- *     family x azimuth kind), one launch per RK4 substage for each
- *     -- by up to nsteps steps.  Membership changes only at step boundaries:
+ *     running requests together -- one nr_batch per kind of request (coordinate
+ *     family x azimuth kind x order x integrator), one launch per substage
+ *     for each -- by up to nsteps steps.  Membership changes only at step boundaries:
  *     a request reaching t_final is retired (Hamiltonian-constraint norms
  *     recorded, state kept if asked, device memory released) and queued
  *     requests are admitted into the freed budget.  A request that
@@ -317,15 +325,15 @@ int nr_batch_rk4_step(nr_batch* batch, const double* dts, int nsteps);
  *   nr_server_set_policy: the order in which queued requests become resident
  *     and running requests are advanced.  NR_SERVE_FIFO (default): arrival
  *     order.  NR_SERVE_SRPT: least remaining work first (remaining steps x
- *     interior points; for a queued request the steps follow from its CFL
- *     step), preemptive at chunk boundaries: a running request that is not
+ *     substeps per step x interior points; for a queued request the steps
+ *     follow from its CFL step), preemptive at chunk boundaries: a running request that is not
  *     selected keeps its state in HBM and resumes later, with a result that is
  *     still bitwise the one it gets alone.  Each chunk advances the longest
  *     prefix of that order whose interior points sum to at most
  *     max_batch_points (at least one request; 0 = no cap, so every running
  *     request advances).  NR_EINVAL for an unknown policy or a negative cap.
  * Each request's result is bitwise what running it alone with nr_rk4_step
- * gives, whichever requests shared the GPU with it. */
+ * or nr_ssprk3_step gives, whichever requests shared the GPU with it. */
 typedef struct nr_server nr_server;
 enum { NR_SERVE_FIFO = 0, NR_SERVE_SRPT = 1 };
 int nr_server_create(size_t hbm_budget_bytes, int max_slots, int device, void* stream, nr_server** out);

@@ -19,6 +19,7 @@ NR_OK = 0
 STATUS = {0: "NR_OK", 1: "NR_EINVAL", 2: "NR_ENOMEM", 3: "NR_ECUDA", 4: "NR_ETIMEOUT", 5: "NR_ENONFINITE",
           6: "NR_EMAP"}
 COORDS = {"sinh_spherical": 0, "sinh_cylindrical": 1, "spherical": 2}
+INTEGRATORS = {"rk4": 0, "ssprk3": 1}
 
 # every entry point declared in include/nr.h
 EXPORTS = (
@@ -27,7 +28,7 @@ EXPORTS = (
     "nr_psi4", "nr_psi4_modes", "nr_get_state", "nr_get_state_compact", "nr_set_state_compact",
     "nr_set_state",
     "nr_sync", "nr_check_finite", "nr_build_maps", "nr_dt_cfl", "nr_fp64_peak", "nr_hamiltonian_noalloc",
-    "nr_batch_create", "nr_batch_destroy", "nr_batch_set_tile", "nr_batch_autotune", "nr_batch_rk4_step",
+    "nr_batch_create", "nr_batch_destroy", "nr_batch_set_tile", "nr_batch_autotune", "nr_batch_rk4_step", "nr_batch_ssprk3_step",
     "nr_server_create", "nr_server_destroy", "nr_server_set_tile", "nr_server_set_policy", "nr_server_submit",
     "nr_server_advance",
     "nr_server_poll", "nr_server_fetch_state", "nr_last_error",
@@ -54,7 +55,7 @@ class NrParams(ctypes.Structure):
         ("NG", ctypes.c_int),
         ("enforce_detgb", ctypes.c_int),
         ("device", ctypes.c_int),
-        ("reserved", ctypes.c_int),
+        ("integrator", ctypes.c_int),
         ("stream", ctypes.c_void_p),
     ]
 
@@ -126,6 +127,7 @@ def lib() -> ctypes.CDLL:
     L.nr_batch_set_tile.argtypes = [vp, ctypes.c_int, ctypes.c_int]
     L.nr_batch_autotune.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), dp]
     L.nr_batch_rk4_step.argtypes = [vp, dp, ctypes.c_int]
+    L.nr_batch_ssprk3_step.argtypes = [vp, dp, ctypes.c_int]
     L.nr_server_create.argtypes = [ctypes.c_size_t, ctypes.c_int, ctypes.c_int, vp, ctypes.POINTER(vp)]
     L.nr_server_destroy.argtypes = [vp]
     L.nr_server_destroy.restype = None
@@ -179,6 +181,7 @@ def make_params(spec: dict, stream=None, device: int = 0) -> NrParams:
     p.h_rmax = float(spec.get("h_rmax", 1e300))
     p.NG = int(spec.get("NG", 3))
     p.enforce_detgb = int(spec.get("enforce_detgb", 1))
+    p.integrator = INTEGRATORS[spec.get("integrator", "rk4")]
     p.device = int(device)
     p.stream = stream
     return p
@@ -365,6 +368,10 @@ class Batch:
     def rk4_step(self, dts, nsteps: int = 1) -> None:
         a = self._dts(dts)
         _check(lib().nr_batch_rk4_step(self.h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(nsteps)))
+
+    def ssprk3_step(self, dts, nsteps: int = 1) -> None:
+        a = self._dts(dts)
+        _check(lib().nr_batch_ssprk3_step(self.h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(nsteps)))
 
 
 SERVE_FIFO, SERVE_SRPT = 0, 1

@@ -1,7 +1,7 @@
 // nr_batch.cu -- batched mode: many grids of uneven sizes advanced together,
-// one launch per RK4 substage over the work items of all grids plus one
-// parity-copy launch, the whole step captured in a CUDA graph; the tile shape
-// is chosen by timing.
+// one launch per RK4 or SSPRK3 substage over the work items of all grids plus
+// one parity-copy launch, the whole step captured in a CUDA graph; the tile
+// shape is chosen by timing.
 //
 // The per-substage kernel and its work items: nr_batch_kernels.cuh.
 #include <string.h>
@@ -35,6 +35,7 @@ using namespace nrk;
 struct nr_batch {
     std::vector<nr_grid*> grids;
     int fam = FAM_SPH;
+    int ord = 4;              // finite-difference order of all grids
     bool two_point = false;   // the grids' azimuth holds two points
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -48,6 +49,7 @@ struct nr_batch {
     int n_inner_stencil = 0;   // the entries the stages before the last copy
     std::vector<double> dts;   // dts of the current table
     bool table_ok = false;
+    bool table_ssp = false;    // the current table (and graph) is for SSPRK3
     cudaGraphExec_t exec = nullptr;
 };
 
@@ -59,8 +61,9 @@ struct DevGuard {
     ~DevGuard() { cudaSetDevice(prev); }
 };
 
-// work list and per-grid stage constants for tile shape b->tile and step sizes dts
-int build_table(nr_batch* b, const double* dts)
+// work list and per-grid stage constants for tile shape b->tile, step sizes dts and the
+// integrator (ssp: SSPRK3, else RK4)
+int build_table(nr_batch* b, const double* dts, bool ssp)
 {
     const TileShape ts = kTiles[b->tile];
     std::vector<BGrid> h(b->grids.size());
@@ -86,13 +89,20 @@ int build_table(nr_batch* b, const double* dts)
         B.w_rhs_end = w + B.tiles_x * tiles_y;
         B.w_end = B.w_rhs_end + (g->n_outer + ts.tx * ts.ty - 1) / (ts.tx * ts.ty);
         w = B.w_end;
-        // the same stage constants as the single-grid RK4 driver
+        // the same stage constants as the single-grid drivers
         const double dt = dts[q];
         const int enf = g->P.enforce_detgb;
-        B.st[0] = Stage{MODE_STAGE1, enf, 0.5 * dt, dt / 6.0};
-        B.st[1] = Stage{MODE_STAGE23, enf, 0.5 * dt, dt / 3.0};
-        B.st[2] = Stage{MODE_STAGE23, enf, dt, dt / 3.0};
-        B.st[3] = Stage{MODE_STAGE4, enf, 0.0, dt / 6.0};
+        B.ssp = ssp ? 1 : 0;
+        if (ssp) {
+            B.st[0] = Stage{MODE_SSP, enf, dt, 1.0, 0.0};
+            B.st[1] = Stage{MODE_SSP, enf, dt, 0.25, 0.75};
+            B.st[2] = Stage{MODE_SSP, enf, dt, 2.0 / 3.0, 1.0 / 3.0};
+        } else {
+            B.st[0] = Stage{MODE_STAGE1, enf, 0.5 * dt, dt / 6.0};
+            B.st[1] = Stage{MODE_STAGE23, enf, 0.5 * dt, dt / 3.0};
+            B.st[2] = Stage{MODE_STAGE23, enf, dt, dt / 3.0};
+            B.st[3] = Stage{MODE_STAGE4, enf, 0.0, dt / 6.0};
+        }
     }
     b->total = w;
     int w1 = 0;
@@ -106,26 +116,38 @@ int build_table(nr_batch* b, const double* dts)
     if (e != cudaSuccess) return nrk_fail(NR_ECUDA, "batch table upload: %s", cudaGetErrorString(e));
     b->dts.assign(dts, dts + b->grids.size());
     b->table_ok = true;
+    b->table_ssp = ssp;
     return NR_OK;
 }
 
 cudaError_t enqueue_stage_launch(nr_batch* b, int stage, cudaStream_t s)
 {
-    cudaError_t e = b->fam == FAM_SPH
-                        ? batch_d1_launch_sph(b->two_point, b->d_grids, (int)b->grids.size(), b->total_d1, stage, s)
-                        : batch_d1_launch_cyl(b->two_point, b->d_grids, (int)b->grids.size(), b->total_d1, stage, s);
+    const int n = (int)b->grids.size();
+    const bool tp = b->two_point;
+    cudaError_t e;
+    if (b->fam == FAM_SPH)
+        e = b->ord == 8 ? batch_d1_sph8(tp, b->d_grids, n, b->total_d1, stage, s)
+                        : batch_d1_sph4(tp, b->d_grids, n, b->total_d1, stage, s);
+    else
+        e = b->ord == 8 ? batch_d1_cyl8(tp, b->d_grids, n, b->total_d1, stage, s)
+                        : batch_d1_cyl4(tp, b->d_grids, n, b->total_d1, stage, s);
     if (e != cudaSuccess) return e;
-    return b->fam == FAM_SPH
-               ? batch_stage_launch_sph(b->two_point, b->tile, b->d_grids, (int)b->grids.size(), b->total, stage, s)
-               : batch_stage_launch_cyl(b->two_point, b->tile, b->d_grids, (int)b->grids.size(), b->total, stage, s);
+    if (b->fam == FAM_SPH)
+        return b->ord == 8 ? batch_stage_sph8(tp, b->tile, b->d_grids, n, b->total, stage, s)
+                           : batch_stage_sph4(tp, b->tile, b->d_grids, n, b->total, stage, s);
+    return b->ord == 8 ? batch_stage_cyl8(tp, b->tile, b->d_grids, n, b->total, stage, s)
+                       : batch_stage_cyl4(tp, b->tile, b->d_grids, n, b->total, stage, s);
 }
 
+// one step of the table's integrator; every stage copies the ghosts the stencils read (the
+// grids' remaining azimuthal copies are refreshed on demand, as after single-grid steps)
 cudaError_t enqueue_step(nr_batch* b, cudaStream_t s)
 {
     cudaError_t e = cudaSuccess;
-    for (int stage = 0; stage < 4 && e == cudaSuccess; stage++) {
+    const int nst = b->table_ssp ? 3 : 4;
+    for (int stage = 0; stage < nst && e == cudaSuccess; stage++) {
         e = enqueue_stage_launch(b, stage, s);
-        const int ninner = stage == 3 ? b->n_inner : b->n_inner_stencil;
+        const int ninner = b->n_inner_stencil;
         if (e == cudaSuccess && ninner) {
             dim3 grd((ninner + 255) / 256, NR_NGF);
             k_batch_inner<<<grd, 256, 0, s>>>(b->d_grids, b->d_inner, ninner, stage);
@@ -148,6 +170,40 @@ bool same_dts(const nr_batch* b, const double* dts)
     return true;
 }
 
+int batch_steps(nr_batch* b, const double* dts, int nsteps, bool ssp, const char* name)
+{
+    if (!b || !dts || nsteps < 0) return nrk_fail(NR_EINVAL, "bad %s arguments", name);
+    for (size_t q = 0; q < b->grids.size(); q++)
+        if (!(dts[q] > 0.0)) return nrk_fail(NR_EINVAL, "dt of grid %zu must be positive", q);
+    if (nsteps == 0) return NR_OK;
+    DevGuard dg(b->device);
+    int rc;
+    if (!b->table_ok || b->table_ssp != ssp || !same_dts(b, dts)) {
+        drop_graph(b);
+        if ((rc = build_table(b, dts, ssp))) return rc;
+    }
+    if (!b->exec) {
+        cudaGraph_t graph;
+        cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return nrk_fail(NR_ECUDA, "capture: %s", cudaGetErrorString(e));
+        cudaError_t le = enqueue_step(b, b->cap);
+        e = cudaStreamEndCapture(b->cap, &graph);
+        if (le != cudaSuccess) return nrk_fail(NR_ECUDA, "batch step: %s", cudaGetErrorString(le));
+        if (e != cudaSuccess) return nrk_fail(NR_ECUDA, "capture end: %s", cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&b->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return nrk_fail(NR_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    }
+    for (int n = 0; n < nsteps; n++) {
+        cudaError_t e = cudaGraphLaunch(b->exec, b->stream);
+        if (e != cudaSuccess) return nrk_fail(NR_ECUDA, "graph launch: %s", cudaGetErrorString(e));
+    }
+    // the azimuthal ghost copies of two-point grids now lag (refreshed on demand)
+    for (nr_grid* g : b->grids) g->ghosts_stale = g->n_inner > g->n_inner_stencil;
+    return NR_OK;
+}
+
+
 }  // namespace
 
 extern "C" {
@@ -160,7 +216,9 @@ int nr_batch_create(nr_grid* const* grids, int ngrids, nr_batch** out)
     for (int q = 0; q < ngrids; q++) {
         if (!grids[q]) return nrk_fail(NR_EINVAL, "grid %d is NULL", q);
         if (grids[q]->device != grids[0]->device) return nrk_fail(NR_EINVAL, "grids on different devices");
-        if (grids[q]->K.ord != 4) return nrk_fail(NR_EINVAL, "batched mode runs the 4th-order scheme (NG = 3) only");
+        if (grids[q]->K.ord != grids[0]->K.ord)
+            return nrk_fail(NR_EINVAL, "grids of the 4th- and the 8th-order scheme cannot share a batch");
+        if (grids[q]->stream != grids[0]->stream) return nrk_fail(NR_EINVAL, "the grids of a batch share one stream");
         if (grids[q]->geo.fam != grids[0]->geo.fam)
             return nrk_fail(NR_EINVAL, "grids of spherical-like and cylindrical-like coordinates cannot share a batch");
         if ((grids[q]->K.ax >= 0) != (grids[0]->K.ax >= 0))
@@ -172,6 +230,7 @@ int nr_batch_create(nr_grid* const* grids, int ngrids, nr_batch** out)
     nr_batch* b = new nr_batch();
     b->grids.assign(grids, grids + ngrids);
     b->fam = grids[0]->geo.fam;
+    b->ord = grids[0]->K.ord;
     b->two_point = grids[0]->K.ax >= 0;
     b->device = grids[0]->device;
     b->stream = grids[0]->stream;
@@ -252,7 +311,7 @@ int nr_batch_autotune(nr_batch* b, const double* dts, int* tile_x, int* tile_y, 
     int rc = NR_OK;
     for (int t = 0; t < kNumTiles && rc == NR_OK; t++) {
         b->tile = t;
-        if ((rc = build_table(b, dts))) break;
+        if ((rc = build_table(b, dts, b->table_ssp))) break;
         // stage 1 writes only the stage buffer and the accumulator: the state is untouched
         float tt = 0.f;
         for (int rep = 0; rep < 4; rep++) {
@@ -278,7 +337,7 @@ int nr_batch_autotune(nr_batch* b, const double* dts, int* tile_x, int* tile_y, 
     if (rc) return rc;
     b->tile = best;
     drop_graph(b);
-    if ((rc = build_table(b, dts))) return rc;
+    if ((rc = build_table(b, dts, b->table_ssp))) return rc;
     if (tile_x) *tile_x = kTiles[best].tx;
     if (tile_y) *tile_y = kTiles[best].ty;
     if (best_ms) *best_ms = best_t;
@@ -287,35 +346,12 @@ int nr_batch_autotune(nr_batch* b, const double* dts, int* tile_x, int* tile_y, 
 
 int nr_batch_rk4_step(nr_batch* b, const double* dts, int nsteps)
 {
-    if (!b || !dts || nsteps < 0) return nrk_fail(NR_EINVAL, "bad nr_batch_rk4_step arguments");
-    for (size_t q = 0; q < b->grids.size(); q++)
-        if (!(dts[q] > 0.0)) return nrk_fail(NR_EINVAL, "dt of grid %zu must be positive", q);
-    if (nsteps == 0) return NR_OK;
-    DevGuard dg(b->device);
-    int rc;
-    if (!b->table_ok || !same_dts(b, dts)) {
-        drop_graph(b);
-        if ((rc = build_table(b, dts))) return rc;
-    }
-    if (!b->exec) {
-        cudaGraph_t graph;
-        cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
-        if (e != cudaSuccess) return nrk_fail(NR_ECUDA, "capture: %s", cudaGetErrorString(e));
-        cudaError_t le = enqueue_step(b, b->cap);
-        e = cudaStreamEndCapture(b->cap, &graph);
-        if (le != cudaSuccess) return nrk_fail(NR_ECUDA, "batch step: %s", cudaGetErrorString(le));
-        if (e != cudaSuccess) return nrk_fail(NR_ECUDA, "capture end: %s", cudaGetErrorString(e));
-        e = cudaGraphInstantiate(&b->exec, graph, 0);
-        cudaGraphDestroy(graph);
-        if (e != cudaSuccess) return nrk_fail(NR_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
-    }
-    for (int n = 0; n < nsteps; n++) {
-        cudaError_t e = cudaGraphLaunch(b->exec, b->stream);
-        if (e != cudaSuccess) return nrk_fail(NR_ECUDA, "graph launch: %s", cudaGetErrorString(e));
-    }
-    // the last stage copies every inner ghost of every grid
-    for (nr_grid* g : b->grids) g->ghosts_stale = false;
-    return NR_OK;
+    return batch_steps(b, dts, nsteps, false, "nr_batch_rk4_step");
+}
+
+int nr_batch_ssprk3_step(nr_batch* b, const double* dts, int nsteps)
+{
+    return batch_steps(b, dts, nsteps, true, "nr_batch_ssprk3_step");
 }
 
 }  // extern "C"

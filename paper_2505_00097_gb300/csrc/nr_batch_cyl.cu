@@ -1,18 +1,8 @@
-// nr_batch_cyl.cu -- batched-mode kernels for cylindrical-like grids.
+// nr_batch_cyl.cu -- batched-mode kernels for cylindrical-like grids, 4th-order scheme.
 #include "nr_batch_kernels.cuh"
 
 namespace nrk {
 
-cudaError_t batch_stage_launch_cyl(bool two_point, int tile, const BGrid* g, int n, int total, int stage,
-                                   cudaStream_t s)
-{
-    return two_point ? dispatch_stage<FAM_CYL, 1>(tile, g, n, total, stage, s)
-                     : dispatch_stage<FAM_CYL, -1>(tile, g, n, total, stage, s);
-}
-
-cudaError_t batch_d1_launch_cyl(bool two_point, const BGrid* g, int n, int total_d1, int stage, cudaStream_t s)
-{
-    return two_point ? launch_batch_d1<1>(g, n, total_d1, stage, s) : launch_batch_d1<-1>(g, n, total_d1, stage, s);
-}
+NRK_BATCH_LAUNCH(cyl4, FAM_CYL, 1, 4)
 
 }  // namespace nrk

@@ -280,6 +280,8 @@ int check_args(int coords, const int Nxx[3], const nr_params* p)
     if (!Nxx) return fail(NR_EINVAL, "Nxx is NULL");
     if (p && p->NG != 3 && p->NG != 5)
         return fail(NR_EINVAL, "NG must be 3 (4th-order FD) or 5 (8th-order FD), with upwinding; got %d", p->NG);
+    if (p && p->integrator != NR_RK4 && p->integrator != NR_SSPRK3)
+        return fail(NR_EINVAL, "integrator must be NR_RK4 or NR_SSPRK3; got %d", p->integrator);
     if (p) {
         for (int g = 1; g < NR_NGF; g++) {
             const int first = g < 17 ? 0 : 17;

@@ -56,9 +56,9 @@ struct Request {
     std::vector<double> state;
 };
 
-size_t grid_bytes_estimate(const int N[3])
+size_t grid_bytes_estimate(const int N[3], int NG)
 {
-    const size_t T = (size_t)(N[0] + 6) * (N[1] + 6) * (N[2] + 6);
+    const size_t T = (size_t)(N[0] + 2 * NG) * (N[1] + 2 * NG) * (N[2] + 2 * NG);
     // four 24-gridfunction sets, two sets of stored first differences (11 gridfunctions
     // each), maps and lists (generous per-point allowance)
     return T * (4 * 24 * sizeof(double) + 2 * 11 * sizeof(double) + 64);
@@ -123,8 +123,12 @@ int chunk_fence(nr_server* s)
     return e == cudaSuccess ? NR_OK : nrk_fail(NR_ECUDA, "server chunk fence: %s", cudaGetErrorString(e));
 }
 
-// grids that can share one batch: same coordinate family and azimuth kind
-int grid_kind(const nr_grid* g) { return 2 * g->K.fam + (g->K.ax >= 0 ? 1 : 0); }
+// requests that can share one batch: same coordinate family, azimuth kind, order and integrator
+int request_kind(const Request* r)
+{
+    const nr_grid* g = r->grid;
+    return 8 * r->P.integrator + 4 * (g->K.ord == 8) + 2 * g->K.fam + (g->K.ax >= 0 ? 1 : 0);
+}
 
 int start_request(nr_server* s, Request* r)
 {
@@ -162,11 +166,14 @@ int finish_request(nr_server* s, Request* r)
     return NR_OK;
 }
 
-// work left, in point-steps; ties broken by arrival (id)
+// right-hand-side evaluations per step
+int64_t substeps(const Request* r) { return r->P.integrator == NR_SSPRK3 ? 3 : 4; }
+
+// work left, in point-substeps; ties broken by arrival (id)
 bool srpt_before(const Request* a, const Request* b)
 {
-    const int64_t wa = (a->steps_total - a->steps_done) * a->interior;
-    const int64_t wb = (b->steps_total - b->steps_done) * b->interior;
+    const int64_t wa = (a->steps_total - a->steps_done) * a->interior * substeps(a);
+    const int64_t wb = (b->steps_total - b->steps_done) * b->interior * substeps(b);
     return wa != wb ? wa < wb : a->id < b->id;
 }
 
@@ -178,7 +185,7 @@ size_t next_queued(const nr_server* s)
     for (size_t q = 1; q < s->queue.size(); q++) {
         const Request* a = s->queue[q];
         const Request* b = s->queue[best];
-        const int64_t wa = a->steps_est * a->interior, wb = b->steps_est * b->interior;
+        const int64_t wa = a->steps_est * a->interior * substeps(a), wb = b->steps_est * b->interior * substeps(b);
         if (wa < wb || (wa == wb && a->id < b->id)) best = q;
     }
     return best;
@@ -240,7 +247,7 @@ int rebuild_batch(nr_server* s)
     if (s->active.empty()) return NR_OK;
     std::map<int, size_t> slot;
     for (Request* r : s->active) {
-        const int k = grid_kind(r->grid);
+        const int k = request_kind(r);
         auto it = slot.find(k);
         if (it == slot.end()) {
             it = slot.emplace(k, s->groups.size()).first;
@@ -312,7 +319,8 @@ int nr_server_submit(nr_server* s, int coords, const int Nxx[3], const nr_params
 {
     if (!s || !Nxx || !params || npunct < 0 || npunct > 16 || (npunct && (!mass || !xyz)) || !(t_final > 0.0))
         return nrk_fail(NR_EINVAL, "bad nr_server_submit arguments");
-    if (params->NG != 3) return nrk_fail(NR_EINVAL, "served mode runs the 4th-order scheme (NG = 3) only");
+    if (params->integrator != NR_RK4 && params->integrator != NR_SSPRK3)
+        return nrk_fail(NR_EINVAL, "unknown integrator %d", params->integrator);
     if (s->running.size() + s->queue.size() > 0 && s->all.size() > 1000000)
         return nrk_fail(NR_EINVAL, "too many requests");
     Request* r = new Request();
@@ -327,7 +335,7 @@ int nr_server_submit(nr_server* s, int coords, const int Nxx[3], const nr_params
     }
     r->t_final = t_final;
     r->keep_state = keep_state;
-    r->bytes = grid_bytes_estimate(Nxx);
+    r->bytes = grid_bytes_estimate(Nxx, params->NG);
     r->interior = (int64_t)Nxx[0] * Nxx[1] * Nxx[2];
     double dt = 0.0;
     if (nr_dt_cfl(coords, Nxx, params, &dt) != NR_OK || !(dt > 0.0)) {
@@ -365,7 +373,9 @@ int nr_server_advance(nr_server* s, int nsteps, int* n_running, int* n_queued)
         for (size_t q = 0; q < s->batches.size(); q++) {
             std::vector<double> dts;
             for (Request* r : s->groups[q]) dts.push_back(r->dt);
-            if ((rc = nr_batch_rk4_step(s->batches[q], dts.data(), (int)k))) return rc;
+            rc = s->groups[q][0]->P.integrator == NR_SSPRK3 ? nr_batch_ssprk3_step(s->batches[q], dts.data(), (int)k)
+                                                             : nr_batch_rk4_step(s->batches[q], dts.data(), (int)k);
+            if (rc) return rc;
         }
         if ((rc = chunk_fence(s))) return rc;
         left -= (int)k;

@@ -1,9 +1,10 @@
-"""Batched mode: many uneven grids advanced by one launch per RK4 substage over all their tiles.
+"""Batched mode: many uneven grids advanced by one launch per substage over all their tiles.
 
 Each grid's state after n batched steps must be bitwise the state after n
-single-grid steps (nr_rk4_step) from the same initial data -- for every tile
-shape the autotuner can pick and in any batch composition -- and therefore
-within the oracle tolerance of the single-grid path.
+single-grid steps (nr_rk4_step, nr_ssprk3_step) from the same initial data -- for
+every tile shape the autotuner can pick, in any batch composition and at both
+finite-difference orders -- and therefore within the oracle tolerance of the
+single-grid path.
 """
 import numpy as np
 import pytest
@@ -17,6 +18,7 @@ from paper_2505_00097_gb300 import workloads as W  # noqa: E402
 pytestmark = pytest.mark.gpu
 
 TILES = [(32, 4), (64, 2), (128, 1), (16, 8), (32, 2), (64, 1), (32, 1)]
+KO8 = [0.3] * 17 + [0.99] * 7
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -55,7 +57,11 @@ def _cyl3d_runs():
     return runs
 
 
-def _states(runs, nsteps, batched, tile=None, autotune=False):
+def _o8(runs):
+    return [dict(s, NG=5, ko_sigma=KO8) for s in runs]
+
+
+def _states(runs, nsteps, batched, tile=None, autotune=False, ssp=False):
     grids = [B.Grid(s) for s in runs]
     for g, s in zip(grids, runs):
         g.set_brill_lindquist(s["masses"], s["positions"], s.get("perturb", 0.0), 7)
@@ -67,10 +73,10 @@ def _states(runs, nsteps, batched, tile=None, autotune=False):
             b.set_tile(*tile)
         if autotune:
             chosen = b.autotune(dts)
-        b.rk4_step(dts, nsteps)
+        (b.ssprk3_step if ssp else b.rk4_step)(dts, nsteps)
     else:
         for g, dt in zip(grids, dts):
-            g.rk4_step(dt, nsteps)
+            (g.ssprk3_step if ssp else g.rk4_step)(dt, nsteps)
     out = []
     for g in grids:
         st = np.empty(24 * g.T)
@@ -113,6 +119,58 @@ def test_batched_cylindrical_3d_bitwise_equals_single_grid(tile):
         assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("ssp", [False, True], ids=["rk4", "ssprk3"])
+@pytest.mark.parametrize("tile", [(32, 4), (128, 1), (16, 8)], ids=["32x4", "128x1", "16x8"])
+def test_batched_8th_order_bitwise_equals_single_grid(tile, ssp):
+    runs = _o8(_cyl_runs())
+    ref, _ = _states(runs, 5, batched=False, ssp=ssp)
+    got, _ = _states(runs, 5, batched=True, tile=tile, ssp=ssp)
+    for a, b in zip(got, ref):
+        assert np.all(np.isfinite(a))
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("three_d", [False, True], ids=["nphi2", "3d"])
+def test_batched_8th_order_spherical_ssprk3(three_d):
+    runs = _o8(_sph_runs(three_d))
+    ref, _ = _states(runs, 4, batched=False, ssp=True)
+    got, _ = _states(runs, 4, batched=True, tile=(32, 4), ssp=True)
+    for a, b in zip(got, ref):
+        assert np.array_equal(a, b)
+
+
+def test_one_batch_switches_integrators():
+    """RK4, then SSPRK3, then RK4 again on one batch: the table and the graph follow the
+    integrator, and each grid ends bitwise where the same sequence of single-grid steps ends."""
+    runs = _cyl_runs()
+    out = []
+    for batched in (False, True):
+        grids = [B.Grid(s) for s in runs]
+        for g, s in zip(grids, runs):
+            g.set_brill_lindquist(s["masses"], s["positions"], 0.0, 0)
+        dts = [g.dt_cfl for g in grids]
+        if batched:
+            b = B.Batch(grids)
+            b.rk4_step(dts, 2)
+            b.ssprk3_step(dts, 2)
+            b.rk4_step(dts, 1)
+            b.close()
+        else:
+            for g, dt in zip(grids, dts):
+                g.rk4_step(dt, 2)
+                g.ssprk3_step(dt, 2)
+                g.rk4_step(dt, 1)
+        st = []
+        for g in grids:
+            a = np.empty(24 * g.T)
+            g.get_state(a, True)
+            st.append(a)
+            g.close()
+        out.append(st)
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
+
+
 def test_batch_membership_does_not_change_results():
     runs = _cyl_runs()
     alone, _ = _states(runs[1:2], 4, batched=True)
@@ -127,6 +185,17 @@ def test_autotune_picks_a_compiled_shape_and_keeps_results():
     assert tuple(chosen[:2]) in TILES and chosen[2] > 0
     for a, b in zip(got, ref):
         assert np.array_equal(a, b)
+
+
+def test_mixed_orders_and_streams_rejected():
+    g4 = B.Grid(W.sinh_cylindrical((8, 2, 16), rho_max=10.0, z_max=10.0))
+    g8 = B.Grid(dict(W.sinh_cylindrical((8, 2, 16), rho_max=10.0, z_max=10.0), NG=5, ko_sigma=KO8))
+    with pytest.raises(B.NrError, match="8th-order"):
+        B.Batch([g4, g8])
+    s = torch.cuda.Stream()
+    g5 = B.Grid(W.sinh_cylindrical((10, 2, 16), rho_max=10.0, z_max=10.0), stream=s.cuda_stream)
+    with pytest.raises(B.NrError, match="stream"):
+        B.Batch([g4, g5])
 
 
 def test_mixed_families_rejected():

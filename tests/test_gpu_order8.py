@@ -165,7 +165,8 @@ def test_headon8_full_size_parity_in_bench_configuration():
     assert_close(got, y, o.T, 1e-10, what="head-on 256x2x512 after 5 SSPRK3 steps, 8th order")
 
 
-def test_batched_mode_takes_the_4th_order_scheme_only():
-    g = B.Grid(SPECS[2])
-    with pytest.raises(B.NrError, match="4th-order"):
-        B.Batch([g])
+def test_batches_hold_one_order():
+    g8 = B.Grid(SPECS[2])
+    g4 = B.Grid(W.sinh_cylindrical((33, 2, 70), rho_max=20.0, z_max=20.0))
+    with pytest.raises(B.NrError, match="8th-order"):
+        B.Batch([g8, g4])

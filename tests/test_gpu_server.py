@@ -43,7 +43,7 @@ def _alone(spec, t_final):
     g = B.Grid(spec)
     g.set_brill_lindquist(spec["masses"], spec["positions"])
     n = max(1, int(np.ceil(t_final / g.dt_cfl - 1e-9)))
-    g.rk4_step(g.dt_cfl, n)
+    (g.ssprk3_step if spec.get("integrator") == "ssprk3" else g.rk4_step)(g.dt_cfl, n)
     st = np.empty(24 * g.T)
     g.get_state(st, True)
     T = g.T
@@ -164,3 +164,39 @@ def test_requests_of_every_kind_share_one_server():
         ref, n, T = _alone(spec, t_final)
         assert np.array_equal(srv.fetch_state(rid, 24 * T), ref)
     srv.close()
+
+
+def test_production_scheme_and_4th_order_requests_share_one_server():
+    """8th-order SSPRK3 requests (the production scheme of Sec. 4.1), an 8th-order RK4 request
+    and 4th-order RK4 requests in one server: one batch per kind, each result bitwise its result
+    alone."""
+    ko8 = [0.3] * 17 + [0.99] * 7
+    specs = []
+    for k, (nr, masses, pos) in enumerate([(14, (1.0,), ((0, 0, 0),)),
+                                           (18, (0.6, 0.4), ((0, 0, 0.4), (0, 0, -0.6))),
+                                           (12, (0.8,), ((0, 0, 0),)),
+                                           (16, (0.5, 0.5), ((0, 0, 0.5), (0, 0, -0.5)))]):
+        s = W.sinh_cylindrical((nr, 2, 2 * nr), rho_max=30.0, z_max=30.0)
+        s.update(masses=masses, positions=pos)
+        if k < 2:
+            s.update(NG=5, ko_sigma=ko8, integrator="ssprk3", cfl=0.35)
+        elif k == 2:
+            s.update(NG=5, ko_sigma=ko8)
+        specs.append(s)
+    t_final = 0.5
+    for policy in ("fifo", "srpt"):
+        srv = B.Server(int(80 * 2 ** 30), 8)
+        srv.set_tile(32, 4)
+        srv.set_policy(policy)
+        ids = [srv.submit(spec, t_final, keep_state=True) for spec in specs]
+        for _ in range(1000):
+            nrun, nq = srv.advance(3)
+            if nrun == 0 and nq == 0:
+                break
+        for rid, spec in zip(ids, specs):
+            p = srv.poll(rid)
+            assert p["status"] == 2
+            ref, n, T = _alone(spec, t_final)
+            assert p["steps_total"] == n
+            assert np.array_equal(srv.fetch_state(rid, 24 * T), ref)
+        srv.close()

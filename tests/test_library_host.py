@@ -130,10 +130,20 @@ def test_ghost_layers_select_the_scheme():
         else:
             with pytest.raises(B.NrError, match="NG"):
                 B.dt_cfl(spec)
+    # the integrator field: RK4 or SSPRK3, anything else is refused (grid set-up and server)
+    spec = W.sinh_cylindrical((8, 2, 16), rho_max=10.0, z_max=10.0)
+    p = B.make_params(spec)
+    Nx = (ctypes.c_int * 3)(8, 2, 16)
+    dt = ctypes.c_double()
+    for integ, ok in ((0, True), (1, True), (2, False), (-1, False)):
+        p.integrator = integ
+        rc = B.lib().nr_dt_cfl(int(spec["coords"]), Nx, ctypes.byref(p), ctypes.byref(dt))
+        assert (rc == 0) == ok
+        if not ok:
+            assert b"integrator" in B.lib().nr_last_error()
     srv = B.Server(2 ** 30, 2)
-    spec = dict(W.sinh_cylindrical((8, 2, 16), rho_max=10.0, z_max=10.0), NG=5, masses=(1.0,), positions=((0, 0, 0),))
-    with pytest.raises(B.NrError, match="4th-order"):
-        srv.submit(spec, 1.0)
+    spec = dict(spec, NG=5, masses=(1.0,), positions=((0, 0, 0),), integrator="ssprk3")
+    assert srv.submit(spec, 1.0) >= 0
     srv.close()
 
 
