@@ -77,7 +77,7 @@ enum { NR_NGF = 24 };
  *     scheme (6th-difference dissipation over 64 S dxx), 5 the 8th-order
  *     production scheme of Sec. 4.1 (10th-difference dissipation over
  *     1024 S dxx, 8th-order one-sided derivatives in the radiation condition);
- *     any other value is NR_EINVAL.  nr_hamiltonian_noalloc takes NG = 3 only.
+ *     any other value is NR_EINVAL.
  *   enforce_detgb: rescale h so det(gammabar)=det(gammahat) after every RK
  *     substage (the Lagrangian choice of Sec. 2.1).
  *   integrator: the time integrator of a served request, NR_RK4 or NR_SSPRK3
@@ -363,7 +363,7 @@ int nr_server_fetch_state(nr_server* server, int64_t id, double* host_state, siz
  * cudaFree or allocating library routine).
  *   Limit: the per-axis arrays must fit 59,360 doubles, i.e.
  *   4 n0 + 4 n1 + 2 n2 (SinhSpherical, Spherical) or 4 n0 + 2 n1 + 3 n2
- *   (SinhCylindrical) with n_d = N_d + 6; larger grids get NR_EINVAL.
+ *   (SinhCylindrical) with n_d = N_d + 2 NG; larger grids get NR_EINVAL.
  *   The first call on a device looks up the array's device address (with that
  *   device current); make that first call before any stream capture.
  *   All calls share the one array and every call overwrites it: calls that

@@ -89,7 +89,7 @@ __global__ void k_na_axes(int coords, int fam, int n0, int n1, int n2, int NG, d
 
 // k_ham with a fixed number of blocks: each block strides over the interior
 // points, so the partials fit the static scratch for any grid size
-template <int FAM>
+template <int FAM, int ORD>
 __global__ void __launch_bounds__(NA_THREADS) k_na_ham(GridK G, const double* __restrict__ y, double* H, double rmin,
                                                         double rmax, double* partials)
 {
@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(NA_THREADS) k_na_ham(GridK G, const double* __
         P.dx = nullptr;
         P.dy = nullptr;
         P.g = make_geo<FAM>(G, p0, p1, p2);
-        const double h = ham_core<FAM, 4>(P);
+        const double h = ham_core<FAM, ORD>(P);
         if (H) H[idx] = h;
         double x[3];
         cart_of(G, p0, p1, p2, x);
@@ -155,8 +155,8 @@ extern "C" int nr_hamiltonian_noalloc(int coords, const int Nxx[3], const nr_par
     if (!params || !Nxx || !y_dev) return nrk_fail(NR_EINVAL, "nr_hamiltonian_noalloc: NULL argument");
     if (coords != NR_SINH_SPHERICAL && coords != NR_SINH_CYLINDRICAL && coords != NR_SPHERICAL)
         return nrk_fail(NR_EINVAL, "nr_hamiltonian_noalloc: unknown coordinate system");
-    if (params->NG != 3) return nrk_fail(NR_EINVAL, "nr_hamiltonian_noalloc: NG must be 3");
-    const int NG = 3;
+    if (params->NG != 3 && params->NG != 5) return nrk_fail(NR_EINVAL, "nr_hamiltonian_noalloc: NG must be 3 or 5");
+    const int NG = params->NG;
     int n[3];
     long T = 1;
     for (int d = 0; d < 3; d++) {
@@ -208,7 +208,7 @@ extern "C" int nr_hamiltonian_noalloc(int coords, const int Nxx[3], const nr_par
     K.NG = NG;
     K.fam = fam;
     K.ax = -1;
-    K.ord = 4;
+    K.ord = 2 * (NG - 1);
     K.T = T;
     double lo[3], hi[3], dx[3];
     if (fam == FAM_CYL) {
@@ -222,8 +222,8 @@ extern "C" int nr_hamiltonian_noalloc(int coords, const int Nxx[3], const nr_par
     }
     for (int d = 0; d < 3; d++) {
         dx[d] = (hi[d] - lo[d]) / Nxx[d];
-        K.inv_d1[d] = 1.0 / (12.0 * dx[d]);
-        K.inv_d2[d] = 1.0 / (12.0 * dx[d] * dx[d]);
+        K.inv_d1[d] = 1.0 / ((K.ord == 8 ? FD<8>::den1 : FD<4>::den1) * dx[d]);
+        K.inv_d2[d] = 1.0 / ((K.ord == 8 ? FD<8>::den2 : FD<4>::den2) * dx[d] * dx[d]);
     }
     double* ax0 = scratch + NA_AXES;
     double* ax1 = ax0 + 4L * n[0];
@@ -242,10 +242,11 @@ extern "C" int nr_hamiltonian_noalloc(int coords, const int Nxx[3], const nr_par
     const long nint = (long)Nxx[0] * Nxx[1] * Nxx[2];
     const int nb = (int)std::min<long>(NA_MAXBLOCKS, (nint + NA_THREADS - 1) / NA_THREADS);
     if (e == cudaSuccess) {
-        if (fam == FAM_SPH)
-            k_na_ham<FAM_SPH><<<nb, NA_THREADS, 0, s>>>(K, y_dev, H_dev, params->h_rmin, params->h_rmax, scratch);
-        else
-            k_na_ham<FAM_CYL><<<nb, NA_THREADS, 0, s>>>(K, y_dev, H_dev, params->h_rmin, params->h_rmax, scratch);
+        const double r0 = params->h_rmin, r1 = params->h_rmax;
+        if (fam == FAM_SPH && NG == 5) k_na_ham<FAM_SPH, 8><<<nb, NA_THREADS, 0, s>>>(K, y_dev, H_dev, r0, r1, scratch);
+        else if (fam == FAM_SPH) k_na_ham<FAM_SPH, 4><<<nb, NA_THREADS, 0, s>>>(K, y_dev, H_dev, r0, r1, scratch);
+        else if (NG == 5) k_na_ham<FAM_CYL, 8><<<nb, NA_THREADS, 0, s>>>(K, y_dev, H_dev, r0, r1, scratch);
+        else k_na_ham<FAM_CYL, 4><<<nb, NA_THREADS, 0, s>>>(K, y_dev, H_dev, r0, r1, scratch);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = launch_ham_reduce(scratch, nb, scratch + NA_RESULT, s);

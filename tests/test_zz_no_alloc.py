@@ -5,7 +5,8 @@ device memory, a caller without an nr_grid, a latency-critical loop -- by keepin
 its scratch in one file-scope device array.  Checked here through the C ABI: two
 calls in a row on different states agree with the grid-based nr_hamiltonian
 within the tolerances of the other Hamiltonian tests (H 1e-12 relative, norms
-1e-10), device free memory does not change across calls, and grids beyond the
+1e-10) at both finite-difference orders, device free memory does not change across
+calls, and grids beyond the
 array's stated limit are rejected.  This file is collected last so that a run
 stopping at the first failure has already run every other test.
 """
@@ -20,9 +21,12 @@ from paper_2505_00097_gb300 import workloads as W  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
+KO8 = [0.3] * 17 + [0.99] * 7
 SPECS = [
     dict(W.sinh_spherical((37, 11, 6)), h_rmin=0.5, h_rmax=8.0),
     dict(W.sinh_cylindrical((33, 2, 70), rho_max=20.0, z_max=20.0), h_rmin=0.5, h_rmax=8.0),
+    dict(W.sinh_spherical((37, 11, 6)), h_rmin=0.5, h_rmax=8.0, NG=5, ko_sigma=KO8),
+    dict(W.sinh_cylindrical((33, 2, 70), rho_max=20.0, z_max=20.0), h_rmin=0.5, h_rmax=8.0, NG=5, ko_sigma=KO8),
 ]
 
 
@@ -34,7 +38,7 @@ def _lib():
     B.lib()
 
 
-@pytest.mark.parametrize("spec", SPECS, ids=["sinhsph", "sinhcyl"])
+@pytest.mark.parametrize("spec", SPECS, ids=["sinhsph", "sinhcyl", "sinhsph-o8", "sinhcyl-o8"])
 def test_noalloc_matches_grid_hamiltonian_two_calls(spec):
     g = B.Grid(spec)
     T = g.T
