@@ -239,8 +239,9 @@ int nr_set_state(nr_grid* grid, const double* src, int from_host);
  * n_state_points doubles).  Inner ghost points hold parity copies of canonical
  * points (Sec. 3), so the compact state determines the full one:
  * nr_set_state_compact scatters it and then applies the inner boundary
- * condition, which leaves the same state, bit for bit, as nr_set_state of the
- * full array it came from.  to_host / from_host = 1: host memory (pinned or
+ * condition (its azimuthal copies on demand, as after nr_rk4_step), which
+ * leaves the same state, bit for bit, as nr_set_state of the full array it
+ * came from.  to_host / from_host = 1: host memory (pinned or
  * pageable), staged through a grid-owned device buffer allocated on first use
  * (NR_ENOMEM / NR_ECUDA if that fails); the call synchronises.  0: device
  * memory, stream-ordered. */

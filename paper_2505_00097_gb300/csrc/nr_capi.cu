@@ -848,8 +848,9 @@ int nr_set_state_compact(nr_grid* g, const double* src, int from_host)
         from = g->stage;
     }
     CUDA_OR_FAIL(launch_compact(g->K, g->canon, nc, from, g->y, false, g->stream));
-    CUDA_OR_FAIL(launch_inner(g->K, g->inner, g->n_inner, g->y, g->stream));
-    g->ghosts_stale = false;
+    // the ghosts the stencils read now; the azimuthal copies on demand (refresh_ghosts)
+    CUDA_OR_FAIL(launch_inner(g->K, g->inner, g->n_inner_stencil, g->y, g->stream));
+    g->ghosts_stale = g->n_inner > g->n_inner_stencil;
     if (from_host) CUDA_OR_FAIL(cudaStreamSynchronize(g->stream));
     return NR_OK;
 }
