@@ -81,6 +81,7 @@ def parse():
     ap.add_argument("--batch-runs", type=int, default=64)
     ap.add_argument("--served-requests", type=int, default=24)
     ap.add_argument("--served-tfinal", type=float, default=2.0)
+    ap.add_argument("--served-rate", type=float, default=20.0, help="mean arrivals per minute of the served stream")
     ap.add_argument("--served-policy", choices=("srpt", "fifo"), default="srpt")
     ap.add_argument("--served-cap", type=int, default=1000000,
                     help="interior points advanced together by the served arm (0: no cap)")
@@ -596,7 +597,7 @@ def run_served(args, world, rank, local):
     from paper_2505_00097_gb300 import binding as B
 
     torch.cuda.set_device(local)
-    reqs = W.config_served(n_requests=args.served_requests, t_final=args.served_tfinal)
+    reqs = W.config_served(n_requests=args.served_requests, t_final=args.served_tfinal, rate_per_min=args.served_rate)
     pts_of = {}
 
     def serve(mode: str):
@@ -663,7 +664,8 @@ def run_served(args, world, rank, local):
         "metric": METRIC, "value": served["value"], "unit": UNIT, "n_gpus": 1, "steps": None, "warmup": 0,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded Poisson request stream)",
-        "config": {"workload": f"served_{len(reqs)}_requests", "rate_per_min": 20, "t_final": args.served_tfinal,
+        "config": {"workload": f"served_{len(reqs)}_requests", "rate_per_min": args.served_rate,
+                   "t_final": args.served_tfinal,
                    "points_range": [1e5, 4e6], "hbm_budget_gb": 80, "policy": args.served_policy,
                    "max_batch_points": args.served_cap},
         "served": served, f"served_{other_name(args.served_policy)}": other, "plain_fifo": plain,

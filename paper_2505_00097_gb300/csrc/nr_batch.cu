@@ -45,8 +45,7 @@ struct nr_batch {
     int total_d1 = 0;          // items of the first-difference pass
     BGrid* d_grids = nullptr;
     BInner* d_inner = nullptr;
-    int n_inner = 0;
-    int n_inner_stencil = 0;   // the entries the stages before the last copy
+    int n_inner_stencil = 0;   // parity copies per stage: the ghosts the stencils read
     std::vector<double> dts;   // dts of the current table
     bool table_ok = false;
     bool table_ssp = false;    // the current table (and graph) is for SSPRK3
@@ -235,30 +234,18 @@ int nr_batch_create(nr_grid* const* grids, int ngrids, nr_batch** out)
     b->device = grids[0]->device;
     b->stream = grids[0]->stream;
     DevGuard dg(b->device);
-    // parity copies of all grids: those the RK-stage stencils read first (every
-    // ghost, unless the azimuth holds two points), then the azimuthal ghosts,
-    // which only the last stage copies -- the same split as the single-grid path
-    std::vector<BInner> inner, rest;
+    // parity copies of all grids that the stage stencils read (every ghost, unless the
+    // azimuth holds two points: then its ghosts are refreshed per grid on demand), from
+    // each grid's partitioned inner list
+    std::vector<BInner> inner;
     for (int q = 0; q < ngrids; q++) {
         const nr_grid* g = grids[q];
-        const int ax = g->K.ax, n0 = g->K.n0, n1 = g->K.n1;
-        for (long idx = 0; idx < g->geo.T; idx++) {
-            if (g->cls[idx] != 2) continue;
-            int m = 0;
-            for (int t = 0; t < 10; t++)
-                if (g->par[10 * idx + t] < 0) m |= 1 << t;
-            const BInner e{q, (int)idx, g->src[idx], m};
-            bool read = true;
-            if (ax >= 0) {
-                const int ia = ax == 1 ? (int)((idx / n0) % n1) : (int)(idx / ((long)n0 * n1));
-                read = ia >= g->K.NG && ia < g->K.NG + (ax == 1 ? g->K.N1 : g->K.N2);
-            }
-            (read ? inner : rest).push_back(e);
+        for (int t = 0; t < g->n_inner_stencil; t++) {
+            const InnerPt& p = g->inner_h[t];
+            inner.push_back(BInner{q, p.dst, p.src, p.negmask});
         }
     }
     b->n_inner_stencil = (int)inner.size();
-    inner.insert(inner.end(), rest.begin(), rest.end());
-    b->n_inner = (int)inner.size();
     cudaError_t e = cudaMalloc(&b->d_grids, sizeof(BGrid) * ngrids);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_inner, sizeof(BInner) * std::max<size_t>(inner.size(), 1));
     if (e == cudaSuccess && !inner.empty())

@@ -612,6 +612,7 @@ int nr_grid_create(int coords, const int Nxx[3], const nr_params* params, nr_gri
     up(g->ax2, a2.data(), sizeof(double) * a2.size());
     up(g->outer, outer.data(), sizeof(OuterPt) * outer.size());
     up(g->inner, inner.data(), sizeof(InnerPt) * inner.size());
+    g->inner_h = inner;
     up(g->canon, canon.data(), sizeof(int) * canon.size());
     up(g->finf, finf.data(), sizeof(double) * NR_NGF);
     up(g->wspeed, ws.data(), sizeof(double) * NR_NGF);

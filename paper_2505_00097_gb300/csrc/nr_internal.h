@@ -148,6 +148,7 @@ struct nr_grid {
     size_t bytes = 0;
     double dt_cfl = 0.0;
     // host copies
+    std::vector<nrk::InnerPt> inner_h;   // the inner list as uploaded (stencil-read entries first)
     std::vector<int32_t> src, cls;
     std::vector<int8_t> par;
     std::vector<double> cart_canon;  // for the puncture-distance check
