@@ -224,7 +224,8 @@ int nr_psi4(nr_grid* grid, const double* y_dev, double* psi4_dev);
  * written to modes_out (host, 2 doubles per mode: re, im).  psi4 of y_dev (NULL:
  * the grid-owned state) is sampled at ntheta Gauss-Legendre nodes in cos(theta)
  * times nphi uniform nodes in phi by cubic Lagrange interpolation in the logical
- * coordinates.  NR_EINVAL if a node's stencil reaches the outer boundary.
+ * coordinates.  NR_EINVAL if a node's stencil reaches the outer boundary or if
+ * modes x nodes ((lmax+1)^2 - 4 times ntheta*nphi) exceeds 2^26.
  * Allocates its scratch and synchronises params.stream. */
 int nr_psi4_modes(nr_grid* grid, const double* y_dev, double Rext, int ntheta, int nphi, int lmax, double* modes_out);
 

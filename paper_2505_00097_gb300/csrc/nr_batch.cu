@@ -207,7 +207,7 @@ int batch_steps(nr_batch* b, const double* dts, int nsteps, bool ssp, const char
 
 extern "C" {
 
-int nr_batch_create(nr_grid* const* grids, int ngrids, nr_batch** out)
+static int nr_batch_create_body(nr_grid* const* grids, int ngrids, nr_batch** out)
 {
     if (!out) return nrk_fail(NR_EINVAL, "out is NULL");
     *out = nullptr;
@@ -227,37 +227,47 @@ int nr_batch_create(nr_grid* const* grids, int ngrids, nr_batch** out)
             if (grids[r] == grids[q]) return nrk_fail(NR_EINVAL, "grid %d appears twice", q);
     }
     nr_batch* b = new nr_batch();
-    b->grids.assign(grids, grids + ngrids);
-    b->fam = grids[0]->geo.fam;
-    b->ord = grids[0]->K.ord;
-    b->two_point = grids[0]->K.ax >= 0;
-    b->device = grids[0]->device;
-    b->stream = grids[0]->stream;
-    DevGuard dg(b->device);
-    // parity copies of all grids that the stage stencils read (every ghost, unless the
-    // azimuth holds two points: then its ghosts are refreshed per grid on demand), from
-    // each grid's partitioned inner list
-    std::vector<BInner> inner;
-    for (int q = 0; q < ngrids; q++) {
-        const nr_grid* g = grids[q];
-        for (int t = 0; t < g->n_inner_stencil; t++) {
-            const InnerPt& p = g->inner_h[t];
-            inner.push_back(BInner{q, p.dst, p.src, p.negmask});
+    try {
+        b->grids.assign(grids, grids + ngrids);
+        b->fam = grids[0]->geo.fam;
+        b->ord = grids[0]->K.ord;
+        b->two_point = grids[0]->K.ax >= 0;
+        b->device = grids[0]->device;
+        b->stream = grids[0]->stream;
+        DevGuard dg(b->device);
+        // parity copies of all grids that the stage stencils read (every ghost, unless the
+        // azimuth holds two points: then its ghosts are refreshed per grid on demand), from
+        // each grid's partitioned inner list
+        std::vector<BInner> inner;
+        for (int q = 0; q < ngrids; q++) {
+            const nr_grid* g = grids[q];
+            for (int t = 0; t < g->n_inner_stencil; t++) {
+                const InnerPt& p = g->inner_h[t];
+                inner.push_back(BInner{q, p.dst, p.src, p.negmask});
+            }
         }
-    }
-    b->n_inner_stencil = (int)inner.size();
-    cudaError_t e = cudaMalloc(&b->d_grids, sizeof(BGrid) * ngrids);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_inner, sizeof(BInner) * std::max<size_t>(inner.size(), 1));
-    if (e == cudaSuccess && !inner.empty())
-        e = cudaMemcpy(b->d_inner, inner.data(), sizeof(BInner) * inner.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
-    if (e != cudaSuccess) {
+        b->n_inner_stencil = (int)inner.size();
+        cudaError_t e = cudaMalloc(&b->d_grids, sizeof(BGrid) * ngrids);
+        if (e == cudaSuccess) e = cudaMalloc(&b->d_inner, sizeof(BInner) * std::max<size_t>(inner.size(), 1));
+        if (e == cudaSuccess && !inner.empty())
+            e = cudaMemcpy(b->d_inner, inner.data(), sizeof(BInner) * inner.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            nr_batch_destroy(b);
+            return nrk_fail(e == cudaErrorMemoryAllocation ? NR_ENOMEM : NR_ECUDA, "batch set-up: %s",
+                            cudaGetErrorString(e));
+        }
+        *out = b;
+        return NR_OK;
+    } catch (...) {
         nr_batch_destroy(b);
-        return nrk_fail(e == cudaErrorMemoryAllocation ? NR_ENOMEM : NR_ECUDA, "batch set-up: %s",
-                        cudaGetErrorString(e));
+        throw;
     }
-    *out = b;
-    return NR_OK;
+}
+
+int nr_batch_create(nr_grid* const* grids, int ngrids, nr_batch** out)
+{
+    return nrk_guard("nr_batch_create", [&] { return nr_batch_create_body(grids, ngrids, out); });
 }
 
 void nr_batch_destroy(nr_batch* b)
@@ -286,7 +296,7 @@ int nr_batch_set_tile(nr_batch* b, int tile_x, int tile_y)
     return nrk_fail(NR_EINVAL, "tile %dx%d is not one of the compiled shapes", tile_x, tile_y);
 }
 
-int nr_batch_autotune(nr_batch* b, const double* dts, int* tile_x, int* tile_y, double* best_ms)
+static int nr_batch_autotune_body(nr_batch* b, const double* dts, int* tile_x, int* tile_y, double* best_ms)
 {
     if (!b || !dts) return nrk_fail(NR_EINVAL, "bad nr_batch_autotune arguments");
     DevGuard dg(b->device);
@@ -331,14 +341,29 @@ int nr_batch_autotune(nr_batch* b, const double* dts, int* tile_x, int* tile_y, 
     return NR_OK;
 }
 
-int nr_batch_rk4_step(nr_batch* b, const double* dts, int nsteps)
+int nr_batch_autotune(nr_batch* b, const double* dts, int* tile_x, int* tile_y, double* best_ms)
+{
+    return nrk_guard("nr_batch_autotune", [&] { return nr_batch_autotune_body(b, dts, tile_x, tile_y, best_ms); });
+}
+
+static int nr_batch_rk4_step_body(nr_batch* b, const double* dts, int nsteps)
 {
     return batch_steps(b, dts, nsteps, false, "nr_batch_rk4_step");
 }
 
-int nr_batch_ssprk3_step(nr_batch* b, const double* dts, int nsteps)
+int nr_batch_rk4_step(nr_batch* b, const double* dts, int nsteps)
+{
+    return nrk_guard("nr_batch_rk4_step", [&] { return nr_batch_rk4_step_body(b, dts, nsteps); });
+}
+
+static int nr_batch_ssprk3_step_body(nr_batch* b, const double* dts, int nsteps)
 {
     return batch_steps(b, dts, nsteps, true, "nr_batch_ssprk3_step");
+}
+
+int nr_batch_ssprk3_step(nr_batch* b, const double* dts, int nsteps)
+{
+    return nrk_guard("nr_batch_ssprk3_step", [&] { return nr_batch_ssprk3_step_body(b, dts, nsteps); });
 }
 
 }  // extern "C"

@@ -434,7 +434,7 @@ int nr_params_default(int coords, nr_params* out)
     return NR_OK;
 }
 
-int nr_build_maps(int coords, const int Nxx[3], int NG, int32_t* src, int8_t* parity, int32_t* cls)
+static int nr_build_maps_body(int coords, const int Nxx[3], int NG, int32_t* src, int8_t* parity, int32_t* cls)
 {
     nr_params p;
     nr_params_default(coords, &p);
@@ -453,7 +453,12 @@ int nr_build_maps(int coords, const int Nxx[3], int NG, int32_t* src, int8_t* pa
     return NR_OK;
 }
 
-int nr_dt_cfl(int coords, const int Nxx[3], const nr_params* params, double* dt_out)
+int nr_build_maps(int coords, const int Nxx[3], int NG, int32_t* src, int8_t* parity, int32_t* cls)
+{
+    return nrk_guard("nr_build_maps", [&] { return nr_build_maps_body(coords, Nxx, NG, src, parity, cls); });
+}
+
+static int nr_dt_cfl_body(int coords, const int Nxx[3], const nr_params* params, double* dt_out)
 {
     int rc = check_args(coords, Nxx, params);
     if (rc) return rc;
@@ -464,7 +469,12 @@ int nr_dt_cfl(int coords, const int Nxx[3], const nr_params* params, double* dt_
     return NR_OK;
 }
 
-int nr_grid_create(int coords, const int Nxx[3], const nr_params* params, nr_grid** out)
+int nr_dt_cfl(int coords, const int Nxx[3], const nr_params* params, double* dt_out)
+{
+    return nrk_guard("nr_dt_cfl", [&] { return nr_dt_cfl_body(coords, Nxx, params, dt_out); });
+}
+
+static int nr_grid_create_body(int coords, const int Nxx[3], const nr_params* params, nr_grid** out)
 {
     if (!out) return fail(NR_EINVAL, "out is NULL");
     *out = nullptr;
@@ -476,155 +486,165 @@ int nr_grid_create(int coords, const int Nxx[3], const nr_params* params, nr_gri
     int rc = check_args(coords, Nxx, &P);
     if (rc) return rc;
     nr_grid* g = new nr_grid();
-    g->P = P;
-    g->device = P.device;
-    g->stream = (cudaStream_t)P.stream;
-    geom_init(coords, Nxx, P.NG, g->geo);
-    const HostGeom& G = g->geo;
-    if ((rc = build_maps_host(G, g->src, g->par, g->cls))) { delete g; return rc; }
-    g->dt_cfl = dt_cfl_host(G, P);
+    try {
+        g->P = P;
+        g->device = P.device;
+        g->stream = (cudaStream_t)P.stream;
+        geom_init(coords, Nxx, P.NG, g->geo);
+        const HostGeom& G = g->geo;
+        if ((rc = build_maps_host(G, g->src, g->par, g->cls))) { delete g; return rc; }
+        g->dt_cfl = dt_cfl_host(G, P);
 
-    std::vector<double> a0, a1, a2;
-    build_axes(G, P, a0, a1, a2);
-    // radiation-condition data of the pure outer points, parity copies of the inner ghosts
-    std::vector<OuterPt> outer;
-    std::vector<InnerPt> inner;
-    std::vector<int> canon;
-    const int n0 = G.n[0], n1 = G.n[1];
-    for (long idx = 0; idx < G.T; idx++) {
-        const int c = g->cls[idx];
-        if (c != 2) canon.push_back((int)idx);
-        if (c == 1) {
-            const int i0 = (int)(idx % n0), i1 = (int)((idx / n0) % n1), i2 = (int)(idx / ((long)n0 * n1));
-            OuterPt o{};
-            o.idx = (int)idx;
-            double f[4];
-            // stencil kind per axis and the denominator of its integer weights
-            const bool o8 = G.NG == 5;
-            const double den = o8 ? 840.0 : 12.0;
-            auto kind = [&](int i, int n) { return o8 ? onesided_window8(i, n) : onesided_kind(i, n); };
-            if (G.fam == FAM_SPH) {
-                axis0_map(G, P, G.xx(0, i0), f);
-                o.kind = kind(i0, G.n[0]);
-                o.w0 = (1.0 / f[1]) / (den * G.dxx[0]);
-                o.w2 = 0.0;
-                o.invr = 1.0 / f[0];
-            } else {
-                double z[4];
-                radial(P.ampl[0], P.sinhw[0], 1, G.xx(0, i0), f);
-                radial(P.ampl[2], P.sinhw[2], 1, G.xx(2, i2), z);
-                const double r = sqrt(f[0] * f[0] + z[0] * z[0]);
-                o.kind = kind(i0, G.n[0]) | (kind(i2, G.n[2]) << 8);
-                o.w0 = (f[0] / r) * (1.0 / f[1]) / (den * G.dxx[0]);
-                o.w2 = (z[0] / r) * (1.0 / z[1]) / (den * G.dxx[2]);
-                o.invr = 1.0 / r;
-            }
-            (void)i1;
-            outer.push_back(o);
-        } else if (c == 2) {
-            InnerPt q{};
-            q.dst = (int)idx;
-            q.src = g->src[idx];
-            int m = 0;
-            for (int t = 0; t < 10; t++)
-                if (g->par[10 * idx + t] < 0) m |= 1 << t;
-            q.negmask = m;
-            inner.push_back(q);
-        }
-    }
-    // ghosts the RK-stage stencils read first: with a two-point azimuth (GridK::ax) the
-    // stencils of interior and pure-outer points never reach an azimuthal ghost
-    const int ax = two_point_axis(G);
-    auto read_by_stencils = [&](const InnerPt& q) {
-        if (ax < 0) return true;
-        const long idx = q.dst;
-        const int ia = ax == 1 ? (int)((idx / n0) % n1) : (int)(idx / ((long)n0 * n1));
-        return ia >= G.NG && ia < G.NG + G.N[ax];
-    };
-    std::stable_partition(inner.begin(), inner.end(), read_by_stencils);
-    g->n_inner_stencil = (int)std::count_if(inner.begin(), inner.end(), read_by_stencils);
-    g->n_outer = (int)outer.size();
-    g->n_inner = (int)inner.size();
-    g->n_canon = (long)canon.size();
-    // Cartesian positions of canonical points, for the puncture check
-    {
-        g->cart_canon.resize(3 * canon.size());
-        for (size_t t = 0; t < canon.size(); t++) {
-            const long idx = canon[t];
-            const int i0 = (int)(idx % n0), i1 = (int)((idx / n0) % n1), i2 = (int)(idx / ((long)n0 * n1));
-            double* x = &g->cart_canon[3 * t];
-            if (G.fam == FAM_SPH) {
-                const double r = a0[3 * n0 + i0], st = a1[2 * n1 + i1], ct = a1[3 * n1 + i1];
-                const double sp_ = a2[i2], cp = a2[G.n[2] + i2];
-                x[0] = r * st * cp;
-                x[1] = r * st * sp_;
-                x[2] = r * ct;
-            } else {
-                const double rho = a0[3 * n0 + i0], sp_ = a1[i1], cp = a1[n1 + i1];
-                x[0] = rho * cp;
-                x[1] = rho * sp_;
-                x[2] = a2[2 * G.n[2] + i2];
+        std::vector<double> a0, a1, a2;
+        build_axes(G, P, a0, a1, a2);
+        // radiation-condition data of the pure outer points, parity copies of the inner ghosts
+        std::vector<OuterPt> outer;
+        std::vector<InnerPt> inner;
+        std::vector<int> canon;
+        const int n0 = G.n[0], n1 = G.n[1];
+        for (long idx = 0; idx < G.T; idx++) {
+            const int c = g->cls[idx];
+            if (c != 2) canon.push_back((int)idx);
+            if (c == 1) {
+                const int i0 = (int)(idx % n0), i1 = (int)((idx / n0) % n1), i2 = (int)(idx / ((long)n0 * n1));
+                OuterPt o{};
+                o.idx = (int)idx;
+                double f[4];
+                // stencil kind per axis and the denominator of its integer weights
+                const bool o8 = G.NG == 5;
+                const double den = o8 ? 840.0 : 12.0;
+                auto kind = [&](int i, int n) { return o8 ? onesided_window8(i, n) : onesided_kind(i, n); };
+                if (G.fam == FAM_SPH) {
+                    axis0_map(G, P, G.xx(0, i0), f);
+                    o.kind = kind(i0, G.n[0]);
+                    o.w0 = (1.0 / f[1]) / (den * G.dxx[0]);
+                    o.w2 = 0.0;
+                    o.invr = 1.0 / f[0];
+                } else {
+                    double z[4];
+                    radial(P.ampl[0], P.sinhw[0], 1, G.xx(0, i0), f);
+                    radial(P.ampl[2], P.sinhw[2], 1, G.xx(2, i2), z);
+                    const double r = sqrt(f[0] * f[0] + z[0] * z[0]);
+                    o.kind = kind(i0, G.n[0]) | (kind(i2, G.n[2]) << 8);
+                    o.w0 = (f[0] / r) * (1.0 / f[1]) / (den * G.dxx[0]);
+                    o.w2 = (z[0] / r) * (1.0 / z[1]) / (den * G.dxx[2]);
+                    o.invr = 1.0 / r;
+                }
+                (void)i1;
+                outer.push_back(o);
+            } else if (c == 2) {
+                InnerPt q{};
+                q.dst = (int)idx;
+                q.src = g->src[idx];
+                int m = 0;
+                for (int t = 0; t < 10; t++)
+                    if (g->par[10 * idx + t] < 0) m |= 1 << t;
+                q.negmask = m;
+                inner.push_back(q);
             }
         }
-    }
+        // ghosts the RK-stage stencils read first: with a two-point azimuth (GridK::ax) the
+        // stencils of interior and pure-outer points never reach an azimuthal ghost
+        const int ax = two_point_axis(G);
+        auto read_by_stencils = [&](const InnerPt& q) {
+            if (ax < 0) return true;
+            const long idx = q.dst;
+            const int ia = ax == 1 ? (int)((idx / n0) % n1) : (int)(idx / ((long)n0 * n1));
+            return ia >= G.NG && ia < G.NG + G.N[ax];
+        };
+        std::stable_partition(inner.begin(), inner.end(), read_by_stencils);
+        g->n_inner_stencil = (int)std::count_if(inner.begin(), inner.end(), read_by_stencils);
+        g->n_outer = (int)outer.size();
+        g->n_inner = (int)inner.size();
+        g->n_canon = (long)canon.size();
+        // Cartesian positions of canonical points, for the puncture check
+        {
+            g->cart_canon.resize(3 * canon.size());
+            for (size_t t = 0; t < canon.size(); t++) {
+                const long idx = canon[t];
+                const int i0 = (int)(idx % n0), i1 = (int)((idx / n0) % n1), i2 = (int)(idx / ((long)n0 * n1));
+                double* x = &g->cart_canon[3 * t];
+                if (G.fam == FAM_SPH) {
+                    const double r = a0[3 * n0 + i0], st = a1[2 * n1 + i1], ct = a1[3 * n1 + i1];
+                    const double sp_ = a2[i2], cp = a2[G.n[2] + i2];
+                    x[0] = r * st * cp;
+                    x[1] = r * st * sp_;
+                    x[2] = r * ct;
+                } else {
+                    const double rho = a0[3 * n0 + i0], sp_ = a1[i1], cp = a1[n1 + i1];
+                    x[0] = rho * cp;
+                    x[1] = rho * sp_;
+                    x[2] = a2[2 * G.n[2] + i2];
+                }
+            }
+        }
 
-    DeviceGuard dg(g->device);
-    const size_t set = (size_t)NR_NGF * G.T;
-    std::vector<double> finf(P.f_inf, P.f_inf + NR_NGF), ws(P.wavespeed, P.wavespeed + NR_NGF);
-    GridK& K = g->K;
-    memset(&K, 0, sizeof K);
-    K.n0 = G.n[0]; K.n1 = G.n[1]; K.n2 = G.n[2];
-    K.N0 = G.N[0]; K.N1 = G.N[1]; K.N2 = G.N[2];
-    K.NG = G.NG;
-    K.fam = G.fam;
-    K.ax = two_point_axis(G);
-    K.ord = 2 * (G.NG - 1);
-    K.T = G.T;
-    for (int d = 0; d < 3; d++) {
-        // the denominators of the integer stencil weights (bssn_point.cuh, FD<ORD>)
-        K.inv_d1[d] = 1.0 / ((K.ord == 8 ? 840.0 : 12.0) * G.dxx[d]);
-        K.inv_d2[d] = 1.0 / ((K.ord == 8 ? 5040.0 : 12.0) * G.dxx[d] * G.dxx[d]);
-    }
-    K.sigma_metric = P.ko_sigma[0];
-    K.sigma_gauge = P.ko_sigma[17];
-    K.eta = P.eta;
-    g->nparts = ham_partials_needed(K);
-    if ((rc = dmalloc(g, &g->y, set)) || (rc = dmalloc(g, &g->ya, set)) || (rc = dmalloc(g, &g->yb, set)) ||
-        (rc = dmalloc(g, &g->acc, set)) || (rc = dmalloc(g, &g->d1x, (size_t)N_D1 * G.T)) ||
-        (rc = dmalloc(g, &g->d1y, K.ax < 0 ? (size_t)N_D1 * G.T : 1)) || (rc = dmalloc(g, &g->ax0, a0.size())) ||
-        (rc = dmalloc(g, &g->ax1, a1.size())) || (rc = dmalloc(g, &g->ax2, a2.size())) ||
-        (rc = dmalloc(g, &g->outer, outer.size())) || (rc = dmalloc(g, &g->inner, inner.size())) ||
-        (rc = dmalloc(g, &g->canon, canon.size())) || (rc = dmalloc(g, &g->finf, NR_NGF)) ||
-        (rc = dmalloc(g, &g->wspeed, NR_NGF)) || (rc = dmalloc(g, &g->partials, 3 * (size_t)g->nparts)) ||
-        (rc = dmalloc(g, &g->hres, 3)) || (rc = dmalloc(g, &g->flag, 1)) || (rc = dmalloc(g, &g->mxyz, 64))) {
+        DeviceGuard dg(g->device);
+        const size_t set = (size_t)NR_NGF * G.T;
+        std::vector<double> finf(P.f_inf, P.f_inf + NR_NGF), ws(P.wavespeed, P.wavespeed + NR_NGF);
+        GridK& K = g->K;
+        memset(&K, 0, sizeof K);
+        K.n0 = G.n[0]; K.n1 = G.n[1]; K.n2 = G.n[2];
+        K.N0 = G.N[0]; K.N1 = G.N[1]; K.N2 = G.N[2];
+        K.NG = G.NG;
+        K.fam = G.fam;
+        K.ax = two_point_axis(G);
+        K.ord = 2 * (G.NG - 1);
+        K.T = G.T;
+        for (int d = 0; d < 3; d++) {
+            // the denominators of the integer stencil weights (bssn_point.cuh, FD<ORD>)
+            K.inv_d1[d] = 1.0 / ((K.ord == 8 ? 840.0 : 12.0) * G.dxx[d]);
+            K.inv_d2[d] = 1.0 / ((K.ord == 8 ? 5040.0 : 12.0) * G.dxx[d] * G.dxx[d]);
+        }
+        K.sigma_metric = P.ko_sigma[0];
+        K.sigma_gauge = P.ko_sigma[17];
+        K.eta = P.eta;
+        g->nparts = ham_partials_needed(K);
+        if ((rc = dmalloc(g, &g->y, set)) || (rc = dmalloc(g, &g->ya, set)) || (rc = dmalloc(g, &g->yb, set)) ||
+            (rc = dmalloc(g, &g->acc, set)) || (rc = dmalloc(g, &g->d1x, (size_t)N_D1 * G.T)) ||
+            (rc = dmalloc(g, &g->d1y, K.ax < 0 ? (size_t)N_D1 * G.T : 1)) || (rc = dmalloc(g, &g->ax0, a0.size())) ||
+            (rc = dmalloc(g, &g->ax1, a1.size())) || (rc = dmalloc(g, &g->ax2, a2.size())) ||
+            (rc = dmalloc(g, &g->outer, outer.size())) || (rc = dmalloc(g, &g->inner, inner.size())) ||
+            (rc = dmalloc(g, &g->canon, canon.size())) || (rc = dmalloc(g, &g->finf, NR_NGF)) ||
+            (rc = dmalloc(g, &g->wspeed, NR_NGF)) || (rc = dmalloc(g, &g->partials, 3 * (size_t)g->nparts)) ||
+            (rc = dmalloc(g, &g->hres, 3)) || (rc = dmalloc(g, &g->flag, 1)) || (rc = dmalloc(g, &g->mxyz, 64))) {
+            free_grid(g);
+            return rc;
+        }
+        K.rfm.ax0 = g->ax0;
+        K.rfm.ax1 = g->ax1;
+        K.rfm.ax2 = g->ax2;
+        cudaError_t e = cudaSuccess;
+        auto up = [&](void* d, const void* h, size_t b) {
+            if (e == cudaSuccess && b) e = cudaMemcpy(d, h, b, cudaMemcpyHostToDevice);
+        };
+        up(g->ax0, a0.data(), sizeof(double) * a0.size());
+        up(g->ax1, a1.data(), sizeof(double) * a1.size());
+        up(g->ax2, a2.data(), sizeof(double) * a2.size());
+        up(g->outer, outer.data(), sizeof(OuterPt) * outer.size());
+        up(g->inner, inner.data(), sizeof(InnerPt) * inner.size());
+        g->inner_h = inner;
+        up(g->canon, canon.data(), sizeof(int) * canon.size());
+        up(g->finf, finf.data(), sizeof(double) * NR_NGF);
+        up(g->wspeed, ws.data(), sizeof(double) * NR_NGF);
+        if (e == cudaSuccess) e = cudaMemset(g->y, 0, sizeof(double) * set);
+        if (e == cudaSuccess) e = cudaMemset(g->acc, 0, sizeof(double) * set);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            free_grid(g);
+            return fail(NR_ECUDA, "grid upload: %s", cudaGetErrorString(e));
+        }
+        *out = g;
+        return NR_OK;
+    } catch (...) {
         free_grid(g);
-        return rc;
+        throw;
     }
-    K.rfm.ax0 = g->ax0;
-    K.rfm.ax1 = g->ax1;
-    K.rfm.ax2 = g->ax2;
-    cudaError_t e = cudaSuccess;
-    auto up = [&](void* d, const void* h, size_t b) {
-        if (e == cudaSuccess && b) e = cudaMemcpy(d, h, b, cudaMemcpyHostToDevice);
-    };
-    up(g->ax0, a0.data(), sizeof(double) * a0.size());
-    up(g->ax1, a1.data(), sizeof(double) * a1.size());
-    up(g->ax2, a2.data(), sizeof(double) * a2.size());
-    up(g->outer, outer.data(), sizeof(OuterPt) * outer.size());
-    up(g->inner, inner.data(), sizeof(InnerPt) * inner.size());
-    g->inner_h = inner;
-    up(g->canon, canon.data(), sizeof(int) * canon.size());
-    up(g->finf, finf.data(), sizeof(double) * NR_NGF);
-    up(g->wspeed, ws.data(), sizeof(double) * NR_NGF);
-    if (e == cudaSuccess) e = cudaMemset(g->y, 0, sizeof(double) * set);
-    if (e == cudaSuccess) e = cudaMemset(g->acc, 0, sizeof(double) * set);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking);
-    if (e != cudaSuccess) {
-        free_grid(g);
-        return fail(NR_ECUDA, "grid upload: %s", cudaGetErrorString(e));
-    }
-    *out = g;
-    return NR_OK;
+}
+
+int nr_grid_create(int coords, const int Nxx[3], const nr_params* params, nr_grid** out)
+{
+    return nrk_guard("nr_grid_create", [&] { return nr_grid_create_body(coords, Nxx, params, out); });
 }
 
 void nr_grid_destroy(nr_grid* grid) { free_grid(grid); }
@@ -651,8 +671,8 @@ int nr_query(const nr_grid* g, nr_grid_info* info)
     return NR_OK;
 }
 
-int nr_set_brill_lindquist(nr_grid* g, int npunct, const double* mass, const double* xyz, double perturb_amp,
-                           uint64_t seed)
+static int nr_set_brill_lindquist_body(nr_grid* g, int npunct, const double* mass, const double* xyz, double perturb_amp,
+                                       uint64_t seed)
 {
     if (!g || npunct < 0 || npunct > 16 || (npunct && (!mass || !xyz)))
         return fail(NR_EINVAL, "bad Brill-Lindquist arguments");
@@ -679,6 +699,13 @@ int nr_set_brill_lindquist(nr_grid* g, int npunct, const double* mass, const dou
     // the host array m must stay valid until the copy is done
     CUDA_OR_FAIL(cudaStreamSynchronize(g->stream));
     return NR_OK;
+}
+
+int nr_set_brill_lindquist(nr_grid* g, int npunct, const double* mass, const double* xyz, double perturb_amp,
+                           uint64_t seed)
+{
+    return nrk_guard("nr_set_brill_lindquist",
+                     [&] { return nr_set_brill_lindquist_body(g, npunct, mass, xyz, perturb_amp, seed); });
 }
 
 int nr_rhs(nr_grid* g, const double* y_dev, double* rhs_dev)

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <exception>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -158,6 +160,22 @@ struct nr_grid {
     cudaGraphExec_t exec_ssp = nullptr;   // SSPRK3 step
     double graph_dt_ssp = 0.0;
 };
+
+// A C-ABI entry point returns a status; no C++ exception (a failed host allocation)
+// may cross the C boundary.
+template <class F>
+int nrk_guard(const char* fn, F&& body) noexcept
+{
+    try {
+        return body();
+    } catch (const std::bad_alloc&) {
+        return nrk::nrk_fail(NR_ENOMEM, "%s: host memory exhausted", fn);
+    } catch (const std::exception& e) {
+        return nrk::nrk_fail(NR_EINVAL, "%s: %s", fn, e.what());
+    } catch (...) {
+        return nrk::nrk_fail(NR_EINVAL, "%s: unexpected error", fn);
+    }
+}
 
 // the parity copies of the grid-owned state that the integrators leave stale (azimuthal
 // ghosts of a two-point azimuth, read by no stencil of a step); stream-ordered

@@ -383,7 +383,7 @@ int nr_psi4(nr_grid* g, const double* y_dev, double* psi4_dev)
     return NR_OK;
 }
 
-int nr_psi4_modes(nr_grid* g, const double* y_dev, double Rext, int ntheta, int nphi, int lmax, double* modes_out)
+static int nr_psi4_modes_body(nr_grid* g, const double* y_dev, double Rext, int ntheta, int nphi, int lmax, double* modes_out)
 {
     if (!g || !modes_out || !(Rext > 0.0) || ntheta < 1 || nphi < 1 || lmax < 2 || lmax > 16 ||
         (long)ntheta * nphi > (1L << 24))
@@ -395,6 +395,9 @@ int nr_psi4_modes(nr_grid* g, const double* y_dev, double Rext, int ntheta, int 
     const int nq = ntheta * nphi;
     int nmodes = 0;
     for (int l = 2; l <= lmax; l++) nmodes += 2 * l + 1;
+    if ((long)nmodes * nq > (1L << 26))
+        return nrk_fail(NR_EINVAL, "nr_psi4_modes: %d modes x %d nodes exceed the 2^26 harmonic table entries", nmodes,
+                        nq);
     std::vector<SpherePt> pts(nq);
     std::vector<double> wy(2L * nmodes * nq);
     // w_q sqrt((2l+1)/4pi) d^l_{m,2}(theta) depends on the theta node only
@@ -473,6 +476,12 @@ int nr_psi4_modes(nr_grid* g, const double* y_dev, double Rext, int ntheta, int 
     cudaFree(dpts);
     if (e != cudaSuccess) return nrk_fail(NR_ECUDA, "nr_psi4_modes: %s", cudaGetErrorString(e));
     return NR_OK;
+}
+
+int nr_psi4_modes(nr_grid* g, const double* y_dev, double Rext, int ntheta, int nphi, int lmax, double* modes_out)
+{
+    return nrk_guard("nr_psi4_modes",
+                     [&] { return nr_psi4_modes_body(g, y_dev, Rext, ntheta, nphi, lmax, modes_out); });
 }
 
 }  // extern "C"

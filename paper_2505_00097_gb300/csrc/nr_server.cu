@@ -280,7 +280,7 @@ int rebuild_batch(nr_server* s)
 
 extern "C" {
 
-int nr_server_create(size_t hbm_budget_bytes, int max_slots, int device, void* stream, nr_server** out)
+static int nr_server_create_body(size_t hbm_budget_bytes, int max_slots, int device, void* stream, nr_server** out)
 {
     if (!out || max_slots < 1 || hbm_budget_bytes == 0) return nrk_fail(NR_EINVAL, "bad nr_server_create arguments");
     nr_server* s = new nr_server();
@@ -290,6 +290,12 @@ int nr_server_create(size_t hbm_budget_bytes, int max_slots, int device, void* s
     s->stream = stream;
     *out = s;
     return NR_OK;
+}
+
+int nr_server_create(size_t hbm_budget_bytes, int max_slots, int device, void* stream, nr_server** out)
+{
+    return nrk_guard("nr_server_create",
+                     [&] { return nr_server_create_body(hbm_budget_bytes, max_slots, device, stream, out); });
 }
 
 void nr_server_destroy(nr_server* s)
@@ -314,8 +320,8 @@ int nr_server_set_tile(nr_server* s, int tile_x, int tile_y)
     return NR_OK;
 }
 
-int nr_server_submit(nr_server* s, int coords, const int Nxx[3], const nr_params* params, int npunct,
-                     const double* mass, const double* xyz, double t_final, int keep_state, int64_t* id_out)
+static int nr_server_submit_body(nr_server* s, int coords, const int Nxx[3], const nr_params* params, int npunct,
+                                 const double* mass, const double* xyz, double t_final, int keep_state, int64_t* id_out)
 {
     if (!s || !Nxx || !params || npunct < 0 || npunct > 16 || (npunct && (!mass || !xyz)) || !(t_final > 0.0))
         return nrk_fail(NR_EINVAL, "bad nr_server_submit arguments");
@@ -350,6 +356,14 @@ int nr_server_submit(nr_server* s, int coords, const int Nxx[3], const nr_params
     return NR_OK;
 }
 
+int nr_server_submit(nr_server* s, int coords, const int Nxx[3], const nr_params* params, int npunct,
+                     const double* mass, const double* xyz, double t_final, int keep_state, int64_t* id_out)
+{
+    return nrk_guard("nr_server_submit", [&] {
+        return nr_server_submit_body(s, coords, Nxx, params, npunct, mass, xyz, t_final, keep_state, id_out);
+    });
+}
+
 int nr_server_set_policy(nr_server* s, int policy, int64_t max_batch_points)
 {
     if (!s) return nrk_fail(NR_EINVAL, "server is NULL");
@@ -360,7 +374,7 @@ int nr_server_set_policy(nr_server* s, int policy, int64_t max_batch_points)
     return NR_OK;
 }
 
-int nr_server_advance(nr_server* s, int nsteps, int* n_running, int* n_queued)
+static int nr_server_advance_body(nr_server* s, int nsteps, int* n_running, int* n_queued)
 {
     if (!s || nsteps < 0) return nrk_fail(NR_EINVAL, "bad nr_server_advance arguments");
     int rc = admit(s);
@@ -405,6 +419,11 @@ int nr_server_advance(nr_server* s, int nsteps, int* n_running, int* n_queued)
     return NR_OK;
 }
 
+int nr_server_advance(nr_server* s, int nsteps, int* n_running, int* n_queued)
+{
+    return nrk_guard("nr_server_advance", [&] { return nr_server_advance_body(s, nsteps, n_running, n_queued); });
+}
+
 int nr_server_poll(nr_server* s, int64_t id, int* status, int64_t* steps_done, int64_t* steps_total, double* l2,
                    double* linf)
 {
@@ -420,7 +439,7 @@ int nr_server_poll(nr_server* s, int64_t id, int* status, int64_t* steps_done, i
     return NR_OK;
 }
 
-int nr_server_fetch_state(nr_server* s, int64_t id, double* host_state, size_t capacity_doubles)
+static int nr_server_fetch_state_body(nr_server* s, int64_t id, double* host_state, size_t capacity_doubles)
 {
     if (!s || !host_state) return nrk_fail(NR_EINVAL, "bad nr_server_fetch_state arguments");
     auto it = s->all.find(id);
@@ -430,6 +449,12 @@ int nr_server_fetch_state(nr_server* s, int64_t id, double* host_state, size_t c
     if (capacity_doubles < r->state.size()) return nrk_fail(NR_EINVAL, "buffer too small");
     memcpy(host_state, r->state.data(), sizeof(double) * r->state.size());
     return NR_OK;
+}
+
+int nr_server_fetch_state(nr_server* s, int64_t id, double* host_state, size_t capacity_doubles)
+{
+    return nrk_guard("nr_server_fetch_state",
+                     [&] { return nr_server_fetch_state_body(s, id, host_state, capacity_doubles); });
 }
 
 }  // extern "C"

@@ -120,3 +120,6 @@ def test_bad_spheres_and_orders_are_refused():
         g.psi4_modes(1.0, 8, 16, 17)
     with pytest.raises(B.NrError):
         g.psi4_modes(-1.0, 8, 16, 4)
+    # 285 modes x 8e6 nodes: refused before any table is built
+    with pytest.raises(B.NrError, match="2\\^26"):
+        g.psi4_modes(1.0, 2000, 4000, 16)
