@@ -421,11 +421,35 @@ def run_ours(args, spec, world, rank, local):
 
         nc = g.info.n_state_points
         stepper = "nr_ssprk3_step" if ssp else "nr_rk4_step"
-        v, nbytes = e2e_run(nc, g.set_state_compact, g.get_state_compact, args.warmup + args.steps)
-        vf, fbytes = e2e_run(T, g.set_state, g.get_state, args.warmup + args.steps + n_e2e)
+        integ = "ssprk3" if ssp else "rk4"
+
+        def io_run(start):
+            """nr_step_io: the compact state in from pinned host memory, one step, the new compact
+            state written to pinned host memory by the step's last stage"""
+            host_in = torch.empty(24 * nc, dtype=torch.float64).pin_memory()
+            host_out = torch.empty(24 * nc, dtype=torch.float64).pin_memory()
+            g.get_state_compact(host_in.data_ptr(), True)
+            if dist is not None:
+                dist.barrier()
+            t0 = time.perf_counter()
+            for s in range(n_e2e):
+                g.step_io(dt, 1, host_in.data_ptr(), host_out.data_ptr(), integ)
+                if h_every and (start + s + 1) % h_every == 0:
+                    g.hamiltonian()
+                host_in, host_out = host_out, host_in
+            torch.cuda.synchronize()
+            el = reduce_max(dist, time.perf_counter() - t0, dev)
+            return world * pts * substeps * n_e2e / el, 24 * nc * 8
+
+        v, nbytes = io_run(args.warmup + args.steps)
+        vc, _ = e2e_run(nc, g.set_state_compact, g.get_state_compact, args.warmup + args.steps + n_e2e)
+        vf, fbytes = e2e_run(T, g.set_state, g.get_state, args.warmup + args.steps + 2 * n_e2e)
         e2e = {"value": v, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "steps": n_e2e,
-               "path": f"nr_set_state_compact(pinned host) + {stepper} + nr_get_state_compact(pinned host) per step "
-                       f"({nc} interior + pure outer points of {T})",
+               "path": f"nr_step_io per step: compact state ({nc} interior + pure outer points of {T}) uploaded from "
+                       f"pinned host memory, one {integ.upper()} step, the new compact state stored to pinned host "
+                       "memory by the step's last stage",
+               "separate_calls": {"value": vc, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+                                  "path": f"nr_set_state_compact + {stepper} + nr_get_state_compact per step"},
                "full_state": {"value": vf, "h2d_bytes_per_step": fbytes, "d2h_bytes_per_step": fbytes,
                               "path": f"nr_set_state(pinned host) + {stepper} + nr_get_state(pinned host) per step"}}
 

@@ -249,6 +249,18 @@ int nr_set_state(nr_grid* grid, const double* src, int from_host);
 int nr_get_state_compact(nr_grid* grid, double* dst, int to_host);
 int nr_set_state_compact(nr_grid* grid, const double* src, int from_host);
 
+/* Host-resident stepping: nr_set_state_compact(host_in) (skipped if NULL), then
+ * nsteps >= 1 steps of integrator (NR_RK4 or NR_SSPRK3) at dt, then the new
+ * compact state into host_out (skipped if NULL); returns when host_out is
+ * written.  Same results, bit for bit, as those calls one after another.
+ * When host_out is pinned (page-locked, hence mapped) host memory, the last
+ * stage of the last step stores each point's new values there itself, over the
+ * host link while the stage computes, so the read-back costs no separate copy;
+ * other host memory takes the gather-and-copy path.  The first such call
+ * allocates a rank table of T ints on the device.  Errors: NR_EINVAL,
+ * NR_ENOMEM, NR_ECUDA. */
+int nr_step_io(nr_grid* grid, int integrator, double dt, int nsteps, const double* host_in, double* host_out);
+
 /* Wait for all work of the grid's stream. */
 int nr_sync(nr_grid* grid);
 

@@ -25,7 +25,7 @@ INTEGRATORS = {"rk4": 0, "ssprk3": 1}
 EXPORTS = (
     "nr_params_default", "nr_grid_create", "nr_grid_destroy", "nr_query", "nr_set_brill_lindquist", "nr_rhs",
     "nr_apply_bcs", "nr_apply_inner_bcs", "nr_rk4_step", "nr_ssprk3_step", "nr_hamiltonian", "nr_momentum",
-    "nr_psi4", "nr_psi4_modes", "nr_get_state", "nr_get_state_compact", "nr_set_state_compact",
+    "nr_psi4", "nr_psi4_modes", "nr_get_state", "nr_get_state_compact", "nr_set_state_compact", "nr_step_io",
     "nr_set_state",
     "nr_sync", "nr_check_finite", "nr_build_maps", "nr_dt_cfl", "nr_fp64_peak", "nr_hamiltonian_noalloc",
     "nr_batch_create", "nr_batch_destroy", "nr_batch_set_tile", "nr_batch_autotune", "nr_batch_rk4_step", "nr_batch_ssprk3_step",
@@ -114,6 +114,7 @@ def lib() -> ctypes.CDLL:
     L.nr_set_state.argtypes = [vp, vp, ctypes.c_int]
     L.nr_get_state_compact.argtypes = [vp, vp, ctypes.c_int]
     L.nr_set_state_compact.argtypes = [vp, vp, ctypes.c_int]
+    L.nr_step_io.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, vp, vp]
     L.nr_sync.argtypes = [vp]
     L.nr_check_finite.argtypes = [vp]
     L.nr_build_maps.argtypes = [ctypes.c_int, ip, ctypes.c_int, ctypes.POINTER(ctypes.c_int32),
@@ -321,6 +322,16 @@ class Grid:
     def set_state_compact(self, src, from_host: bool) -> None:
         addr = src.ctypes.data if isinstance(src, np.ndarray) else (src.data_ptr() if not isinstance(src, int) else src)
         _check(lib().nr_set_state_compact(self.h, addr, int(bool(from_host))))
+
+    def step_io(self, dt: float, nsteps: int = 1, host_in=None, host_out=None, integrator: str = "rk4") -> None:
+        """nr_step_io: compact state in from host_in, nsteps steps, compact state out to host_out
+        (numpy arrays, pinned torch CPU tensors or raw addresses; None skips)."""
+        def addr(a):
+            if a is None or isinstance(a, int):
+                return a
+            return a.ctypes.data if isinstance(a, np.ndarray) else a.data_ptr()
+        _check(lib().nr_step_io(self.h, INTEGRATORS[integrator], float(dt), int(nsteps), addr(host_in),
+                                addr(host_out)))
 
     def sync(self) -> None:
         _check(lib().nr_sync(self.h))

@@ -338,7 +338,7 @@ void free_grid(nr_grid* g)
     if (g->exec) cudaGraphExecDestroy(g->exec);
     if (g->exec_ssp) cudaGraphExecDestroy(g->exec_ssp);
     void* ptrs[] = {g->y, g->ya, g->yb, g->acc, g->d1x, g->d1y, g->ax0, g->ax1, g->ax2, g->outer, g->inner, g->canon,
-                    g->finf, g->wspeed, g->partials, g->hres, g->flag, g->mxyz, g->stage};
+                    g->finf, g->wspeed, g->partials, g->hres, g->flag, g->mxyz, g->stage, g->crank};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (g->cap) cudaStreamDestroy(g->cap);
@@ -369,13 +369,19 @@ int enqueue_stage(nr_grid* g, cudaStream_t s, const double* yin, double* out, co
 
 // one classic RK4 step: y1 = y + dt/2 k1, y2 = y + dt/2 k2, y3 = y + dt k3,
 // y_{n+1} = y + dt/6 (k1 + 2 k2 + 2 k3 + k4), accumulated in acc
-int enqueue_rk4(nr_grid* g, cudaStream_t s, double dt)
+// mirror (may be NULL): host-mirror fields for the last stage (nr_step_io)
+int enqueue_rk4(nr_grid* g, cudaStream_t s, double dt, const Stage* mirror = nullptr)
 {
     const int enf = g->P.enforce_detgb;
     Stage s1{MODE_STAGE1, enf, 0.5 * dt, dt / 6.0};
     Stage s2{MODE_STAGE23, enf, 0.5 * dt, dt / 3.0};
     Stage s3{MODE_STAGE23, enf, dt, dt / 3.0};
     Stage s4{MODE_STAGE4, enf, 0.0, dt / 6.0};
+    if (mirror) {
+        s4.mirror = mirror->mirror;
+        s4.rank = mirror->rank;
+        s4.mirror_n = mirror->mirror_n;
+    }
     int rc;
     // every stage copies only the ghosts the stencils read; the rest of y_{n+1}'s are
     // refreshed on demand (refresh_ghosts)
@@ -389,12 +395,17 @@ int enqueue_rk4(nr_grid* g, cudaStream_t s, double dt)
 
 // one SSPRK3 step (Gottlieb-Shu-Tadmor): y1 = y + dt k(y), y2 = 3/4 y + 1/4 (y1 + dt k(y1)),
 // y_{n+1} = 1/3 y + 2/3 (y2 + dt k(y2)), the last stage in place
-int enqueue_ssprk3(nr_grid* g, cudaStream_t s, double dt)
+int enqueue_ssprk3(nr_grid* g, cudaStream_t s, double dt, const Stage* mirror = nullptr)
 {
     const int enf = g->P.enforce_detgb;
     Stage s1{MODE_SSP, enf, dt, 1.0, 0.0};
     Stage s2{MODE_SSP, enf, dt, 0.25, 0.75};
     Stage s3{MODE_SSP, enf, dt, 2.0 / 3.0, 1.0 / 3.0};
+    if (mirror) {
+        s3.mirror = mirror->mirror;
+        s3.rank = mirror->rank;
+        s3.mirror_n = mirror->mirror_n;
+    }
     int rc;
     const int ns = g->n_inner_stencil;
     if ((rc = enqueue_stage(g, s, g->y, g->ya, g->y, nullptr, s1, ns))) return rc;
@@ -881,6 +892,51 @@ int nr_set_state_compact(nr_grid* g, const double* src, int from_host)
     g->ghosts_stale = g->n_inner > g->n_inner_stencil;
     if (from_host) CUDA_OR_FAIL(cudaStreamSynchronize(g->stream));
     return NR_OK;
+}
+
+static int nr_step_io_body(nr_grid* g, int integrator, double dt, int nsteps, const double* host_in, double* host_out)
+{
+    if (!g || !(dt > 0.0) || nsteps < 1 || (integrator != NR_RK4 && integrator != NR_SSPRK3))
+        return fail(NR_EINVAL, "bad nr_step_io arguments");
+    DeviceGuard dg(g->device);
+    int rc;
+    if (host_in && (rc = nr_set_state_compact(g, host_in, 1))) return rc;
+    auto steps = [&](int n) { return integrator == NR_SSPRK3 ? nr_ssprk3_step(g, dt, n) : nr_rk4_step(g, dt, n); };
+    if (nsteps > 1 && (rc = steps(nsteps - 1))) return rc;
+    cudaPointerAttributes a{};
+    void* mapped = nullptr;
+    if (host_out && cudaPointerGetAttributes(&a, host_out) == cudaSuccess && a.type == cudaMemoryTypeHost)
+        mapped = a.devicePointer;
+    cudaGetLastError();   // an unregistered pointer leaves no error behind
+    if (!mapped) {
+        if ((rc = steps(1))) return rc;
+        if (host_out) return nr_get_state_compact(g, host_out, 1);
+        CUDA_OR_FAIL(cudaStreamSynchronize(g->stream));
+        return NR_OK;
+    }
+    if (!g->crank) {
+        std::vector<int> r(g->geo.T, -1);
+        int t = 0;
+        for (long idx = 0; idx < g->geo.T; idx++)
+            if (g->cls[idx] != 2) r[idx] = t++;
+        CUDA_OR_FAIL(cudaMalloc(&g->crank, sizeof(int) * r.size()));
+        CUDA_OR_FAIL(cudaMemcpy(g->crank, r.data(), sizeof(int) * r.size(), cudaMemcpyHostToDevice));
+    }
+    // the last step launched directly, its last stage writing the compact state to host_out
+    Stage m{};
+    m.mirror = (double*)mapped;
+    m.rank = g->crank;
+    m.mirror_n = g->n_canon;
+    rc = integrator == NR_SSPRK3 ? enqueue_ssprk3(g, g->stream, dt, &m) : enqueue_rk4(g, g->stream, dt, &m);
+    if (rc) return rc;
+    g->ghosts_stale = g->n_inner > g->n_inner_stencil;
+    CUDA_OR_FAIL(cudaStreamSynchronize(g->stream));
+    return NR_OK;
+}
+
+int nr_step_io(nr_grid* g, int integrator, double dt, int nsteps, const double* host_in, double* host_out)
+{
+    return nrk_guard("nr_step_io", [&] { return nr_step_io_body(g, integrator, dt, nsteps, host_in, host_out); });
 }
 
 int nr_sync(nr_grid* g)

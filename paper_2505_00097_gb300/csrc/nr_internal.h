@@ -67,6 +67,11 @@ struct Stage {
     double cnext;
     double cacc;
     double cyn;
+    // last stage of nr_step_io: the new state of every computed point also goes to the
+    // caller's mapped host buffer, compact layout mirror[g * mirror_n + rank[idx]]
+    double* mirror = nullptr;
+    const int* rank = nullptr;
+    long mirror_n = 0;
 };
 
 // Pure-outer points whose radiation condition runs inside the k_rhs launch
@@ -138,6 +143,7 @@ struct nr_grid {
     int* flag = nullptr;
     double* mxyz = nullptr;
     double* stage = nullptr;   // compact-state staging for host transfers (allocated on first use)
+    int* crank = nullptr;      // compact position of each point, -1 at inner ghosts (first nr_step_io)
     int n_outer = 0, n_inner = 0, nparts = 0;
     // inner ghosts read by the stencils of an RK stage: the first n_inner_stencil
     // entries of inner (all of them unless the azimuth holds two points; then the

@@ -77,6 +77,11 @@ __device__ __forceinline__ void stage_store(const Stage& st, long T, long idx, c
     if (st.enforce) enforce_det(v);
 #pragma unroll
     for (int g = 0; g < NGF; g++) out[g * T + idx] = v[g];
+    if (st.mirror) {
+        const long r = st.rank[idx];
+#pragma unroll
+        for (int g = 0; g < NGF; g++) st.mirror[g * st.mirror_n + r] = v[g];
+    }
 }
 
 // one-sided / centred first-derivative stencil sums (weights of 12 h f')

@@ -139,3 +139,35 @@ def test_stale_azimuthal_ghosts_are_refreshed_before_use():
     types = [4, 5, 6, 7, 8, 9, 4, 5, 6, 7, 8, 9, 0, 0, 1, 2, 3, 1, 2, 3, 1, 2, 3, 0]
     for gf in range(24):
         assert np.array_equal(yh[gf, gh], par[gh, types[gf]] * yh[gf, src[gh]])
+
+
+@pytest.mark.parametrize("integrator", ["rk4", "ssprk3"])
+@pytest.mark.parametrize("spec", [SPECS[0], SPECS[2], SPECS[1]], ids=["cyl2", "cyl2-o8", "sph3d"])
+def test_step_io_equals_the_separate_calls(spec, integrator):
+    """nr_step_io (upload, steps, read-back by the last stage into pinned host memory; or the
+    gather-and-copy path for pageable memory) gives bit for bit what nr_set_state_compact, the
+    steps and nr_get_state_compact give."""
+    masses, pos = (0.6, 0.4), ((0.0, 0.0, 0.45), (0.0, 0.0, -0.55))
+    g0 = B.Grid(spec)
+    g0.set_brill_lindquist(masses, pos, 1e-8, 5)
+    nc = g0.info.n_state_points
+    c0 = np.empty(24 * nc)
+    g0.get_state_compact(c0, True)
+    dt = g0.dt_cfl
+    step = g0.ssprk3_step if integrator == "ssprk3" else g0.rk4_step
+    g0.set_state_compact(c0, True)
+    step(dt, 3)
+    ref = np.empty(24 * nc)
+    g0.get_state_compact(ref, True)
+    full_ref = np.empty(24 * g0.T)
+    g0.get_state(full_ref, True)
+    pinned_in = torch.from_numpy(c0).pin_memory()
+    for out in (torch.zeros(24 * nc, dtype=torch.float64).pin_memory(), np.zeros(24 * nc)):
+        g = B.Grid(spec)
+        g.step_io(dt, 3, pinned_in, out, integrator)
+        got = out.numpy() if isinstance(out, torch.Tensor) else out
+        assert np.array_equal(got.view(np.uint64), ref.view(np.uint64))
+        full = np.empty(24 * g.T)
+        g.get_state(full, True)
+        assert np.array_equal(full.view(np.uint64), full_ref.view(np.uint64))
+        g.close()
