@@ -113,8 +113,8 @@ typedef struct {
     int64_t n_inner;   /* inner ghost points (parity copies) */
     double dt_cfl;     /* cfl * min over interior points and axes of |S_d| dxx_d */
     size_t device_bytes; /* device memory held by the grid */
-    int64_t n_inner_stencil; /* inner ghosts the RK stages before the last copy (all, unless the
-                                azimuth holds two points: then its ghosts are copied in stage 4 only) */
+    int64_t n_inner_stencil; /* inner ghosts every RK stage copies (all, unless the azimuth holds
+                                two points: then its ghosts are refreshed on demand, see nr_rk4_step) */
     int launches_per_step;   /* kernel launches of one nr_rk4_step (the on-demand ghost refresh
                                 described at nr_rk4_step is one more, outside the step) */
     int launches_per_ssprk3_step; /* kernel launches of one nr_ssprk3_step */

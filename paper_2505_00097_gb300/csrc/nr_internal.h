@@ -147,7 +147,7 @@ struct nr_grid {
     int n_outer = 0, n_inner = 0, nparts = 0;
     // inner ghosts read by the stencils of an RK stage: the first n_inner_stencil
     // entries of inner (all of them unless the azimuth holds two points; then the
-    // azimuthal ghosts, read by nothing within a step, are copied in stage 4 only)
+    // azimuthal ghosts, read by nothing within a step, are refreshed on demand)
     int n_inner_stencil = 0;
     // the azimuthal ghosts of the grid-owned state (entries n_inner_stencil.. of inner) lag
     // behind after nr_rk4_step / nr_ssprk3_step; refresh_ghosts copies them before any use
