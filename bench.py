@@ -53,8 +53,8 @@ UNIT = "point-updates/s"
 # A workload without a capture reports no FLOP rate.
 F_ALG = {"headon": 3212.3, "large3d": 4318.9, "headon8": 4129.9}
 # DRAM bytes (read + write) of the same two launches in that capture, or None
-TRAFFIC = {"headon": 24018432 + 86784 + 83933440 + 275405824,
-           "headon8": 24949760 + 130048 + 87550464 + 332789504}
+TRAFFIC = {"headon": 24016640 + 90880 + 83629056 + 279618560,
+           "headon8": 24949248 + 122368 + 87210496 + 350553856}
 # The same for the diagnostics (Hamiltonian and momentum constraints, psi4), per interior
 # point of one call, from one ncu capture of those kernels, by workload (head-on: k_ham 416 /
 # 258 / 651 DADD / DMUL / DFMA, k_mom 137 / 162 / 269, k_psi4 551 / 505 / 1103; the reductions
