@@ -69,8 +69,7 @@ int build_table(nr_batch* b, const double* dts, bool ssp)
     int w = 0;
     for (size_t q = 0; q < b->grids.size(); q++) {
         nr_grid* g = b->grids[q];
-        BGrid& B = h[q];
-        memset(&B, 0, sizeof B);
+        BGrid& B = h[q];   // value-initialised by the vector
         B.K = g->K;
         B.y = g->y;
         B.ya = g->ya;
@@ -97,10 +96,10 @@ int build_table(nr_batch* b, const double* dts, bool ssp)
             B.st[1] = Stage{MODE_SSP, enf, dt, 0.25, 0.75};
             B.st[2] = Stage{MODE_SSP, enf, dt, 2.0 / 3.0, 1.0 / 3.0};
         } else {
-            B.st[0] = Stage{MODE_STAGE1, enf, 0.5 * dt, dt / 6.0};
-            B.st[1] = Stage{MODE_STAGE23, enf, 0.5 * dt, dt / 3.0};
-            B.st[2] = Stage{MODE_STAGE23, enf, dt, dt / 3.0};
-            B.st[3] = Stage{MODE_STAGE4, enf, 0.0, dt / 6.0};
+            B.st[0] = Stage{MODE_STAGE1, enf, 0.5 * dt, dt / 6.0, 0.0};
+            B.st[1] = Stage{MODE_STAGE23, enf, 0.5 * dt, dt / 3.0, 0.0};
+            B.st[2] = Stage{MODE_STAGE23, enf, dt, dt / 3.0, 0.0};
+            B.st[3] = Stage{MODE_STAGE4, enf, 0.0, dt / 6.0, 0.0};
         }
     }
     b->total = w;

@@ -373,10 +373,10 @@ int enqueue_stage(nr_grid* g, cudaStream_t s, const double* yin, double* out, co
 int enqueue_rk4(nr_grid* g, cudaStream_t s, double dt, const Stage* mirror = nullptr)
 {
     const int enf = g->P.enforce_detgb;
-    Stage s1{MODE_STAGE1, enf, 0.5 * dt, dt / 6.0};
-    Stage s2{MODE_STAGE23, enf, 0.5 * dt, dt / 3.0};
-    Stage s3{MODE_STAGE23, enf, dt, dt / 3.0};
-    Stage s4{MODE_STAGE4, enf, 0.0, dt / 6.0};
+    Stage s1{MODE_STAGE1, enf, 0.5 * dt, dt / 6.0, 0.0};
+    Stage s2{MODE_STAGE23, enf, 0.5 * dt, dt / 3.0, 0.0};
+    Stage s3{MODE_STAGE23, enf, dt, dt / 3.0, 0.0};
+    Stage s4{MODE_STAGE4, enf, 0.0, dt / 6.0, 0.0};
     if (mirror) {
         s4.mirror = mirror->mirror;
         s4.rank = mirror->rank;
@@ -723,7 +723,7 @@ int nr_rhs(nr_grid* g, const double* y_dev, double* rhs_dev)
 {
     if (!g || !y_dev || !rhs_dev || y_dev == rhs_dev) return fail(NR_EINVAL, "bad nr_rhs arguments");
     DeviceGuard dg(g->device);
-    Stage st{MODE_RHS, 0, 0.0, 0.0};
+    Stage st{MODE_RHS, 0, 0.0, 0.0, 0.0};
     CUDA_OR_FAIL(launch_rhs(g->K, y_dev, g->d1x, g->d1y, rhs_dev, nullptr, nullptr, st, g->stream));
     return NR_OK;
 }
@@ -732,7 +732,7 @@ int nr_apply_bcs(nr_grid* g, const double* y_dev, double* rhs_dev)
 {
     if (!g || !y_dev || !rhs_dev || y_dev == rhs_dev) return fail(NR_EINVAL, "bad nr_apply_bcs arguments");
     DeviceGuard dg(g->device);
-    Stage st{MODE_RHS, 0, 0.0, 0.0};
+    Stage st{MODE_RHS, 0, 0.0, 0.0, 0.0};
     CUDA_OR_FAIL(launch_outer(g->K, g->outer, g->n_outer, y_dev, rhs_dev, nullptr, nullptr, g->finf, g->wspeed, st,
                               g->stream));
     CUDA_OR_FAIL(launch_inner(g->K, g->inner, g->n_inner, rhs_dev, g->stream));
