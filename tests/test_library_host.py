@@ -190,3 +190,50 @@ def test_header_is_plain_c_and_the_example_links(tmp_path):
                         "-o", str(tmp_path / "example"), lib, "-Wl,-rpath," + os.path.dirname(lib)],
                        capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_null_handles_are_refused_by_every_entry_point():
+    """Every entry point that takes a grid, batch or server handle returns NR_EINVAL (and a
+    message) for a NULL handle instead of touching memory; destroy calls accept NULL."""
+    L = B.lib()
+    d = ctypes.c_double()
+    i = ctypes.c_int()
+    i64 = ctypes.c_int64()
+    calls = {
+        "nr_query": (None, None),
+        "nr_set_brill_lindquist": (None, 0, None, None, 0.0, 0),
+        "nr_rhs": (None, None, None),
+        "nr_apply_bcs": (None, None, None),
+        "nr_apply_inner_bcs": (None, None),
+        "nr_rk4_step": (None, 0.1, 1),
+        "nr_ssprk3_step": (None, 0.1, 1),
+        "nr_hamiltonian": (None, None, None, ctypes.byref(d), ctypes.byref(d)),
+        "nr_momentum": (None, None, None, ctypes.byref(d), ctypes.byref(d)),
+        "nr_psi4": (None, None, None),
+        "nr_psi4_modes": (None, None, 1.0, 8, 16, 4, None),
+        "nr_get_state": (None, None, 1),
+        "nr_set_state": (None, None, 1),
+        "nr_get_state_compact": (None, None, 1),
+        "nr_set_state_compact": (None, None, 1),
+        "nr_step_io": (None, 0, 0.1, 1, None, None),
+        "nr_sync": (None,),
+        "nr_check_finite": (None,),
+        "nr_batch_set_tile": (None, 32, 4),
+        "nr_batch_autotune": (None, None, None, None, None),
+        "nr_batch_rk4_step": (None, None, 1),
+        "nr_batch_ssprk3_step": (None, None, 1),
+        "nr_server_set_tile": (None, 32, 4),
+        "nr_server_set_policy": (None, 0, 0),
+        "nr_server_submit": (None, 0, None, None, 0, None, None, 1.0, 0, ctypes.byref(i64)),
+        "nr_server_advance": (None, 1, ctypes.byref(i), ctypes.byref(i)),
+        "nr_server_poll": (None, 0, ctypes.byref(i), ctypes.byref(i64), ctypes.byref(i64), ctypes.byref(d),
+                           ctypes.byref(d)),
+        "nr_server_fetch_state": (None, 0, None, 0),
+    }
+    for name, args in calls.items():
+        fn = getattr(L, name)
+        assert fn(*args) == 1, name
+        assert L.nr_last_error(), name
+    L.nr_grid_destroy(None)
+    L.nr_batch_destroy(None)
+    L.nr_server_destroy(None)
