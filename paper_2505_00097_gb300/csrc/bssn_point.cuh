@@ -246,6 +246,19 @@ __device__ __forceinline__ double contract6(const double gw[6], const double H[6
     return t;
 }
 
+// ---- exact scaling by 2^K on the integer pipe.  The FP64 pipe bounds every kernel of the
+// point code and the integer pipe idles, so x * 2^K moves the exponent field of a normal
+// number by K instead of issuing an FP64 multiply; the result is the same bits.  Zeros,
+// infinities and NaNs pass through unchanged (so do denormals, which no BSSN state holds);
+// a result that would leave the normal range is not rounded to zero or infinity.
+template <int K>
+__device__ __forceinline__ double sc2(double x)
+{
+    const int hi = __double2hiint(x), lo = __double2loint(x);
+    const unsigned e = ((unsigned)hi >> 20) & 0x7FFu;
+    return __hiloint2double(e - 1u < 0x7FEu ? hi + K * (1 << 20) : hi, lo);
+}
+
 // ---- rotation generators acting on vectors / symmetric tensors: out += c * J_pq (.)
 __device__ __forceinline__ void j01v(double c, const double V[3], double o[3]) { o[1] = fma(c, V[0], o[1]); o[0] = fma(-c, V[1], o[0]); }
 __device__ __forceinline__ void j02v(double c, const double V[3], double o[3]) { o[2] = fma(c, V[0], o[2]); o[0] = fma(-c, V[2], o[0]); }
@@ -253,7 +266,7 @@ __device__ __forceinline__ void j12v(double c, const double V[3], double o[3]) {
 
 __device__ __forceinline__ void j01s(double c, const double T[6], double o[6])
 {
-    double c2 = c + c;
+    const double c2 = sc2<1>(c);
     o[0] = fma(-c2, T[1], o[0]);
     o[1] = fma(c, T[0] - T[3], o[1]);
     o[2] = fma(-c, T[4], o[2]);
@@ -262,7 +275,7 @@ __device__ __forceinline__ void j01s(double c, const double T[6], double o[6])
 }
 __device__ __forceinline__ void j02s(double c, const double T[6], double o[6])
 {
-    double c2 = c + c;
+    const double c2 = sc2<1>(c);
     o[0] = fma(-c2, T[2], o[0]);
     o[1] = fma(-c, T[4], o[1]);
     o[2] = fma(c, T[0] - T[5], o[2]);
@@ -271,7 +284,7 @@ __device__ __forceinline__ void j02s(double c, const double T[6], double o[6])
 }
 __device__ __forceinline__ void j12s(double c, const double T[6], double o[6])
 {
-    double c2 = c + c;
+    const double c2 = sc2<1>(c);
     o[1] = fma(-c, T[2], o[1]);
     o[2] = fma(c, T[1], o[2]);
     o[3] = fma(-c2, T[4], o[3]);
@@ -379,7 +392,7 @@ __device__ __forceinline__ void metric_first(const PointIn& P, MetricPart& M)
 #pragma unroll
     for (int s = 0; s < 6; s++) gi[s] *= idet;
 #pragma unroll
-    for (int s = 0; s < 6; s++) gw[s] = offd(s) ? gi[s] + gi[s] : gi[s];
+    for (int s = 0; s < 6; s++) gw[s] = offd(s) ? sc2<1>(gi[s]) : gi[s];
 
     // ---------------- first frame derivatives of h
     double (*dh)[6] = M.dh;
@@ -400,7 +413,7 @@ __device__ __forceinline__ void metric_first(const PointIn& P, MetricPart& M)
 #pragma unroll
         for (int s = 0; s < 6; s++) {
             const int i = spi(s), j = spj(s);
-            Dl[k][s] = 0.5 * (Dh[i][sp(j, k)] + Dh[j][sp(i, k)] - Dh[k][s]);
+            Dl[k][s] = sc2<-1>(Dh[i][sp(j, k)] + Dh[j][sp(i, k)] - Dh[k][s]);
         }
     double (*Dup)[6] = M.Dup;
 #pragma unroll
@@ -422,7 +435,7 @@ __device__ __forceinline__ void metric_first(const PointIn& P, MetricPart& M)
         double t = gw[0] * dh[m][0];
 #pragma unroll
         for (int s = 1; s < 6; s++) t = fma(gw[s], dh[m][s], t);
-        M.Dtr[m] = m == AX ? 0.0 : 0.5 * t;
+        M.Dtr[m] = m == AX ? 0.0 : sc2<-1>(t);
     }
 }
 
@@ -475,14 +488,14 @@ __device__ __forceinline__ void metric_part(const PointIn& P, MetricPart& M)
         j01s(g.a, h, Y1);                                                        // Y1 = Omega_1 h
         if constexpr (FAM == FAM_SPH) { j02s(g.b, h, Y2); j12s(g.c, h, Y2); }    // Y2 = Omega_2 h
         double X01[6], X02[6], X12[6];
-        const double a2 = g.a + g.a;
+        const double a2 = sc2<1>(g.a);
         if constexpr (FAM == FAM_SPH) {
             const double c1 = fma(g.a, gi[1], -g.c * gi[5]);
             const double c2 = fma(g.b, gi[2], g.c * gi[4]);
             const double g01 = fma(gi[1], g.e0a, -c1 * g.a);
             const double g02 = fma(gi[2], g.e0b, -c2 * g.b);
             const double g12 = fma(gi[2], g.e0c, fma(gi[4], g.e1c, -c2 * g.c));
-            const double b2 = g.b + g.b, cc2 = g.c + g.c;
+            const double b2 = sc2<1>(g.b), cc2 = sc2<1>(g.c);
             const double a11 = g.a * gi[3], a12 = g.a * gi[4];
             const double b12 = g.b * gi[4], b22 = g.b * gi[5];
             const double k12 = g.c * gi[4], k22 = g.c * gi[5];
@@ -561,7 +574,7 @@ __device__ __forceinline__ void metric_part(const PointIn& P, MetricPart& M)
     double dW[3];
 #pragma unroll
     for (int k = 0; k < 3; k++) dW[k] = der1<AX, S, ORD>(P, G_CF, k);
-    const double mhiW = -0.5 * M.iW;
+    const double mhiW = -sc2<-1>(M.iW);
 #pragma unroll
     for (int k = 0; k < 3; k++) M.dphi[k] = k == AX ? 0.0 : mhiW * dW[k];
     {
@@ -570,7 +583,7 @@ __device__ __forceinline__ void metric_part(const PointIn& P, MetricPart& M)
 #pragma unroll
         for (int s = 0; s < 6; s++) {
             const int i = spi(s), j = spj(s);
-            const double Hphi = hzero(AX, s) ? 0.0 : fma(mhiW, HW[s], 2.0 * M.dphi[i] * M.dphi[j]);
+            const double Hphi = hzero(AX, s) ? 0.0 : fma(mhiW, HW[s], sc2<1>(M.dphi[i] * M.dphi[j]));
             M.DDphi[s] = Hphi - dot3<AX>(Dup[0][s], Dup[1][s], Dup[2][s], M.dphi);
         }
     }
@@ -608,6 +621,10 @@ __device__ __forceinline__ void rhs_core(const PointIn& P, double eta, double ou
 #pragma unroll
     for (int i = 0; i < 3; i++) { lam[i] = ld(F(G_LAM + i)); vet[i] = ld(F(G_VET + i)); bet[i] = ld(F(G_BET + i)); }
     const double K = ld(F(G_TRK)), al = ld(F(G_ALPHA));
+    const double al2 = sc2<1>(al);   // 2 alpha
+    double dphi2[3];                 // 2 d_k phi
+#pragma unroll
+    for (int k = 0; k < 3; k++) dphi2[k] = sc2<1>(dphi[k]);
     double dK[3], dal[3], dvet[3][3];
 #pragma unroll
     for (int k = 0; k < 3; k++) {
@@ -640,7 +657,7 @@ __device__ __forceinline__ void rhs_core(const PointIn& P, double eta, double ou
     const double trA = Aud[0][0] + Aud[1][1] + Aud[2][2];
     double AA = a[0] * Auu[0];
 #pragma unroll
-    for (int s = 1; s < 6; s++) AA = fma(offd(s) ? a[s] + a[s] : a[s], Auu[s], AA);
+    for (int s = 1; s < 6; s++) AA = fma(offd(s) ? sc2<1>(a[s]) : a[s], Auu[s], AA);
 
     // ---------------- shift: Dhat_k beta^i, second covariant derivatives, divergences
     double Db[3][3];  // Db[i][k] = Dhat_k beta^i
@@ -683,8 +700,9 @@ __device__ __forceinline__ void rhs_core(const PointIn& P, double eta, double ou
             double u[3] = {0, 0, 0};
             j01v(g.a * g.a, vet, u);
             double t[3];
+            const double a2 = sc2<1>(g.a);
 #pragma unroll
-            for (int i = 0; i < 3; i++) t[i] = fma(g.a + g.a, dvet[1][i], u[i]);
+            for (int i = 0; i < 3; i++) t[i] = fma(a2, dvet[1][i], u[i]);
             j01v(1.0, t, DDb[3]);
         }
         if constexpr (FAM == FAM_SPH) {
@@ -718,7 +736,7 @@ __device__ __forceinline__ void rhs_core(const PointIn& P, double eta, double ou
                 double t[3], u[3];
 #pragma unroll
                 for (int i = 0; i < 3; i++) {
-                    const double e2 = dvet[2][i] + dvet[2][i];
+                    const double e2 = sc2<1>(dvet[2][i]);
                     t[i] = g.b * (e2 + Z[i]);
                     u[i] = g.c * (e2 + Z[i]);
                 }
@@ -797,7 +815,7 @@ __device__ __forceinline__ void rhs_core(const PointIn& P, double eta, double ou
 #pragma unroll
             for (int k = 0; k < 3; k++) t = fma(h[sp(k, j)], Db[k][i], fma(h[sp(i, k)], Db[k][j], t));
             const double gij = (i == j) ? 1.0 + h[s] : h[s];
-            r[s] = fma(-2.0 * al, a[s], fma(-tt, gij, t));
+            r[s] = fma(-al2, a[s], fma(-tt, gij, t));
         }
         oms<FAM, 1>(g, vet[1], h, r);
         oms<FAM, 2>(g, vet[2], h, r);
@@ -810,7 +828,7 @@ __device__ __forceinline__ void rhs_core(const PointIn& P, double eta, double ou
 #pragma unroll
         for (int s = 0; s < 6; s++) {
             const int i = spi(s), j = spj(s);
-            const double t = fma(2.0 * al, fma(2.0, dphi[i] * dphi[j], -DDphi[s]), -DDal[s]);
+            const double t = fma(al2, fma(dphi2[i], dphi[j], -DDphi[s]), -DDal[s]);
             X[s] = fma(al, Ric[s], fma(2.0, fma(dal[i], dphi[j], dal[j] * dphi[i]), t));
         }
         double trX = gw[0] * X[0];
@@ -830,7 +848,7 @@ __device__ __forceinline__ void rhs_core(const PointIn& P, double eta, double ou
             const double AAij = fma(a[sp(i, 2)], Aud[2][j], fma(a[sp(i, 1)], Aud[1][j], a[sp(i, 0)] * Aud[0][j]));
             const double gij = (i == j) ? 1.0 + h[s] : h[s];
             const double XTF = fma(-third_trX, gij, X[s]);
-            r[s] = fma(W2, XTF, fma(-2.0 * al, AAij, fma(c_div, a[s], t)));
+            r[s] = fma(W2, XTF, fma(-al2, AAij, fma(c_div, a[s], t)));
         }
         oms<FAM, 1>(g, vet[1], a, r);
         oms<FAM, 2>(g, vet[2], a, r);
@@ -868,8 +886,8 @@ __device__ __forceinline__ void rhs_core(const PointIn& P, double eta, double ou
             // + 2 alpha Abar^jk Delta^i_jk
             double w = Auu[0] * Dup[i][0];
 #pragma unroll
-            for (int s = 1; s < 6; s++) w = fma(offd(s) ? Auu[s] + Auu[s] : Auu[s], Dup[i][s], w);
-            rl[i] = fma(2.0 * al, w, t);
+            for (int s = 1; s < 6; s++) w = fma(offd(s) ? sc2<1>(Auu[s]) : Auu[s], Dup[i][s], w);
+            rl[i] = fma(al2, w, t);
         }
         // Lie-derivative part: - lambda^j Dhat_j beta^i + beta^j (Omega_j lambda)^i
 #pragma unroll
@@ -891,7 +909,7 @@ __device__ __forceinline__ void rhs_core(const PointIn& P, double eta, double ou
         dv[1] = g.a * vet[0];
         if constexpr (FAM == FAM_SPH) dv[2] = fma(g.b, vet[0], g.c * vet[1]);
         else dv[2] = g.d22 * vet[2];
-        out[G_ALPHA] = -2.0 * al * K;
+        out[G_ALPHA] = -al2 * K;
 #pragma unroll
         for (int i = 0; i < 3; i++) {
             out[G_VET + i] = fma(-vet[i], dv[i], bet[i]);
