@@ -44,17 +44,16 @@ UNIT = "point-updates/s"
 # the k_d1 pre-pass and k_rhs), by workload (the kernel variant it runs), from
 # the kernels' DADD/DMUL/DFMA thread-instruction counts in one ncu capture:
 # (DADD + DMUL + 2 DFMA) / interior points (profiles/k_rhs_headon_256x2x512.md,
-# profiles/k_rhs_general_3d.md).  Head-on 256x2x512 (cylindrical, two-point
-# azimuth): k_rhs 308 + 376 + 2 x 1242 = 3168, k_d1 44.3.  Large 3D
-# (spherical, general): k_rhs 382 + 479 + 2 x 1684 = 4229, k_d1 89.9 (4 FLOP per
-# stored difference, 22 differences per point over the 1.03x larger region).
-# Head-on with the 8th-order scheme (headon8): k_rhs 403 + 432 + 2 x 1586 =
-# 4007, k_d1 122.9 (profiles/k_rhs_headon8_256x2x512.md).
-# A workload without a capture reports no FLOP rate.
-F_ALG = {"headon": 3212.3, "large3d": 4318.9, "headon8": 4129.9}
+# profiles/k_rhs_headon8_256x2x512.md, profiles/k_rhs_general_3d.md).  Head-on
+# 256x2x512 (cylindrical, two-point azimuth): k_rhs 288 + 350 + 2 x 1243 = 3124,
+# k_d1 44.3.  Head-on with the 8th-order scheme: k_rhs 384 + 406 + 2 x 1587 = 3964,
+# k_d1 122.9.  Large 3D (spherical, general): k_rhs 355 + 449 + 2 x 1684 = 4172, k_d1
+# 89.9 (4 FLOP per stored difference, 22 differences per point over the 1.03x larger
+# region).  A workload without a capture reports no FLOP rate.
+F_ALG = {"headon": 3168.3, "large3d": 4261.9, "headon8": 4086.9}
 # DRAM bytes (read + write) of the same two launches in that capture, or None
-TRAFFIC = {"headon": 24016640 + 90880 + 83629056 + 279618560,
-           "headon8": 24949248 + 122368 + 87210496 + 350553856}
+TRAFFIC = {"headon": 24017408 + 91904 + 85831424 + 300615168,
+           "headon8": 24951296 + 124160 + 92246784 + 303696640}
 # The same for the diagnostics (Hamiltonian and momentum constraints, psi4), per interior
 # point of one call, from one ncu capture of those kernels, by workload (head-on: k_ham 416 /
 # 258 / 651 DADD / DMUL / DFMA, k_mom 137 / 162 / 269, k_psi4 551 / 505 / 1103; the reductions
