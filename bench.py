@@ -55,10 +55,10 @@ F_ALG = {"headon": 3168.3, "large3d": 4261.9, "headon8": 4086.9}
 TRAFFIC = {"headon": 24017408 + 91904 + 85831424 + 300615168,
            "headon8": 24951296 + 124160 + 92246784 + 303696640}
 # The same for the diagnostics (Hamiltonian and momentum constraints, psi4), per interior
-# point of one call, from one ncu capture of those kernels, by workload (head-on: k_ham 416 /
-# 258 / 651 DADD / DMUL / DFMA, k_mom 137 / 162 / 269, k_psi4 551 / 505 / 1103; the reductions
+# point of one call, from one ncu capture of those kernels, by workload (head-on: k_ham 409 /
+# 231 / 651 DADD / DMUL / DFMA, k_mom 132 / 141 / 269, k_psi4 549 / 477 / 1103; the reductions
 # and ghost copies add < 0.1; profiles/diagnostics_headon_256x2x512.md); absent: not captured
-DIAG_FLOPS = {"headon": {"hamiltonian": 1976.0, "momentum": 837.0, "psi4": 3262.0}}
+DIAG_FLOPS = {"headon": {"hamiltonian": 1942.0, "momentum": 811.0, "psi4": 3232.0}}
 # psi4 modes on the workload's extraction sphere: l <= 8, Gauss-Legendre x uniform nodes
 PSI4_LMAX, PSI4_NTHETA, PSI4_NPHI = 8, 24, 48
 # FP64 pipe of one SM: 2 DFMA per clock (ncu peak_sustained of
