@@ -129,3 +129,24 @@ def test_det_enforcement_isolated_by_a_vanishing_step():
     assert x.min() < 1e-6 and x.max() > 2.0 ** -10 and (x > 2.0 ** -10).sum() > 10   # both branches ran
     assert np.abs(h - href).max() <= 4e-16 * np.abs(href).max()
     assert np.abs(det(h) - 1.0).max() <= 1e-15
+
+
+@pytest.mark.parametrize("bad", [float("nan"), float("inf")], ids=["nan", "inf"])
+def test_a_non_finite_value_spreads_and_is_reported(bad):
+    """A single non-finite h_ij value at one interior point reaches W and alpha through the
+    stencils within a few steps (also through the exponent-field scalings of the point code),
+    and nr_check_finite reports NR_ENONFINITE; a finite state passes."""
+    spec = W.sinh_cylindrical((16, 2, 24), rho_max=20.0, z_max=20.0)
+    g = B.Grid(spec)
+    g.set_brill_lindquist((1.0,), ((0.0, 0.0, 0.0),), 0.0, 0)
+    g.check_finite()
+    y = np.empty(24 * g.T)
+    g.get_state(y, True)
+    n0, n1 = g.n[0], g.n[1]
+    idx = 3 + 5 + n0 * (3 + n1 * (3 + 10))   # an interior point
+    y[0 * g.T + idx] = bad
+    g.set_state(y, True)
+    g.rk4_step(g.dt_cfl, 3)
+    with pytest.raises(B.NrError) as ei:
+        g.check_finite()
+    assert ei.value.code == 5
