@@ -45,15 +45,15 @@ UNIT = "point-updates/s"
 # the kernels' DADD/DMUL/DFMA thread-instruction counts in one ncu capture:
 # (DADD + DMUL + 2 DFMA) / interior points (profiles/k_rhs_headon_256x2x512.md,
 # profiles/k_rhs_headon8_256x2x512.md, profiles/k_rhs_general_3d.md).  Head-on
-# 256x2x512 (cylindrical, two-point azimuth): k_rhs 288 + 350 + 2 x 1243 = 3124,
-# k_d1 44.3.  Head-on with the 8th-order scheme: k_rhs 384 + 406 + 2 x 1587 = 3964,
+# 256x2x512 (cylindrical, two-point azimuth): k_rhs 288 + 346 + 2 x 1243 = 3120,
+# k_d1 44.3.  Head-on with the 8th-order scheme: k_rhs 384 + 402 + 2 x 1587 = 3960,
 # k_d1 122.9.  Large 3D (spherical, general): k_rhs 355 + 449 + 2 x 1684 = 4172, k_d1
 # 89.9 (4 FLOP per stored difference, 22 differences per point over the 1.03x larger
 # region).  A workload without a capture reports no FLOP rate.
-F_ALG = {"headon": 3168.3, "large3d": 4261.9, "headon8": 4086.9}
+F_ALG = {"headon": 3164.3, "large3d": 4261.9, "headon8": 4082.9}
 # DRAM bytes (read + write) of the same two launches in that capture, or None
-TRAFFIC = {"headon": 24017408 + 91904 + 85831424 + 300615168,
-           "headon8": 24951296 + 124160 + 92246784 + 303696640}
+TRAFFIC = {"headon": 24019200 + 91136 + 90408448 + 298524160,
+           "headon8": 24949504 + 123904 + 89595136 + 280801280}
 # The same for the diagnostics (Hamiltonian and momentum constraints, psi4), per interior
 # point of one call, from one ncu capture of those kernels, by workload (head-on: k_ham 409 /
 # 231 / 651 DADD / DMUL / DFMA, k_mom 132 / 141 / 269, k_psi4 549 / 477 / 1103; the reductions

@@ -112,6 +112,19 @@ __device__ __forceinline__ double mixraw8(const double* f, long sa, long sb)
                 d1raw8(f + sb, sa), d1raw8(f + 2 * sb, sa), d1raw8(f + 3 * sb, sa), d1raw8(f + 4 * sb, sa));
 }
 
+// ---- exact scaling by 2^K on the integer pipe.  The FP64 pipe bounds every kernel of the
+// point code and the integer pipe idles, so x * 2^K moves the exponent field of a normal
+// number by K instead of issuing an FP64 multiply; the result is the same bits.  Zeros,
+// infinities and NaNs pass through unchanged (so do denormals, which no BSSN state holds);
+// a result that would leave the normal range is not rounded to zero or infinity.
+template <int K>
+__device__ __forceinline__ double sc2(double x)
+{
+    const int hi = __double2hiint(x), lo = __double2loint(x);
+    const unsigned e = ((unsigned)hi >> 20) & 0x7FFu;
+    return __hiloint2double(e - 1u < 0x7FEu ? hi + K * (1 << 20) : hi, lo);
+}
+
 // Finite-difference families: order ORD = N_FD with N_G = ORD/2 + 1 ghost layers
 // (Sec. 3).  den1, den2: denominators of the integer first- and second-derivative
 // weights (Geo: D = 1/(den1 dxx S), D2 = 1/(den2 dxx^2 S^2)); ko_den = 2^(2r) of
@@ -124,12 +137,14 @@ struct FD<4> {
     static constexpr int M = 2;
     static constexpr double den1 = 12.0, den2 = 12.0, ko_den = 64.0;
     static constexpr double ax_d2 = 32.0, ax_up = 16.0, ax_ko = 32.0;
+    static constexpr int ax_d2_log2 = 5;
 };
 template <>
 struct FD<8> {
     static constexpr int M = 4;
     static constexpr double den1 = 840.0, den2 = 5040.0, ko_den = 1024.0;
     static constexpr double ax_d2 = 16384.0, ax_up = 768.0, ax_ko = 512.0;
+    static constexpr int ax_d2_log2 = 14;
 };
 template <int ORD>
 __device__ __forceinline__ double d1r(const double* f, long s)
@@ -205,7 +220,7 @@ __device__ __forceinline__ double hess(const double* f, const double* fx, const 
         else return g.DD[1] * m;
     }
     if constexpr (KL == 3) {
-        if constexpr (AX == 1) return fma(FD<ORD>::ax_d2 * g.D2[1], ld(f + ox) - ld(f), g.a * df[0]);
+        if constexpr (AX == 1) return fma(sc2<FD<ORD>::ax_d2_log2>(g.D2[1]), ld(f + ox) - ld(f), g.a * df[0]);
         else return fma(g.D2[1], d2r<ORD>(f, st[1]), g.a * df[0]);
     }
     if constexpr (KL == 4) {
@@ -215,7 +230,8 @@ __device__ __forceinline__ double hess(const double* f, const double* fx, const 
     }
     if constexpr (KL == 5) {
         if constexpr (FAM == FAM_SPH) {
-            if constexpr (AX == 2) return fma(FD<ORD>::ax_d2 * g.D2[2], ld(f + ox) - ld(f), fma(g.b, df[0], g.c * df[1]));
+            if constexpr (AX == 2)
+                return fma(sc2<FD<ORD>::ax_d2_log2>(g.D2[2]), ld(f + ox) - ld(f), fma(g.b, df[0], g.c * df[1]));
             else return fma(g.D2[2], d2r<ORD>(f, st[2]), fma(g.b, df[0], g.c * df[1]));
         } else {
             return fma(g.D2[2], d2r<ORD>(f, st[2]), -g.d22 * df[2]);
@@ -244,19 +260,6 @@ __device__ __forceinline__ double contract6(const double gw[6], const double H[6
     for (int kl = 1; kl < 6; kl++)
         if (!hzero(AX, kl)) t = fma(gw[kl], H[kl], t);
     return t;
-}
-
-// ---- exact scaling by 2^K on the integer pipe.  The FP64 pipe bounds every kernel of the
-// point code and the integer pipe idles, so x * 2^K moves the exponent field of a normal
-// number by K instead of issuing an FP64 multiply; the result is the same bits.  Zeros,
-// infinities and NaNs pass through unchanged (so do denormals, which no BSSN state holds);
-// a result that would leave the normal range is not rounded to zero or infinity.
-template <int K>
-__device__ __forceinline__ double sc2(double x)
-{
-    const int hi = __double2hiint(x), lo = __double2loint(x);
-    const unsigned e = ((unsigned)hi >> 20) & 0x7FFu;
-    return __hiloint2double(e - 1u < 0x7FEu ? hi + K * (1 << 20) : hi, lo);
 }
 
 // ---- rotation generators acting on vectors / symmetric tensors: out += c * J_pq (.)
@@ -1054,7 +1057,7 @@ __device__ __forceinline__ void advko_weights(const double u[3], const bool fwd[
     for (int d = 0; d < 3; d++) {
         const double kap = (0.1875 * sigma) * D[d];
         if (d == AX) {
-            W.cax = fma(16.0, u[d], 32.0 * kap);
+            W.cax = fma(16.0, u[d], sc2<5>(kap));   // FD<4>::ax_up u + FD<4>::ax_ko kap
             continue;
         }
         const double p = fwd[d] ? u[d] : 0.0, q = fwd[d] ? 0.0 : u[d];
@@ -1122,7 +1125,7 @@ __device__ __forceinline__ void advko_weights8(const double u[3], const bool fwd
     for (int d = 0; d < 3; d++) {
         const double kap = (0.8203125 * sigma) * D[d];
         if (d == AX) {
-            W.cax = fma(768.0, u[d], 512.0 * kap);
+            W.cax = fma(768.0, u[d], sc2<9>(kap));  // FD<8>::ax_up u + FD<8>::ax_ko kap
             continue;
         }
         const double p = fwd[d] ? u[d] : 0.0, q = fwd[d] ? 0.0 : u[d];
@@ -1169,7 +1172,9 @@ __device__ __forceinline__ void add_adv_ko(const double* y, long T, const long s
     for (int d = 0; d < 3; d++) {
         const double v = ld(y + (long)(G_VET + d) * T);
         u[d] = fabs(v) * D[d];
-        fwd[d] = v > 0.0;
+        // v > 0 by the sign of the bit pattern, on the integer pipe: the same answer for
+        // every value but NaN (+0 and -0 both give the backward stencil)
+        fwd[d] = __double_as_longlong(v) > 0;
     }
     if constexpr (ORD == 8) {
         AdvKoW8 Wm, Wg;

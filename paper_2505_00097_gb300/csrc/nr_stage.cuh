@@ -17,7 +17,8 @@ namespace nrk {
 // 3e-19 |f|, far under an ulp.  Elsewhere f = expm1(-log1p(x)/3).  f(0) = 0 exactly.
 __device__ __forceinline__ double rcbrt1p_m1(double x)
 {
-    if (fabs(x) <= 0x1p-10) {
+    // |x| <= 2^-10 by the magnitude bits, on the integer pipe (NaN takes the other branch)
+    if ((unsigned long long)(__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFLL) <= 0x3F50000000000000ULL) {
         double p = fma(728.0 / 6561.0, x, -91.0 / 729.0);
         p = fma(p, x, 35.0 / 243.0);
         p = fma(p, x, -14.0 / 81.0);
