@@ -180,6 +180,28 @@ __host__ __device__ constexpr bool ax_ok()
 }
 // a Hessian component known to vanish: a mixed pair that involves the axis
 __host__ __device__ constexpr bool hzero(int AX, int kl) { return AX >= 0 && offd(kl) && (spi(kl) == AX || spj(kl) == AX); }
+// Dhat_k V^i known to vanish: no difference along k = AX, and the generator Omega_AX never
+// reaches component i (cylindrical-like: Omega_1 = a J01 leaves component 2 alone;
+// spherical-like: Omega_2 = b J02 + c J12 reaches all three)
+template <int FAM, int AX>
+__host__ __device__ constexpr bool dvz(int i, int k)
+{
+    return FAM == FAM_CYL && AX == 1 && k == 1 && i == 2;
+}
+// Dhat_k Dhat_l V^i known to vanish (kl symmetric index): on a cylindrical-like grid
+// with a two-point azimuth, the (rho, phi) and (phi, z) pairs of component z
+template <int FAM, int AX>
+__host__ __device__ constexpr bool dlz(int k, int s)
+{
+    // Delta_kij known to vanish: Delta_2(12) = 1/2 Dhat_1 h_22, and on a cylindrical-like grid
+    // with a two-point azimuth Omega_1 h leaves the (2,2) component alone
+    return FAM == FAM_CYL && AX == 1 && k == 2 && s == 4;
+}
+template <int FAM, int AX>
+__host__ __device__ constexpr bool ddbz(int kl, int i)
+{
+    return FAM == FAM_CYL && AX == 1 && i == 2 && (kl == 1 || kl == 4);
+}
 
 // Gridfunctions with second derivatives (h, W, alpha, vet) have their raw first
 // differences along axis 0 (and, for a general grid, axis 1) stored by a
@@ -416,14 +438,23 @@ __device__ __forceinline__ void metric_first(const PointIn& P, MetricPart& M)
 #pragma unroll
         for (int s = 0; s < 6; s++) {
             const int i = spi(s), j = spj(s);
-            Dl[k][s] = sc2<-1>(Dh[i][sp(j, k)] + Dh[j][sp(i, k)] - Dh[k][s]);
+            // Delta_kij = 1/2 (Dhat_i h_jk + Dhat_j h_ik - Dhat_k h_ij); with k = j (k = i) the
+            // last two (the first and last) terms are the same number and cancel exactly
+            if (k == j)
+                Dl[k][s] = sc2<-1>(Dh[i][sp(k, k)]);
+            else if (k == i)
+                Dl[k][s] = sc2<-1>(Dh[j][sp(k, k)]);
+            else
+                Dl[k][s] = sc2<-1>(Dh[i][sp(j, k)] + Dh[j][sp(i, k)] - Dh[k][s]);
         }
     double (*Dup)[6] = M.Dup;
 #pragma unroll
     for (int k = 0; k < 3; k++)
 #pragma unroll
-        for (int s = 0; s < 6; s++)
-            Dup[k][s] = fma(gsym(gi, k, 2), Dl[2][s], fma(gsym(gi, k, 1), Dl[1][s], gsym(gi, k, 0) * Dl[0][s]));
+        for (int s = 0; s < 6; s++) {
+            double t = fma(gsym(gi, k, 1), Dl[1][s], gsym(gi, k, 0) * Dl[0][s]);
+            Dup[k][s] = dlz<FAM, AX>(2, s) ? t : fma(gsym(gi, k, 2), Dl[2][s], t);
+        }
     double* Dvec = M.Dvec;
 #pragma unroll
     for (int k = 0; k < 3; k++) {
@@ -505,8 +536,9 @@ __device__ __forceinline__ void metric_part(const PointIn& P, MetricPart& M)
 #pragma unroll
             for (int s = 0; s < 6; s++) {
                 X01[s] = fma(a2, V1[s], fma(g01, h[s], fma(a11, Y1[s], a12 * Y2[s])));
-                X02[s] = fma(b2, V2[s], fma(g02, h[s], fma(b12, Y1[s], b22 * Y2[s])));
-                X12[s] = fma(cc2, V2[s], fma(g12, h[s], fma(k12, Y1[s], k22 * Y2[s])));
+                // (Omega_1 h)_22 = 0; X01's (2,2) component is never read
+                X02[s] = fma(b2, V2[s], fma(g02, h[s], s == 5 ? b22 * Y2[s] : fma(b12, Y1[s], b22 * Y2[s])));
+                X12[s] = fma(cc2, V2[s], fma(g12, h[s], s == 5 ? k22 * Y2[s] : fma(k12, Y1[s], k22 * Y2[s])));
             }
         } else {
             const double g01 = gi[1] * (g.e0a - g.a * g.a);
@@ -536,8 +568,12 @@ __device__ __forceinline__ void metric_part(const PointIn& P, MetricPart& M)
 #pragma unroll
         for (int m = 0; m < 3; m++)
 #pragma unroll
-            for (int k = 0; k < 3; k++)
-                Yv[j][m][k] = fma(gsym(gi, k, 2), Dl[j][sp(m, 2)], fma(gsym(gi, k, 1), Dl[j][sp(m, 1)], gsym(gi, k, 0) * Dl[j][sp(m, 0)]));
+            for (int k = 0; k < 3; k++) {
+                double t = gsym(gi, k, 0) * Dl[j][sp(m, 0)];
+                if (!dlz<FAM, AX>(j, sp(m, 1))) t = fma(gsym(gi, k, 1), Dl[j][sp(m, 1)], t);
+                if (!dlz<FAM, AX>(j, sp(m, 2))) t = fma(gsym(gi, k, 2), Dl[j][sp(m, 2)], t);
+                Yv[j][m][k] = t;
+            }
     {
         double Aij[3][3];
 #pragma unroll
@@ -562,13 +598,22 @@ __device__ __forceinline__ void metric_part(const PointIn& P, MetricPart& M)
                 C = fma(Dup[m][sp(i, k)], Yv[m][j][k], C);
             }
             // 1/2 (gammabar_ki Dhat_j lambda^k + gammabar_kj Dhat_i lambda^k)
-            double t2 = Dlam[j][i] + Dlam[i][j];
+            // (Dlam[j][k] = Dhat_j lambda^k; the terms that vanish on a two-point axis skipped)
+            const bool zji = dvz<FAM, AX>(i, j), zij = dvz<FAM, AX>(j, i);
+            double t2 = zji ? (zij ? 0.0 : Dlam[i][j]) : (zij ? Dlam[j][i] : Dlam[j][i] + Dlam[i][j]);
 #pragma unroll
-            for (int k = 0; k < 3; k++) t2 = fma(h[sp(k, i)], Dlam[j][k], fma(h[sp(k, j)], Dlam[i][k], t2));
+            for (int k = 0; k < 3; k++) {
+                if (!dvz<FAM, AX>(k, i)) t2 = fma(h[sp(k, j)], Dlam[i][k], t2);
+                if (!dvz<FAM, AX>(k, j)) t2 = fma(h[sp(k, i)], Dlam[j][k], t2);
+            }
             // Delta^k Delta_(ij)k
             double t3 = Dvec[0] * (Dl[i][sp(j, 0)] + Dl[j][sp(i, 0)]);
-            t3 = fma(Dvec[1], Dl[i][sp(j, 1)] + Dl[j][sp(i, 1)], t3);
-            t3 = fma(Dvec[2], Dl[i][sp(j, 2)] + Dl[j][sp(i, 2)], t3);
+#pragma unroll
+            for (int k = 1; k < 3; k++) {
+                const bool z1 = dlz<FAM, AX>(i, sp(j, k)), z2 = dlz<FAM, AX>(j, sp(i, k));
+                if (z1 && z2) continue;
+                t3 = fma(Dvec[k], z1 ? Dl[j][sp(i, k)] : z2 ? Dl[i][sp(j, k)] : Dl[i][sp(j, k)] + Dl[j][sp(i, k)], t3);
+            }
             M.Ric[s] = fma(-0.5, Lfull[s], fma(0.5, t2 + t3, Aij[i][j] + Aij[j][i] + C));
         }
     }
@@ -586,8 +631,13 @@ __device__ __forceinline__ void metric_part(const PointIn& P, MetricPart& M)
 #pragma unroll
         for (int s = 0; s < 6; s++) {
             const int i = spi(s), j = spj(s);
-            const double Hphi = hzero(AX, s) ? 0.0 : fma(mhiW, HW[s], sc2<1>(M.dphi[i] * M.dphi[j]));
-            M.DDphi[s] = Hphi - dot3<AX>(Dup[0][s], Dup[1][s], Dup[2][s], M.dphi);
+            const double dd = dot3<AX>(Dup[0][s], Dup[1][s], Dup[2][s], M.dphi);
+            if (hzero(AX, s))
+                M.DDphi[s] = -dd;
+            else if (i == AX || j == AX)   // d_AX phi = 0
+                M.DDphi[s] = fma(mhiW, HW[s], -dd);
+            else
+                M.DDphi[s] = fma(mhiW, HW[s], fma(sc2<1>(M.dphi[i]), M.dphi[j], -dd));
         }
     }
 }
@@ -641,7 +691,10 @@ __device__ __forceinline__ void rhs_core(const PointIn& P, double eta, double ou
         double Hal[6];
         hess6<FAM, AX, S, ORD>(F(G_ALPHA), dxp<S>(P, G_ALPHA), dyp<AX, S>(P, G_ALPHA), st, P.ox, g, dal, Hal);
 #pragma unroll
-        for (int s = 0; s < 6; s++) DDal[s] = Hal[s] - dot3<AX>(Dup[0][s], Dup[1][s], Dup[2][s], dal);
+        for (int s = 0; s < 6; s++) {
+            const double dd = dot3<AX>(Dup[0][s], Dup[1][s], Dup[2][s], dal);
+            DDal[s] = hzero(AX, s) ? -dd : Hal[s] - dd;
+        }
     }
 
     // ---------------- Abar with raised indices
@@ -664,19 +717,19 @@ __device__ __forceinline__ void rhs_core(const PointIn& P, double eta, double ou
 
     // ---------------- shift: Dhat_k beta^i, second covariant derivatives, divergences
     double Db[3][3];  // Db[i][k] = Dhat_k beta^i
-#pragma unroll
-    for (int i = 0; i < 3; i++)
-#pragma unroll
-        for (int k = 0; k < 3; k++) Db[i][k] = dvet[k][i];
     {
-        double t1[3] = {0, 0, 0}, t2[3] = {0, 0, 0};
-        omv<FAM, 1>(g, 1.0, vet, t1);
-        omv<FAM, 2>(g, 1.0, vet, t2);
+        // the generator terms accumulate onto the differences (no additions of zeros)
+        double c1[3] = {dvet[1][0], dvet[1][1], dvet[1][2]}, c2[3] = {dvet[2][0], dvet[2][1], dvet[2][2]};
+        omv<FAM, 1>(g, 1.0, vet, c1);
+        omv<FAM, 2>(g, 1.0, vet, c2);
 #pragma unroll
-        for (int i = 0; i < 3; i++) { Db[i][1] += t1[i]; Db[i][2] += t2[i]; }
+        for (int i = 0; i < 3; i++) { Db[i][0] = dvet[0][i]; Db[i][1] = c1[i]; Db[i][2] = c2[i]; }
     }
     const double divhat = Db[0][0] + Db[1][1] + Db[2][2];
-    const double divbar = fma(Dtr[2], vet[2], fma(Dtr[1], vet[1], fma(Dtr[0], vet[0], divhat)));
+    double divbar = divhat;
+#pragma unroll
+    for (int m = 0; m < 3; m++)
+        if (m != AX) divbar = fma(Dtr[m], vet[m], divbar);
     // DDb[kl][i] = Dhat_k Dhat_l beta^i
     double DDb[6][3];
     {
@@ -705,7 +758,7 @@ __device__ __forceinline__ void rhs_core(const PointIn& P, double eta, double ou
             double t[3];
             const double a2 = sc2<1>(g.a);
 #pragma unroll
-            for (int i = 0; i < 3; i++) t[i] = fma(a2, dvet[1][i], u[i]);
+            for (int i = 0; i < 3; i++) t[i] = AX == 1 ? u[i] : fma(a2, dvet[1][i], u[i]);   // e_1 vet = 0 on AX = 1
             j01v(1.0, t, DDb[3]);
         }
         if constexpr (FAM == FAM_SPH) {
@@ -761,7 +814,8 @@ __device__ __forceinline__ void rhs_core(const PointIn& P, double eta, double ou
     for (int i = 0; i < 3; i++) {
         double t = gw[0] * DDb[0][i];
 #pragma unroll
-        for (int kl = 1; kl < 6; kl++) t = fma(gw[kl], DDb[kl][i], t);
+        for (int kl = 1; kl < 6; kl++)
+            if (!ddbz<FAM, AX>(kl, i)) t = fma(gw[kl], DDb[kl][i], t);
         LapB[i] = t;
     }
     // e_l (Dbar_k beta^k) = sum_k DDb[kl][k] + sum_m [e_l(Delta^k_km) vet^m + Delta^k_km e_l vet^m]
@@ -794,11 +848,17 @@ __device__ __forceinline__ void rhs_core(const PointIn& P, double eta, double ou
         omv<FAM, 2>(g, 1.0, Dtr, OD[2]);
 #pragma unroll
         for (int l = 0; l < 3; l++) {
-            double t = DDb[sp(l, 0)][0] + DDb[sp(l, 1)][1] + DDb[sp(l, 2)][2];
+            double t = DDb[sp(l, 0)][0] + DDb[sp(l, 1)][1];
+            if (!ddbz<FAM, AX>(sp(l, 2), 2)) t += DDb[sp(l, 2)][2];
 #pragma unroll
             for (int m = 0; m < 3; m++) {
-                const double edtr = fma(0.5, GH[sp(l, m)] - Q[sp(l, m)], -OD[l][m]);
-                t = fma(edtr, vet[m], fma(Dtr[m], dvet[l][m], t));
+                // with exactly one of l, m on the two-point axis, GH, Q and (Omega_l Dtr)_m all
+                // vanish; Dtr[AX] = 0 and e_AX vet = 0
+                if (l != AX && m != AX) t = fma(Dtr[m], dvet[l][m], t);
+                if (AX < 0 || (l == AX) == (m == AX)) {
+                    const double edtr = fma(0.5, GH[sp(l, m)] - Q[sp(l, m)], -OD[l][m]);
+                    t = fma(edtr, vet[m], t);
+                }
             }
             gdiv[l] = t;
         }
@@ -814,9 +874,14 @@ __device__ __forceinline__ void rhs_core(const PointIn& P, double eta, double ou
 #pragma unroll
         for (int s = 0; s < 6; s++) {
             const int i = spi(s), j = spj(s);
-            double t = Db[j][i] + Db[i][j];
+            // (Db[k][i] = 0 where dvz(k, i): those terms are skipped)
+            const bool zji = dvz<FAM, AX>(j, i), zij = dvz<FAM, AX>(i, j);
+            double t = zji ? (zij ? 0.0 : Db[i][j]) : (zij ? Db[j][i] : Db[j][i] + Db[i][j]);
 #pragma unroll
-            for (int k = 0; k < 3; k++) t = fma(h[sp(k, j)], Db[k][i], fma(h[sp(i, k)], Db[k][j], t));
+            for (int k = 0; k < 3; k++) {
+                if (!dvz<FAM, AX>(k, j)) t = fma(h[sp(i, k)], Db[k][j], t);
+                if (!dvz<FAM, AX>(k, i)) t = fma(h[sp(k, j)], Db[k][i], t);
+            }
             const double gij = (i == j) ? 1.0 + h[s] : h[s];
             r[s] = fma(-al2, a[s], fma(-tt, gij, t));
         }
@@ -831,8 +896,17 @@ __device__ __forceinline__ void rhs_core(const PointIn& P, double eta, double ou
 #pragma unroll
         for (int s = 0; s < 6; s++) {
             const int i = spi(s), j = spj(s);
-            const double t = fma(al2, fma(dphi2[i], dphi[j], -DDphi[s]), -DDal[s]);
-            X[s] = fma(al, Ric[s], fma(2.0, fma(dal[i], dphi[j], dal[j] * dphi[i]), t));
+            // 2 (d_i alpha d_j phi + d_j alpha d_i phi) + 2 alpha d_i phi d_j phi; both vanish
+            // when i or j is the two-point axis
+            double t;
+            if (i == AX || j == AX)
+                t = fma(al2, -DDphi[s], -DDal[s]);
+            else if (i == j)
+                t = fma(sc2<2>(dal[i]), dphi[i], fma(al2, fma(dphi2[i], dphi[j], -DDphi[s]), -DDal[s]));
+            else
+                t = fma(sc2<1>(dal[i]), dphi[j], fma(sc2<1>(dal[j]), dphi[i],
+                        fma(al2, fma(dphi2[i], dphi[j], -DDphi[s]), -DDal[s])));
+            X[s] = fma(al, Ric[s], t);
         }
         double trX = gw[0] * X[0];
 #pragma unroll
@@ -844,10 +918,12 @@ __device__ __forceinline__ void rhs_core(const PointIn& P, double eta, double ou
 #pragma unroll
         for (int s = 0; s < 6; s++) {
             const int i = spi(s), j = spj(s);
-            double t = 0.0;
-            t = fma(a[sp(0, j)], Db[0][i], a[sp(i, 0)] * Db[0][j]);
+            double t = fma(a[sp(0, j)], Db[0][i], a[sp(i, 0)] * Db[0][j]);
 #pragma unroll
-            for (int k = 1; k < 3; k++) t = fma(a[sp(k, j)], Db[k][i], fma(a[sp(i, k)], Db[k][j], t));
+            for (int k = 1; k < 3; k++) {
+                if (!dvz<FAM, AX>(k, j)) t = fma(a[sp(i, k)], Db[k][j], t);
+                if (!dvz<FAM, AX>(k, i)) t = fma(a[sp(k, j)], Db[k][i], t);
+            }
             const double AAij = fma(a[sp(i, 2)], Aud[2][j], fma(a[sp(i, 1)], Aud[1][j], a[sp(i, 0)] * Aud[0][j]));
             const double gij = (i == j) ? 1.0 + h[s] : h[s];
             const double XTF = fma(-third_trX, gij, X[s]);
@@ -865,13 +941,19 @@ __device__ __forceinline__ void rhs_core(const PointIn& P, double eta, double ou
         for (int s = 1; s < 6; s++) {
             const int i = spi(s), j = spj(s);
             lapal = fma(gw[s], DDal[s], lapal);
-            gap = fma(gi[s], fma(dal[i], dphi[j], (i == j) ? 0.0 : dal[j] * dphi[i]), gap);
+            if (i == AX || j == AX) continue;   // d_AX alpha = d_AX phi = 0
+            gap = fma(gi[s], (i == j) ? dal[i] * dphi[i] : fma(dal[i], dphi[j], dal[j] * dphi[i]), gap);
         }
         out[G_TRK] = fma(al, fma((1.0 / 3.0) * K, K, AA), -W2 * fma(2.0, gap, lapal));
     }
     // Eq. Lambda_RHS_orig_final (with the alpha factors restored) + Lie terms
     double rl[3], rperp[3];
     {
+        // wl_j = -2 (d_j alpha - 6 alpha d_j phi); zero along the two-point axis
+        double wl[3];
+        const double al12 = 12.0 * al;
+#pragma unroll
+        for (int k = 0; k < 3; k++) wl[k] = k == AX ? 0.0 : fma(al12, dphi[k], -sc2<1>(dal[k]));
 #pragma unroll
         for (int i = 0; i < 3; i++) {
             // (2/3) Delta^i Dbar.beta + (1/3) gammabar^ik e_k Dbar.beta (the Lie-derivative part
@@ -880,12 +962,11 @@ __device__ __forceinline__ void rhs_core(const PointIn& P, double eta, double ou
             t = fma((2.0 / 3.0) * Dvec[i], divbar, t);
             t = fma((1.0 / 3.0), fma(gsym(gi, i, 2), gdiv[2], fma(gsym(gi, i, 1), gdiv[1], gsym(gi, i, 0) * gdiv[0])), t);
             // -2 Abar^ij (d_j alpha - 6 alpha d_j phi) - 4/3 alpha gammabar^ij d_j K
-            double u = 0.0;
-            u = Auu[sp(i, 0)] * fma(-6.0 * al, dphi[0], dal[0]);
-            u = fma(Auu[sp(i, 1)], fma(-6.0 * al, dphi[1], dal[1]), u);
-            u = fma(Auu[sp(i, 2)], fma(-6.0 * al, dphi[2], dal[2]), u);
-            double v = fma(gsym(gi, i, 2), dK[2], fma(gsym(gi, i, 1), dK[1], gsym(gi, i, 0) * dK[0]));
-            t = fma(-2.0, u, fma((-4.0 / 3.0) * al, v, t));
+            const double v = dot3<AX>(gsym(gi, i, 0), gsym(gi, i, 1), gsym(gi, i, 2), dK);
+            t = fma((-4.0 / 3.0) * al, v, t);
+#pragma unroll
+            for (int k = 0; k < 3; k++)
+                if (k != AX) t = fma(Auu[sp(i, k)], wl[k], t);
             // + 2 alpha Abar^jk Delta^i_jk
             double w = Auu[0] * Dup[i][0];
 #pragma unroll
@@ -896,7 +977,11 @@ __device__ __forceinline__ void rhs_core(const PointIn& P, double eta, double ou
 #pragma unroll
         for (int i = 0; i < 3; i++) rperp[i] = rl[i];
 #pragma unroll
-        for (int i = 0; i < 3; i++) rl[i] = fma(-lam[2], Db[i][2], fma(-lam[1], Db[i][1], fma(-lam[0], Db[i][0], rl[i])));
+        for (int i = 0; i < 3; i++) {
+            double t = fma(-lam[0], Db[i][0], rl[i]);
+            if (!dvz<FAM, AX>(i, 1)) t = fma(-lam[1], Db[i][1], t);
+            rl[i] = fma(-lam[2], Db[i][2], t);
+        }
         omv<FAM, 1>(g, vet[1], lam, rl);
         omv<FAM, 2>(g, vet[2], lam, rl);
 #pragma unroll
