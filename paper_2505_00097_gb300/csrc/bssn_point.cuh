@@ -561,61 +561,83 @@ __device__ __forceinline__ void metric_part(const PointIn& P, MetricPart& M)
         for (int k = 0; k < 3; k++) Dlam[j][k] = der1<AX, S, ORD>(P, G_LAM + k, j);
     omv<FAM, 1>(g, 1.0, lam, Dlam[1]);
     omv<FAM, 2>(g, 1.0, lam, Dlam[2]);
-    // Y[j][m][k] = gammabar^kl Delta_jml
-    double Yv[3][3][3];
+    // Quadratic terms. With R[i][m][l] = gammabar^lk Delta^m_ik,
+    //   gammabar^kl Delta^m_ki Delta_jml = sum_ml R[i][m][l] Delta_jml   (A_ij; Delta_jml is
+    //                                      symmetric in ml, so R is summed over the pair first)
+    //   gammabar^kl Delta^m_ik Delta_mjl = sum_ml R[i][m][l] Delta_mjl   (C_ij, symmetric)
+    // and R_ij = -1/2 Lfull_ij + A_ij + A_ji + C_ij + 1/2 (Lambda and Delta^k terms), each
+    // component one chain with the 1/2 taken into the factors.
+    double R[3][3][3];
 #pragma unroll
-    for (int j = 0; j < 3; j++)
+    for (int i = 0; i < 3; i++)
 #pragma unroll
         for (int m = 0; m < 3; m++)
 #pragma unroll
+            for (int l = 0; l < 3; l++)
+                R[i][m][l] = fma(Dup[m][sp(2, i)], gsym(gi, 2, l),
+                                 fma(Dup[m][sp(1, i)], gsym(gi, 1, l), Dup[m][sp(0, i)] * gsym(gi, 0, l)));
+    double Rp[3][6];   // Rp[i][p] = R[i][m][l] + R[i][l][m] for the pair p = (m, l), R[i][m][m] on the diagonal
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int p = 0; p < 6; p++) Rp[i][p] = offd(p) ? R[i][spi(p)][spj(p)] + R[i][spj(p)][spi(p)] : R[i][spi(p)][spi(p)];
+    double hDvec[3], hDlam[3][3];   // halves, exact
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        hDvec[k] = sc2<-1>(Dvec[k]);
+#pragma unroll
+        for (int n = 0; n < 3; n++) hDlam[k][n] = sc2<-1>(Dlam[k][n]);
+    }
+#pragma unroll
+    for (int s = 0; s < 6; s++) {
+        const int i = spi(s), j = spj(s);
+        // C_ij
+        double t = R[i][0][0] * Dl[0][sp(j, 0)];
+#pragma unroll
+        for (int q = 1; q < 9; q++) {
+            const int m = q / 3, l = q % 3;
+            if (!dlz<FAM, AX>(m, sp(j, l))) t = fma(R[i][m][l], Dl[m][sp(j, l)], t);
+        }
+        // (Dl[k][p] = 0 where dlz(k, p) and Dlam[j][k] = Dhat_j lambda^k = 0 where dvz(k, j):
+        // those terms are skipped)
+        if (i == j) {
+            // 2 A_ii
+#pragma unroll
+            for (int p = 0; p < 6; p++)
+                if (!dlz<FAM, AX>(i, p)) t = fma(sc2<1>(Rp[i][p]), Dl[i][p], t);
+            // 1/2 Delta^k (2 Delta_iik)
+#pragma unroll
+            for (int k = 0; k < 3; k++)
+                if (!dlz<FAM, AX>(i, sp(i, k))) t = fma(Dvec[k], Dl[i][sp(i, k)], t);
+            // 1/2 (2 gammabar_ki Dhat_i lambda^k)
+            if (!dvz<FAM, AX>(i, i)) t += Dlam[i][i];
+#pragma unroll
+            for (int k = 0; k < 3; k++)
+                if (!dvz<FAM, AX>(k, i)) t = fma(h[sp(k, i)], Dlam[i][k], t);
+        } else {
+            // A_ij + A_ji
+#pragma unroll
+            for (int p = 0; p < 6; p++)
+                if (!dlz<FAM, AX>(j, p)) t = fma(Rp[i][p], Dl[j][p], t);
+#pragma unroll
+            for (int p = 0; p < 6; p++)
+                if (!dlz<FAM, AX>(i, p)) t = fma(Rp[j][p], Dl[i][p], t);
+            // 1/2 Delta^k (Delta_ijk + Delta_jik)
+#pragma unroll
             for (int k = 0; k < 3; k++) {
-                double t = gsym(gi, k, 0) * Dl[j][sp(m, 0)];
-                if (!dlz<FAM, AX>(j, sp(m, 1))) t = fma(gsym(gi, k, 1), Dl[j][sp(m, 1)], t);
-                if (!dlz<FAM, AX>(j, sp(m, 2))) t = fma(gsym(gi, k, 2), Dl[j][sp(m, 2)], t);
-                Yv[j][m][k] = t;
-            }
-    {
-        double Aij[3][3];
-#pragma unroll
-        for (int i = 0; i < 3; i++)
-#pragma unroll
-            for (int j = 0; j < 3; j++) {
-                double t = Dup[0][sp(0, i)] * Yv[j][0][0];
-#pragma unroll
-                for (int q = 1; q < 9; q++) {
-                    const int k = q / 3, m = q % 3;
-                    t = fma(Dup[m][sp(k, i)], Yv[j][m][k], t);
-                }
-                Aij[i][j] = t;
-            }
-#pragma unroll
-        for (int s = 0; s < 6; s++) {
-            const int i = spi(s), j = spj(s);
-            double C = Dup[0][sp(i, 0)] * Yv[0][j][0];
-#pragma unroll
-            for (int q = 1; q < 9; q++) {
-                const int k = q / 3, m = q % 3;
-                C = fma(Dup[m][sp(i, k)], Yv[m][j][k], C);
+                if (!dlz<FAM, AX>(i, sp(j, k))) t = fma(hDvec[k], Dl[i][sp(j, k)], t);
+                if (!dlz<FAM, AX>(j, sp(i, k))) t = fma(hDvec[k], Dl[j][sp(i, k)], t);
             }
             // 1/2 (gammabar_ki Dhat_j lambda^k + gammabar_kj Dhat_i lambda^k)
-            // (Dlam[j][k] = Dhat_j lambda^k; the terms that vanish on a two-point axis skipped)
-            const bool zji = dvz<FAM, AX>(i, j), zij = dvz<FAM, AX>(j, i);
-            double t2 = zji ? (zij ? 0.0 : Dlam[i][j]) : (zij ? Dlam[j][i] : Dlam[j][i] + Dlam[i][j]);
+            if (!dvz<FAM, AX>(i, j)) t += hDlam[j][i];
+            if (!dvz<FAM, AX>(j, i)) t += hDlam[i][j];
 #pragma unroll
             for (int k = 0; k < 3; k++) {
-                if (!dvz<FAM, AX>(k, i)) t2 = fma(h[sp(k, j)], Dlam[i][k], t2);
-                if (!dvz<FAM, AX>(k, j)) t2 = fma(h[sp(k, i)], Dlam[j][k], t2);
+                if (!dvz<FAM, AX>(k, i)) t = fma(h[sp(k, j)], hDlam[i][k], t);
+                if (!dvz<FAM, AX>(k, j)) t = fma(h[sp(k, i)], hDlam[j][k], t);
             }
-            // Delta^k Delta_(ij)k
-            double t3 = Dvec[0] * (Dl[i][sp(j, 0)] + Dl[j][sp(i, 0)]);
-#pragma unroll
-            for (int k = 1; k < 3; k++) {
-                const bool z1 = dlz<FAM, AX>(i, sp(j, k)), z2 = dlz<FAM, AX>(j, sp(i, k));
-                if (z1 && z2) continue;
-                t3 = fma(Dvec[k], z1 ? Dl[j][sp(i, k)] : z2 ? Dl[i][sp(j, k)] : Dl[i][sp(j, k)] + Dl[j][sp(i, k)], t3);
-            }
-            M.Ric[s] = fma(-0.5, Lfull[s], fma(0.5, t2 + t3, Aij[i][j] + Aij[j][i] + C));
         }
+        M.Ric[s] = fma(-0.5, Lfull[s], t);
     }
 
     // ---------------- conformal factor: phi = -1/2 ln W
