@@ -54,4 +54,5 @@ def test_workload_descriptions(name):
     assert c["integrator"] == ("SSPRK3" if name == "headon8" else "RK4")
     assert "l2_policy" in c
     if name in bench.F_ALG:
-        assert bench.F_ALG[name] > 3000
+        # a BSSN RHS evaluation with 4th- or 8th-order stencils: a few thousand FLOP per point
+        assert 1000 < bench.F_ALG[name] < 10000
