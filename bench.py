@@ -45,20 +45,20 @@ UNIT = "point-updates/s"
 # the kernels' DADD/DMUL/DFMA thread-instruction counts in one ncu capture:
 # (DADD + DMUL + 2 DFMA) / interior points (profiles/k_rhs_headon_256x2x512.md,
 # profiles/k_rhs_headon8_256x2x512.md, profiles/k_rhs_general_3d.md).  Head-on
-# 256x2x512 (cylindrical, two-point azimuth): k_rhs 224 + 322 + 2 x 1169 = 2884,
-# k_d1 44.3.  Head-on with the 8th-order scheme: k_rhs 329 + 381 + 2 x 1523 = 3756,
-# k_d1 122.9.  Large 3D (spherical, general): k_rhs 302 + 424 + 2 x 1675 = 4076, k_d1
+# 256x2x512 (cylindrical, two-point azimuth): k_rhs 202 + 322 + 2 x 1163 = 2850,
+# k_d1 44.3.  Head-on with the 8th-order scheme: k_rhs 307 + 381 + 2 x 1517 = 3722,
+# k_d1 122.9.  Large 3D (spherical, general): k_rhs 301 + 423 + 2 x 1661 = 4046, k_d1
 # 89.9 (4 FLOP per stored difference, 22 differences per point over the 1.03x larger
 # region).  A workload without a capture reports no FLOP rate.
-F_ALG = {"headon": 2928.3, "large3d": 4165.9, "headon8": 3878.9}
+F_ALG = {"headon": 2894.3, "large3d": 4135.9, "headon8": 3844.9}
 # DRAM bytes (read + write) of the same two launches in that capture, or None
-TRAFFIC = {"headon": 24018944 + 91904 + 92586240 + 454588416,
-           "headon8": 24950528 + 132864 + 89829632 + 375074048}
+TRAFFIC = {"headon": 24018688 + 98816 + 94506752 + 450309120,
+           "headon8": 24950784 + 136704 + 87655936 + 339959296}
 # The same for the diagnostics (Hamiltonian and momentum constraints, psi4), per interior
 # point of one call, from one ncu capture of those kernels, by workload (head-on: k_ham 361 /
-# 216 / 640 DADD / DMUL / DFMA, k_mom 114 / 141 / 269, k_psi4 525 / 477 / 1109; the reductions
+# 216 / 640 DADD / DMUL / DFMA, k_mom 114 / 141 / 269, k_psi4 502 / 461 / 1080; the reductions
 # and ghost copies add < 0.1; profiles/diagnostics_headon_256x2x512.md); absent: not captured
-DIAG_FLOPS = {"headon": {"hamiltonian": 1857.0, "momentum": 793.0, "psi4": 3220.0}}
+DIAG_FLOPS = {"headon": {"hamiltonian": 1857.0, "momentum": 793.0, "psi4": 3123.0}}
 # psi4 modes on the workload's extraction sphere: l <= 8, Gauss-Legendre x uniform nodes
 PSI4_LMAX, PSI4_NTHETA, PSI4_NPHI = 8, 24, 48
 # FP64 pipe of one SM: 2 DFMA per clock (ncu peak_sustained of

@@ -380,7 +380,8 @@ struct MetricPart {
     double Dvec[3];      // Delta^k
     double Dtr[3];       // Delta^k_km
     double Ric[6];       // Rbar_ij
-    double W, iW, dphi[3], DDphi[6];
+    double W, iW, dphi[3];
+    double DDphir[6];    // Dbar_i Dbar_j phi - 2 e_i phi e_j phi (what every consumer needs)
 };
 
 // The conformal metric and its inverse, first frame derivatives of h, and
@@ -652,14 +653,9 @@ __device__ __forceinline__ void metric_part(const PointIn& P, MetricPart& M)
         hess6<FAM, AX, S, ORD>(F(G_CF), dxp<S>(P, G_CF), dyp<AX, S>(P, G_CF), st, P.ox, g, dW, HW);
 #pragma unroll
         for (int s = 0; s < 6; s++) {
-            const int i = spi(s), j = spj(s);
+            // e_i e_j phi = -1/2 W^-1 H_ij W + 2 e_i phi e_j phi; the second term is left out
             const double dd = dot3<AX>(Dup[0][s], Dup[1][s], Dup[2][s], M.dphi);
-            if (hzero(AX, s))
-                M.DDphi[s] = -dd;
-            else if (i == AX || j == AX)   // d_AX phi = 0
-                M.DDphi[s] = fma(mhiW, HW[s], -dd);
-            else
-                M.DDphi[s] = fma(mhiW, HW[s], fma(sc2<1>(M.dphi[i]), M.dphi[j], -dd));
+            M.DDphir[s] = hzero(AX, s) ? -dd : fma(mhiW, HW[s], -dd);
         }
     }
 }
@@ -687,7 +683,7 @@ __device__ __forceinline__ void rhs_core(const PointIn& P, double eta, double ou
     const double* GH = M.GH;
     const double* Ric = M.Ric;
     const double* dphi = M.dphi;
-    const double* DDphi = M.DDphi;
+    const double* DDphir = M.DDphir;
     const double W = M.W;
 
     double a[6], lam[3], vet[3], bet[3];
@@ -697,9 +693,6 @@ __device__ __forceinline__ void rhs_core(const PointIn& P, double eta, double ou
     for (int i = 0; i < 3; i++) { lam[i] = ld(F(G_LAM + i)); vet[i] = ld(F(G_VET + i)); bet[i] = ld(F(G_BET + i)); }
     const double K = ld(F(G_TRK)), al = ld(F(G_ALPHA));
     const double al2 = sc2<1>(al);   // 2 alpha
-    double dphi2[3];                 // 2 d_k phi
-#pragma unroll
-    for (int k = 0; k < 3; k++) dphi2[k] = sc2<1>(dphi[k]);
     double dK[3], dal[3], dvet[3][3];
 #pragma unroll
     for (int k = 0; k < 3; k++) {
@@ -918,16 +911,13 @@ __device__ __forceinline__ void rhs_core(const PointIn& P, double eta, double ou
 #pragma unroll
         for (int s = 0; s < 6; s++) {
             const int i = spi(s), j = spj(s);
-            // 2 (d_i alpha d_j phi + d_j alpha d_i phi) + 2 alpha d_i phi d_j phi; both vanish
-            // when i or j is the two-point axis
-            double t;
-            if (i == AX || j == AX)
-                t = fma(al2, -DDphi[s], -DDal[s]);
-            else if (i == j)
-                t = fma(sc2<2>(dal[i]), dphi[i], fma(al2, fma(dphi2[i], dphi[j], -DDphi[s]), -DDal[s]));
-            else
-                t = fma(sc2<1>(dal[i]), dphi[j], fma(sc2<1>(dal[j]), dphi[i],
-                        fma(al2, fma(dphi2[i], dphi[j], -DDphi[s]), -DDal[s])));
+            // 2 alpha (2 e_i phi e_j phi - Dbar_i Dbar_j phi) = -2 alpha DDphir, and
+            // 2 (e_i alpha e_j phi + e_j alpha e_i phi), which vanishes when i or j is the
+            // two-point axis
+            double t = fma(-al2, DDphir[s], -DDal[s]);
+            if (i != AX && j != AX)
+                t = i == j ? fma(sc2<2>(dal[i]), dphi[i], t)
+                           : fma(sc2<1>(dal[i]), dphi[j], fma(sc2<1>(dal[j]), dphi[i], t));
             X[s] = fma(al, Ric[s], t);
         }
         double trX = gw[0] * X[0];
@@ -1051,14 +1041,15 @@ __device__ __forceinline__ double ham_core(const PointIn& P)
     double AA = Aud[0][0] * Aud[0][0];
 #pragma unroll
     for (int q = 1; q < 9; q++) AA = fma(Aud[q / 3][q % 3], Aud[q % 3][q / 3], AA);
-    double R = gw[0] * M.Ric[0], gp = gw[0] * M.dphi[0] * M.dphi[0], lp = gw[0] * M.DDphi[0];
+    // gammabar^ij (Dbar_i Dbar_j phi + e_i phi e_j phi) = lp + 3 gp with lp over DDphir
+    double R = gw[0] * M.Ric[0], gp = gw[0] * M.dphi[0] * M.dphi[0], lp = gw[0] * M.DDphir[0];
 #pragma unroll
     for (int s = 1; s < 6; s++) {
         R = fma(gw[s], M.Ric[s], R);
         gp = fma(gw[s], M.dphi[spi(s)] * M.dphi[spj(s)], gp);
-        lp = fma(gw[s], M.DDphi[s], lp);
+        lp = fma(gw[s], M.DDphir[s], lp);
     }
-    return fma((2.0 / 3.0) * K, K, fma(M.W * M.W, fma(-8.0, gp + lp, R), -AA));
+    return fma((2.0 / 3.0) * K, K, fma(M.W * M.W, fma(-8.0, fma(3.0, gp, lp), R), -AA));
 }
 
 // Momentum constraint, Eq. Mconstraint.  Its first two terms are Dbar_j Abar^ij
@@ -1151,8 +1142,8 @@ __device__ __forceinline__ double mom_core(const PointIn& P, double Mv[3])
 // a two-point axis the sum is (16u + 32kap)(f_other - f).
 struct AdvKoW {
     double w[3][6];   // per axis: offsets -3, -2, -1, +1, +2, +3
-    double c0;        // centre weight summed over the axes
-    double cax;       // two-point axis: weight of f_other - f
+    double c0;        // centre weight summed over the axes (with -cax folded in)
+    double cax;       // two-point axis: weight of f_other (the sum along it is cax (f_other - f))
 };
 
 template <int AX>
@@ -1177,7 +1168,7 @@ __device__ __forceinline__ void advko_weights(const double u[3], const bool fwd[
         W.w[d][5] = pk;
         c0 = d == 0 ? fma(-10.0, u[d], -20.0 * kap) : c0 + fma(-10.0, u[d], -20.0 * kap);
     }
-    W.c0 = c0;
+    W.c0 = AX >= 0 ? c0 - W.cax : c0;
 }
 
 template <int AX>
@@ -1187,7 +1178,7 @@ __device__ __forceinline__ double advko_apply(const double* f, const long st[3],
 #pragma unroll
     for (int d = 0; d < 3; d++) {
         if (d == AX) {
-            k = fma(W.cax, ld(f + ox) - ld(f), k);
+            k = fma(W.cax, ld(f + ox), k);
             continue;
         }
         const long s = st[d];
@@ -1219,8 +1210,8 @@ __host__ __device__ constexpr int off10(int j) { return j < 5 ? j - 5 : j - 4; }
 
 struct AdvKoW8 {
     double w[3][10];   // per axis, offsets off10(j)
-    double c0;         // centre weight summed over the axes
-    double cax;        // two-point axis: weight of f_other - f
+    double c0;         // centre weight summed over the axes (with -cax folded in)
+    double cax;        // two-point axis: weight of f_other (the sum along it is cax (f_other - f))
 };
 
 template <int AX>
@@ -1247,7 +1238,7 @@ __device__ __forceinline__ void advko_weights8(const double u[3], const bool fwd
         const double c = fma(-378.0, u[d], -252.0 * kap);   // p + q = u
         c0 = d == 0 ? c : c0 + c;
     }
-    W.c0 = c0;
+    W.c0 = AX >= 0 ? c0 - W.cax : c0;
 }
 
 template <int AX>
@@ -1257,7 +1248,7 @@ __device__ __forceinline__ double advko_apply8(const double* f, const long st[3]
 #pragma unroll
     for (int d = 0; d < 3; d++) {
         if (d == AX) {
-            k = fma(W.cax, ld(f + ox) - ld(f), k);
+            k = fma(W.cax, ld(f + ox), k);
             continue;
         }
 #pragma unroll

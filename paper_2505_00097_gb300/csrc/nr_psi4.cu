@@ -97,14 +97,15 @@ __device__ __forceinline__ void psi4_core(const PointIn& P, const double tet[3][
 #pragma unroll
     for (int s = 0; s < 6; s++) {
         const double w = offd(s) ? 2.0 : 1.0;
-        lap = fma(w * gi[s], M.DDphi[s], lap);
+        lap = fma(w * gi[s], M.DDphir[s], lap);
         gp = fma(w * gi[s], M.dphi[spi(s)] * M.dphi[spj(s)], gp);
     }
     double E[6];
 #pragma unroll
     for (int s = 0; s < 6; s++) {
         const int i = spi(s), j = spj(s);
-        const double Rphi = -2.0 * M.DDphi[s] - 2.0 * gf6[s] * (lap + 2.0 * gp) + 4.0 * M.dphi[i] * M.dphi[j];
+        // with Dbar_i Dbar_j phi = DDphir_ij + 2 e_i phi e_j phi, the e_i phi e_j phi terms cancel
+        const double Rphi = -2.0 * M.DDphir[s] - 2.0 * gf6[s] * (lap + 4.0 * gp);
         // K_ik gamma^kl K_lj, gamma^kl = W^2 gammabar^kl
         double kk = 0.0;
 #pragma unroll
