@@ -55,10 +55,10 @@ F_ALG = {"headon": 2894.3, "large3d": 4135.9, "headon8": 3844.9}
 TRAFFIC = {"headon": 24018688 + 98816 + 94506752 + 450309120,
            "headon8": 24950784 + 136704 + 87655936 + 339959296}
 # The same for the diagnostics (Hamiltonian and momentum constraints, psi4), per interior
-# point of one call, from one ncu capture of those kernels, by workload (head-on: k_ham 361 /
-# 216 / 640 DADD / DMUL / DFMA, k_mom 114 / 141 / 269, k_psi4 502 / 461 / 1080; the reductions
+# point of one call, from one ncu capture of those kernels, by workload (head-on: k_ham 360 /
+# 216 / 635 DADD / DMUL / DFMA, k_mom 114 / 141 / 269, k_psi4 502 / 461 / 1080; the reductions
 # and ghost copies add < 0.1; profiles/diagnostics_headon_256x2x512.md); absent: not captured
-DIAG_FLOPS = {"headon": {"hamiltonian": 1857.0, "momentum": 793.0, "psi4": 3123.0}}
+DIAG_FLOPS = {"headon": {"hamiltonian": 1846.0, "momentum": 793.0, "psi4": 3123.0}}
 # psi4 modes on the workload's extraction sphere: l <= 8, Gauss-Legendre x uniform nodes
 PSI4_LMAX, PSI4_NTHETA, PSI4_NPHI = 8, 24, 48
 # FP64 pipe of one SM: 2 DFMA per clock (ncu peak_sustained of
