@@ -188,15 +188,15 @@ __host__ __device__ constexpr bool dvz(int i, int k)
 {
     return FAM == FAM_CYL && AX == 1 && k == 1 && i == 2;
 }
-// Dhat_k Dhat_l V^i known to vanish (kl symmetric index): on a cylindrical-like grid
-// with a two-point azimuth, the (rho, phi) and (phi, z) pairs of component z
+// Delta_ks (s = ij symmetric) known to vanish: Delta_2(12) = 1/2 Dhat_1 h_22, and on a
+// cylindrical-like grid with a two-point azimuth Omega_1 h leaves the (2,2) component alone
 template <int FAM, int AX>
 __host__ __device__ constexpr bool dlz(int k, int s)
 {
-    // Delta_kij known to vanish: Delta_2(12) = 1/2 Dhat_1 h_22, and on a cylindrical-like grid
-    // with a two-point azimuth Omega_1 h leaves the (2,2) component alone
     return FAM == FAM_CYL && AX == 1 && k == 2 && s == 4;
 }
+// Dhat_k Dhat_l V^i known to vanish (kl symmetric index): on a cylindrical-like grid
+// with a two-point azimuth, the (rho, phi) and (phi, z) pairs of component z
 template <int FAM, int AX>
 __host__ __device__ constexpr bool ddbz(int kl, int i)
 {
