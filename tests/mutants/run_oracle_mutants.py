@@ -1,7 +1,7 @@
 """Mutation check of the oracle's pins (test infrastructure; not collected by pytest).
 
-Each entry below plants one plausible mistake in the oracle's BSSN right-hand side or
-Hamiltonian constraint: a wrong coefficient, sign, index or a dropped term. For every
+Each entry below plants one plausible mistake in the oracle: its BSSN right-hand side,
+constraints, stencils, boundary condition, det enforcement or integrators: a wrong coefficient, sign, index or a dropped term. For every
 mutant the script runs the oracle pin tests on a copy of the repository and reports
 whether some pin fails ("killed") or all pass ("SURVIVED").
 
@@ -55,6 +55,18 @@ MUT = [
  ("H: AA sign", "H[idx] = (2.0 / 3.0) * F.K * F.K - G.AA", "H[idx] = (2.0 / 3.0) * F.K * F.K + G.AA"),
  ("H: 8 gp", "(Rs - 8.0 * gp - 8.0 * lp)", "(Rs - 4.0 * gp - 8.0 * lp)"),
  ("H: 8 lp", "(Rs - 8.0 * gp - 8.0 * lp)", "(Rs - 8.0 * gp - 4.0 * lp)"),
+ ("M: 6 Abar dphi", "(div + dterm + 6.0 * ph - (2.0 / 3.0) * kk)", "(div + dterm + 4.0 * ph - (2.0 / 3.0) * kk)"),
+ ("M: 2/3 dK", "(div + dterm + 6.0 * ph - (2.0 / 3.0) * kk)", "(div + dterm + 6.0 * ph - (1.0 / 3.0) * kk)"),
+ ("M: Delta term sign", "(div + dterm + 6.0 * ph", "(div - dterm + 6.0 * ph"),
+ ("KO: 1/64 normalisation", "ko += p->ko_sigma[gf] / (64.0 * h[d] * R.S[d]) * orc_ko6(f, st[d]);", "ko += p->ko_sigma[gf] / (32.0 * h[d] * R.S[d]) * orc_ko6(f, st[d]);"),
+ ("upwind: direction", "fwd[k] = vet > 0.0;", "fwd[k] = vet < 0.0;"),
+ ("outer BC: 1/r term", "rhs[gf * T + idx] = -p->wavespeed[gf] * (radial + (f[0] - p->f_inf[gf]) / r);", "rhs[gf * T + idx] = -p->wavespeed[gf] * radial;"),
+ ("outer BC: sign", "rhs[gf * T + idx] = -p->wavespeed[gf] * (radial + (f[0] - p->f_inf[gf]) / r);", "rhs[gf * T + idx] = p->wavespeed[gf] * (radial + (f[0] - p->f_inf[gf]) / r);"),
+ ("RK4: weight of k2", "(k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i])", "(k1[i] + k2[i] + 3.0 * k3[i] + k4[i])"),
+ ("RK4: midpoint", "yt[i] = y[i] + dt * k3[i];", "yt[i] = y[i] + 0.5 * dt * k3[i];"),
+ ("det: exponent", "double f1 = expm1(-log1p(e1 + e2 + e3) / 3.0);", "double f1 = expm1(-log1p(e1 + e2 + e3) / 2.0);"),
+ ("SSPRK3: stage 2", "y2[i] = 0.75 * y[i] + 0.25 * (y1[i] + dt * k[i]);", "y2[i] = 0.5 * y[i] + 0.5 * (y1[i] + dt * k[i]);"),
+ ("SSPRK3: stage 3", "y[i] = (1.0 / 3.0) * y[i] + (2.0 / 3.0) * (y2[i] + dt * k[i]);", "y[i] = 0.5 * y[i] + 0.5 * (y2[i] + dt * k[i]);"),
  ("Ric: DLam Gamma sign", "for (int m = 0; m < 3; m++) s += M->Gam[k][j][m] * F->Lam[m];", "for (int m = 0; m < 3; m++) s -= M->Gam[k][j][m] * F->Lam[m];"),
  ("DDphi: dW dW sign", "+ F->dW[i] * F->dW[j] / (2.0 * F->W * F->W);", "- F->dW[i] * F->dW[j] / (2.0 * F->W * F->W);"),
  ("DDphi: connection sign", "for (int k = 0; k < 3; k++) s -= G->Gb[k][i][j] * G->dphi[k];", "for (int k = 0; k < 3; k++) s += G->Gb[k][i][j] * G->dphi[k];"),
@@ -64,8 +76,9 @@ MUT = [
  ("DDb: second connection sign", "s += M->Gam[i][l][m] * Db[m][k] - M->Gam[m][l][k] * Db[i][m];", "s += M->Gam[i][l][m] * Db[m][k] + M->Gam[m][l][k] * Db[i][m];"),
 ]
 
-TESTS = ["tests/test_oracle_physics.py", "tests/test_oracle_gauge.py", "tests/test_oracle_lambda_pin.py",
-         "tests/test_oracle_kerr_schild.py", "tests/test_oracle_momentum.py"]
+TESTS = ["tests/test_oracle_stencils.py", "tests/test_oracle_upwind.py", "tests/test_oracle_order8.py", "tests/test_oracle_momentum.py",
+         "tests/test_oracle_physics.py", "tests/test_oracle_gauge.py", "tests/test_oracle_lambda_pin.py",
+         "tests/test_oracle_kerr_schild.py"]
 
 
 def main():
