@@ -66,6 +66,12 @@ MUT = [
  ("RK4: midpoint", "yt[i] = y[i] + dt * k3[i];", "yt[i] = y[i] + 0.5 * dt * k3[i];"),
  ("det: exponent", "double f1 = expm1(-log1p(e1 + e2 + e3) / 3.0);", "double f1 = expm1(-log1p(e1 + e2 + e3) / 2.0);"),
  ("SSPRK3: stage 2", "y2[i] = 0.75 * y[i] + 0.25 * (y1[i] + dt * k[i]);", "y2[i] = 0.5 * y[i] + 0.5 * (y1[i] + dt * k[i]);"),
+ ("psi4: E kk sign", "E[i][j] = Ric[i][j] - kk + F->K * Kd[i][j];", "E[i][j] = Ric[i][j] + kk + F->K * Kd[i][j];"),
+ ("psi4: E K Kd", "E[i][j] = Ric[i][j] - kk + F->K * Kd[i][j];", "E[i][j] = Ric[i][j] - kk;"),
+ ("psi4: B derivative index", "if (e) b += gam[i][m] * e * DK[k][l][j];", "if (e) b += gam[i][m] * e * DK[l][k][j];"),
+ ("psi4: real part B sign", "psi4[idx] = -0.5 * (Et[1][1] - Et[2][2]) + Bt[1][2];", "psi4[idx] = -0.5 * (Et[1][1] - Et[2][2]) - Bt[1][2];"),
+ ("psi4: imaginary part E", "psi4[T + idx] = Et[1][2] + 0.5 * (Bt[1][1] - Bt[2][2]);", "psi4[T + idx] = -Et[1][2] + 0.5 * (Bt[1][1] - Bt[2][2]);"),
+ ("psi4: Gram-Schmidt step", "for (int d = 0; d < 3; d++) u[a][d] -= dot * u[b][d];", "for (int d = 0; d < 3; d++) u[a][d] -= 0.0 * dot * u[b][d];"),
  ("SSPRK3: stage 3", "y[i] = (1.0 / 3.0) * y[i] + (2.0 / 3.0) * (y2[i] + dt * k[i]);", "y[i] = 0.5 * y[i] + 0.5 * (y2[i] + dt * k[i]);"),
  ("Ric: DLam Gamma sign", "for (int m = 0; m < 3; m++) s += M->Gam[k][j][m] * F->Lam[m];", "for (int m = 0; m < 3; m++) s -= M->Gam[k][j][m] * F->Lam[m];"),
  ("DDphi: dW dW sign", "+ F->dW[i] * F->dW[j] / (2.0 * F->W * F->W);", "- F->dW[i] * F->dW[j] / (2.0 * F->W * F->W);"),
@@ -78,7 +84,7 @@ MUT = [
 
 TESTS = ["tests/test_oracle_stencils.py", "tests/test_oracle_upwind.py", "tests/test_oracle_order8.py", "tests/test_oracle_momentum.py",
          "tests/test_oracle_physics.py", "tests/test_oracle_gauge.py", "tests/test_oracle_lambda_pin.py",
-         "tests/test_oracle_kerr_schild.py"]
+         "tests/test_oracle_kerr_schild.py", "tests/test_oracle_psi4.py"]
 
 
 def main():
