@@ -72,6 +72,11 @@ MUT = [
  ("psi4: real part B sign", "psi4[idx] = -0.5 * (Et[1][1] - Et[2][2]) + Bt[1][2];", "psi4[idx] = -0.5 * (Et[1][1] - Et[2][2]) - Bt[1][2];"),
  ("psi4: imaginary part E", "psi4[T + idx] = Et[1][2] + 0.5 * (Bt[1][1] - Bt[2][2]);", "psi4[T + idx] = -Et[1][2] + 0.5 * (Bt[1][1] - Bt[2][2]);"),
  ("psi4: Gram-Schmidt step", "for (int d = 0; d < 3; d++) u[a][d] -= dot * u[b][d];", "for (int d = 0; d < 3; d++) u[a][d] -= 0.0 * dot * u[b][d];"),
+ ("parity: tensor sign", "for (int s = 0; s < 6; s++) par[4 + s] = (int8_t)(pd[SYM_I[s]] * pd[SYM_J[s]]);", "for (int s = 0; s < 6; s++) par[4 + s] = (int8_t)(pd[SYM_I[s]]);"),
+ ("rescale: vector dS sign", "Rd[k] = -R->dS[i][k] / (S * S);", "Rd[k] = R->dS[i][k] / (S * S);"),
+ ("rescale: vector ddS cross term", "+ 2.0 * R->dS[i][k] * R->dS[i][l] / (S * S * S);", "+ R->dS[i][k] * R->dS[i][l] / (S * S * S);"),
+ ("rescale: tensor cross term", "+ R->dS[i][k] * R->dS[j][l] + R->dS[i][l] * R->dS[j][k] +", "+ 2.0 * R->dS[i][k] * R->dS[j][l] +"),
+ ("BL: psi", "psi += mass[q] / (2.0 * d);", "psi += mass[q] / d;"),
  ("SSPRK3: stage 3", "y[i] = (1.0 / 3.0) * y[i] + (2.0 / 3.0) * (y2[i] + dt * k[i]);", "y[i] = 0.5 * y[i] + 0.5 * (y2[i] + dt * k[i]);"),
  ("Ric: DLam Gamma sign", "for (int m = 0; m < 3; m++) s += M->Gam[k][j][m] * F->Lam[m];", "for (int m = 0; m < 3; m++) s -= M->Gam[k][j][m] * F->Lam[m];"),
  ("DDphi: dW dW sign", "+ F->dW[i] * F->dW[j] / (2.0 * F->W * F->W);", "- F->dW[i] * F->dW[j] / (2.0 * F->W * F->W);"),
@@ -82,7 +87,7 @@ MUT = [
  ("DDb: second connection sign", "s += M->Gam[i][l][m] * Db[m][k] - M->Gam[m][l][k] * Db[i][m];", "s += M->Gam[i][l][m] * Db[m][k] + M->Gam[m][l][k] * Db[i][m];"),
 ]
 
-TESTS = ["tests/test_oracle_stencils.py", "tests/test_oracle_upwind.py", "tests/test_oracle_order8.py", "tests/test_oracle_momentum.py",
+TESTS = ["tests/test_oracle_grid.py", "tests/test_oracle_stencils.py", "tests/test_oracle_upwind.py", "tests/test_oracle_order8.py", "tests/test_oracle_momentum.py",
          "tests/test_oracle_physics.py", "tests/test_oracle_gauge.py", "tests/test_oracle_lambda_pin.py",
          "tests/test_oracle_kerr_schild.py", "tests/test_oracle_psi4.py"]
 
