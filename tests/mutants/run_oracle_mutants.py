@@ -77,6 +77,8 @@ MUT = [
  ("rescale: vector ddS cross term", "+ 2.0 * R->dS[i][k] * R->dS[i][l] / (S * S * S);", "+ R->dS[i][k] * R->dS[i][l] / (S * S * S);"),
  ("rescale: tensor cross term", "+ R->dS[i][k] * R->dS[j][l] + R->dS[i][l] * R->dS[j][k] +", "+ 2.0 * R->dS[i][k] * R->dS[j][l] +"),
  ("BL: psi", "psi += mass[q] / (2.0 * d);", "psi += mass[q] / d;"),
+ ("ord8: KO normalisation", "ko += p->ko_sigma[gf] / (ldexp(1.0, 2 * r) * h[d] * R.S[d]) * sten(f, st[d], Wd.ko, -r, r);", "ko += p->ko_sigma[gf] / (ldexp(1.0, 2 * r - 1) * h[d] * R.S[d]) * sten(f, st[d], Wd.ko, -r, r);"),
+ ("ord8: upwind window", "for (int i = 0; i < n; i++) x[i] = i - (m - 1);", "for (int i = 0; i < n; i++) x[i] = i - (m + 1);"),
  ("SSPRK3: stage 3", "y[i] = (1.0 / 3.0) * y[i] + (2.0 / 3.0) * (y2[i] + dt * k[i]);", "y[i] = 0.5 * y[i] + 0.5 * (y2[i] + dt * k[i]);"),
  ("Ric: DLam Gamma sign", "for (int m = 0; m < 3; m++) s += M->Gam[k][j][m] * F->Lam[m];", "for (int m = 0; m < 3; m++) s -= M->Gam[k][j][m] * F->Lam[m];"),
  ("DDphi: dW dW sign", "+ F->dW[i] * F->dW[j] / (2.0 * F->W * F->W);", "- F->dW[i] * F->dW[j] / (2.0 * F->W * F->W);"),
