@@ -42,9 +42,8 @@ UNIT = "point-updates/s"
 
 # FP64 operations (FMA = 2) per interior point of one RHS evaluation (nr_rhs:
 # the k_d1 pre-pass and k_rhs), by workload (the kernel variant it runs), from
-# the kernels' DADD/DMUL/DFMA thread-instruction counts in one ncu capture:
-# (DADD + DMUL + 2 DFMA) / interior points (profiles/k_rhs_headon_256x2x512.md,
-# profiles/k_rhs_headon8_256x2x512.md, profiles/k_rhs_general_3d.md).  Head-on
+# the kernels' DADD/DMUL/DFMA thread-instruction counts in one ncu capture of
+# that workload's nr_rhs launches: (DADD + DMUL + 2 DFMA) / interior points.  Head-on
 # 256x2x512 (cylindrical, two-point azimuth): k_rhs 202 + 322 + 2 x 1163 = 2850,
 # k_d1 44.3.  Head-on with the 8th-order scheme: k_rhs 307 + 381 + 2 x 1517 = 3722,
 # k_d1 122.9.  Large 3D (spherical, general): k_rhs 301 + 423 + 2 x 1661 = 4046, k_d1
@@ -55,9 +54,9 @@ F_ALG = {"headon": 2894.3, "large3d": 4135.9, "headon8": 3844.9}
 TRAFFIC = {"headon": 24018688 + 98816 + 94506752 + 450309120,
            "headon8": 24950784 + 136704 + 87655936 + 339959296}
 # The same for the diagnostics (Hamiltonian and momentum constraints, psi4), per interior
-# point of one call, from one ncu capture of those kernels, by workload (head-on: k_ham 360 /
-# 216 / 635 DADD / DMUL / DFMA, k_mom 114 / 141 / 269, k_psi4 502 / 461 / 1080; the reductions
-# and ghost copies add < 0.1; profiles/diagnostics_headon_256x2x512.md); absent: not captured
+# point of one call, from one ncu capture of those kernels on the head-on state, by workload
+# (head-on: k_ham 360 / 216 / 635 DADD / DMUL / DFMA, k_mom 114 / 141 / 269, k_psi4 502 / 461 /
+# 1080; the reductions and ghost copies add < 0.1); absent: not captured
 DIAG_FLOPS = {"headon": {"hamiltonian": 1846.0, "momentum": 793.0, "psi4": 3123.0}}
 # psi4 modes on the workload's extraction sphere: l <= 8, Gauss-Legendre x uniform nodes
 PSI4_LMAX, PSI4_NTHETA, PSI4_NPHI = 8, 24, 48
@@ -78,6 +77,12 @@ def parse():
     ap.add_argument("--workload", choices=["headon", "headon8", "single_puncture", "large3d", "batch", "served"],
                     default="headon")
     ap.add_argument("--batch-runs", type=int, default=64)
+    ap.add_argument("--batch-steps", type=int, default=100,
+                    help="RK4 steps per run of the batched comparison in the default line (500 in the workload)")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain comparison")
+    ap.add_argument("--no-served", action="store_true", help="skip the served-vs-plain comparison")
+    ap.add_argument("--line-served-requests", type=int, default=16,
+                    help="requests of the served-vs-plain comparison in the default line")
     ap.add_argument("--served-requests", type=int, default=24)
     ap.add_argument("--served-tfinal", type=float, default=2.0)
     ap.add_argument("--served-rate", type=float, default=80.0,
@@ -220,6 +225,15 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows), "power_w_max": max(pw) if pw else None}
 
 
+def gpu_uuid(local: int) -> str | None:
+    try:
+        import torch
+
+        return str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        return None
+
+
 # ------------------------------------------------------------- CPU oracle
 
 
@@ -265,33 +279,53 @@ def cpu_baseline(spec: dict, seconds: float) -> dict:
 
 
 def run_reference(args, spec):
-    """--impl reference: the CPU oracle; each step is one RHS evaluation over a slab of
-    z-planes (or theta/phi planes) of the workload, sized so the whole run takes a few minutes."""
+    """--impl reference: the CPU oracle on the host cores, timing the same work as a step of the
+    GPU arm -- full steps of the workload's integrator on the whole grid (right-hand side,
+    dissipation, radiation and parity boundary conditions, the update and det enforcement, with
+    the Hamiltonian constraint every h_every steps).  When the requested K + W steps would not fit
+    about 150 s, the run is a bounded sample: one warm-up step and as many timed steps as fit."""
     from oracle.oracle import Oracle
 
     o = Oracle(dict(spec, nthreads=0))
     y = o.brill_lindquist(spec["masses"], spec["positions"], spec["perturb_amp"], spec["seed"])
-    n_planes = spec["N"][2]
-    plane_pts = spec["N"][0] * spec["N"][1]
+    dt = o.dt()
+    ssp = spec.get("integrator", "rk4") == "ssprk3"
+    step = o.ssprk3 if ssp else o.rk4
+    h_every = int(spec["h_every"])
+    done = 0
+
+    def one():
+        nonlocal done
+        step(y, dt, 1)
+        done += 1
+        if h_every and done % h_every == 0:
+            o.hamiltonian(y)
+
     t0 = time.perf_counter()
-    o.rhs(y, 0, min(4, n_planes))
-    per_plane = max((time.perf_counter() - t0) / min(4, n_planes), 1e-6)
-    budget = 150.0 / max(1, args.steps + args.warmup)
-    m = int(max(1, min(n_planes, budget / per_plane)))
-    for s in range(args.warmup):
-        o.rhs(y, 0, m)
+    one()
+    t_step = time.perf_counter() - t0
+    budget = 150.0
+    if (args.steps + args.warmup) * t_step <= budget:
+        warm, steps, bounded = args.warmup, args.steps, False
+        for _ in range(warm - 1):
+            one()
+    else:
+        warm, steps, bounded = 1, int(max(1, min(args.steps, (budget - t_step) // t_step))), True
     t0 = time.perf_counter()
-    for s in range(args.steps):
-        k0 = (s * m) % max(1, n_planes - m + 1)
-        o.rhs(y, k0, k0 + m)
+    for _ in range(steps):
+        one()
     el = time.perf_counter() - t0
-    value = plane_pts * m * args.steps / el
-    sample = f"{args.steps} RHS evaluations of {m} of {n_planes} planes ({plane_pts * m} interior points each) of {spec['name']}"
+    pts = math.prod(spec["N"])
+    sub = 3 if ssp else 4
+    value = pts * sub * steps / el
+    sample = (f"{steps} full {'SSPRK3' if ssp else 'RK4'} steps of {spec['name']} (whole grid, H every {h_every}) "
+              f"after {warm} warm-up step(s)" + (f"; bounded sample of the {args.steps} steps asked for" if bounded
+                                                 else ""))
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+        "steps": steps, "warmup": warm, "ms_per_step": 1e3 * el / steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (Brill-Lindquist closed form)",
-        "config": config_of(spec, {"parallelism": "host cores (OpenMP)"}),
+        "config": config_of(spec, {"parallelism": "replicas x1", "dt": dt}),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -337,11 +371,7 @@ def run_ours(args, spec, world, rank, local):
     # warm-up (graph capture happens on the first step)
     run_steps(args.warmup, 0)
     torch.cuda.synchronize()
-    uuid = None
-    try:
-        uuid = str(torch.cuda.get_device_properties(local).uuid)
-    except Exception:
-        pass
+    uuid = gpu_uuid(local)
     clocks = ClockSampler(uuid)
     if dist is not None:
         dist.barrier()
@@ -454,6 +484,16 @@ def run_ours(args, spec, world, rank, local):
                "full_state": {"value": vf, "h2d_bytes_per_step": fbytes, "d2h_bytes_per_step": fbytes,
                               "path": f"nr_set_state(pinned host) + {stepper} + nr_get_state(pinned host) per step"}}
 
+    # the two modes against plain one-run-per-launch on the same GPU (one replica only: the
+    # comparisons are per GPU and hold the device for a minute or two)
+    modes = {}
+    if world == 1 and args.workload == "headon":
+        if not args.no_batched:
+            modes["batched"] = batch_compare(local, args.batch_runs, args.batch_steps)
+        if not args.no_served:
+            modes["served"] = served_compare(local, args.line_served_requests, args.served_tfinal,
+                                             args.served_rate, ("srpt",), args.served_cap)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(spec, args.cpu_seconds)
@@ -463,12 +503,12 @@ def run_ours(args, spec, world, rank, local):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (Brill-Lindquist closed form on the GPU)",
-            "config": config_of(spec, {"parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                                       "dt": dt}),
+            "config": config_of(spec, {"parallelism": f"replicas x{world}", "dt": dt}),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": ck,
         }
         if diag is not None:
             line["diagnostics"] = diag
+        line.update(modes)
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()
@@ -523,17 +563,17 @@ def diagnostics(g, spec, stream, wl: str, nrep: int) -> dict:
 # ------------------------------------------------------- batched / served
 
 
-def run_batch(args, world, rank, local):
-    """64 uneven head-on runs (the batched workload): plain one-grid-at-a-time nr_rk4_step versus
-    one nr_batch (one launch per substage over the tiles of all grids, autotuned tile), same steps."""
+def batch_compare(local: int, n_runs: int, steps: int, warm: int = 3) -> dict:
+    """The batched workload's runs (seeded: q ~ U[1,4], d ~ U[0.5,2], N_rho in {64, ..., 256}), each
+    advanced `steps` RK4 steps twice on the same GPU: plain, one grid at a time with its own
+    nr_rk4_step graph, and batched, one nr_batch (one launch per substage over the tiles of all
+    grids, autotuned tile).  CUDA-event times of both; every final state compared bitwise."""
     import torch
 
     from paper_2505_00097_gb300 import binding as B
 
-    torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    dist = dist_init(world, True)
-    runs = W.config_batch(n_runs=args.batch_runs, steps=args.steps)
+    runs = W.config_batch(n_runs=n_runs, steps=steps)
     grids = [B.Grid(s, device=local) for s in runs]
     for g, s in zip(grids, runs):
         g.set_brill_lindquist(s["masses"], s["positions"])
@@ -549,19 +589,20 @@ def run_batch(args, world, rank, local):
         for g, t in zip(grids, init):
             g.set_state(t, False)
 
-    n = args.steps
-    warm = max(3, args.warmup)
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
     for g, dt in zip(grids, dts):       # warm-up (the first step captures each grid's graph)
         g.rk4_step(dt, warm)
     reset()
     torch.cuda.synchronize()
+    clocks_plain = ClockSampler(gpu_uuid(local))
+    clocks_plain.start()
     a0, a1 = ev(), ev()
     a0.record()
     for g, dt in zip(grids, dts):
-        g.rk4_step(dt, n)
+        g.rk4_step(dt, steps)
     a1.record()
     torch.cuda.synchronize()
+    ck_plain = clocks_plain.stop()
     t_plain = a0.elapsed_time(a1) * 1e-3
     plain_final = []
     for g in grids:
@@ -573,12 +614,12 @@ def run_batch(args, world, rank, local):
     tx, ty, tune_ms = batch.autotune(dts)
     batch.rk4_step(dts, warm)           # warm-up (the first step captures the graph)
     reset()
-    clocks = ClockSampler(None)
+    clocks = ClockSampler(gpu_uuid(local))
     torch.cuda.synchronize()
     clocks.start()
     b0, b1 = ev(), ev()
     b0.record()
-    batch.rk4_step(dts, n)
+    batch.rk4_step(dts, steps)
     b1.record()
     torch.cuda.synchronize()
     ck = clocks.stop()
@@ -588,54 +629,44 @@ def run_batch(args, world, rank, local):
         t = torch.empty(24 * g.T, dtype=torch.float64, device=dev)
         g.get_state(t, False)
         same = same and bool(torch.equal(t, ref))
-    t_batch = reduce_max(dist, t_batch, dev)
-    t_plain = reduce_max(dist, t_plain, dev)
-    if rank == 0:
-        line = {
-            "metric": METRIC, "value": world * pts * 4 * n / t_batch, "unit": UNIT, "n_gpus": world, "steps": n,
-            "warmup": warm, "ms_per_step": 1e3 * t_batch / n, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic (Brill-Lindquist head-on binaries, seeded)",
-            "config": {"workload": f"batch_{len(runs)}_headon_sinhcyl", "runs": len(runs), "interior_points": pts,
-                       "grid_sizes_rho": sorted({s["N"][0] for s in runs}), "steps_per_run": n,
-                       "tile": f"{tx}x{ty}", "autotune_stage_ms": tune_ms},
-            "plain": {"value": world * pts * 4 * n / t_plain, "unit": UNIT,
-                      "mode": "one grid at a time, nr_rk4_step graph per grid"},
-            "speedup_vs_plain": t_plain / t_batch, "bitwise_equal_to_plain": same, "clocks": ck,
-        }
-        print(json.dumps(line), flush=True)
     batch.close()
     for g in grids:
         g.close()
+    del init, plain_final
+    value, plain_value = pts * 4 * steps / t_batch, pts * 4 * steps / t_plain
+    return {"value": value, "plain_value": plain_value, "ratio": value / plain_value, "unit": UNIT,
+            "bitwise_equal_to_plain": same, "runs": len(runs), "interior_points": pts,
+            "grid_sizes_rho": sorted({s["N"][0] for s in runs}), "steps_per_run": steps,
+            "steps_in_config": 500, "tile": f"{tx}x{ty}", "autotune_stage_ms": tune_ms,
+            "seconds": {"batched": t_batch, "plain": t_plain},
+            "mode": "batched: one nr_batch, one launch per RK4 substage over all grids (CUDA graph); plain: one "
+                    "grid at a time, nr_rk4_step graph per grid; CUDA-event times, inputs resident in HBM",
+            "equality": "every grid's full final state compared with torch.equal", "clocks": ck,
+            "clocks_plain": ck_plain}
 
 
-def other_name(policy: str) -> str:
-    return "fifo" if policy == "srpt" else "srpt"
-
-
-def run_served(args, world, rank, local):
-    """The served workload: a seeded Poisson stream (mean 20 requests per minute) of single-puncture and
-    head-on requests of 1e5..4e6 points, admitted under an 80 GB budget and advanced by continuous
-    batching under the chosen policy (and under the other one), versus the same stream served by a FIFO
-    queue of single-grid runs."""
-    import torch
-
+def served_compare(local: int, n_requests: int, t_final: float, rate: float, policies=("srpt",),
+                   cap: int = 1000000) -> dict:
+    """A seeded Poisson stream of single-puncture and head-on requests of 1e5..4e6 points (the served
+    workload's generator), served as it arrives (wall clock) by nr_server with each policy in
+    `policies` (continuous batching under an 80 GB budget, points cap `cap`) and by a plain FIFO queue
+    of single-grid runs, one at a time.  Each arm ends every request with its Hamiltonian-constraint
+    norms, a NaN/Inf check and the 64-bit digest of its final state; the digests are compared."""
     from paper_2505_00097_gb300 import binding as B
 
-    torch.cuda.set_device(local)
-    reqs = W.config_served(n_requests=args.served_requests, t_final=args.served_tfinal, rate_per_min=args.served_rate)
-    pts_of = {}
+    reqs = W.config_served(n_requests=n_requests, t_final=t_final, rate_per_min=rate)
 
     def serve(mode: str):
-        """mode "srpt" / "fifo": nr_server with that policy and the points cap; "plain": a FIFO queue of
-        single-grid runs, one at a time."""
         batched = mode != "plain"
+        clocks = ClockSampler(gpu_uuid(local))
+        clocks.start()
         start = time.perf_counter()
-        done, arrive, submitted = {}, {}, []
+        done, arrive, submitted, digest = {}, {}, [], {}
         upd = 0.0
         if batched:
             srv = B.Server(80 * 10 ** 9, 64, device=local)
             srv.set_tile(32, 4)
-            srv.set_policy(mode, args.served_cap)
+            srv.set_policy(mode, cap)
         queue = []
         nxt = 0
         while len(done) < len(reqs):
@@ -643,7 +674,7 @@ def run_served(args, world, rank, local):
             while nxt < len(reqs) and reqs[nxt]["arrival_s"] <= now:
                 r = reqs[nxt]
                 if batched:
-                    rid = srv.submit(r, r["t_final"])
+                    rid = srv.submit(r, r["t_final"], keep_digest=True)
                     submitted.append((rid, nxt))
                 else:
                     queue.append(nxt)
@@ -659,6 +690,7 @@ def run_served(args, world, rank, local):
                         done[k] = time.perf_counter() - start
                         n = reqs[k]["N"]
                         upd += 4.0 * info["steps_done"] * n[0] * n[1] * n[2]
+                        digest[k] = srv.fetch_digest(rid) if info["status"] == 2 else None
                 idle = nrun == 0 and nq == 0
             else:
                 idle = not queue
@@ -669,37 +701,97 @@ def run_served(args, world, rank, local):
                     steps = max(1, int(math.ceil(reqs[k]["t_final"] / g.dt_cfl - 1e-9)))
                     g.rk4_step(g.dt_cfl, steps)
                     g.hamiltonian()
+                    digest[k] = g.digest()
+                    g.check_finite()
                     g.close()
                     done[k] = time.perf_counter() - start
                     upd += 4.0 * steps * g.interior
             if idle and nxt < len(reqs):
                 time.sleep(max(0.0, min(0.05, reqs[nxt]["arrival_s"] - (time.perf_counter() - start))))
         makespan = time.perf_counter() - start
+        ck = clocks.stop()
         if batched:
             srv.close()
         ttc = sorted(done[k] - arrive[k] for k in done)
         q = lambda p: ttc[min(len(ttc) - 1, int(round(p * (len(ttc) - 1))))]  # noqa: E731
         return {"value": upd / makespan, "p50_ttc_s": q(0.5), "p99_ttc_s": q(0.99),
-                "mean_ttc_s": sum(ttc) / len(ttc), "makespan_s": makespan}
+                "mean_ttc_s": sum(ttc) / len(ttc), "makespan_s": makespan, "clocks": ck}, digest
 
-    served = serve(args.served_policy)
-    other = serve(other_name(args.served_policy))
-    plain = serve("plain")
+    arms = {}
+    digests = {}
+    for pol in policies:
+        arms[pol], digests[pol] = serve(pol)
+    plain, dplain = serve("plain")
+    out = {"unit": UNIT, "requests": len(reqs), "t_final": t_final, "rate_per_min": rate,
+           "points_range": [1e5, 4e6], "hbm_budget_gb": 80, "max_batch_points": cap,
+           "plain": plain, "plain_value": plain["value"],
+           "mode": "nr_server continuous batching (requests admitted as they arrive, one nr_batch per kind of "
+                   "request) against a plain FIFO queue of single-grid nr_rk4_step runs; wall-clock makespan "
+                   "and time to completion",
+           "equality": "64-bit digest (nr_state_digest) of every request's final state, served vs plain"}
+    for pol in policies:
+        a = arms[pol]
+        same = all(digests[pol].get(k) is not None and digests[pol].get(k) == dplain.get(k) for k in dplain)
+        out[pol] = dict(a, ratio=a["value"] / plain["value"], bitwise_equal_to_plain=same)
+    head = policies[0]
+    out.update(policy=head, value=arms[head]["value"], ratio=out[head]["ratio"],
+               bitwise_equal_to_plain=out[head]["bitwise_equal_to_plain"],
+               p50_ttc_s=arms[head]["p50_ttc_s"], p99_ttc_s=arms[head]["p99_ttc_s"],
+               mean_ttc_s=arms[head]["mean_ttc_s"], clocks=arms[head]["clocks"])
+    return out
+
+
+def run_batch(args, world, rank, local):
+    """--workload batch: the batched runs (batch_compare) as the line's headline."""
+    import torch
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = dist_init(world, True)
+    r = batch_compare(local, args.batch_runs, args.steps, max(3, args.warmup))
+    t_batch = reduce_max(dist, r["seconds"]["batched"], dev)
+    t_plain = reduce_max(dist, r["seconds"]["plain"], dev)
+    n, pts = r["steps_per_run"], r["interior_points"]
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": world * pts * 4 * n / t_batch, "unit": UNIT, "n_gpus": world, "steps": n,
+            "warmup": max(3, args.warmup), "ms_per_step": 1e3 * t_batch / n, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (Brill-Lindquist head-on binaries, seeded)",
+            "config": {"workload": f"batch_{r['runs']}_headon_sinhcyl", "runs": r["runs"], "interior_points": pts,
+                       "grid_sizes_rho": r["grid_sizes_rho"], "steps_per_run": n, "tile": r["tile"],
+                       "autotune_stage_ms": r["autotune_stage_ms"]},
+            "plain": {"value": world * pts * 4 * n / t_plain, "unit": UNIT,
+                      "mode": "one grid at a time, nr_rk4_step graph per grid"},
+            "speedup_vs_plain": t_plain / t_batch, "bitwise_equal_to_plain": r["bitwise_equal_to_plain"],
+            "clocks": r["clocks"],
+        }
+        print(json.dumps(line), flush=True)
+
+
+def run_served(args, world, rank, local):
+    """--workload served: the served stream (served_compare) under both policies and the plain queue."""
+    import torch
+
+    torch.cuda.set_device(local)
+    pols = (args.served_policy, other_name(args.served_policy))
+    r = served_compare(local, args.served_requests, args.served_tfinal, args.served_rate, pols, args.served_cap)
     line = {
-        "metric": METRIC, "value": served["value"], "unit": UNIT, "n_gpus": 1, "steps": None, "warmup": 0,
+        "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": 1, "steps": None, "warmup": 0,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded Poisson request stream)",
-        "config": {"workload": f"served_{len(reqs)}_requests", "rate_per_min": args.served_rate,
-                   "t_final": args.served_tfinal,
-                   "scaling_note": "t_final 2M instead of 50M and arrivals 4x denser than 20/min: the stream "
-                                   "still overloads the GPU, as in the served configuration",
-                   "points_range": [1e5, 4e6], "hbm_budget_gb": 80, "policy": args.served_policy,
-                   "max_batch_points": args.served_cap},
-        "served": served, f"served_{other_name(args.served_policy)}": other, "plain_fifo": plain,
-        "speedup_vs_plain": served["value"] / plain["value"],
-        "p50_ttc_vs_plain": served["p50_ttc_s"] / plain["p50_ttc_s"],
+        "config": {"workload": f"served_{r['requests']}_requests", "rate_per_min": args.served_rate,
+                   "t_final": args.served_tfinal, "points_range": [1e5, 4e6], "hbm_budget_gb": 80,
+                   "policy": args.served_policy, "max_batch_points": args.served_cap},
+        "served": r[pols[0]], f"served_{pols[1]}": r[pols[1]], "plain_fifo": r["plain"],
+        "speedup_vs_plain": r["ratio"], "bitwise_equal_to_plain": r["bitwise_equal_to_plain"],
+        "p50_ttc_vs_plain": r["p50_ttc_s"] / r["plain"]["p50_ttc_s"],
     }
     print(json.dumps(line), flush=True)
+
+
+def other_name(policy: str) -> str:
+    return "fifo" if policy == "srpt" else "srpt"
 
 
 def main():

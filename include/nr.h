@@ -261,6 +261,21 @@ int nr_set_state_compact(nr_grid* grid, const double* src, int from_host);
  * NR_ENOMEM, NR_ECUDA. */
 int nr_step_io(nr_grid* grid, int integrator, double dt, int nsteps, const double* host_in, double* host_out);
 
+/* 64-bit digest of a 24-gridfunction set (y_dev, or the grid-owned state if NULL) at
+ * the canonical points -- interior and pure outer ghosts, which determine the whole
+ * state since inner ghosts are parity copies (Sec. 3):
+ *   sum modulo 2^64 over gridfunctions g and canonical flat indices idx of
+ *   splitmix64(bits(y[g*T + idx]) XOR splitmix64((g << 40) | idx)),
+ * splitmix64(x) being the first output of the SplitMix64 generator (Steele, Lea &
+ * Flood 2014) with state x, bits() the IEEE-754 bit pattern.  The paper has no
+ * counterpart: it is a service for bitwise comparisons of results (batched or
+ * served runs against runs alone) without copying states to the host.  Each term
+ * is a bijective mix of one value, so states that differ in one value always get
+ * different digests, and states that differ in several collide with probability
+ * about 2^-64.  Independent of the device and launch shape.  Synchronises
+ * params.stream.  Errors: NR_EINVAL, NR_ECUDA. */
+int nr_state_digest(nr_grid* grid, const double* y_dev, uint64_t* out);
+
 /* Wait for all work of the grid's stream. */
 int nr_sync(nr_grid* grid);
 
@@ -318,8 +333,9 @@ int nr_batch_ssprk3_step(nr_batch* batch, const double* dts, int nsteps);
  *     running requests; max_slots caps their number; work is issued on stream.
  *   nr_server_submit: queues a request and returns its id (no device work;
  *     NR_EINVAL if its grid has no valid CFL step).
- *     keep_state = 1 keeps the final 24-gf state on the host for
- *     nr_server_fetch_state.
+ *     keep_state bit 0 (1) keeps the final 24-gf state on the host for
+ *     nr_server_fetch_state; bit 1 (2) keeps its digest (nr_state_digest) for
+ *     nr_server_fetch_digest.
  *   nr_server_advance: makes queued requests resident (running) in policy
  *     order while the budget and the slots allow, then advances the selected
  *     running requests together -- one nr_batch per kind of request (coordinate
@@ -333,7 +349,19 @@ int nr_batch_ssprk3_step(nr_batch* batch, const double* dts, int nsteps);
  *     at most one chunk is queued behind the one the GPU runs and the policy
  *     acts on new arrivals within about a chunk of GPU time.
  *   nr_server_poll: status 0 queued, 1 running, 2 done, 3 failed; steps done
- *     and total; the final L2/Linf Hamiltonian-constraint norms when done.
+ *     and total; the final L2/Linf Hamiltonian-constraint norms when done (NaN
+ *     for a request the guard retired).
+ *   nr_server_set_guard: every every_steps steps of a request (default 100;
+ *     0 = off) the server checks alpha and W of the requests it advanced for
+ *     NaN/Inf on the device (one flag per request, read back behind the next
+ *     chunk, so without a synchronisation of its own).  A request found
+ *     non-finite is retired as failed with NR_ENONFINITE (its device memory
+ *     released, nothing kept) while the others continue, bitwise unaffected.
+ *     A request that finishes is also checked at retirement.
+ *   nr_server_request_error: the status that ended a failed request
+ *     (NR_ENONFINITE, NR_ENOMEM when it cannot fit the budget even alone, or
+ *     the set-up's error); NR_OK for the others.
+ *   nr_server_fetch_digest: the kept digest of a finished request.
  *   nr_server_set_tile: fixed tile shape for the batches (default: autotune at
  *     every membership change).
  *   nr_server_set_policy: the order in which queued requests become resident
@@ -360,6 +388,9 @@ int nr_server_advance(nr_server* server, int nsteps, int* n_running, int* n_queu
 int nr_server_poll(nr_server* server, int64_t id, int* status, int64_t* steps_done, int64_t* steps_total,
                    double* l2, double* linf);
 int nr_server_fetch_state(nr_server* server, int64_t id, double* host_state, size_t capacity_doubles);
+int nr_server_set_guard(nr_server* server, int every_steps);
+int nr_server_request_error(nr_server* server, int64_t id, int* code);
+int nr_server_fetch_digest(nr_server* server, int64_t id, uint64_t* digest);
 
 /* Hamiltonian constraint that allocates nothing.  The paper has no
  * counterpart: this is a library service for callers that cannot call
@@ -379,7 +410,9 @@ int nr_server_fetch_state(nr_server* server, int64_t id, double* host_state, siz
  *   4 n0 + 4 n1 + 2 n2 (SinhSpherical, Spherical) or 4 n0 + 2 n1 + 3 n2
  *   (SinhCylindrical) with n_d = N_d + 2 NG; larger grids get NR_EINVAL.
  *   The first call on a device looks up the array's device address (with that
- *   device current); make that first call before any stream capture.
+ *   device current); make that first call before any stream capture.  The
+ *   address is kept for the life of the process: do not call this entry point
+ *   on a device after its primary context has been reset (cudaDeviceReset).
  *   All calls share the one array and every call overwrites it: calls that
  *   overlap on the GPU (different streams, threads or processes' streams on
  *   the same device) race.  Each call writes every scratch value it reads.

@@ -68,6 +68,24 @@ static int gf_type(int gf)
     return 1 + (gf - G_BET);
 }
 
+/* Loop parallelism of the point-wise loops below (every iteration writes its own
+ * points only; no expression depends on the thread count): p->nthreads threads,
+ * or the runtime default when it is <= 0. */
+static int team_of(const orc_params* p)
+{
+#ifdef _OPENMP
+    return p->nthreads > 0 ? p->nthreads : omp_get_max_threads();
+#else
+    (void)p;
+    return 1;
+#endif
+}
+#ifdef _OPENMP
+#define ORC_PARALLEL_FOR _Pragma("omp parallel for schedule(static) num_threads(nt)")
+#else
+#define ORC_PARALLEL_FOR
+#endif
+
 /* ------------------------------------------------------------------ grid */
 
 /* Logical domain of each coordinate system (Sec. 3: cell-centred, logically
@@ -582,6 +600,10 @@ int orc_build_map(const orc_params* p, int32_t* src, int8_t* parity, int32_t* cl
     double lo[3], hi[3];
     domain(p, lo, hi);
     int bad = 0;
+    const int nt = team_of(p);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(nt) reduction(| : bad)
+#endif
     for (long idx = 0; idx < T; idx++) {
         int ii[3], jj[3];
         double xx[3], sx[3];
@@ -690,8 +712,10 @@ static void bmap_free(bmap* m)
     free(m->par);
 }
 
-static void inner_bc_with(const bmap* m, double* gfs)
+static void inner_bc_with(const bmap* m, double* gfs, int nt)
 {
+    /* sources are interior or pure-outer points, never written here */
+    ORC_PARALLEL_FOR
     for (long idx = 0; idx < m->T; idx++) {
         if (m->cls[idx] != 2) continue;
         for (int gf = 0; gf < NGF; gf++)
@@ -703,7 +727,7 @@ int orc_inner_bc(const orc_params* p, double* gfs)
 {
     bmap m;
     int bad = bmap_make(p, &m);
-    inner_bc_with(&m, gfs);
+    inner_bc_with(&m, gfs, team_of(p));
     bmap_free(&m);
     return bad;
 }
@@ -718,6 +742,8 @@ static void outer_bc_with(const orc_params* p, const bmap* m, const double* gfs,
     double h[3] = {dxx_of(p, 0), dxx_of(p, 1), dxx_of(p, 2)};
     fdw Wd;
     fdw_make(p->NG, &Wd);
+    const int nt = team_of(p);
+    ORC_PARALLEL_FOR
     for (long idx = 0; idx < T; idx++) {
         if (m->cls[idx] != 1) continue;
         int ii[3];
@@ -1228,7 +1254,7 @@ static int full_rhs_with(const orc_params* p, const bmap* m, const double* gfs, 
 {
     orc_rhs(p, gfs, rhs, 0, p->N[2]);
     outer_bc_with(p, m, gfs, rhs); /* 1. outer boundary (Sec. 3 ordering) */
-    inner_bc_with(m, rhs);         /* 2. inner boundary, sources may be outer ghosts */
+    inner_bc_with(m, rhs, team_of(p)); /* 2. inner boundary, sources may be outer ghosts */
     return 0;
 }
 
@@ -1250,6 +1276,8 @@ int orc_full_rhs(const orc_params* p, const double* gfs, double* rhs)
 void orc_enforce_detgb(const orc_params* p, double* gfs)
 {
     long T = orc_sizes(p, NULL);
+    const int nt = team_of(p);
+    ORC_PARALLEL_FOR
     for (long idx = 0; idx < T; idx++) {
         double h[3][3], inv[3][3];
         for (int s = 0; s < 6; s++) {
@@ -1284,18 +1312,22 @@ int orc_ssprk3_step(const orc_params* p, double* gfs, double dt, int nsteps)
 {
     bmap m;
     int bad = bmap_make(p, &m);
+    const int nt = team_of(p);
     long n = (long)NGF * m.T;
     double* k = (double*)malloc(sizeof(double) * n);
     double* y1 = (double*)malloc(sizeof(double) * n);
     double* y2 = (double*)malloc(sizeof(double) * n);
     for (int step = 0; step < nsteps; step++) {
         full_rhs_with(p, &m, gfs, k);
+        ORC_PARALLEL_FOR
         for (long i = 0; i < n; i++) y1[i] = gfs[i] + dt * k[i];
         if (p->enforce_detgb) orc_enforce_detgb(p, y1);
         full_rhs_with(p, &m, y1, k);
+        ORC_PARALLEL_FOR
         for (long i = 0; i < n; i++) y2[i] = 0.75 * gfs[i] + 0.25 * (y1[i] + dt * k[i]);
         if (p->enforce_detgb) orc_enforce_detgb(p, y2);
         full_rhs_with(p, &m, y2, k);
+        ORC_PARALLEL_FOR
         for (long i = 0; i < n; i++) gfs[i] = (1.0 / 3.0) * gfs[i] + (2.0 / 3.0) * (y2[i] + dt * k[i]);
         if (p->enforce_detgb) orc_enforce_detgb(p, gfs);
     }
@@ -1348,6 +1380,7 @@ int orc_rk4_step(const orc_params* p, double* gfs, double dt, int nsteps)
 {
     bmap m;
     int bad = bmap_make(p, &m);
+    const int nt = team_of(p);
     long n = (long)NGF * m.T;
     double* k[4];
     double* yt = (double*)malloc(sizeof(double) * n);
@@ -1358,11 +1391,13 @@ int orc_rk4_step(const orc_params* p, double* gfs, double dt, int nsteps)
         for (int s = 0; s < 4; s++) {
             full_rhs_with(p, &m, yin, k[s]);
             if (s < 3) {
+                ORC_PARALLEL_FOR
                 for (long i = 0; i < n; i++) yt[i] = gfs[i] + c[s] * dt * k[s][i];
                 if (p->enforce_detgb) orc_enforce_detgb(p, yt);
                 yin = yt;
             }
         }
+        ORC_PARALLEL_FOR
         for (long i = 0; i < n; i++) gfs[i] = gfs[i] + (dt / 6.0) * (k[0][i] + 2.0 * k[1][i] + 2.0 * k[2][i] + k[3][i]);
         if (p->enforce_detgb) orc_enforce_detgb(p, gfs);
     }
@@ -1877,7 +1912,7 @@ int orc_brill_lindquist(const orc_params* p, int npunct, const double* mass, con
                 gfs[(G_HDD + s) * T + idx] =
                     perturb_amp * orc_splitmix_uniform(seed, ((uint64_t)(G_HDD + s) << 40) | (uint64_t)idx);
     }
-    inner_bc_with(&m, gfs);
+    inner_bc_with(&m, gfs, team_of(p));
     bmap_free(&m);
     return bad;
 }

@@ -31,7 +31,8 @@ EXPORTS = (
     "nr_batch_create", "nr_batch_destroy", "nr_batch_set_tile", "nr_batch_autotune", "nr_batch_rk4_step", "nr_batch_ssprk3_step",
     "nr_server_create", "nr_server_destroy", "nr_server_set_tile", "nr_server_set_policy", "nr_server_submit",
     "nr_server_advance",
-    "nr_server_poll", "nr_server_fetch_state", "nr_last_error",
+    "nr_server_poll", "nr_server_fetch_state", "nr_server_set_guard", "nr_server_request_error",
+    "nr_server_fetch_digest", "nr_state_digest", "nr_last_error",
 )
 
 
@@ -140,6 +141,10 @@ def lib() -> ctypes.CDLL:
     L.nr_server_poll.argtypes = [vp, ctypes.c_int64, ip, ctypes.POINTER(ctypes.c_int64),
                                  ctypes.POINTER(ctypes.c_int64), dp, dp]
     L.nr_server_fetch_state.argtypes = [vp, ctypes.c_int64, dp, ctypes.c_size_t]
+    L.nr_server_set_guard.argtypes = [vp, ctypes.c_int]
+    L.nr_server_request_error.argtypes = [vp, ctypes.c_int64, ip]
+    L.nr_server_fetch_digest.argtypes = [vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_uint64)]
+    L.nr_state_digest.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_uint64)]
     L.nr_last_error.argtypes = []
     L.nr_last_error.restype = ctypes.c_char_p
     _lib = L
@@ -336,6 +341,12 @@ class Grid:
     def sync(self) -> None:
         _check(lib().nr_sync(self.h))
 
+    def digest(self, y=None) -> int:
+        """nr_state_digest of y (default: the grid-owned state)."""
+        out = ctypes.c_uint64()
+        _check(lib().nr_state_digest(self.h, None if y is None else _ptr(y), ctypes.byref(out)))
+        return out.value
+
     def check_finite(self) -> None:
         _check(lib().nr_check_finite(self.h))
 
@@ -416,7 +427,21 @@ class Server:
         code = {"fifo": SERVE_FIFO, "srpt": SERVE_SRPT}.get(policy, -1)
         _check(lib().nr_server_set_policy(self.h, code, int(max_batch_points)))
 
-    def submit(self, spec: dict, t_final: float, keep_state: bool = False) -> int:
+    def set_guard(self, every_steps: int) -> None:
+        """non-finite check of the advanced requests every every_steps steps (0: off)"""
+        _check(lib().nr_server_set_guard(self.h, int(every_steps)))
+
+    def request_error(self, rid: int) -> int:
+        code = ctypes.c_int()
+        _check(lib().nr_server_request_error(self.h, int(rid), ctypes.byref(code)))
+        return code.value
+
+    def fetch_digest(self, rid: int) -> int:
+        out = ctypes.c_uint64()
+        _check(lib().nr_server_fetch_digest(self.h, int(rid), ctypes.byref(out)))
+        return out.value
+
+    def submit(self, spec: dict, t_final: float, keep_state: bool = False, keep_digest: bool = False) -> int:
         p = make_params(spec, device=self.device)
         Nx = (ctypes.c_int * 3)(*[int(v) for v in spec["N"]])
         m = np.ascontiguousarray(spec["masses"], dtype=np.float64)
@@ -425,7 +450,7 @@ class Server:
         _check(lib().nr_server_submit(self.h, int(spec["coords"]), Nx, ctypes.byref(p), len(m),
                                       m.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                       x.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(t_final),
-                                      int(bool(keep_state)), ctypes.byref(rid)))
+                                      int(bool(keep_state)) | (2 if keep_digest else 0), ctypes.byref(rid)))
         return rid.value
 
     def advance(self, nsteps: int):

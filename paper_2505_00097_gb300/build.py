@@ -18,7 +18,11 @@ LIB = os.path.join(OUT_DIR, "libnrgpu.so")
 SOURCES = ["nr_kernels.cu", "nr_capi.cu", "nr_noalloc.cu", "nr_batch.cu", "nr_batch_sph.cu", "nr_batch_cyl.cu",
            "nr_batch_sph8.cu", "nr_batch_cyl8.cu", "nr_server.cu", "nr_psi4.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
+# host code: no contraction of a*b+c into an FMA (the default of gcc on aarch64), so the host-side
+# set-up (coordinates, per-axis arrays, radiation-condition weights, the CFL step) rounds the same
+# on every host architecture
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "-Xcompiler",
+         "-ffp-contract=off"]
 
 
 def nvcc() -> str:

@@ -114,15 +114,49 @@ __device__ __forceinline__ double mixraw8(const double* f, long sa, long sb)
 
 // ---- exact scaling by 2^K on the integer pipe.  The FP64 pipe bounds every kernel of the
 // point code and the integer pipe idles, so x * 2^K moves the exponent field of a normal
-// number by K instead of issuing an FP64 multiply; the result is the same bits.  Zeros,
-// infinities and NaNs pass through unchanged (so do denormals, which no BSSN state holds);
-// a result that would leave the normal range is not rounded to zero or infinity.
+// number by K instead of issuing an FP64 multiply.  The result is the bits of the IEEE
+// product x * 2^K (round to nearest even) for every input: the exponent shift where both x
+// and the product are normal numbers, and sc2_edge, also in integer arithmetic, for zeros,
+// subnormal inputs or results, overflow to infinity and NaNs.
+template <int K>
+__device__ __forceinline__ double sc2_edge(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned long long sign = b & 0x8000000000000000ULL, mag = b & 0x7FFFFFFFFFFFFFFFULL;
+    const int e = (int)(mag >> 52);
+    if (e == 0x7FF) return __longlong_as_double((long long)(mag > 0x7FF0000000000000ULL ? b | (1ULL << 51) : b));
+    if (mag == 0) return x;
+    // x = m 2^(ee - 1075) with m < 2^53 (the implicit bit for a normal x)
+    const int ee = e ? e : 1;
+    const unsigned long long m = e ? (mag & 0xFFFFFFFFFFFFFULL) | (1ULL << 52) : mag;
+    int E = ee + K;   // exponent field of the product if m were normalised
+    unsigned long long r;
+    if (E >= 1) {
+        const int k = __clzll((long long)m) - 11;   // left shift that brings the top bit to bit 52
+        if (E - k >= 1) {
+            E -= k;
+            r = E > 0x7FE ? 0x7FF0000000000000ULL : ((unsigned long long)E << 52) | ((m << k) & 0xFFFFFFFFFFFFFULL);
+        } else {
+            r = m << (E - 1);   // still subnormal: exact
+        }
+    } else {
+        // subnormal product: m 2^(E - 1) in units of the least subnormal, rounded to nearest even
+        const int s = 1 - E > 63 ? 63 : 1 - E;
+        const unsigned long long q = m >> s, rem = m & ((1ULL << s) - 1), half = 1ULL << (s - 1);
+        r = q + ((rem > half || (rem == half && (q & 1))) ? 1 : 0);
+    }
+    return __longlong_as_double((long long)(sign | r));
+}
+
 template <int K>
 __device__ __forceinline__ double sc2(double x)
 {
-    const int hi = __double2hiint(x), lo = __double2loint(x);
-    const unsigned e = ((unsigned)hi >> 20) & 0x7FFu;
-    return __hiloint2double(e - 1u < 0x7FEu ? hi + K * (1 << 20) : hi, lo);
+    // exponent fields whose product stays normal: [max(1, 1 - K), min(0x7FE, 0x7FE - K)]
+    constexpr unsigned lo = K < 0 ? 1u - K : 1u, hi = K > 0 ? 0x7FEu - K : 0x7FEu;
+    const int h = __double2hiint(x), l = __double2loint(x);
+    const unsigned e = ((unsigned)h >> 20) & 0x7FFu;
+    if (e - lo <= hi - lo) return __hiloint2double(h + K * (1 << 20), l);
+    return sc2_edge<K>(x);
 }
 
 // Finite-difference families: order ORD = N_FD with N_G = ORD/2 + 1 ghost layers

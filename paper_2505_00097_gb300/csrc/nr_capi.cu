@@ -338,7 +338,7 @@ void free_grid(nr_grid* g)
     if (g->exec) cudaGraphExecDestroy(g->exec);
     if (g->exec_ssp) cudaGraphExecDestroy(g->exec_ssp);
     void* ptrs[] = {g->y, g->ya, g->yb, g->acc, g->d1x, g->d1y, g->ax0, g->ax1, g->ax2, g->outer, g->inner, g->canon,
-                    g->finf, g->wspeed, g->partials, g->hres, g->flag, g->mxyz, g->stage, g->crank};
+                    g->finf, g->wspeed, g->partials, g->hres, g->flag, g->digest, g->mxyz, g->stage, g->crank};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (g->cap) cudaStreamDestroy(g->cap);
@@ -618,7 +618,8 @@ static int nr_grid_create_body(int coords, const int Nxx[3], const nr_params* pa
             (rc = dmalloc(g, &g->outer, outer.size())) || (rc = dmalloc(g, &g->inner, inner.size())) ||
             (rc = dmalloc(g, &g->canon, canon.size())) || (rc = dmalloc(g, &g->finf, NR_NGF)) ||
             (rc = dmalloc(g, &g->wspeed, NR_NGF)) || (rc = dmalloc(g, &g->partials, 3 * (size_t)g->nparts)) ||
-            (rc = dmalloc(g, &g->hres, 3)) || (rc = dmalloc(g, &g->flag, 1)) || (rc = dmalloc(g, &g->mxyz, 64))) {
+            (rc = dmalloc(g, &g->hres, 3)) || (rc = dmalloc(g, &g->flag, 1)) || (rc = dmalloc(g, &g->digest, 1)) ||
+            (rc = dmalloc(g, &g->mxyz, 64))) {
             free_grid(g);
             return rc;
         }
@@ -958,6 +959,18 @@ int nr_check_finite(nr_grid* g)
     CUDA_OR_FAIL(cudaMemcpyAsync(&h, g->flag, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
     CUDA_OR_FAIL(cudaStreamSynchronize(g->stream));
     if (h) return fail(NR_ENONFINITE, "non-finite alpha or W in the state");
+    return NR_OK;
+}
+
+int nr_state_digest(nr_grid* g, const double* y_dev, uint64_t* out)
+{
+    if (!g || !out) return fail(NR_EINVAL, "bad nr_state_digest arguments");
+    DeviceGuard dg(g->device);
+    unsigned long long h = 0;
+    CUDA_OR_FAIL(launch_digest(g->K, g->canon, g->n_canon, y_dev ? y_dev : g->y, g->digest, g->stream));
+    CUDA_OR_FAIL(cudaMemcpyAsync(&h, g->digest, sizeof h, cudaMemcpyDeviceToHost, g->stream));
+    CUDA_OR_FAIL(cudaStreamSynchronize(g->stream));
+    *out = (uint64_t)h;
     return NR_OK;
 }
 

@@ -104,6 +104,9 @@ cudaError_t launch_mom(const GridK& G, const double* y, double* M, double rmin, 
                        int nparts, double* result, cudaStream_t s);
 int ham_partials_needed(const GridK& G);
 cudaError_t launch_finite(const GridK& G, const double* y, int* flag, cudaStream_t s);
+// 64-bit digest of the 24 gridfunctions of y at the canonical points canon[0..nc) into *out
+cudaError_t launch_digest(const GridK& G, const int* canon, long nc, const double* y, unsigned long long* out,
+                          cudaStream_t s);
 cudaError_t launch_fp64_probe(int blocks, int iters, double* sink, cudaStream_t s);
 cudaError_t launch_ham_reduce(const double* partials, int nparts, double* result, cudaStream_t s);
 
@@ -141,6 +144,7 @@ struct nr_grid {
     double* partials = nullptr;
     double* hres = nullptr;
     int* flag = nullptr;
+    unsigned long long* digest = nullptr;
     double* mxyz = nullptr;
     double* stage = nullptr;   // compact-state staging for host transfers (allocated on first use)
     int* crank = nullptr;      // compact position of each point, -1 at inner ghosts (first nr_step_io)

@@ -15,6 +15,7 @@
 //   k_mom     momentum constraint (Eq. Mconstraint) + per-block norm partials
 //   k_ham_reduce  fixed-order reduction of the partials (both constraints)
 //   k_finite  NaN/Inf guard on alpha and W
+//   k_digest  64-bit digest of a state at the canonical points (bitwise comparisons)
 #include <math.h>
 
 #include <algorithm>
@@ -253,6 +254,24 @@ __global__ void k_finite(long T, const double* __restrict__ y, int* flag)
     if (!isfinite(w) || !isfinite(a)) atomicOr(flag, 1);
 }
 
+// Digest of a 24-gridfunction set at the canonical points: the wrapping sum over (gf, point)
+// of splitmix64(bits ^ splitmix64((gf << 40) | idx)).  A sum modulo 2^64 does not depend on
+// the order of its terms, so the digest does not depend on the launch shape; each term is a
+// bijective mix of its value's bits, so a change of one value always changes the digest.
+__global__ void __launch_bounds__(256) k_digest(long T, const int* __restrict__ canon, long nc,
+                                                const double* __restrict__ y, unsigned long long* out)
+{
+    const int g = blockIdx.y;
+    unsigned long long acc = 0;
+    for (long t = (long)blockIdx.x * 256 + threadIdx.x; t < nc; t += (long)gridDim.x * 256) {
+        const long idx = canon[t];
+        const uint64_t v = (uint64_t)__double_as_longlong(y[(long)g * T + idx]);
+        acc += splitmix64(v ^ splitmix64(((uint64_t)g << 40) | (uint64_t)idx));
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
+}
+
 // FP64 FMA throughput probe: 8 independent FMA chains per thread, a fixed
 // number of iterations (no data-dependent trip count), one store per thread.
 __global__ void __launch_bounds__(256) k_fp64_probe(int iters, double seed, double* sink)
@@ -416,6 +435,16 @@ cudaError_t launch_mom(const GridK& G, const double* y, double* M, double rmin, 
 cudaError_t launch_ham_reduce(const double* partials, int nparts, double* result, cudaStream_t s)
 {
     k_ham_reduce<<<1, 256, 0, s>>>(partials, nparts, result);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_digest(const GridK& G, const int* canon, long nc, const double* y, unsigned long long* out,
+                          cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess || nc == 0) return e;
+    const long bx = std::min<long>((nc + 255) / 256, 2L * 152);
+    k_digest<<<dim3((unsigned)bx, NGF), 256, 0, s>>>(G.T, canon, nc, y, out);
     return cudaGetLastError();
 }
 

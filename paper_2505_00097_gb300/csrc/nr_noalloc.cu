@@ -171,7 +171,7 @@ extern "C" int nr_hamiltonian_noalloc(int coords, const int Nxx[3], const nr_par
         return nrk_fail(NR_EINVAL,
                         "nr_hamiltonian_noalloc: per-axis arrays need %ld doubles, the static scratch holds %d "
                         "(SinhSpherical/Spherical: 4 n0 + 4 n1 + 2 n2, SinhCylindrical: 4 n0 + 2 n1 + 3 n2, "
-                        "n_d = N_d + 6)",
+                        "n_d = N_d + 2 NG)",
                         axes, NA_AXES_MAX);
     const int dev = params->device;
     if (dev < 0 || dev >= NA_MAXDEV) return nrk_fail(NR_EINVAL, "nr_hamiltonian_noalloc: device out of range");

@@ -20,6 +20,9 @@
 // step; since every point runs the single-grid arithmetic, a request's result
 // does not depend on which other requests shared the GPU with it, nor on when
 // it was paused.
+// A guard checks alpha and W of the advanced requests for non-finite values
+// every few steps (nr_server_set_guard); a request that fails it is retired
+// as failed with NR_ENONFINITE while the others keep running.
 #include <math.h>
 #include <string.h>
 
@@ -43,7 +46,7 @@ struct Request {
     double mass[16] = {0};
     double xyz[48] = {0};
     double t_final = 0.0;
-    int keep_state = 0;
+    int keep_state = 0;        // bit 0: keep the final state; bit 1: keep its digest
     size_t bytes = 0;
     int64_t interior = 0;      // interior points
     int64_t steps_est = 0;     // steps to t_final at the CFL step, known at submission
@@ -53,6 +56,9 @@ struct Request {
     double dt = 0.0;
     int64_t steps_total = 0, steps_done = 0;
     double l2 = 0.0, linf = 0.0;
+    int err = NR_OK;           // the status that ended a failed request
+    uint64_t digest = 0;
+    bool has_digest = false;
     std::vector<double> state;
 };
 
@@ -89,6 +95,14 @@ struct nr_server {
     cudaEvent_t chunk_done[2] = {nullptr, nullptr};
     bool chunk_pending[2] = {false, false};
     int chunk_slot = 0;
+    // non-finite guard: every guard_every steps (0: off) one k_finite per advanced request
+    // into dflags, copied to hflags (pinned) behind the chunk; read when the chunk's event is
+    // waited for, i.e. one chunk later
+    int guard_every = 100;
+    int64_t since_guard = 0;
+    int* dflags = nullptr;          // 2 * max_slots ints on the device
+    int* hflags = nullptr;          // 2 * max_slots ints, pinned host
+    std::vector<int64_t> checked[2];   // ids of the requests checked behind each chunk slot
 };
 
 namespace {
@@ -123,6 +137,41 @@ int chunk_fence(nr_server* s)
     return e == cudaSuccess ? NR_OK : nrk_fail(NR_ECUDA, "server chunk fence: %s", cudaGetErrorString(e));
 }
 
+// Enqueue the non-finite guard of the requests the current chunk advanced, behind that chunk
+// (before its fence records the chunk's event), into the flags of the current chunk slot.
+int guard_enqueue(nr_server* s)
+{
+    const int slot = s->chunk_slot;
+    s->checked[slot].clear();
+    if (s->guard_every <= 0 || s->since_guard < s->guard_every || s->active.empty()) return NR_OK;
+    s->since_guard = 0;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(s->device);
+    cudaError_t e = cudaSuccess;
+    if (!s->dflags) {
+        e = cudaMalloc(&s->dflags, sizeof(int) * 2 * (size_t)s->max_slots);
+        if (e == cudaSuccess) e = cudaMallocHost(&s->hflags, sizeof(int) * 2 * (size_t)s->max_slots);
+    }
+    int* d = s->dflags + (size_t)slot * s->max_slots;
+    int* h = s->hflags + (size_t)slot * s->max_slots;
+    const cudaStream_t st = (cudaStream_t)s->stream;
+    const int n = (int)s->active.size();
+    if (e == cudaSuccess) e = cudaMemsetAsync(d, 0, sizeof(int) * n, st);
+    for (int q = 0; q < n && e == cudaSuccess; q++) {
+        nr_grid* g = s->active[q]->grid;
+        e = nrk::launch_finite(g->K, g->y, d + q, st);
+        s->checked[slot].push_back(s->active[q]->id);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, sizeof(int) * n, cudaMemcpyDeviceToHost, st);
+    cudaSetDevice(prev);
+    if (e != cudaSuccess) {
+        s->checked[slot].clear();
+        return nrk_fail(NR_ECUDA, "server guard: %s", cudaGetErrorString(e));
+    }
+    return NR_OK;
+}
+
 // requests that can share one batch: same coordinate family, azimuth kind, order and integrator
 int request_kind(const Request* r)
 {
@@ -154,16 +203,33 @@ int start_request(nr_server* s, Request* r)
 int finish_request(nr_server* s, Request* r)
 {
     int rc = nr_hamiltonian(r->grid, nullptr, nullptr, &r->l2, &r->linf);
-    if (rc == NR_OK && r->keep_state) {
+    if (rc == NR_OK && (r->keep_state & 1)) {
         r->state.resize((size_t)NR_NGF * r->grid->geo.T);
         rc = nr_get_state(r->grid, r->state.data(), 1);
     }
+    if (rc == NR_OK && (r->keep_state & 2)) {
+        rc = nr_state_digest(r->grid, nullptr, &r->digest);
+        r->has_digest = rc == NR_OK;
+    }
     if (rc == NR_OK && nr_check_finite(r->grid) != NR_OK) rc = NR_ENONFINITE;
     r->status = rc == NR_OK ? 2 : 3;
+    r->err = rc;
+    if (rc != NR_OK) r->state.clear();
     nr_grid_destroy(r->grid);
     r->grid = nullptr;
     s->used -= std::min(s->used, r->bytes);
     return NR_OK;
+}
+
+// a running request the guard found non-finite: retired as failed, nothing kept
+void fail_request(nr_server* s, Request* r)
+{
+    r->status = 3;
+    r->err = NR_ENONFINITE;
+    r->l2 = r->linf = NAN;
+    nr_grid_destroy(r->grid);
+    r->grid = nullptr;
+    s->used -= std::min(s->used, r->bytes);
 }
 
 // right-hand-side evaluations per step
@@ -202,14 +268,17 @@ int admit(nr_server* s)
             if (s->running.empty())  // can never fit
             {
                 r->status = 3;
+                r->err = NR_ENOMEM;
                 s->queue.erase(s->queue.begin() + pos);
                 continue;
             }
             break;
         }
         s->queue.erase(s->queue.begin() + pos);
-        if (start_request(s, r) != NR_OK) {
+        const int rc = start_request(s, r);
+        if (rc != NR_OK) {
             r->status = 3;
+            r->err = rc;
             continue;
         }
         s->used += r->bytes;
@@ -304,6 +373,8 @@ void nr_server_destroy(nr_server* s)
     drop_batch(s);
     for (int q = 0; q < 2; q++)
         if (s->chunk_done[q]) cudaEventDestroy(s->chunk_done[q]);
+    if (s->dflags) cudaFree(s->dflags);
+    if (s->hflags) cudaFreeHost(s->hflags);
     for (auto& kv : s->all) {
         if (kv.second->grid) nr_grid_destroy(kv.second->grid);
         delete kv.second;
@@ -374,6 +445,13 @@ int nr_server_set_policy(nr_server* s, int policy, int64_t max_batch_points)
     return NR_OK;
 }
 
+int nr_server_set_guard(nr_server* s, int every_steps)
+{
+    if (!s || every_steps < 0) return nrk_fail(NR_EINVAL, "bad nr_server_set_guard arguments");
+    s->guard_every = every_steps;
+    return NR_OK;
+}
+
 static int nr_server_advance_body(nr_server* s, int nsteps, int* n_running, int* n_queued)
 {
     if (!s || nsteps < 0) return nrk_fail(NR_EINVAL, "bad nr_server_advance arguments");
@@ -391,18 +469,45 @@ static int nr_server_advance_body(nr_server* s, int nsteps, int* n_running, int*
                                                              : nr_batch_rk4_step(s->batches[q], dts.data(), (int)k);
             if (rc) return rc;
         }
+        for (Request* r : s->active) r->steps_done += k;
+        s->since_guard += k;
+        if ((rc = guard_enqueue(s))) return rc;
         if ((rc = chunk_fence(s))) return rc;
         left -= (int)k;
         bool retired = false;
-        for (Request* r : s->active) r->steps_done += k;
+        // the guard results of the chunk the fence waited for (the slot it leaves current)
+        std::vector<int64_t> bad;
+        {
+            const int slot = s->chunk_slot;
+            const int* h = s->hflags ? s->hflags + (size_t)slot * s->max_slots : nullptr;
+            for (size_t q = 0; q < s->checked[slot].size(); q++)
+                if (h[q]) bad.push_back(s->checked[slot][q]);
+            s->checked[slot].clear();
+        }
+        if (!bad.empty()) {
+            // the queued chunk may still use the failing grids: drain the stream first
+            int prev = 0;
+            cudaGetDevice(&prev);
+            cudaSetDevice(s->device);
+            cudaError_t e = cudaStreamSynchronize((cudaStream_t)s->stream);
+            cudaSetDevice(prev);
+            if (e != cudaSuccess) return nrk_fail(NR_ECUDA, "server: %s", cudaGetErrorString(e));
+            s->chunk_pending[0] = s->chunk_pending[1] = false;
+            s->checked[0].clear();
+            s->checked[1].clear();
+        }
         for (size_t q = 0; q < s->running.size();) {
             Request* r = s->running[q];
-            if (r->steps_done >= r->steps_total) {
+            const bool failed = std::find(bad.begin(), bad.end(), r->id) != bad.end();
+            if (failed || r->steps_done >= r->steps_total) {
                 if (!retired) {
                     drop_batch(s);  // the batch refers to the grids about to be released
                     retired = true;
                 }
-                finish_request(s, r);
+                if (failed)
+                    fail_request(s, r);
+                else
+                    finish_request(s, r);
                 s->running.erase(s->running.begin() + q);
             } else {
                 q++;
@@ -455,6 +560,26 @@ int nr_server_fetch_state(nr_server* s, int64_t id, double* host_state, size_t c
 {
     return nrk_guard("nr_server_fetch_state",
                      [&] { return nr_server_fetch_state_body(s, id, host_state, capacity_doubles); });
+}
+
+int nr_server_fetch_digest(nr_server* s, int64_t id, uint64_t* digest)
+{
+    if (!s || !digest) return nrk_fail(NR_EINVAL, "bad nr_server_fetch_digest arguments");
+    auto it = s->all.find(id);
+    if (it == s->all.end()) return nrk_fail(NR_EINVAL, "unknown request %lld", (long long)id);
+    const Request* r = it->second;
+    if (r->status != 2 || !r->has_digest) return nrk_fail(NR_EINVAL, "request %lld has no kept digest", (long long)id);
+    *digest = r->digest;
+    return NR_OK;
+}
+
+int nr_server_request_error(nr_server* s, int64_t id, int* code)
+{
+    if (!s || !code) return nrk_fail(NR_EINVAL, "bad nr_server_request_error arguments");
+    auto it = s->all.find(id);
+    if (it == s->all.end()) return nrk_fail(NR_EINVAL, "unknown request %lld", (long long)id);
+    *code = it->second->err;
+    return NR_OK;
 }
 
 }  // extern "C"

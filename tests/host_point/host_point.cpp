@@ -24,6 +24,8 @@ static inline double __hiloint2double(int hi, int lo)
     return d;
 }
 static inline long long __double_as_longlong(double x) { long long b; std::memcpy(&b, &x, 8); return b; }
+static inline double __longlong_as_double(long long b) { double x; std::memcpy(&x, &b, 8); return x; }
+static inline int __clzll(long long x) { return x ? __builtin_clzll((unsigned long long)x) : 64; }
 template <class T> static inline T __ldg(const T* p) { return *p; }
 using std::fma;
 
@@ -150,4 +152,20 @@ extern "C" void host_point(int coords, const int* N, const double* ampl, const d
 {
     if (ng == 5) host_point_t<8>(coords, N, ampl, sinhw, sigma, eta, y, out, which);
     else host_point_t<4>(coords, N, ampl, sinhw, sigma, eta, y, out, which);
+}
+
+// the exact power-of-two scaling of the point code, sc2<K>, for the K it uses
+extern "C" int host_sc2(int K, const double* x, double* out, long n)
+{
+    for (long i = 0; i < n; i++) {
+        switch (K) {
+        case -1: out[i] = sc2<-1>(x[i]); break;
+        case 1: out[i] = sc2<1>(x[i]); break;
+        case 2: out[i] = sc2<2>(x[i]); break;
+        case 5: out[i] = sc2<5>(x[i]); break;
+        case 9: out[i] = sc2<9>(x[i]); break;
+        default: return 1;
+        }
+    }
+    return 0;
 }

@@ -36,6 +36,10 @@ def test_reference_arm_prints_one_contract_line():
     assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
     assert line["config"]["workload"] == "headon_sinhcyl_16x2x32"
+    # the same work as a step of the GPU arm (full integrator steps of the whole grid), described by the
+    # same config the GPU arm prints at one replica
+    assert "2 full RK4 steps" in cb["sample"]
+    assert line["config"]["parallelism"] == "replicas x1" and line["config"]["dt"] > 0
 
 
 def test_cpu_baseline_object():

@@ -200,3 +200,51 @@ def test_production_scheme_and_4th_order_requests_share_one_server():
             assert p["steps_total"] == n
             assert np.array_equal(srv.fetch_state(rid, 24 * T), ref)
         srv.close()
+
+
+def _diverging():
+    """a request whose CFL factor of 5 puts RK4 outside its stability region: non-finite within a few steps"""
+    s = W.sinh_cylindrical((12, 2, 24), rho_max=30.0, z_max=30.0)
+    s.update(masses=(1.0,), positions=((0, 0, 0),), cfl=5.0)
+    return s
+
+
+@pytest.mark.parametrize("every", [5, 0], ids=["guard-every-5", "guard-off"])
+def test_a_diverging_request_fails_and_the_others_are_unaffected(every):
+    """A request that goes non-finite is retired as failed with NR_ENONFINITE -- by the guard within
+    its first checks (every 5 steps), or, with the guard off, at its retirement -- while every other
+    request finishes with its result alone, bit for bit (state and digest)."""
+    reqs = _requests()[:3]
+    t_final = 2.0
+    srv = B.Server(int(80 * 2 ** 30), 8)
+    srv.set_tile(32, 4)
+    srv.set_guard(every)
+    ids = [srv.submit(reqs[0], t_final, keep_state=True, keep_digest=True),
+           srv.submit(reqs[1], t_final, keep_state=True, keep_digest=True)]
+    bad = srv.submit(_diverging(), 40.0, keep_state=True, keep_digest=True)
+    srv.advance(3)
+    ids.append(srv.submit(reqs[2], t_final, keep_state=True, keep_digest=True))
+    for _ in range(1000):
+        nrun, nq = srv.advance(5)
+        if nrun == 0 and nq == 0:
+            break
+    p = srv.poll(bad)
+    assert p["status"] == 3 and srv.request_error(bad) == 5        # NR_ENONFINITE
+    if every:
+        assert p["steps_done"] <= 3 + 2 * every < p["steps_total"]   # caught by the guard, not at the end
+        assert np.isnan(p["l2"])
+    else:
+        assert p["steps_done"] == p["steps_total"]
+    with pytest.raises(B.NrError):
+        srv.fetch_state(bad, 1)
+    for rid, spec in zip(ids, reqs):
+        info = srv.poll(rid)
+        assert info["status"] == 2 and srv.request_error(rid) == 0
+        ref, n, T = _alone(spec, t_final)
+        assert info["steps_done"] == n
+        assert np.array_equal(srv.fetch_state(rid, 24 * T), ref)
+        g = B.Grid(spec)
+        g.set_state(ref, True)
+        assert srv.fetch_digest(rid) == g.digest()
+        g.close()
+    srv.close()

@@ -171,3 +171,53 @@ def test_step_io_equals_the_separate_calls(spec, integrator):
         g.get_state(full, True)
         assert np.array_equal(full.view(np.uint64), full_ref.view(np.uint64))
         g.close()
+
+
+_M64 = np.uint64(0xFFFFFFFFFFFFFFFF)
+
+
+def _splitmix64(x):
+    """first output of SplitMix64 (Steele, Lea & Flood 2014) for states x (uint64, wrapping)"""
+    z = x + np.uint64(0x9E3779B97F4A7C15)
+    z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+    z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+    return z ^ (z >> np.uint64(31))
+
+
+def _host_digest(state, canon, T):
+    """the digest nr_state_digest documents, over the canonical points, in numpy"""
+    total = np.uint64(0)
+    idx = canon.astype(np.uint64)
+    with np.errstate(over="ignore"):
+        for g in range(24):
+            bits = state[g * T + canon].view(np.uint64)
+            key = _splitmix64((np.uint64(g) << np.uint64(40)) | idx)
+            total = total + np.sum(_splitmix64(bits ^ key), dtype=np.uint64)
+    return int(total & _M64)
+
+
+@pytest.mark.parametrize("spec", SPECS, ids=IDS)
+def test_state_digest_is_the_documented_sum(spec):
+    """nr_state_digest equals the documented sum computed on the host from the fetched state, for
+    the grid-owned state and for a caller-owned copy; changing one canonical value changes it and
+    changing an inner ghost does not."""
+    g = B.Grid(spec)
+    g.set_brill_lindquist((0.6, 0.4), ((0.0, 0.0, 0.45), (0.0, 0.0, -0.55)), 1e-8, 5)
+    g.rk4_step(g.dt_cfl, 2)
+    T = g.T
+    canon = _canon(spec)
+    full = np.empty(24 * T)
+    g.get_state(full, True)
+    d = g.digest()
+    assert d == _host_digest(full, canon, T)
+    y = torch.from_numpy(full).to(DEV)
+    assert g.digest(y) == d
+    y2 = full.copy()
+    t = canon[canon.size // 2]
+    y2[13 * T + t] = np.nextafter(y2[13 * T + t], np.inf)
+    assert g.digest(torch.from_numpy(y2).to(DEV)) != d
+    ghost = np.setdiff1d(np.arange(T), canon)[0]
+    y3 = full.copy()
+    y3[5 * T + ghost] += 1.0
+    assert g.digest(torch.from_numpy(y3).to(DEV)) == d
+    g.close()

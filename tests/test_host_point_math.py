@@ -127,3 +127,40 @@ def test_planted_mistake_is_caught(lib):
     ref[g * o.T:(g + 1) * o.T] *= 1.0 + 1e-9
     with pytest.raises(AssertionError):
         assert_close(got, ref, o.T, 1e-12, mask=m, what="planted")
+
+
+def _sc2_inputs():
+    """Every exponent field with a few mantissas, both signs, zeros, the subnormal range,
+    the edges of the normal range, infinities and NaNs, plus random bit patterns."""
+    bits = []
+    for e in range(0x800):
+        for m in (0, 1, 0x8000000000000, 0xFFFFFFFFFFFFF, 0x123456789ABCD, 0x8000000000001, 0x7FFFFFFFFFFFF):
+            for s in (0, 1):
+                bits.append((s << 63) | (e << 52) | m)
+    # subnormals whose scaling by 2^-1 rounds (ties to even and not) or renormalises
+    for m in (2, 3, 5, 6, 7, 0x10, 0x11, 0x13, 0xFFFFF, 0x80000000, 0x4000000000000, 0xFFFFFFFFFFFFE):
+        bits += [m, (1 << 63) | m]
+    rng = np.random.default_rng(7)
+    bits += [int(v) for v in rng.integers(0, 2 ** 63, size=20000, dtype=np.int64)]
+    bits += [int(v) | (1 << 63) for v in rng.integers(0, 2 ** 63, size=20000, dtype=np.int64)]
+    return np.array(bits, dtype=np.uint64).view(np.float64)
+
+
+@pytest.mark.parametrize("K", [-1, 1, 2, 5, 9])
+def test_power_of_two_scaling_is_the_ieee_product(lib, K):
+    """sc2<K>, the point code's integer-pipe scaling by 2^K, gives the bits of the IEEE product
+    x * 2^K for every input: normal numbers, zeros of both signs, subnormal inputs and results
+    (rounded to nearest even), overflow to infinity, infinities and NaNs (quiet, payload kept)."""
+    x = _sc2_inputs()
+    out = np.empty_like(x)
+    L = lib
+    L.host_sc2.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                           ctypes.c_long]
+    L.host_sc2.restype = ctypes.c_int
+    dp = ctypes.POINTER(ctypes.c_double)
+    assert L.host_sc2(K, x.ctypes.data_as(dp), out.ctypes.data_as(dp), x.size) == 0
+    with np.errstate(over="ignore", under="ignore", invalid="ignore"):
+        ref = x * np.float64(2.0) ** K
+    bad = np.nonzero(out.view(np.uint64) != ref.view(np.uint64))[0]
+    assert bad.size == 0, [(hex(int(x.view(np.uint64)[i])), hex(int(out.view(np.uint64)[i])),
+                            hex(int(ref.view(np.uint64)[i]))) for i in bad[:8]]

@@ -27,7 +27,9 @@ SPECS = [
     dict(W.sinh_cylindrical((33, 2, 70), rho_max=20.0, z_max=20.0), h_rmin=0.5, h_rmax=8.0),
     dict(W.sinh_spherical((37, 11, 6)), h_rmin=0.5, h_rmax=8.0, NG=5, ko_sigma=KO8),
     dict(W.sinh_cylindrical((33, 2, 70), rho_max=20.0, z_max=20.0), h_rmin=0.5, h_rmax=8.0, NG=5, ko_sigma=KO8),
+    dict(W.spherical((21, 9, 8)), h_rmin=0.5, h_rmax=6.0),
 ]
+IDS = ["sinhsph", "sinhcyl", "sinhsph-o8", "sinhcyl-o8", "spherical"]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -38,32 +40,43 @@ def _lib():
     B.lib()
 
 
-@pytest.mark.parametrize("spec", SPECS, ids=["sinhsph", "sinhcyl", "sinhsph-o8", "sinhcyl-o8"])
-def test_noalloc_matches_grid_hamiltonian_two_calls(spec):
+def _free():
+    torch.cuda.synchronize()
+    return torch.cuda.mem_get_info()[0]
+
+
+@pytest.mark.parametrize("use_stream", [False, True], ids=["legacy-stream", "torch-stream"])
+@pytest.mark.parametrize("spec", SPECS, ids=IDS)
+def test_noalloc_matches_grid_hamiltonian_two_calls(spec, use_stream):
     g = B.Grid(spec)
     T = g.T
-    free = []
-    for call, seed in enumerate((101, 202)):
-        y = torch.from_numpy(W.random_state(g.n, seed=seed, smooth=True)).to("cuda:0")
-        H_ref = torch.full((T,), float("nan"), dtype=torch.float64, device="cuda:0")
-        H_na = torch.full((T,), float("nan"), dtype=torch.float64, device="cuda:0")
-        l2_ref, linf_ref = g.hamiltonian(y, H_ref)
-        torch.cuda.synchronize()
-        free.append(torch.cuda.mem_get_info()[0])
-        l2, linf = B.hamiltonian_noalloc(spec, y, H_na)
-        torch.cuda.synchronize()
-        free.append(torch.cuda.mem_get_info()[0])
-        a, b = H_na.cpu().numpy(), H_ref.cpu().numpy()
+    # every input and output of both calls exists before the first call
+    ys = [torch.from_numpy(W.random_state(g.n, seed=seed, smooth=True)).to("cuda:0") for seed in (101, 202)]
+    H_ref = [torch.full((T,), float("nan"), dtype=torch.float64, device="cuda:0") for _ in ys]
+    H_na = [torch.full((T,), float("nan"), dtype=torch.float64, device="cuda:0") for _ in ys]
+    refs = [g.hamiltonian(y, h) for y, h in zip(ys, H_ref)]
+    stream = torch.cuda.Stream() if use_stream else None
+    handle = stream.cuda_stream if use_stream else None
+    before, after = [], []
+    for call, y in enumerate(ys):
+        before.append(_free())
+        l2, linf = B.hamiltonian_noalloc(spec, y, H_na[call], stream=handle)
+        after.append(_free())
+        a, b = H_na[call].cpu().numpy(), H_ref[call].cpu().numpy()
         assert np.all(np.isfinite(a))
         err = np.abs(a - b).max() / np.abs(b).max()
         assert err <= 1e-12, (call, err)
+        l2_ref, linf_ref = refs[call]
         assert l2 == pytest.approx(l2_ref, rel=1e-10)
         assert linf == pytest.approx(linf_ref, rel=1e-10)
         # norms only, no H output
-        l2b, linfb = B.hamiltonian_noalloc(spec, y)
+        before.append(_free())
+        l2b, linfb = B.hamiltonian_noalloc(spec, y, stream=handle)
+        after.append(_free())
         assert l2b == pytest.approx(l2_ref, rel=1e-10) and linfb == pytest.approx(linf_ref, rel=1e-10)
-    # after the first call set up the device address, calls allocate nothing
-    assert free[1] == free[2] == free[3], free
+    # device free memory is the same on either side of every call after the first (which sets up
+    # the device address of the scratch array)
+    assert before[1:] == after[1:], (before, after)
     g.close()
 
 
