@@ -18,7 +18,18 @@ synthetic closed-form initial data generated on the GPU.
 N > 1 runs under torch.distributed.run, one independent replica per GPU
 (the simulations do not exchange data: weak scaling, no collective on the
 data path).  --impl reference times the CPU oracle (plain C, OpenMP over the
-host cores) on a bounded sample of the same workload.
+host cores) on full RK4 steps of the same workload (a bounded number of them).
+
+At one GPU the default line also carries the two modes against plain
+one-run-per-launch on the same GPU, each with its own clock record:
+  "batched": the batched workload's seeded runs (64 head-on binaries of
+    N_rho 64..256; 100 of its 500 steps each), one nr_batch against one grid at
+    a time, final states compared bitwise;
+  "served": the served workload's seeded Poisson stream (16 requests of
+    1e5..4e6 points, to t = 2M at 80 arrivals per minute, which overloads the
+    GPU as the configured 64 requests to t = 50M at 20 per minute do), the
+    SRPT server against a plain FIFO queue of single-grid runs, p50/p99/mean
+    time to completion of both, final states compared by digest.
 """
 from __future__ import annotations
 
@@ -50,6 +61,19 @@ UNIT = "point-updates/s"
 # 89.9 (4 FLOP per stored difference, 22 differences per point over the 1.03x larger
 # region).  A workload without a capture reports no FLOP rate.
 F_ALG = {"headon": 2894.3, "large3d": 4135.9, "headon8": 3844.9}
+# FLOPs of the same right-hand side in the point code's source (a host census of the code those counts
+# were taken from: FMA = 2, one division; without the k_d1 pre-pass); a test recomputes it, so that a
+# change of the kernels' arithmetic cannot leave F_ALG behind unnoticed
+KERNEL_CENSUS = {"headon": 2901, "headon8": 3765, "large3d": 4133}
+# FLOPs over twice the FP64 instructions of the same source (k_d1 + k_rhs): the fraction of the FLOP peak
+# that a fully busy FP64 pipe reaches with this mix (a DADD or DMUL takes an FMA's issue slot for 1 FLOP)
+MIX_CEILING = {"headon": 0.8428, "headon8": 0.8367, "large3d": 0.8438}
+# FP64 operations (add + mul + div) per interior point of one RHS evaluation as the oracle's counting
+# build counts them: the plain coordinate-basis evaluation of the same discretisation with generic index
+# loops and the reference metric evaluated at every point -- the work of the method evaluated plainly.
+# Achieved against it (frac_method) can exceed 1: the kernels compute the same discrete right-hand side
+# with about a tenth of those operations
+F_METHOD = {"headon": 28967, "headon8": 49631, "large3d": 28970}
 # DRAM bytes (read + write) of the same two launches in that capture, or None
 TRAFFIC = {"headon": 24018688 + 98816 + 94506752 + 450309120,
            "headon8": 24950784 + 136704 + 87655936 + 339959296}
@@ -422,9 +446,17 @@ def run_ours(args, spec, world, rank, local):
     f_alg = F_ALG.get(args.workload)
     if f_alg:
         ach = f_alg * pts / (rhs_ms * 1e-3)
-        roof.update(achieved=ach / 1e12, frac=ach / peak, flops_per_point=f_alg)
+        roof.update(achieved=ach / 1e12, frac=ach / peak, flops_per_point=f_alg,
+                    flops_source="the compiled kernels' DADD + DMUL + 2 DFMA per interior point (ncu)",
+                    mix_ceiling=MIX_CEILING[args.workload])
     else:
         roof.update(achieved=None, frac=None, flops_per_point=None)
+    f_method = F_METHOD.get(args.workload)
+    if f_method:
+        am = f_method * pts / (rhs_ms * 1e-3)
+        roof.update(flops_per_point_method=f_method, achieved_method=am / 1e12, frac_method=am / peak,
+                    method_source="the oracle's counting build: add + mul + div per interior point of the plain "
+                                  "coordinate-basis right-hand side")
 
     # end to end through the C ABI with host buffers: every step uploads the state from
     # pinned host memory, advances it, and reads the new state back.  The headline uses the
@@ -665,7 +697,7 @@ def served_compare(local: int, n_requests: int, t_final: float, rate: float, pol
         upd = 0.0
         if batched:
             srv = B.Server(80 * 10 ** 9, 64, device=local)
-            srv.set_tile(32, 4)
+            srv.set_tile(16, 8)
             srv.set_policy(mode, cap)
         queue = []
         nxt = 0

@@ -311,7 +311,7 @@ int nr_dt_cfl(int coords, const int Nxx[3], const nr_params* params, double* dt_
  *     on the grids' stream.  Errors: NR_EINVAL (mixed families, orders,
  *     devices, streams or azimuth kinds, duplicates), NR_ENOMEM, NR_ECUDA.
  *   nr_batch_set_tile: tile shape tile_x x tile_y of interior points per work
- *     item, one of 32x4, 64x2, 128x1, 16x8, 32x2, 64x1, 32x1 (default 32x4).
+ *     item, one of 32x4, 64x2, 128x1, 16x8, 32x2, 64x1, 32x1 (default 16x8).
  *   nr_batch_autotune: times one substage launch of each compiled tile shape
  *     on the batch (it writes only the RK work buffers, not the states), keeps
  *     the fastest and returns it (synchronises).
@@ -391,6 +391,72 @@ int nr_server_fetch_state(nr_server* server, int64_t id, double* host_state, siz
 int nr_server_set_guard(nr_server* server, int every_steps);
 int nr_server_request_error(nr_server* server, int64_t id, int* code);
 int nr_server_fetch_digest(nr_server* server, int64_t id, uint64_t* digest);
+
+/* Partitioned grid: one grid cut into partitions, the chare decomposition of
+ * Sec. 3 ("Charm++ parallelization": the grid divided into chares of
+ * prod_i N_i / N_chare^i points, each larger than N_G; face-sequential halo
+ * exchange E-W, N-S, T-B; per-chare send lists, built at set-up, for inner
+ * boundary points whose source lies on another chare).
+ *   parts[3]: partitions per axis.  The interior along axis d is cut into
+ *     parts[d] slabs of N_d / parts[d] points (rounded down at the cut k:
+ *     N_G + floor(k N_d / parts[d])), each at least N_G thick (NR_EINVAL
+ *     otherwise; so a two-point azimuth is never cut); at most 4096 partitions.
+ *     Partition q = q0 + parts[0] (q1 + parts[1] q2) owns its interior box and,
+ *     at the grid's edges, the ghost layers beyond it, and stores that box
+ *     widened by N_G on every side: T_q = prod_d (N_d,q + 2 N_G) points per
+ *     gridfunction, its own four 24-gridfunction sets.
+ *   Each substage of nr_part_rk4_step / nr_part_ssprk3_step computes, on every
+ *     partition, the right-hand side and the update of the points it owns, then
+ *     fills the inner boundary points -- from sources on the same partition by
+ *     parity copies, from sources on other partitions by messages -- and then
+ *     the halos, one axis after the other.  A message is gathered into a send
+ *     buffer on its source partition, copied to a receive buffer of its
+ *     destination (cudaMemcpyAsync), and scattered there with its parity signs.
+ *     All partitions live on params->device.  Every point runs the arithmetic of
+ *     nr_rk4_step / nr_ssprk3_step on the same values, so the evolution is
+ *     bitwise that of the whole grid.  A step is captured in a CUDA graph
+ *     (re-captured when dt or the integrator changes).
+ *   nr_part_set_brill_lindquist: as nr_set_brill_lindquist (the perturbation
+ *     counter is the whole grid's flat index), then the boundary fills.
+ *   nr_part_set_state / nr_part_get_state: the whole grid's 24-gridfunction set
+ *     (24*T doubles, the layout of nr_get_state) to every partition's box /
+ *     from the points each partition owns; from_host / to_host = 1: host memory,
+ *     staged through a device buffer of the whole set allocated on first use
+ *     (the call synchronises); 0: device memory, stream-ordered.  The state set
+ *     must hold the inner ghosts' parity copies, as every state of the method.
+ *   nr_part_digest: nr_state_digest of the whole grid's state, summed over the
+ *     partitions (the same value as for the unsplit grid); synchronises.
+ *   nr_part_query: partitions, messages per phase (0: inner boundary across
+ *     partitions; 1..3: halos along axes 0..2), CFL step, device bytes.
+ *   nr_part_plan_info / nr_part_plan_boxes / nr_part_plan_records (host only, no
+ *   GPU): the plan of the grid (coords, Nxx, NG) cut by parts.  Boxes: 15 ints
+ *     per partition, interior lo[3], hi[3], owned lo[3], hi[3] (global padded
+ *     indices, hi exclusive) and the local origin[3] (lo - NG); local index of
+ *     global (g0,g1,g2): (g0-o0) + m0 ((g1-o1) + m1 (g2-o2)), m_d = hi_d - lo_d
+ *     + 2 NG.  Records of phase 0..3: 5 ints each, source partition, source
+ *     local index, destination partition, destination local index, parity mask
+ *     (bit t: sign -1 for tensor type t, as in nr_build_maps; phase 0 lists every
+ *     inner boundary fill, within a partition too, phases 1..3 the halo copies
+ *     along axes 0..2 in the order they are applied).  records[4] of plan_info:
+ *     the counts per phase; capacity: the records rec can hold (NR_EINVAL if
+ *     too small).
+ * Errors: NR_EINVAL, NR_EMAP, NR_ENOMEM, NR_ECUDA. */
+typedef struct nr_part nr_part;
+int nr_part_create(int coords, const int Nxx[3], const nr_params* params, const int parts[3], nr_part** out);
+void nr_part_destroy(nr_part* part);
+int nr_part_query(const nr_part* part, int64_t* nparts, int64_t messages[4], double* dt_cfl, size_t* device_bytes);
+int nr_part_set_brill_lindquist(nr_part* part, int npunct, const double* mass, const double* xyz, double perturb_amp,
+                                uint64_t seed);
+int nr_part_set_state(nr_part* part, const double* src, int from_host);
+int nr_part_get_state(nr_part* part, double* dst, int to_host);
+int nr_part_rk4_step(nr_part* part, double dt, int nsteps);
+int nr_part_ssprk3_step(nr_part* part, double dt, int nsteps);
+int nr_part_digest(nr_part* part, uint64_t* out);
+int nr_part_sync(nr_part* part);
+int nr_part_plan_info(int coords, const int Nxx[3], int NG, const int parts[3], int64_t* nparts, int64_t records[4]);
+int nr_part_plan_boxes(int coords, const int Nxx[3], int NG, const int parts[3], int32_t* boxes);
+int nr_part_plan_records(int coords, const int Nxx[3], int NG, const int parts[3], int phase, int32_t* rec,
+                         int64_t capacity);
 
 /* Hamiltonian constraint that allocates nothing.  The paper has no
  * counterpart: this is a library service for callers that cannot call

@@ -32,7 +32,10 @@ EXPORTS = (
     "nr_server_create", "nr_server_destroy", "nr_server_set_tile", "nr_server_set_policy", "nr_server_submit",
     "nr_server_advance",
     "nr_server_poll", "nr_server_fetch_state", "nr_server_set_guard", "nr_server_request_error",
-    "nr_server_fetch_digest", "nr_state_digest", "nr_last_error",
+    "nr_server_fetch_digest", "nr_state_digest",
+    "nr_part_create", "nr_part_destroy", "nr_part_query", "nr_part_set_brill_lindquist", "nr_part_set_state",
+    "nr_part_get_state", "nr_part_rk4_step", "nr_part_ssprk3_step", "nr_part_digest", "nr_part_sync",
+    "nr_part_plan_info", "nr_part_plan_boxes", "nr_part_plan_records", "nr_last_error",
 )
 
 
@@ -145,6 +148,22 @@ def lib() -> ctypes.CDLL:
     L.nr_server_request_error.argtypes = [vp, ctypes.c_int64, ip]
     L.nr_server_fetch_digest.argtypes = [vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_uint64)]
     L.nr_state_digest.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_uint64)]
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    L.nr_part_create.argtypes = [ctypes.c_int, ip, P, ip, ctypes.POINTER(vp)]
+    L.nr_part_destroy.argtypes = [vp]
+    L.nr_part_destroy.restype = None
+    L.nr_part_query.argtypes = [vp, i64p, i64p, dp, ctypes.POINTER(ctypes.c_size_t)]
+    L.nr_part_set_brill_lindquist.argtypes = [vp, ctypes.c_int, dp, dp, ctypes.c_double, ctypes.c_uint64]
+    L.nr_part_set_state.argtypes = [vp, vp, ctypes.c_int]
+    L.nr_part_get_state.argtypes = [vp, vp, ctypes.c_int]
+    L.nr_part_rk4_step.argtypes = [vp, ctypes.c_double, ctypes.c_int]
+    L.nr_part_ssprk3_step.argtypes = [vp, ctypes.c_double, ctypes.c_int]
+    L.nr_part_digest.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
+    L.nr_part_sync.argtypes = [vp]
+    L.nr_part_plan_info.argtypes = [ctypes.c_int, ip, ctypes.c_int, ip, i64p, i64p]
+    L.nr_part_plan_boxes.argtypes = [ctypes.c_int, ip, ctypes.c_int, ip, i32p]
+    L.nr_part_plan_records.argtypes = [ctypes.c_int, ip, ctypes.c_int, ip, ctypes.c_int, i32p, ctypes.c_int64]
     L.nr_last_error.argtypes = []
     L.nr_last_error.restype = ctypes.c_char_p
     _lib = L
@@ -471,3 +490,81 @@ class Server:
         _check(lib().nr_server_fetch_state(self.h, int(rid), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                            size))
         return out
+
+
+def part_plan(coords: int, N, NG: int, parts):
+    """Host-only plan of a grid cut into partitions: (boxes [nparts, 15], records per phase [n, 5])."""
+    Nx = (ctypes.c_int * 3)(*[int(v) for v in N])
+    Px = (ctypes.c_int * 3)(*[int(v) for v in parts])
+    npart = ctypes.c_int64()
+    counts = (ctypes.c_int64 * 4)()
+    _check(lib().nr_part_plan_info(int(coords), Nx, int(NG), Px, ctypes.byref(npart), counts))
+    boxes = np.zeros((npart.value, 15), dtype=np.int32)
+    _check(lib().nr_part_plan_boxes(int(coords), Nx, int(NG), Px, boxes.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
+    recs = []
+    for ph in range(4):
+        r = np.zeros((max(1, counts[ph]), 5), dtype=np.int32)
+        _check(lib().nr_part_plan_records(int(coords), Nx, int(NG), Px, ph, r.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                          int(counts[ph])))
+        recs.append(r[:counts[ph]])
+    return boxes, recs
+
+
+class PartGrid:
+    """nr_part: one grid cut into partitions (library-owned states on one GPU)."""
+
+    def __init__(self, spec: dict, parts, stream=None, device: int = 0):
+        self.spec = dict(spec)
+        self.params = make_params(spec, stream=stream, device=device)
+        h = ctypes.c_void_p()
+        Nx = (ctypes.c_int * 3)(*[int(v) for v in spec["N"]])
+        Px = (ctypes.c_int * 3)(*[int(v) for v in parts])
+        _check(lib().nr_part_create(int(spec["coords"]), Nx, ctypes.byref(self.params), Px, ctypes.byref(h)))
+        self.h = h
+        NG = int(spec.get("NG", 3))
+        self.n = tuple(int(v) + 2 * NG for v in spec["N"])
+        self.T = self.n[0] * self.n[1] * self.n[2]
+        npart, dt, nbytes = ctypes.c_int64(), ctypes.c_double(), ctypes.c_size_t()
+        msgs = (ctypes.c_int64 * 4)()
+        _check(lib().nr_part_query(self.h, ctypes.byref(npart), msgs, ctypes.byref(dt), ctypes.byref(nbytes)))
+        self.nparts, self.messages, self.dt_cfl, self.device_bytes = npart.value, list(msgs), dt.value, nbytes.value
+
+    def close(self) -> None:
+        if self.h:
+            lib().nr_part_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_brill_lindquist(self, masses, positions, perturb_amp: float = 0.0, seed: int = 0) -> None:
+        m = np.ascontiguousarray(masses, dtype=np.float64)
+        x = np.ascontiguousarray(positions, dtype=np.float64).reshape(-1)
+        _check(lib().nr_part_set_brill_lindquist(self.h, len(m), m.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                                 x.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(perturb_amp),
+                                                 ctypes.c_uint64(int(seed))))
+
+    def set_state(self, src, from_host: bool) -> None:
+        addr = src.ctypes.data if isinstance(src, np.ndarray) else (src.data_ptr() if not isinstance(src, int) else src)
+        _check(lib().nr_part_set_state(self.h, addr, int(bool(from_host))))
+
+    def get_state(self, dst, to_host: bool) -> None:
+        addr = dst.ctypes.data if isinstance(dst, np.ndarray) else (dst.data_ptr() if not isinstance(dst, int) else dst)
+        _check(lib().nr_part_get_state(self.h, addr, int(bool(to_host))))
+
+    def rk4_step(self, dt: float, nsteps: int = 1) -> None:
+        _check(lib().nr_part_rk4_step(self.h, float(dt), int(nsteps)))
+
+    def ssprk3_step(self, dt: float, nsteps: int = 1) -> None:
+        _check(lib().nr_part_ssprk3_step(self.h, float(dt), int(nsteps)))
+
+    def digest(self) -> int:
+        out = ctypes.c_uint64()
+        _check(lib().nr_part_digest(self.h, ctypes.byref(out)))
+        return out.value
+
+    def sync(self) -> None:
+        _check(lib().nr_part_sync(self.h))

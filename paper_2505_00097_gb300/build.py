@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libnrgpu.so")
 SOURCES = ["nr_kernels.cu", "nr_capi.cu", "nr_noalloc.cu", "nr_batch.cu", "nr_batch_sph.cu", "nr_batch_cyl.cu",
-           "nr_batch_sph8.cu", "nr_batch_cyl8.cu", "nr_server.cu", "nr_psi4.cu"]
+           "nr_batch_sph8.cu", "nr_batch_cyl8.cu", "nr_server.cu", "nr_psi4.cu", "nr_part.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # host code: no contraction of a*b+c into an FMA (the default of gcc on aarch64), so the host-side
 # set-up (coordinates, per-axis arrays, radiation-condition weights, the CFL step) rounds the same

@@ -40,7 +40,7 @@ struct nr_batch {
     int device = 0;
     cudaStream_t stream = nullptr;
     cudaStream_t cap = nullptr;
-    int tile = 0;
+    int tile = 3;             // kTiles index: 16x8, the shape the autotuner picks on the workloads
     int total = 0;
     int total_d1 = 0;          // items of the first-difference pass
     BGrid* d_grids = nullptr;

@@ -416,6 +416,117 @@ int enqueue_ssprk3(nr_grid* g, cudaStream_t s, double dt, const Stage* mirror = 
 
 }  // namespace
 
+// Host-side set-up of one grid: everything nr_grid_create computes before it touches the
+// device (coordinates, per-axis arrays, boundary maps, radiation-condition data, CFL step).
+int nrk::host_setup(int coords, const int Nxx[3], const nr_params& P, HostSetup& H)
+{
+    int rc = check_args(coords, Nxx, &P);
+    if (rc) return rc;
+    geom_init(coords, Nxx, P.NG, H.G);
+    const HostGeom& G = H.G;
+    if ((rc = build_maps_host(G, H.src, H.par, H.cls))) return rc;
+    H.dt = dt_cfl_host(G, P);
+    std::vector<double>&a0 = H.a0, &a1 = H.a1, &a2 = H.a2;
+    build_axes(G, P, a0, a1, a2);
+    // radiation-condition data of the pure outer points, parity copies of the inner ghosts
+    std::vector<OuterPt>& outer = H.outer;
+    std::vector<InnerPt>& inner = H.inner;
+    std::vector<int>& canon = H.canon;
+    outer.clear();
+    inner.clear();
+    canon.clear();
+    const int n0 = G.n[0], n1 = G.n[1];
+    for (long idx = 0; idx < G.T; idx++) {
+        const int c = H.cls[idx];
+        if (c != 2) canon.push_back((int)idx);
+        if (c == 1) {
+            const int i0 = (int)(idx % n0), i1 = (int)((idx / n0) % n1), i2 = (int)(idx / ((long)n0 * n1));
+            OuterPt o{};
+            o.idx = (int)idx;
+            double f[4];
+            // stencil kind per axis and the denominator of its integer weights
+            const bool o8 = G.NG == 5;
+            const double den = o8 ? 840.0 : 12.0;
+            auto kind = [&](int i, int n) { return o8 ? onesided_window8(i, n) : onesided_kind(i, n); };
+            if (G.fam == FAM_SPH) {
+                axis0_map(G, P, G.xx(0, i0), f);
+                o.kind = kind(i0, G.n[0]);
+                o.w0 = (1.0 / f[1]) / (den * G.dxx[0]);
+                o.w2 = 0.0;
+                o.invr = 1.0 / f[0];
+            } else {
+                double z[4];
+                radial(P.ampl[0], P.sinhw[0], 1, G.xx(0, i0), f);
+                radial(P.ampl[2], P.sinhw[2], 1, G.xx(2, i2), z);
+                const double r = sqrt(f[0] * f[0] + z[0] * z[0]);
+                o.kind = kind(i0, G.n[0]) | (kind(i2, G.n[2]) << 8);
+                o.w0 = (f[0] / r) * (1.0 / f[1]) / (den * G.dxx[0]);
+                o.w2 = (z[0] / r) * (1.0 / z[1]) / (den * G.dxx[2]);
+                o.invr = 1.0 / r;
+            }
+            (void)i1;
+            outer.push_back(o);
+        } else if (c == 2) {
+            InnerPt q{};
+            q.dst = (int)idx;
+            q.src = H.src[idx];
+            int m = 0;
+            for (int t = 0; t < 10; t++)
+                if (H.par[10 * idx + t] < 0) m |= 1 << t;
+            q.negmask = m;
+            inner.push_back(q);
+        }
+    }
+    // ghosts the RK-stage stencils read first: with a two-point azimuth (GridK::ax) the
+    // stencils of interior and pure-outer points never reach an azimuthal ghost
+    const int ax = two_point_axis(G);
+    auto read_by_stencils = [&](const InnerPt& q) {
+        if (ax < 0) return true;
+        const long idx = q.dst;
+        const int ia = ax == 1 ? (int)((idx / n0) % n1) : (int)(idx / ((long)n0 * n1));
+        return ia >= G.NG && ia < G.NG + G.N[ax];
+    };
+    std::stable_partition(inner.begin(), inner.end(), read_by_stencils);
+    H.n_inner_stencil = (int)std::count_if(inner.begin(), inner.end(), read_by_stencils);
+    // Cartesian positions of canonical points, for the puncture check
+    H.cart_canon.resize(3 * canon.size());
+    for (size_t t = 0; t < canon.size(); t++) {
+        const long idx = canon[t];
+        const int i0 = (int)(idx % n0), i1 = (int)((idx / n0) % n1), i2 = (int)(idx / ((long)n0 * n1));
+        double* x = &H.cart_canon[3 * t];
+        if (G.fam == FAM_SPH) {
+            const double r = a0[3 * n0 + i0], st = a1[2 * n1 + i1], ct = a1[3 * n1 + i1];
+            const double sp_ = a2[i2], cp = a2[G.n[2] + i2];
+            x[0] = r * st * cp;
+            x[1] = r * st * sp_;
+            x[2] = r * ct;
+        } else {
+            const double rho = a0[3 * n0 + i0], sp_ = a1[i1], cp = a1[n1 + i1];
+            x[0] = rho * cp;
+            x[1] = rho * sp_;
+            x[2] = a2[2 * G.n[2] + i2];
+        }
+    }
+    GridK& K = H.K;
+    memset(&K, 0, sizeof K);
+    K.n0 = G.n[0]; K.n1 = G.n[1]; K.n2 = G.n[2];
+    K.N0 = G.N[0]; K.N1 = G.N[1]; K.N2 = G.N[2];
+    K.NG = G.NG;
+    K.fam = G.fam;
+    K.ax = two_point_axis(G);
+    K.ord = 2 * (G.NG - 1);
+    K.T = G.T;
+    for (int d = 0; d < 3; d++) {
+        // the denominators of the integer stencil weights (bssn_point.cuh, FD<ORD>)
+        K.inv_d1[d] = 1.0 / ((K.ord == 8 ? 840.0 : 12.0) * G.dxx[d]);
+        K.inv_d2[d] = 1.0 / ((K.ord == 8 ? 5040.0 : 12.0) * G.dxx[d] * G.dxx[d]);
+    }
+    K.sigma_metric = P.ko_sigma[0];
+    K.sigma_gauge = P.ko_sigma[17];
+    K.eta = P.eta;
+    return NR_OK;
+}
+
 extern "C" {
 
 const char* nr_last_error(void) { return g_err.c_str(); }
@@ -494,122 +605,45 @@ static int nr_grid_create_body(int coords, const int Nxx[3], const nr_params* pa
         P = *params;
     else
         nr_params_default(coords, &P);
-    int rc = check_args(coords, Nxx, &P);
+    HostSetup H;
+    int rc = host_setup(coords, Nxx, P, H);
     if (rc) return rc;
+    return grid_from_setup(H, P, out);
+}
+
+}  // extern "C"
+
+// A grid from its host-side set-up (consumed): device buffers allocated and uploaded on P.device.
+int nrk::grid_from_setup(HostSetup& H, const nr_params& P, nr_grid** out)
+{
+    int rc = NR_OK;
+    *out = nullptr;
     nr_grid* g = new nr_grid();
     try {
         g->P = P;
         g->device = P.device;
         g->stream = (cudaStream_t)P.stream;
-        geom_init(coords, Nxx, P.NG, g->geo);
+        g->geo = H.G;
         const HostGeom& G = g->geo;
-        if ((rc = build_maps_host(G, g->src, g->par, g->cls))) { delete g; return rc; }
-        g->dt_cfl = dt_cfl_host(G, P);
-
-        std::vector<double> a0, a1, a2;
-        build_axes(G, P, a0, a1, a2);
-        // radiation-condition data of the pure outer points, parity copies of the inner ghosts
-        std::vector<OuterPt> outer;
-        std::vector<InnerPt> inner;
-        std::vector<int> canon;
-        const int n0 = G.n[0], n1 = G.n[1];
-        for (long idx = 0; idx < G.T; idx++) {
-            const int c = g->cls[idx];
-            if (c != 2) canon.push_back((int)idx);
-            if (c == 1) {
-                const int i0 = (int)(idx % n0), i1 = (int)((idx / n0) % n1), i2 = (int)(idx / ((long)n0 * n1));
-                OuterPt o{};
-                o.idx = (int)idx;
-                double f[4];
-                // stencil kind per axis and the denominator of its integer weights
-                const bool o8 = G.NG == 5;
-                const double den = o8 ? 840.0 : 12.0;
-                auto kind = [&](int i, int n) { return o8 ? onesided_window8(i, n) : onesided_kind(i, n); };
-                if (G.fam == FAM_SPH) {
-                    axis0_map(G, P, G.xx(0, i0), f);
-                    o.kind = kind(i0, G.n[0]);
-                    o.w0 = (1.0 / f[1]) / (den * G.dxx[0]);
-                    o.w2 = 0.0;
-                    o.invr = 1.0 / f[0];
-                } else {
-                    double z[4];
-                    radial(P.ampl[0], P.sinhw[0], 1, G.xx(0, i0), f);
-                    radial(P.ampl[2], P.sinhw[2], 1, G.xx(2, i2), z);
-                    const double r = sqrt(f[0] * f[0] + z[0] * z[0]);
-                    o.kind = kind(i0, G.n[0]) | (kind(i2, G.n[2]) << 8);
-                    o.w0 = (f[0] / r) * (1.0 / f[1]) / (den * G.dxx[0]);
-                    o.w2 = (z[0] / r) * (1.0 / z[1]) / (den * G.dxx[2]);
-                    o.invr = 1.0 / r;
-                }
-                (void)i1;
-                outer.push_back(o);
-            } else if (c == 2) {
-                InnerPt q{};
-                q.dst = (int)idx;
-                q.src = g->src[idx];
-                int m = 0;
-                for (int t = 0; t < 10; t++)
-                    if (g->par[10 * idx + t] < 0) m |= 1 << t;
-                q.negmask = m;
-                inner.push_back(q);
-            }
-        }
-        // ghosts the RK-stage stencils read first: with a two-point azimuth (GridK::ax) the
-        // stencils of interior and pure-outer points never reach an azimuthal ghost
-        const int ax = two_point_axis(G);
-        auto read_by_stencils = [&](const InnerPt& q) {
-            if (ax < 0) return true;
-            const long idx = q.dst;
-            const int ia = ax == 1 ? (int)((idx / n0) % n1) : (int)(idx / ((long)n0 * n1));
-            return ia >= G.NG && ia < G.NG + G.N[ax];
-        };
-        std::stable_partition(inner.begin(), inner.end(), read_by_stencils);
-        g->n_inner_stencil = (int)std::count_if(inner.begin(), inner.end(), read_by_stencils);
-        g->n_outer = (int)outer.size();
-        g->n_inner = (int)inner.size();
-        g->n_canon = (long)canon.size();
-        // Cartesian positions of canonical points, for the puncture check
-        {
-            g->cart_canon.resize(3 * canon.size());
-            for (size_t t = 0; t < canon.size(); t++) {
-                const long idx = canon[t];
-                const int i0 = (int)(idx % n0), i1 = (int)((idx / n0) % n1), i2 = (int)(idx / ((long)n0 * n1));
-                double* x = &g->cart_canon[3 * t];
-                if (G.fam == FAM_SPH) {
-                    const double r = a0[3 * n0 + i0], st = a1[2 * n1 + i1], ct = a1[3 * n1 + i1];
-                    const double sp_ = a2[i2], cp = a2[G.n[2] + i2];
-                    x[0] = r * st * cp;
-                    x[1] = r * st * sp_;
-                    x[2] = r * ct;
-                } else {
-                    const double rho = a0[3 * n0 + i0], sp_ = a1[i1], cp = a1[n1 + i1];
-                    x[0] = rho * cp;
-                    x[1] = rho * sp_;
-                    x[2] = a2[2 * G.n[2] + i2];
-                }
-            }
-        }
+        g->src = std::move(H.src);
+        g->par = std::move(H.par);
+        g->cls = std::move(H.cls);
+        g->dt_cfl = H.dt;
+        g->cart_canon = std::move(H.cart_canon);
+        g->n_inner_stencil = H.n_inner_stencil;
+        g->n_outer = (int)H.outer.size();
+        g->n_inner = (int)H.inner.size();
+        g->n_canon = (long)H.canon.size();
+        const std::vector<double>&a0 = H.a0, &a1 = H.a1, &a2 = H.a2;
+        const std::vector<OuterPt>& outer = H.outer;
+        const std::vector<InnerPt>& inner = H.inner;
+        const std::vector<int>& canon = H.canon;
 
         DeviceGuard dg(g->device);
         const size_t set = (size_t)NR_NGF * G.T;
         std::vector<double> finf(P.f_inf, P.f_inf + NR_NGF), ws(P.wavespeed, P.wavespeed + NR_NGF);
         GridK& K = g->K;
-        memset(&K, 0, sizeof K);
-        K.n0 = G.n[0]; K.n1 = G.n[1]; K.n2 = G.n[2];
-        K.N0 = G.N[0]; K.N1 = G.N[1]; K.N2 = G.N[2];
-        K.NG = G.NG;
-        K.fam = G.fam;
-        K.ax = two_point_axis(G);
-        K.ord = 2 * (G.NG - 1);
-        K.T = G.T;
-        for (int d = 0; d < 3; d++) {
-            // the denominators of the integer stencil weights (bssn_point.cuh, FD<ORD>)
-            K.inv_d1[d] = 1.0 / ((K.ord == 8 ? 840.0 : 12.0) * G.dxx[d]);
-            K.inv_d2[d] = 1.0 / ((K.ord == 8 ? 5040.0 : 12.0) * G.dxx[d] * G.dxx[d]);
-        }
-        K.sigma_metric = P.ko_sigma[0];
-        K.sigma_gauge = P.ko_sigma[17];
-        K.eta = P.eta;
+        K = H.K;
         g->nparts = ham_partials_needed(K);
         if ((rc = dmalloc(g, &g->y, set)) || (rc = dmalloc(g, &g->ya, set)) || (rc = dmalloc(g, &g->yb, set)) ||
             (rc = dmalloc(g, &g->acc, set)) || (rc = dmalloc(g, &g->d1x, (size_t)N_D1 * G.T)) ||
@@ -653,6 +687,8 @@ static int nr_grid_create_body(int coords, const int Nxx[3], const nr_params* pa
         throw;
     }
 }
+
+extern "C" {
 
 int nr_grid_create(int coords, const int Nxx[3], const nr_params* params, nr_grid** out)
 {

@@ -96,17 +96,19 @@ cudaError_t launch_inner(const GridK& G, const InnerPt* pts, int npts, double* y
 // gather (src: 24-gf set, dst: compact [gf][t]) or scatter (the reverse) over the canonical points
 cudaError_t launch_compact(const GridK& G, const int* canon, long nc, const double* src, double* dst, bool gather,
                            cudaStream_t s);
+// ctr: perturbation counter per canonical point (NULL: its flat index in G)
 cudaError_t launch_bl(const GridK& G, const int* canon_idx, long ncanon, int np, const double* mxyz, double amp,
-                      uint64_t seed, double* y, cudaStream_t s);
+                      uint64_t seed, double* y, cudaStream_t s, const int* ctr = nullptr);
 cudaError_t launch_ham(const GridK& G, const double* y, double* H, double rmin, double rmax, double* partials,
                        int nparts, double* result, cudaStream_t s);
 cudaError_t launch_mom(const GridK& G, const double* y, double* M, double rmin, double rmax, double* partials,
                        int nparts, double* result, cudaStream_t s);
 int ham_partials_needed(const GridK& G);
 cudaError_t launch_finite(const GridK& G, const double* y, int* flag, cudaStream_t s);
-// 64-bit digest of the 24 gridfunctions of y at the canonical points canon[0..nc) into *out
+// 64-bit digest of the 24 gridfunctions of y at the canonical points canon[0..nc) into *out; ctr: the
+// key of each point (NULL: its flat index in G)
 cudaError_t launch_digest(const GridK& G, const int* canon, long nc, const double* y, unsigned long long* out,
-                          cudaStream_t s);
+                          cudaStream_t s, const int* ctr = nullptr);
 cudaError_t launch_fp64_probe(int blocks, int iters, double* sink, cudaStream_t s);
 cudaError_t launch_ham_reduce(const double* partials, int nparts, double* result, cudaStream_t s);
 
@@ -122,7 +124,33 @@ struct HostGeom {
     double xx(int d, int i) const { return lo[d] + ((double)(i - NG) + 0.5) * dxx[d]; }
 };
 
+// Host-side set-up of one grid, as nr_grid_create computes it before touching the device:
+// boundary maps, per-axis reference-metric arrays (layout of Rfm), radiation-condition data of
+// the pure-outer points and parity copies of the inner ghosts (flat indices of the padded grid;
+// the inner ghosts the RK-stage stencils read first), the canonical points and the CFL step.
+// K is complete but for its device pointers (rfm).
+struct HostSetup {
+    HostGeom G;
+    GridK K;
+    std::vector<int32_t> src, cls;
+    std::vector<int8_t> par;
+    std::vector<double> a0, a1, a2;
+    std::vector<OuterPt> outer;
+    std::vector<InnerPt> inner;
+    int n_inner_stencil = 0;
+    std::vector<int> canon;
+    std::vector<double> cart_canon;
+    double dt = 0.0;
+};
+int host_setup(int coords, const int Nxx[3], const nr_params& P, HostSetup& H);
+
 }  // namespace nrk
+
+// a grid from its host-side set-up H (its vectors are moved from): device buffers allocated and
+// uploaded on P.device (nr_grid_create = host_setup + grid_from_setup)
+namespace nrk {
+int grid_from_setup(HostSetup& H, const nr_params& P, nr_grid** out);
+}
 
 // one grid: host maps, device buffers and the CUDA-graph RK4 driver state
 struct nr_grid {

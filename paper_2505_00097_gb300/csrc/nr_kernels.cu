@@ -88,12 +88,15 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x)
     return z ^ (z >> 31);
 }
 
-__global__ void k_bl(GridK G, const int* __restrict__ canon, long ncanon, int np, const double* __restrict__ mxyz,
-                     double amp, uint64_t seed, double* y)
+// ctr (NULL: the flat index itself): the perturbation counter of each canonical point -- its flat
+// index on the whole grid when G describes one partition of it
+__global__ void k_bl(GridK G, const int* __restrict__ canon, const int* __restrict__ ctr, long ncanon, int np,
+                     const double* __restrict__ mxyz, double amp, uint64_t seed, double* y)
 {
     const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= ncanon) return;
     const long idx = canon[t];
+    const uint64_t key = ctr ? (uint64_t)ctr[t] : (uint64_t)idx;
     const int i0 = (int)(idx % G.n0), i1 = (int)((idx / G.n0) % G.n1), i2 = (int)(idx / ((long)G.n0 * G.n1));
     double x[3];
     cart_of(G, i0, i1, i2, x);
@@ -108,7 +111,7 @@ __global__ void k_bl(GridK G, const int* __restrict__ canon, long ncanon, int np
     y[(long)G_ALPHA * G.T + idx] = w;
     if (amp != 0.0) {
         for (int s = 0; s < 6; s++) {
-            const uint64_t u = splitmix64(seed ^ (((uint64_t)(G_HDD + s) << 40) | (uint64_t)idx));
+            const uint64_t u = splitmix64(seed ^ (((uint64_t)(G_HDD + s) << 40) | key));
             y[(long)(G_HDD + s) * G.T + idx] = amp * (2.0 * ((double)(u >> 11) * 0x1.0p-53) - 1.0);
         }
     }
@@ -258,15 +261,18 @@ __global__ void k_finite(long T, const double* __restrict__ y, int* flag)
 // of splitmix64(bits ^ splitmix64((gf << 40) | idx)).  A sum modulo 2^64 does not depend on
 // the order of its terms, so the digest does not depend on the launch shape; each term is a
 // bijective mix of its value's bits, so a change of one value always changes the digest.
-__global__ void __launch_bounds__(256) k_digest(long T, const int* __restrict__ canon, long nc,
-                                                const double* __restrict__ y, unsigned long long* out)
+// ctr (NULL: the flat index itself): the key of each canonical point -- its flat index on the
+// whole grid when the set is one partition of it.
+__global__ void __launch_bounds__(256) k_digest(long T, const int* __restrict__ canon, const int* __restrict__ ctr,
+                                                long nc, const double* __restrict__ y, unsigned long long* out)
 {
     const int g = blockIdx.y;
     unsigned long long acc = 0;
     for (long t = (long)blockIdx.x * 256 + threadIdx.x; t < nc; t += (long)gridDim.x * 256) {
         const long idx = canon[t];
+        const uint64_t key = ctr ? (uint64_t)ctr[t] : (uint64_t)idx;
         const uint64_t v = (uint64_t)__double_as_longlong(y[(long)g * T + idx]);
-        acc += splitmix64(v ^ splitmix64(((uint64_t)g << 40) | (uint64_t)idx));
+        acc += splitmix64(v ^ splitmix64(((uint64_t)g << 40) | key));
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
     if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
@@ -386,11 +392,12 @@ cudaError_t launch_compact(const GridK& G, const int* canon, long nc, const doub
 }
 
 cudaError_t launch_bl(const GridK& G, const int* canon_idx, long ncanon, int np, const double* mxyz, double amp,
-                      uint64_t seed, double* y, cudaStream_t s)
+                      uint64_t seed, double* y, cudaStream_t s, const int* ctr)
 {
     const int b = 256;
     const long n = (ncanon + b - 1) / b;
-    k_bl<<<(unsigned)n, b, 0, s>>>(G, canon_idx, ncanon, np, mxyz, amp, seed, y);
+    if (n == 0) return cudaSuccess;
+    k_bl<<<(unsigned)n, b, 0, s>>>(G, canon_idx, ctr, ncanon, np, mxyz, amp, seed, y);
     return cudaGetLastError();
 }
 
@@ -439,12 +446,12 @@ cudaError_t launch_ham_reduce(const double* partials, int nparts, double* result
 }
 
 cudaError_t launch_digest(const GridK& G, const int* canon, long nc, const double* y, unsigned long long* out,
-                          cudaStream_t s)
+                          cudaStream_t s, const int* ctr)
 {
     cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess || nc == 0) return e;
     const long bx = std::min<long>((nc + 255) / 256, 2L * 152);
-    k_digest<<<dim3((unsigned)bx, NGF), 256, 0, s>>>(G.T, canon, nc, y, out);
+    k_digest<<<dim3((unsigned)bx, NGF), 256, 0, s>>>(G.T, canon, ctr, nc, y, out);
     return cudaGetLastError();
 }
 

@@ -20,6 +20,10 @@
 // step; since every point runs the single-grid arithmetic, a request's result
 // does not depend on which other requests shared the GPU with it, nor on when
 // it was paused.
+// The host-side set-up of the requests next in line (coordinates, per-axis arrays,
+// boundary maps: the part of nr_grid_create that runs on the CPU) is computed
+// ahead by a worker thread while the GPU advances the running requests, so
+// that admission only allocates, uploads and sets initial data.
 // A guard checks alpha and W of the advanced requests for non-finite values
 // every few steps (nr_server_set_guard); a request that fails it is retired
 // as failed with NR_ENONFINITE while the others keep running.
@@ -27,8 +31,12 @@
 #include <string.h>
 
 #include <algorithm>
+#include <condition_variable>
 #include <deque>
 #include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
 #include <vector>
 
 #include "nr_internal.h"
@@ -57,6 +65,11 @@ struct Request {
     int64_t steps_total = 0, steps_done = 0;
     double l2 = 0.0, linf = 0.0;
     int err = NR_OK;           // the status that ended a failed request
+    // host-side set-up computed ahead by the server's worker: 0 none, 1 asked for, 2 being computed,
+    // 3 ready (setup_rc: its status)
+    int setup_state = 0;
+    int setup_rc = NR_OK;
+    std::unique_ptr<nrk::HostSetup> setup;
     uint64_t digest = 0;
     bool has_digest = false;
     std::vector<double> state;
@@ -103,6 +116,13 @@ struct nr_server {
     int* dflags = nullptr;          // 2 * max_slots ints on the device
     int* hflags = nullptr;          // 2 * max_slots ints, pinned host
     std::vector<int64_t> checked[2];   // ids of the requests checked behind each chunk slot
+    // the set-up worker: computes HostSetup for the requests in prep_jobs (under mu)
+    std::thread worker;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<Request*> prep_jobs;
+    bool stop = false;
+    int prefetch = 2;   // queued requests whose set-up is computed ahead, in admission order
 };
 
 namespace {
@@ -179,12 +199,62 @@ int request_kind(const Request* r)
     return 8 * r->P.integrator + 4 * (g->K.ord == 8) + 2 * g->K.fam + (g->K.ax >= 0 ? 1 : 0);
 }
 
+void worker_loop(nr_server* s)
+{
+    std::unique_lock<std::mutex> lk(s->mu);
+    for (;;) {
+        s->cv.wait(lk, [&] { return s->stop || !s->prep_jobs.empty(); });
+        if (s->stop) return;
+        Request* r = s->prep_jobs.front();
+        s->prep_jobs.pop_front();
+        if (r->setup_state != 1) continue;
+        r->setup_state = 2;
+        nr_params P = r->P;
+        P.device = s->device;
+        P.stream = s->stream;
+        lk.unlock();
+        std::unique_ptr<nrk::HostSetup> H(new nrk::HostSetup());
+        int rc;
+        try {
+            rc = nrk::host_setup(r->coords, r->N, P, *H);
+        } catch (...) {
+            rc = NR_ENOMEM;
+        }
+        lk.lock();
+        r->setup = std::move(H);
+        r->setup_rc = rc;
+        r->setup_state = 3;
+        s->cv.notify_all();
+    }
+}
+
+// ask the worker for the set-up of the next queued requests in admission order
+void prefetch_setups(nr_server* s);
+
 int start_request(nr_server* s, Request* r)
 {
     nr_params P = r->P;
     P.device = s->device;
     P.stream = s->stream;
-    int rc = nr_grid_create(r->coords, r->N, &P, &r->grid);
+    std::unique_ptr<nrk::HostSetup> H;
+    int rc = NR_OK;
+    {
+        std::unique_lock<std::mutex> lk(s->mu);
+        if (r->setup_state == 1) {   // asked for, not started: computed here instead
+            r->setup_state = 0;
+        } else if (r->setup_state >= 2) {
+            s->cv.wait(lk, [&] { return r->setup_state == 3; });
+            H = std::move(r->setup);
+            rc = r->setup_rc;
+            r->setup_state = 0;
+        }
+    }
+    if (!H) {
+        H.reset(new nrk::HostSetup());
+        rc = nrk::host_setup(r->coords, r->N, P, *H);
+    }
+    if (rc == NR_OK) rc = nrk::grid_from_setup(*H, P, &r->grid);
+    H.reset();
     if (rc) return rc;
     rc = nr_set_brill_lindquist(r->grid, r->np, r->mass, r->xyz, 0.0, 0);
     if (rc) {
@@ -285,7 +355,30 @@ int admit(nr_server* s)
         s->running.push_back(r);
         s->batch_dirty = true;
     }
+    prefetch_setups(s);
     return NR_OK;
+}
+
+void prefetch_setups(nr_server* s)
+{
+    if (s->prefetch <= 0 || s->queue.empty()) return;
+    // the admission order of the queue: policy order (next_queued picks the first of it)
+    std::vector<Request*> order(s->queue.begin(), s->queue.end());
+    if (s->policy == NR_SERVE_SRPT)
+        std::stable_sort(order.begin(), order.end(), [](const Request* a, const Request* b) {
+            const int64_t wa = a->steps_est * a->interior * substeps(a), wb = b->steps_est * b->interior * substeps(b);
+            return wa != wb ? wa < wb : a->id < b->id;
+        });
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (!s->worker.joinable()) s->worker = std::thread(worker_loop, s);
+    int k = 0;
+    for (Request* r : order) {
+        if (k++ >= s->prefetch) break;
+        if (r->setup_state != 0) continue;
+        r->setup_state = 1;
+        s->prep_jobs.push_back(r);
+    }
+    s->cv.notify_all();
 }
 
 // the running requests the next chunk advances: the longest prefix of the
@@ -370,6 +463,13 @@ int nr_server_create(size_t hbm_budget_bytes, int max_slots, int device, void* s
 void nr_server_destroy(nr_server* s)
 {
     if (!s) return;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+        s->prep_jobs.clear();
+    }
+    s->cv.notify_all();
+    if (s->worker.joinable()) s->worker.join();
     drop_batch(s);
     for (int q = 0; q < 2; q++)
         if (s->chunk_done[q]) cudaEventDestroy(s->chunk_done[q]);
