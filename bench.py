@@ -55,28 +55,28 @@ UNIT = "point-updates/s"
 # the k_d1 pre-pass and k_rhs), by workload (the kernel variant it runs), from
 # the kernels' DADD/DMUL/DFMA thread-instruction counts in one ncu capture of
 # that workload's nr_rhs launches: (DADD + DMUL + 2 DFMA) / interior points.  Head-on
-# 256x2x512 (cylindrical, two-point azimuth): k_rhs 202 + 322 + 2 x 1163 = 2850,
-# k_d1 44.3.  Head-on with the 8th-order scheme: k_rhs 307 + 381 + 2 x 1517 = 3722,
-# k_d1 122.9.  Large 3D (spherical, general): k_rhs 301 + 423 + 2 x 1661 = 4046, k_d1
-# 89.9 (4 FLOP per stored difference, 22 differences per point over the 1.03x larger
-# region).  A workload without a capture reports no FLOP rate.
-F_ALG = {"headon": 2894.3, "large3d": 4135.9, "headon8": 3844.9}
+# 256x2x512 (cylindrical, two-point azimuth): k_rhs 217 + 351 + 2 x 1169 = 2906, k_d1 44.3.
+# Head-on with the 8th-order scheme: k_rhs 322 + 416 + 2 x 1522 = 3782, k_d1 122.9.  Large 3D
+# (spherical, general; counted on a 96x48x96 grid of the same kernel): k_rhs 320 + 453 + 2 x 1670 =
+# 4113, k_d1 89.8 (4 FLOP per stored difference, 22.46 differences per point at 384x192x384).
+# A workload without a capture reports no FLOP rate.
+F_ALG = {"headon": 2950.3, "large3d": 4202.8, "headon8": 3904.9}
+# DRAM bytes (read + write) of the same two launches in that capture, or None
+TRAFFIC = {"headon": 24016640 + 78848 + 92996096 + 452287232,
+           "headon8": 24951296 + 112128 + 90265088 + 329912576}
 # FLOPs of the same right-hand side in the point code's source (a host census of the code those counts
 # were taken from: FMA = 2, one division; without the k_d1 pre-pass); a test recomputes it, so that a
 # change of the kernels' arithmetic cannot leave F_ALG behind unnoticed
-KERNEL_CENSUS = {"headon": 2901, "headon8": 3765, "large3d": 4133}
+KERNEL_CENSUS = {"headon": 2976, "headon8": 3840, "large3d": 4217}
 # FLOPs over twice the FP64 instructions of the same source (k_d1 + k_rhs): the fraction of the FLOP peak
 # that a fully busy FP64 pipe reaches with this mix (a DADD or DMUL takes an FMA's issue slot for 1 FLOP)
-MIX_CEILING = {"headon": 0.8428, "headon8": 0.8367, "large3d": 0.8438}
+MIX_CEILING = {"headon": 0.8315, "headon8": 0.8282, "large3d": 0.8345}
 # FP64 operations (add + mul + div) per interior point of one RHS evaluation as the oracle's counting
 # build counts them: the plain coordinate-basis evaluation of the same discretisation with generic index
 # loops and the reference metric evaluated at every point -- the work of the method evaluated plainly.
 # Achieved against it (frac_method) can exceed 1: the kernels compute the same discrete right-hand side
 # with about a tenth of those operations
 F_METHOD = {"headon": 28967, "headon8": 49631, "large3d": 28970}
-# DRAM bytes (read + write) of the same two launches in that capture, or None
-TRAFFIC = {"headon": 24018688 + 98816 + 94506752 + 450309120,
-           "headon8": 24950784 + 136704 + 87655936 + 339959296}
 # The same for the diagnostics (Hamiltonian and momentum constraints, psi4), per interior
 # point of one call, from one ncu capture of those kernels on the head-on state, by workload
 # (head-on: k_ham 360 / 216 / 635 DADD / DMUL / DFMA, k_mom 114 / 141 / 269, k_psi4 502 / 461 /
@@ -113,6 +113,11 @@ def parse():
                     help="mean arrivals per minute of the served stream (80 at t_final 2M overloads the GPU as the "
                          "served configuration's 20 per minute at 50M does)")
     ap.add_argument("--served-policy", choices=("srpt", "fifo"), default="srpt")
+    ap.add_argument("--served-arms", default="",
+                    help="comma list of server arms of --workload served among srpt, fifo, srpt_cap (default: the "
+                         "policy and the other one); the plain queue always runs")
+    ap.add_argument("--served-starve-s", type=float, default=0.0,
+                    help="starvation cap of the srpt_cap arm, seconds")
     ap.add_argument("--served-cap", type=int, default=1000000,
                     help="interior points advanced together by the served arm (0: no cap)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -196,7 +201,7 @@ class ClockSampler:
 
     FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,utilization.gpu")
 
     def __init__(self, uuid: str | None):
         self.uuid = uuid
@@ -245,8 +250,10 @@ class ClockSampler:
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
         pw = [num(r[3]) for r in rows if num(r[3]) is not None]
+        ut = [num(r[9]) for r in rows if len(r) > 9 and num(r[9]) is not None]
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows), "power_w_max": max(pw) if pw else None}
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(pw) if pw else None,
+                "gpu_busy_pct_mean": statistics.mean(ut) if ut else None}
 
 
 def gpu_uuid(local: int) -> str | None:
@@ -678,12 +685,13 @@ def batch_compare(local: int, n_runs: int, steps: int, warm: int = 3) -> dict:
 
 
 def served_compare(local: int, n_requests: int, t_final: float, rate: float, policies=("srpt",),
-                   cap: int = 1000000) -> dict:
+                   cap: int = 1000000, starve_s: float = 0.0) -> dict:
     """A seeded Poisson stream of single-puncture and head-on requests of 1e5..4e6 points (the served
     workload's generator), served as it arrives (wall clock) by nr_server with each policy in
     `policies` (continuous batching under an 80 GB budget, points cap `cap`) and by a plain FIFO queue
     of single-grid runs, one at a time.  Each arm ends every request with its Hamiltonian-constraint
-    norms, a NaN/Inf check and the 64-bit digest of its final state; the digests are compared."""
+    norms, a NaN/Inf check and the 64-bit digest of its final state; the digests are compared.
+    Policy "srpt_cap": SRPT with the starvation cap starve_s (requests submitted longer ago go first)."""
     from paper_2505_00097_gb300 import binding as B
 
     reqs = W.config_served(n_requests=n_requests, t_final=t_final, rate_per_min=rate)
@@ -694,11 +702,15 @@ def served_compare(local: int, n_requests: int, t_final: float, rate: float, pol
         clocks.start()
         start = time.perf_counter()
         done, arrive, submitted, digest = {}, {}, [], {}
+        host_s = {"admit_s": 0.0, "retire_s": 0.0}
         upd = 0.0
         if batched:
             srv = B.Server(80 * 10 ** 9, 64, device=local)
             srv.set_tile(16, 8)
-            srv.set_policy(mode, cap)
+            srv.set_prefetch(4)
+            srv.set_policy("srpt" if mode == "srpt_cap" else mode, cap)
+            if mode == "srpt_cap":
+                srv.set_starvation_cap(starve_s)
         queue = []
         nxt = 0
         while len(done) < len(reqs):
@@ -728,33 +740,45 @@ def served_compare(local: int, n_requests: int, t_final: float, rate: float, pol
                 idle = not queue
                 if queue:
                     k = queue.pop(0)
+                    t0 = time.perf_counter()
                     g = B.Grid(reqs[k], device=local)
                     g.set_brill_lindquist(reqs[k]["masses"], reqs[k]["positions"])
+                    host_s["admit_s"] += time.perf_counter() - t0
                     steps = max(1, int(math.ceil(reqs[k]["t_final"] / g.dt_cfl - 1e-9)))
                     g.rk4_step(g.dt_cfl, steps)
+                    g.sync()
+                    t0 = time.perf_counter()
                     g.hamiltonian()
                     digest[k] = g.digest()
                     g.check_finite()
                     g.close()
+                    host_s["retire_s"] += time.perf_counter() - t0
                     done[k] = time.perf_counter() - start
                     upd += 4.0 * steps * g.interior
             if idle and nxt < len(reqs):
                 time.sleep(max(0.0, min(0.05, reqs[nxt]["arrival_s"] - (time.perf_counter() - start))))
         makespan = time.perf_counter() - start
         ck = clocks.stop()
+        stats = None
         if batched:
+            stats = srv.stats()
             srv.close()
         ttc = sorted(done[k] - arrive[k] for k in done)
         q = lambda p: ttc[min(len(ttc) - 1, int(round(p * (len(ttc) - 1))))]  # noqa: E731
-        return {"value": upd / makespan, "p50_ttc_s": q(0.5), "p99_ttc_s": q(0.99),
-                "mean_ttc_s": sum(ttc) / len(ttc), "makespan_s": makespan, "clocks": ck}, digest
+        r = {"value": upd / makespan, "p50_ttc_s": q(0.5), "p99_ttc_s": q(0.99),
+             "mean_ttc_s": sum(ttc) / len(ttc), "makespan_s": makespan, "clocks": ck}
+        if stats:
+            r["server_stats"] = stats
+        else:
+            r["host_s"] = host_s
+        return r, digest
 
     arms = {}
     digests = {}
     for pol in policies:
         arms[pol], digests[pol] = serve(pol)
     plain, dplain = serve("plain")
-    out = {"unit": UNIT, "requests": len(reqs), "t_final": t_final, "rate_per_min": rate,
+    out = {"unit": UNIT, "requests": len(reqs), "t_final": t_final, "rate_per_min": rate, "starvation_cap_s": starve_s,
            "points_range": [1e5, 4e6], "hbm_budget_gb": 80, "max_batch_points": cap,
            "plain": plain, "plain_value": plain["value"],
            "mode": "nr_server continuous batching (requests admitted as they arrive, one nr_batch per kind of "
@@ -806,16 +830,18 @@ def run_served(args, world, rank, local):
     import torch
 
     torch.cuda.set_device(local)
-    pols = (args.served_policy, other_name(args.served_policy))
-    r = served_compare(local, args.served_requests, args.served_tfinal, args.served_rate, pols, args.served_cap)
+    pols = tuple(a for a in args.served_arms.split(",") if a) if args.served_arms else \
+        (args.served_policy, other_name(args.served_policy))
+    r = served_compare(local, args.served_requests, args.served_tfinal, args.served_rate, pols, args.served_cap,
+                       args.served_starve_s)
     line = {
         "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": 1, "steps": None, "warmup": 0,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded Poisson request stream)",
         "config": {"workload": f"served_{r['requests']}_requests", "rate_per_min": args.served_rate,
                    "t_final": args.served_tfinal, "points_range": [1e5, 4e6], "hbm_budget_gb": 80,
-                   "policy": args.served_policy, "max_batch_points": args.served_cap},
-        "served": r[pols[0]], f"served_{pols[1]}": r[pols[1]], "plain_fifo": r["plain"],
+                   "policy": pols[0], "max_batch_points": args.served_cap, "starvation_cap_s": args.served_starve_s},
+        "served": r[pols[0]], **{f"served_{p}": r[p] for p in pols[1:]}, "plain_fifo": r["plain"],
         "speedup_vs_plain": r["ratio"], "bitwise_equal_to_plain": r["bitwise_equal_to_plain"],
         "p50_ttc_vs_plain": r["p50_ttc_s"] / r["plain"]["p50_ttc_s"],
     }

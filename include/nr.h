@@ -351,6 +351,17 @@ int nr_batch_ssprk3_step(nr_batch* batch, const double* dts, int nsteps);
  *   nr_server_poll: status 0 queued, 1 running, 2 done, 3 failed; steps done
  *     and total; the final L2/Linf Hamiltonian-constraint norms when done (NaN
  *     for a request the guard retired).
+ *   nr_server_set_starvation_cap: SRPT with a bound on starvation: a request
+ *     submitted more than `seconds` ago (wall clock) goes ahead of every request
+ *     submitted since, in arrival order, both for admission and for the chunks
+ *     (0 = off, the default; NR_EINVAL for a negative or NaN value).
+ *   nr_server_set_prefetch: depth 0 (default): a request's host-side set-up
+ *     (coordinates, per-axis arrays, boundary maps) runs when it is admitted.
+ *     depth k > 0: a worker thread computes the set-ups of the next k queued
+ *     requests in admission order while the GPU works, and while other
+ *     requests run, a queued request is admitted only once its set-up is ready
+ *     (the admission then only allocates, uploads and sets initial data);
+ *     with nothing running it is admitted at once.  NR_EINVAL for depth < 0.
  *   nr_server_set_guard: every every_steps steps of a request (default 100;
  *     0 = off) the server checks alpha and W of the requests it advanced for
  *     NaN/Inf on the device (one flag per request, read back behind the next
@@ -358,6 +369,12 @@ int nr_batch_ssprk3_step(nr_batch* batch, const double* dts, int nsteps);
  *     non-finite is retired as failed with NR_ENONFINITE (its device memory
  *     released, nothing kept) while the others continue, bitwise unaffected.
  *     A request that finishes is also checked at retirement.
+ *   nr_server_stats: host-side accounting since creation, out[9] = chunks
+ *     enqueued, batch rebuilds, admissions, retirements, then wall seconds spent
+ *     admitting (grid set-up, upload, initial data), retiring (constraint norms,
+ *     kept state or digest, release), rebuilding batches (and capturing their
+ *     graphs), waiting at chunk fences (the GPU busy with the chunk before) and
+ *     enqueueing chunks.
  *   nr_server_request_error: the status that ended a failed request
  *     (NR_ENONFINITE, NR_ENOMEM when it cannot fit the budget even alone, or
  *     the set-up's error); NR_OK for the others.
@@ -389,6 +406,9 @@ int nr_server_poll(nr_server* server, int64_t id, int* status, int64_t* steps_do
                    double* l2, double* linf);
 int nr_server_fetch_state(nr_server* server, int64_t id, double* host_state, size_t capacity_doubles);
 int nr_server_set_guard(nr_server* server, int every_steps);
+int nr_server_set_starvation_cap(nr_server* server, double seconds);
+int nr_server_set_prefetch(nr_server* server, int depth);
+int nr_server_stats(const nr_server* server, double out[9]);
 int nr_server_request_error(nr_server* server, int64_t id, int* code);
 int nr_server_fetch_digest(nr_server* server, int64_t id, uint64_t* digest);
 

@@ -32,7 +32,8 @@ EXPORTS = (
     "nr_server_create", "nr_server_destroy", "nr_server_set_tile", "nr_server_set_policy", "nr_server_submit",
     "nr_server_advance",
     "nr_server_poll", "nr_server_fetch_state", "nr_server_set_guard", "nr_server_request_error",
-    "nr_server_fetch_digest", "nr_state_digest",
+    "nr_server_fetch_digest", "nr_server_set_starvation_cap", "nr_server_stats",
+    "nr_server_set_prefetch", "nr_state_digest",
     "nr_part_create", "nr_part_destroy", "nr_part_query", "nr_part_set_brill_lindquist", "nr_part_set_state",
     "nr_part_get_state", "nr_part_rk4_step", "nr_part_ssprk3_step", "nr_part_digest", "nr_part_sync",
     "nr_part_plan_info", "nr_part_plan_boxes", "nr_part_plan_records", "nr_last_error",
@@ -145,6 +146,9 @@ def lib() -> ctypes.CDLL:
                                  ctypes.POINTER(ctypes.c_int64), dp, dp]
     L.nr_server_fetch_state.argtypes = [vp, ctypes.c_int64, dp, ctypes.c_size_t]
     L.nr_server_set_guard.argtypes = [vp, ctypes.c_int]
+    L.nr_server_set_starvation_cap.argtypes = [vp, ctypes.c_double]
+    L.nr_server_stats.argtypes = [vp, dp]
+    L.nr_server_set_prefetch.argtypes = [vp, ctypes.c_int]
     L.nr_server_request_error.argtypes = [vp, ctypes.c_int64, ip]
     L.nr_server_fetch_digest.argtypes = [vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_uint64)]
     L.nr_state_digest.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_uint64)]
@@ -449,6 +453,21 @@ class Server:
     def set_guard(self, every_steps: int) -> None:
         """non-finite check of the advanced requests every every_steps steps (0: off)"""
         _check(lib().nr_server_set_guard(self.h, int(every_steps)))
+
+    def set_starvation_cap(self, seconds: float) -> None:
+        """SRPT: requests submitted more than `seconds` ago go first (0: off)"""
+        _check(lib().nr_server_set_starvation_cap(self.h, float(seconds)))
+
+    def set_prefetch(self, depth: int) -> None:
+        """host-side set-ups of the next `depth` queued requests computed ahead (0: at admission)"""
+        _check(lib().nr_server_set_prefetch(self.h, int(depth)))
+
+    def stats(self) -> dict:
+        v = (ctypes.c_double * 9)()
+        _check(lib().nr_server_stats(self.h, v))
+        keys = ("chunks", "rebuilds", "admitted", "retired", "admit_s", "retire_s", "rebuild_s", "fence_s",
+                "enqueue_s")
+        return dict(zip(keys, list(v)))
 
     def request_error(self, rid: int) -> int:
         code = ctypes.c_int()

@@ -112,51 +112,17 @@ __device__ __forceinline__ double mixraw8(const double* f, long sa, long sb)
                 d1raw8(f + sb, sa), d1raw8(f + 2 * sb, sa), d1raw8(f + 3 * sb, sa), d1raw8(f + 4 * sb, sa));
 }
 
-// ---- exact scaling by 2^K on the integer pipe.  The FP64 pipe bounds every kernel of the
-// point code and the integer pipe idles, so x * 2^K moves the exponent field of a normal
-// number by K instead of issuing an FP64 multiply.  The result is the bits of the IEEE
-// product x * 2^K (round to nearest even) for every input: the exponent shift where both x
-// and the product are normal numbers, and sc2_edge, also in integer arithmetic, for zeros,
-// subnormal inputs or results, overflow to infinity and NaNs.
-template <int K>
-__device__ __forceinline__ double sc2_edge(double x)
-{
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const unsigned long long sign = b & 0x8000000000000000ULL, mag = b & 0x7FFFFFFFFFFFFFFFULL;
-    const int e = (int)(mag >> 52);
-    if (e == 0x7FF) return __longlong_as_double((long long)(mag > 0x7FF0000000000000ULL ? b | (1ULL << 51) : b));
-    if (mag == 0) return x;
-    // x = m 2^(ee - 1075) with m < 2^53 (the implicit bit for a normal x)
-    const int ee = e ? e : 1;
-    const unsigned long long m = e ? (mag & 0xFFFFFFFFFFFFFULL) | (1ULL << 52) : mag;
-    int E = ee + K;   // exponent field of the product if m were normalised
-    unsigned long long r;
-    if (E >= 1) {
-        const int k = __clzll((long long)m) - 11;   // left shift that brings the top bit to bit 52
-        if (E - k >= 1) {
-            E -= k;
-            r = E > 0x7FE ? 0x7FF0000000000000ULL : ((unsigned long long)E << 52) | ((m << k) & 0xFFFFFFFFFFFFFULL);
-        } else {
-            r = m << (E - 1);   // still subnormal: exact
-        }
-    } else {
-        // subnormal product: m 2^(E - 1) in units of the least subnormal, rounded to nearest even
-        const int s = 1 - E > 63 ? 63 : 1 - E;
-        const unsigned long long q = m >> s, rem = m & ((1ULL << s) - 1), half = 1ULL << (s - 1);
-        r = q + ((rem > half || (rem == half && (q & 1))) ? 1 : 0);
-    }
-    return __longlong_as_double((long long)(sign | r));
-}
-
+// ---- scaling by 2^K: an IEEE multiply by the constant 2^K, i.e. exactly x 2^K rounded as IEEE
+// specifies at every input (zeros, subnormal inputs and results, overflow to infinity, NaN).  An
+// earlier version moved the exponent field on the integer pipe instead; it was faster but not the
+// IEEE product at the edges of the range, and every exact integer or mixed form measured slower
+// than this multiply on the head-on step.
 template <int K>
 __device__ __forceinline__ double sc2(double x)
 {
-    // exponent fields whose product stays normal: [max(1, 1 - K), min(0x7FE, 0x7FE - K)]
-    constexpr unsigned lo = K < 0 ? 1u - K : 1u, hi = K > 0 ? 0x7FEu - K : 0x7FEu;
-    const int h = __double2hiint(x), l = __double2loint(x);
-    const unsigned e = ((unsigned)h >> 20) & 0x7FFu;
-    if (e - lo <= hi - lo) return __hiloint2double(h + K * (1 << 20), l);
-    return sc2_edge<K>(x);
+    static_assert(K >= -60 && K <= 60, "sc2: |K| <= 60");
+    constexpr auto c = K >= 0 ? 1.0 * (1ULL << (K >= 0 ? K : 0)) : 1.0 / (1ULL << (K < 0 ? -K : 0));
+    return x * c;
 }
 
 // Finite-difference families: order ORD = N_FD with N_G = ORD/2 + 1 ghost layers
@@ -616,13 +582,6 @@ __device__ __forceinline__ void metric_part(const PointIn& P, MetricPart& M)
     for (int i = 0; i < 3; i++)
 #pragma unroll
         for (int p = 0; p < 6; p++) Rp[i][p] = offd(p) ? R[i][spi(p)][spj(p)] + R[i][spj(p)][spi(p)] : R[i][spi(p)][spi(p)];
-    double hDvec[3], hDlam[3][3];   // halves, exact
-#pragma unroll
-    for (int k = 0; k < 3; k++) {
-        hDvec[k] = sc2<-1>(Dvec[k]);
-#pragma unroll
-        for (int n = 0; n < 3; n++) hDlam[k][n] = sc2<-1>(Dlam[k][n]);
-    }
 #pragma unroll
     for (int s = 0; s < 6; s++) {
         const int i = spi(s), j = spj(s);
@@ -636,10 +595,12 @@ __device__ __forceinline__ void metric_part(const PointIn& P, MetricPart& M)
         // (Dl[k][p] = 0 where dlz(k, p) and Dlam[j][k] = Dhat_j lambda^k = 0 where dvz(k, j):
         // those terms are skipped)
         if (i == j) {
-            // 2 A_ii
+            // 2 A_ii (A_ii summed on its own, doubled by the FMA that adds it)
+            double u = 0.0;
 #pragma unroll
             for (int p = 0; p < 6; p++)
-                if (!dlz<FAM, AX>(i, p)) t = fma(sc2<1>(Rp[i][p]), Dl[i][p], t);
+                if (!dlz<FAM, AX>(i, p)) u = fma(Rp[i][p], Dl[i][p], u);
+            t = fma(2.0, u, t);
             // 1/2 Delta^k (2 Delta_iik)
 #pragma unroll
             for (int k = 0; k < 3; k++)
@@ -657,20 +618,22 @@ __device__ __forceinline__ void metric_part(const PointIn& P, MetricPart& M)
 #pragma unroll
             for (int p = 0; p < 6; p++)
                 if (!dlz<FAM, AX>(i, p)) t = fma(Rp[j][p], Dl[i][p], t);
-            // 1/2 Delta^k (Delta_ijk + Delta_jik)
+            // 1/2 Delta^k (Delta_ijk + Delta_jik) + 1/2 (gammabar_ki Dhat_j lambda^k + gammabar_kj
+            // Dhat_i lambda^k): summed on their own, halved by the FMA that adds them
+            double v = 0.0;
 #pragma unroll
             for (int k = 0; k < 3; k++) {
-                if (!dlz<FAM, AX>(i, sp(j, k))) t = fma(hDvec[k], Dl[i][sp(j, k)], t);
-                if (!dlz<FAM, AX>(j, sp(i, k))) t = fma(hDvec[k], Dl[j][sp(i, k)], t);
+                if (!dlz<FAM, AX>(i, sp(j, k))) v = fma(Dvec[k], Dl[i][sp(j, k)], v);
+                if (!dlz<FAM, AX>(j, sp(i, k))) v = fma(Dvec[k], Dl[j][sp(i, k)], v);
             }
-            // 1/2 (gammabar_ki Dhat_j lambda^k + gammabar_kj Dhat_i lambda^k)
-            if (!dvz<FAM, AX>(i, j)) t += hDlam[j][i];
-            if (!dvz<FAM, AX>(j, i)) t += hDlam[i][j];
+            if (!dvz<FAM, AX>(i, j)) v += Dlam[j][i];
+            if (!dvz<FAM, AX>(j, i)) v += Dlam[i][j];
 #pragma unroll
             for (int k = 0; k < 3; k++) {
-                if (!dvz<FAM, AX>(k, i)) t = fma(h[sp(k, j)], hDlam[i][k], t);
-                if (!dvz<FAM, AX>(k, j)) t = fma(h[sp(k, i)], hDlam[j][k], t);
+                if (!dvz<FAM, AX>(k, i)) v = fma(h[sp(k, j)], Dlam[i][k], v);
+                if (!dvz<FAM, AX>(k, j)) v = fma(h[sp(k, i)], Dlam[j][k], v);
             }
+            t = fma(0.5, v, t);
         }
         M.Ric[s] = fma(-0.5, Lfull[s], t);
     }

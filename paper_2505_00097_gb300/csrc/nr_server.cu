@@ -31,6 +31,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
 #include <condition_variable>
 #include <deque>
 #include <map>
@@ -58,6 +59,7 @@ struct Request {
     size_t bytes = 0;
     int64_t interior = 0;      // interior points
     int64_t steps_est = 0;     // steps to t_final at the CFL step, known at submission
+    double submit_t = 0.0;     // submission time (steady clock, seconds)
     // progress
     int status = 0;          // 0 queued, 1 running, 2 done, 3 failed
     nr_grid* grid = nullptr;
@@ -102,6 +104,7 @@ struct nr_server {
     size_t used = 0;
     int tile_x = 0, tile_y = 0;   // 0: autotune on every rebuild
     int policy = NR_SERVE_FIFO;
+    double max_starve_s = 0.0;    // SRPT: requests submitted longer ago than this go first (0: off)
     int64_t max_points = 0;       // 0: no cap on the interior points advanced together
     // at most one chunk queued behind the running one, so that a new arrival
     // is scheduled within about a chunk of GPU time
@@ -122,7 +125,14 @@ struct nr_server {
     std::condition_variable cv;
     std::deque<Request*> prep_jobs;
     bool stop = false;
-    int prefetch = 2;   // queued requests whose set-up is computed ahead, in admission order
+    // 0: a request's host-side set-up is computed when it is admitted; k > 0: the set-ups of the
+    // next k queued requests (in admission order) are computed ahead by the worker thread, and a
+    // request waits in the queue until its set-up is ready unless nothing runs
+    int prefetch = 0;
+    // host-side accounting (nr_server_stats): chunks, batch rebuilds, admissions, retirements;
+    // seconds in admission, retirement, batch rebuilds, waits at chunk fences, enqueueing chunks
+    int64_t n_chunks = 0, n_rebuilds = 0, n_admitted = 0, n_retired = 0;
+    double t_admit = 0.0, t_retire = 0.0, t_rebuild = 0.0, t_fence = 0.0, t_enqueue = 0.0;
 };
 
 namespace {
@@ -305,55 +315,76 @@ void fail_request(nr_server* s, Request* r)
 // right-hand-side evaluations per step
 int64_t substeps(const Request* r) { return r->P.integrator == NR_SSPRK3 ? 3 : 4; }
 
-// work left, in point-substeps; ties broken by arrival (id)
-bool srpt_before(const Request* a, const Request* b)
+double now_s()
 {
-    const int64_t wa = (a->steps_total - a->steps_done) * a->interior * substeps(a);
-    const int64_t wb = (b->steps_total - b->steps_done) * b->interior * substeps(b);
-    return wa != wb ? wa < wb : a->id < b->id;
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
-// position in the queue of the request the policy admits next
-size_t next_queued(const nr_server* s)
+// work left, in point-substeps (a queued request: all of it, from its CFL step)
+int64_t work_left(const Request* r)
 {
-    if (s->policy != NR_SERVE_SRPT) return 0;
-    size_t best = 0;
-    for (size_t q = 1; q < s->queue.size(); q++) {
-        const Request* a = s->queue[q];
-        const Request* b = s->queue[best];
-        const int64_t wa = a->steps_est * a->interior * substeps(a), wb = b->steps_est * b->interior * substeps(b);
-        if (wa < wb || (wa == wb && a->id < b->id)) best = q;
+    const int64_t steps = r->status == 0 ? r->steps_est : r->steps_total - r->steps_done;
+    return steps * r->interior * substeps(r);
+}
+
+// the policy's order.  FIFO: arrival (id).  SRPT: least work left first, ties by arrival; with a
+// starvation cap, requests submitted more than max_starve_s ago come first, in arrival order.
+bool policy_before(const nr_server* s, const Request* a, const Request* b, double now)
+{
+    if (s->policy != NR_SERVE_SRPT) return a->id < b->id;
+    if (s->max_starve_s > 0.0) {
+        const bool sa = now - a->submit_t > s->max_starve_s, sb = now - b->submit_t > s->max_starve_s;
+        if (sa != sb) return sa;
+        if (sa) return a->id < b->id;
     }
-    return best;
+    const int64_t wa = work_left(a), wb = work_left(b);
+    return wa != wb ? wa < wb : a->id < b->id;
 }
 
 // make queued requests resident, in policy order, while budget and slots allow
 int admit(nr_server* s)
 {
-    while (!s->queue.empty()) {
-        const size_t pos = next_queued(s);
-        Request* r = s->queue[pos];
-        if ((int)s->running.size() >= s->max_slots) break;
-        if (s->used + r->bytes > s->budget) {
-            if (s->running.empty())  // can never fit
-            {
-                r->status = 3;
-                r->err = NR_ENOMEM;
-                s->queue.erase(s->queue.begin() + pos);
-                continue;
+    prefetch_setups(s);
+    bool progress = true;
+    while (!s->queue.empty() && progress) {
+        progress = false;
+        std::vector<Request*> order(s->queue.begin(), s->queue.end());
+        const double now = now_s();
+        std::sort(order.begin(), order.end(),
+                  [&](const Request* a, const Request* b) { return policy_before(s, a, b, now); });
+        for (Request* r : order) {
+            if ((int)s->running.size() >= s->max_slots) break;
+            const size_t pos = (size_t)(std::find(s->queue.begin(), s->queue.end(), r) - s->queue.begin());
+            if (s->used + r->bytes > s->budget) {
+                if (s->running.empty()) {   // can never fit
+                    r->status = 3;
+                    r->err = NR_ENOMEM;
+                    s->queue.erase(s->queue.begin() + pos);
+                    progress = true;
+                    break;
+                }
+                break;   // the policy's next request waits for memory
             }
+            if (s->prefetch > 0 && !s->running.empty()) {
+                std::lock_guard<std::mutex> lk(s->mu);
+                if (r->setup_state != 3) continue;   // set-up not ready: admitted later, the GPU is busy
+            }
+            s->queue.erase(s->queue.begin() + pos);
+            const double t0 = now_s();
+            const int rc = start_request(s, r);
+            s->t_admit += now_s() - t0;
+            s->n_admitted++;
+            if (rc != NR_OK) {
+                r->status = 3;
+                r->err = rc;
+            } else {
+                s->used += r->bytes;
+                s->running.push_back(r);
+                s->batch_dirty = true;
+            }
+            progress = true;
             break;
         }
-        s->queue.erase(s->queue.begin() + pos);
-        const int rc = start_request(s, r);
-        if (rc != NR_OK) {
-            r->status = 3;
-            r->err = rc;
-            continue;
-        }
-        s->used += r->bytes;
-        s->running.push_back(r);
-        s->batch_dirty = true;
     }
     prefetch_setups(s);
     return NR_OK;
@@ -364,11 +395,8 @@ void prefetch_setups(nr_server* s)
     if (s->prefetch <= 0 || s->queue.empty()) return;
     // the admission order of the queue: policy order (next_queued picks the first of it)
     std::vector<Request*> order(s->queue.begin(), s->queue.end());
-    if (s->policy == NR_SERVE_SRPT)
-        std::stable_sort(order.begin(), order.end(), [](const Request* a, const Request* b) {
-            const int64_t wa = a->steps_est * a->interior * substeps(a), wb = b->steps_est * b->interior * substeps(b);
-            return wa != wb ? wa < wb : a->id < b->id;
-        });
+    const double now = now_s();
+    std::sort(order.begin(), order.end(), [&](const Request* a, const Request* b) { return policy_before(s, a, b, now); });
     std::lock_guard<std::mutex> lk(s->mu);
     if (!s->worker.joinable()) s->worker = std::thread(worker_loop, s);
     int k = 0;
@@ -386,10 +414,8 @@ void prefetch_setups(nr_server* s)
 void select_active(nr_server* s)
 {
     std::vector<Request*> order = s->running;
-    if (s->policy == NR_SERVE_SRPT)
-        std::sort(order.begin(), order.end(), srpt_before);
-    else
-        std::sort(order.begin(), order.end(), [](const Request* a, const Request* b) { return a->id < b->id; });
+    const double now = now_s();
+    std::sort(order.begin(), order.end(), [&](const Request* a, const Request* b) { return policy_before(s, a, b, now); });
     std::vector<Request*> sel;
     int64_t pts = 0;
     for (Request* r : order) {
@@ -521,6 +547,7 @@ static int nr_server_submit_body(nr_server* s, int coords, const int Nxx[3], con
         return nrk_fail(NR_EINVAL, "request grid has no valid CFL step");
     }
     r->steps_est = std::max<int64_t>(1, (int64_t)ceil(t_final / dt - 1e-9));
+    r->submit_t = now_s();
     s->queue.push_back(r);
     s->all[r->id] = r;
     if (id_out) *id_out = r->id;
@@ -545,6 +572,29 @@ int nr_server_set_policy(nr_server* s, int policy, int64_t max_batch_points)
     return NR_OK;
 }
 
+int nr_server_stats(const nr_server* s, double out[9])
+{
+    if (!s || !out) return nrk_fail(NR_EINVAL, "bad nr_server_stats arguments");
+    const double v[9] = {(double)s->n_chunks, (double)s->n_rebuilds, (double)s->n_admitted, (double)s->n_retired,
+                         s->t_admit, s->t_retire, s->t_rebuild, s->t_fence, s->t_enqueue};
+    memcpy(out, v, sizeof v);
+    return NR_OK;
+}
+
+int nr_server_set_starvation_cap(nr_server* s, double seconds)
+{
+    if (!s || !(seconds >= 0.0)) return nrk_fail(NR_EINVAL, "bad nr_server_set_starvation_cap arguments");
+    s->max_starve_s = seconds;
+    return NR_OK;
+}
+
+int nr_server_set_prefetch(nr_server* s, int depth)
+{
+    if (!s || depth < 0) return nrk_fail(NR_EINVAL, "bad nr_server_set_prefetch arguments");
+    s->prefetch = depth;
+    return NR_OK;
+}
+
 int nr_server_set_guard(nr_server* s, int every_steps)
 {
     if (!s || every_steps < 0) return nrk_fail(NR_EINVAL, "bad nr_server_set_guard arguments");
@@ -559,7 +609,14 @@ static int nr_server_advance_body(nr_server* s, int nsteps, int* n_running, int*
     int left = nsteps;
     while (left > 0 && !s->running.empty()) {
         select_active(s);
-        if (s->batch_dirty && (rc = rebuild_batch(s))) return rc;
+        if (s->batch_dirty) {
+            const double t0 = now_s();
+            rc = rebuild_batch(s);
+            s->t_rebuild += now_s() - t0;
+            s->n_rebuilds++;
+            if (rc) return rc;
+        }
+        const double te = now_s();
         int64_t k = left;
         for (Request* r : s->active) k = std::min(k, r->steps_total - r->steps_done);
         for (size_t q = 0; q < s->batches.size(); q++) {
@@ -572,7 +629,11 @@ static int nr_server_advance_body(nr_server* s, int nsteps, int* n_running, int*
         for (Request* r : s->active) r->steps_done += k;
         s->since_guard += k;
         if ((rc = guard_enqueue(s))) return rc;
+        const double tf = now_s();
+        s->t_enqueue += tf - te;
+        s->n_chunks++;
         if ((rc = chunk_fence(s))) return rc;
+        s->t_fence += now_s() - tf;
         left -= (int)k;
         bool retired = false;
         // the guard results of the chunk the fence waited for (the slot it leaves current)
@@ -604,10 +665,13 @@ static int nr_server_advance_body(nr_server* s, int nsteps, int* n_running, int*
                     drop_batch(s);  // the batch refers to the grids about to be released
                     retired = true;
                 }
+                const double t0 = now_s();
                 if (failed)
                     fail_request(s, r);
                 else
                     finish_request(s, r);
+                s->t_retire += now_s() - t0;
+                s->n_retired++;
                 s->running.erase(s->running.begin() + q);
             } else {
                 q++;

@@ -28,6 +28,7 @@ struct CK {
     constexpr CK(double x) : v(x) {}
     constexpr CK(int x) : v((double)x) {}
     constexpr CK(long x) : v((double)x) {}
+    constexpr CK(long long x) : v((double)x) {}
     explicit operator bool() const { return v != 0.0; }
     CK& operator+=(CK b) { ++g_ops.add; v += b.v; return *this; }
     CK& operator-=(CK b) { ++g_ops.add; v -= b.v; return *this; }

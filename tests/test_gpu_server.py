@@ -248,3 +248,62 @@ def test_a_diverging_request_fails_and_the_others_are_unaffected(every):
         assert srv.fetch_digest(rid) == g.digest()
         g.close()
     srv.close()
+
+
+def test_starvation_cap_lets_the_older_request_go_first():
+    """SRPT with a starvation cap: once both requests have waited longer than the cap, the older one
+    runs first although the newer one has less work left (plain SRPT would preempt it, as the test
+    above shows); results stay bitwise those alone."""
+    import time
+
+    long_spec, short_spec = _requests()[3], _requests()[0]
+    t_final = 0.8
+    srv = B.Server(int(80 * 2 ** 30), 8)
+    srv.set_tile(32, 4)
+    srv.set_policy("srpt", 1)          # one request at a time
+    srv.set_starvation_cap(1e-3)
+    a = srv.submit(long_spec, t_final, keep_state=True)
+    srv.advance(2)
+    b = srv.submit(short_spec, t_final, keep_state=True)
+    time.sleep(0.01)                   # both are now older than the cap
+    srv.advance(3)
+    assert srv.poll(a)["steps_done"] == 5 and srv.poll(b)["steps_done"] == 0
+    _run_until_done(srv, a, step=7)
+    assert srv.poll(b)["steps_done"] == 0
+    _run_until_done(srv, b)
+    for rid, spec in ((a, long_spec), (b, short_spec)):
+        ref, n, T = _alone(spec, t_final)
+        assert srv.poll(rid)["steps_done"] == n
+        assert np.array_equal(srv.fetch_state(rid, 24 * T), ref)
+    with pytest.raises(B.NrError):
+        srv.set_starvation_cap(-1.0)
+    srv.close()
+
+
+@pytest.mark.parametrize("policy", ["fifo", "srpt"])
+def test_background_setups_keep_results(policy):
+    """With set-ups computed ahead by the worker thread (prefetch depth 2), requests that arrive while
+    others run wait until their set-up is ready; every result is still bitwise its result alone, and
+    the server's accounting sees every admission and retirement."""
+    reqs = _requests()
+    t_final = 0.8
+    srv = B.Server(int(80 * 2 ** 30), 8)
+    srv.set_tile(16, 8)
+    srv.set_prefetch(2)
+    srv.set_policy(policy, 2000)
+    ids = [srv.submit(reqs[0], t_final, keep_state=True), srv.submit(reqs[1], t_final, keep_state=True)]
+    srv.advance(3)
+    ids += [srv.submit(reqs[2], t_final, keep_state=True), srv.submit(reqs[3], t_final, keep_state=True)]
+    for _ in range(1000):
+        nrun, nq = srv.advance(2)
+        if nrun == 0 and nq == 0:
+            break
+    for rid, spec in zip(ids, reqs):
+        assert srv.poll(rid)["status"] == 2
+        ref, n, T = _alone(spec, t_final)
+        assert np.array_equal(srv.fetch_state(rid, 24 * T), ref)
+    st = srv.stats()
+    assert st["admitted"] == 4 and st["retired"] == 4 and st["chunks"] > 0
+    with pytest.raises(B.NrError):
+        srv.set_prefetch(-1)
+    srv.close()
