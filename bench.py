@@ -79,9 +79,9 @@ MIX_CEILING = {"headon": 0.8315, "headon8": 0.8282, "large3d": 0.8345}
 F_METHOD = {"headon": 28967, "headon8": 49631, "large3d": 28970}
 # The same for the diagnostics (Hamiltonian and momentum constraints, psi4), per interior
 # point of one call, from one ncu capture of those kernels on the head-on state, by workload
-# (head-on: k_ham 360 / 216 / 635 DADD / DMUL / DFMA, k_mom 114 / 141 / 269, k_psi4 502 / 461 /
-# 1080; the reductions and ghost copies add < 0.1); absent: not captured
-DIAG_FLOPS = {"headon": {"hamiltonian": 1846.0, "momentum": 793.0, "psi4": 3123.0}}
+# (head-on: k_ham 366 / 238 / 640 DADD / DMUL / DFMA, k_mom 119 / 162 / 269, k_psi4 505 / 483 /
+# 1085; the reductions and ghost copies add < 0.1); absent: not captured
+DIAG_FLOPS = {"headon": {"hamiltonian": 1884.0, "momentum": 819.0, "psi4": 3158.0}}
 # psi4 modes on the workload's extraction sphere: l <= 8, Gauss-Legendre x uniform nodes
 PSI4_LMAX, PSI4_NTHETA, PSI4_NPHI = 8, 24, 48
 # FP64 pipe of one SM: 2 DFMA per clock (ncu peak_sustained of
@@ -98,7 +98,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["headon", "headon8", "single_puncture", "large3d", "batch", "served"],
+    ap.add_argument("--workload", choices=["headon", "headon8", "single_puncture", "large3d", "large3d8", "batch",
+                                           "served"],
                     default="headon")
     ap.add_argument("--batch-runs", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=100,
@@ -130,7 +131,7 @@ def parse():
 
 def workload(name: str) -> dict:
     return {"headon": W.config_headon, "single_puncture": W.config_single_puncture,
-            "large3d": W.config_large3d, "headon8": W.config_headon8}[name]()
+            "large3d": W.config_large3d, "headon8": W.config_headon8, "large3d8": W.config_large3d8}[name]()
 
 
 def config_of(spec: dict, extra: dict | None = None) -> dict:

@@ -86,6 +86,16 @@ def config_large3d() -> dict:
     return s
 
 
+def config_large3d8() -> dict:
+    """The large 3D configuration with the production scheme of Sec. 4.1: 8th-order finite differences
+    (NG = 5), SSPRK3 at CFL 0.35 (as the head-on production workload), Kreiss-Oliger 0.3 on the metric and
+    0.99 on the gauge gridfunctions; the general (three-dimensional) 8th-order kernel."""
+    s = config_large3d()
+    s.update(name="vacuum3d8_sinhsph_384x192x384", NG=5, ko_sigma=[0.3] * 17 + [0.99] * 7, integrator="ssprk3",
+             cfl=0.35)
+    return s
+
+
 def config_batch(n_runs: int = 64, steps: int = 500, seed: int = MASTER_SEED + 4) -> list[dict]:
     """64 head-on runs: q~U[1,4], d~U[0.5,2], N_rho in {64,96,128,192,256}, N_z=2 N_rho, N_phi=2."""
     rng = np.random.default_rng(seed)
