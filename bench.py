@@ -67,16 +67,16 @@ TRAFFIC = {"headon": 24016640 + 78848 + 92996096 + 452287232,
 # FLOPs of the same right-hand side in the point code's source (a host census of the code those counts
 # were taken from: FMA = 2, one division; without the k_d1 pre-pass); a test recomputes it, so that a
 # change of the kernels' arithmetic cannot leave F_ALG behind unnoticed
-KERNEL_CENSUS = {"headon": 2976, "headon8": 3840, "large3d": 4217}
+KERNEL_CENSUS = {"headon": 2976, "headon8": 3840, "large3d": 4217, "large3d8": 5590}
 # FLOPs over twice the FP64 instructions of the same source (k_d1 + k_rhs): the fraction of the FLOP peak
 # that a fully busy FP64 pipe reaches with this mix (a DADD or DMUL takes an FMA's issue slot for 1 FLOP)
-MIX_CEILING = {"headon": 0.8315, "headon8": 0.8282, "large3d": 0.8345}
+MIX_CEILING = {"headon": 0.8315, "headon8": 0.8282, "large3d": 0.8345, "large3d8": 0.8272}
 # FP64 operations (add + mul + div) per interior point of one RHS evaluation as the oracle's counting
 # build counts them: the plain coordinate-basis evaluation of the same discretisation with generic index
 # loops and the reference metric evaluated at every point -- the work of the method evaluated plainly.
 # Achieved against it (frac_method) can exceed 1: the kernels compute the same discrete right-hand side
 # with about a tenth of those operations
-F_METHOD = {"headon": 28967, "headon8": 49631, "large3d": 28970}
+F_METHOD = {"headon": 28967, "headon8": 49631, "large3d": 28970, "large3d8": 49634}
 # The same for the diagnostics (Hamiltonian and momentum constraints, psi4), per interior
 # point of one call, from one ncu capture of those kernels on the head-on state, by workload
 # (head-on: k_ham 366 / 238 / 640 DADD / DMUL / DFMA, k_mom 119 / 162 / 269, k_psi4 505 / 483 /
@@ -99,9 +99,11 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["headon", "headon8", "single_puncture", "large3d", "large3d8", "batch",
-                                           "served"],
+                                           "served", "part"],
                     default="headon")
     ap.add_argument("--batch-runs", type=int, default=64)
+    ap.add_argument("--parts", default="1,1,4",
+                    help="--workload part: partitions per axis of the head-on grid (the chare decomposition)")
     ap.add_argument("--batch-steps", type=int, default=100,
                     help="RK4 steps per run of the batched comparison in the default line (500 in the workload)")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain comparison")
@@ -121,6 +123,12 @@ def parse():
                     help="starvation cap of the srpt_cap arm, seconds")
     ap.add_argument("--served-cap", type=int, default=1000000,
                     help="interior points advanced together by the served arm (0: no cap)")
+    ap.add_argument("--profile", choices=("rhs", "diagnostics"), default=None,
+                    help="for profiler captures: one nr_rhs (k_d1 + k_rhs) of the workload's initial state, or one "
+                         "call each of the constraint and psi4 diagnostics after 4 steps; no timing, no JSON line")
+    ap.add_argument("--profile-grid", default="",
+                    help="with --profile: interior points as N0,N1,N2 instead of the workload's (a smaller grid of "
+                         "the same kernel)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-diagnostics", action="store_true")
@@ -849,13 +857,95 @@ def run_served(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def run_part(args, world, rank, local):
+    """--workload part: the head-on grid cut into partitions (the chare decomposition of Sec. 3: per substage
+    each partition's points, then inner-boundary messages and face-by-face halos) against the whole grid,
+    the same steps on the same GPU; CUDA-event times; final states compared by digest."""
+    import torch
+
+    from paper_2505_00097_gb300 import binding as B
+
+    torch.cuda.set_device(local)
+    spec = W.config_headon()
+    parts = tuple(int(v) for v in args.parts.split(","))
+    n = args.steps
+    warm = max(3, args.warmup)
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    g = B.Grid(spec, device=local)
+    g.set_brill_lindquist(spec["masses"], spec["positions"])
+    pg = B.PartGrid(spec, parts, device=local)
+    pg.set_brill_lindquist(spec["masses"], spec["positions"])
+    dt = g.dt_cfl
+    g.rk4_step(dt, warm)
+    pg.rk4_step(dt, warm)
+    torch.cuda.synchronize()
+    a0, a1 = ev(), ev()
+    a0.record()
+    g.rk4_step(dt, n)
+    a1.record()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(gpu_uuid(local))
+    clocks.start()
+    b0, b1 = ev(), ev()
+    b0.record()
+    pg.rk4_step(dt, n)
+    b1.record()
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    t_whole, t_part = a0.elapsed_time(a1) * 1e-3, b0.elapsed_time(b1) * 1e-3
+    same = pg.digest() == g.digest()
+    pts = g.interior
+    line = {
+        "metric": METRIC, "value": pts * 4 * n / t_part, "unit": UNIT, "n_gpus": 1, "steps": n, "warmup": warm,
+        "ms_per_step": 1e3 * t_part / n, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic (Brill-Lindquist closed form on the GPU)",
+        "config": {"workload": f"headon_sinhcyl_256x2x512_in_{parts[0]}x{parts[1]}x{parts[2]}_partitions",
+                   "parts": list(parts), "messages_per_substage": pg.messages},
+        "whole_grid": {"value": pts * 4 * n / t_whole, "ms_per_step": 1e3 * t_whole / n},
+        "exchange_overhead": t_part / t_whole - 1.0, "bitwise_equal_to_whole_grid": same, "clocks": ck,
+        "note": "all partitions on one GPU: every message is a device-local copy",
+    }
+    print(json.dumps(line), flush=True)
+    pg.close()
+    g.close()
+
+
 def other_name(policy: str) -> str:
     return "fifo" if policy == "srpt" else "srpt"
+
+
+def run_profile(args):
+    """--profile: the launches a profiler capture looks at, on cuda:0, nothing timed."""
+    import torch
+
+    from paper_2505_00097_gb300 import binding as B
+
+    spec = workload(args.workload)
+    if args.profile_grid:
+        spec["N"] = tuple(int(v) for v in args.profile_grid.split(","))
+    g = B.Grid(spec)
+    g.set_brill_lindquist(spec["masses"], spec["positions"], spec["perturb_amp"], spec["seed"])
+    if args.profile == "rhs":
+        y = torch.empty(24 * g.T, dtype=torch.float64, device="cuda")
+        o = torch.empty_like(y)
+        g.get_state(y, False)
+        g.rhs(y, o)
+    else:
+        g.rk4_step(g.dt_cfl, 4)
+        g.hamiltonian(None, torch.empty(g.T, dtype=torch.float64, device="cuda"), norms=False)
+        g.momentum(None, torch.empty(3 * g.T, dtype=torch.float64, device="cuda"), norms=False)
+        g.psi4(torch.empty(2 * g.T, dtype=torch.float64, device="cuda"))
+    torch.cuda.synchronize()
+    print(f"profile {args.profile}: {spec['name']} interior {g.interior}", flush=True)
+    g.close()
 
 
 def main():
     args = parse()
     world, rank, local = dist_env()
+    if args.profile:
+        run_profile(args)
+        return
     if args.workload == "batch":
         if args.steps == 2000:
             args.steps = 100
@@ -864,6 +954,12 @@ def main():
     if args.workload == "served":
         if rank == 0:
             run_served(args, world, rank, local)
+        return
+    if args.workload == "part":
+        if args.steps == 2000:
+            args.steps = 200
+        if rank == 0:
+            run_part(args, world, rank, local)
         return
     spec = workload(args.workload)
     if args.impl == "reference":

@@ -285,6 +285,11 @@ struct nr_part {
     int parts[3] = {1, 1, 1};
     int device = 0;
     cudaStream_t stream = nullptr, cap = nullptr;
+    // per-partition streams and events: inside the captured step each partition's kernels form their
+    // own branch of the graph, so the partitions' launches overlap on the GPU
+    std::vector<cudaStream_t> pstream;
+    std::vector<cudaEvent_t> pevent;
+    cudaEvent_t fork = nullptr;
     std::vector<PartDev> p;
     std::vector<DevMsg> msg[4];
     double* finf = nullptr;
@@ -354,6 +359,11 @@ void free_part(nr_part* s)
     for (void* q : ptrs)
         if (q) cudaFree(q);
     if (s->cap) cudaStreamDestroy(s->cap);
+    for (cudaStream_t q : s->pstream)
+        if (q) cudaStreamDestroy(q);
+    for (cudaEvent_t e : s->pevent)
+        if (e) cudaEventDestroy(e);
+    if (s->fork) cudaEventDestroy(s->fork);
     cudaSetDevice(prev);
     delete s;
 }
@@ -375,16 +385,27 @@ double* buf_of(PartDev& d, int which) { return which == 0 ? d.y : which == 1 ? d
 // the parity copies within partitions, then the messages phase by phase
 int enqueue_stage(nr_part* s, cudaStream_t st, int in, int out, const Stage& sg, bool yn_is_y, bool use_acc)
 {
-    for (PartDev& d : s->p) {
+    // every partition's points (and its own parity copies) on its own stream, forked from and joined
+    // back into st; with one partition, on st itself
+    const bool forked = s->p.size() > 1 && st == s->cap;
+    if (forked) PCUDA(cudaEventRecord(s->fork, st));
+    for (size_t q = 0; q < s->p.size(); q++) {
+        PartDev& d = s->p[q];
+        cudaStream_t ps = forked ? s->pstream[q] : st;
+        if (forked) PCUDA(cudaStreamWaitEvent(ps, s->fork, 0));
         OuterArgs oa;
         oa.pts = d.outer;
         oa.npts = d.n_outer;
         oa.finf = s->finf;
         oa.wspeed = s->wspeed;
         PCUDA(launch_rhs(d.K, buf_of(d, in), d.d1x, d.d1y, buf_of(d, out), yn_is_y ? d.y : nullptr,
-                         use_acc ? d.acc : nullptr, sg, st, oa));
+                         use_acc ? d.acc : nullptr, sg, ps, oa));
+        PCUDA(launch_inner(d.K, d.inner, d.n_inner, buf_of(d, out), ps));
+        if (forked) {
+            PCUDA(cudaEventRecord(s->pevent[q], ps));
+            PCUDA(cudaStreamWaitEvent(st, s->pevent[q], 0));
+        }
     }
-    for (PartDev& d : s->p) PCUDA(launch_inner(d.K, d.inner, d.n_inner, buf_of(d, out), st));
     for (int ph = 0; ph < 4; ph++) {
         for (DevMsg& m : s->msg[ph]) {
             PartDev& a = s->p[m.src];
@@ -549,9 +570,16 @@ static int nr_part_create_body(int coords, const int Nxx[3], const nr_params* pa
                 }
             }
         cudaError_t e = cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming);
+        s->pstream.assign(s->p.size(), nullptr);
+        s->pevent.assign(s->p.size(), nullptr);
+        for (size_t q = 0; q < s->p.size() && e == cudaSuccess; q++) {
+            e = cudaStreamCreateWithFlags(&s->pstream[q], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->pevent[q], cudaEventDisableTiming);
+        }
         if (e != cudaSuccess) {
             free_part(s);
-            return nrk_fail(NR_ECUDA, "partition stream: %s", cudaGetErrorString(e));
+            return nrk_fail(NR_ECUDA, "partition streams: %s", cudaGetErrorString(e));
         }
         *out = s;
         return NR_OK;
