@@ -40,7 +40,7 @@ def _worker(rank, world, port, out):
 def test_two_rank_aggregation_gloo():
     world = 2
     port = _free_port()
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()
     out = mgr.dict()
     mp.spawn(_worker, args=(world, port, out), nprocs=world, join=True)
     assert out[0][0] == out[1][0] == 20.0          # max over ranks

@@ -89,7 +89,7 @@ def _worker(rank, world, port, case, out):
 def test_plan_exchange_between_two_gloo_ranks(case):
     world = 2
     port = _free_port()
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()
     out = mgr.dict()
     mp.spawn(_worker, args=(world, port, case, out), nprocs=world, join=True)
     assert out[0][0] and out[1][0]
