@@ -59,11 +59,16 @@ UNIT = "point-updates/s"
 # Head-on with the 8th-order scheme: k_rhs 322 + 416 + 2 x 1522 = 3782, k_d1 122.9.  Large 3D
 # (spherical, general; counted on a 96x48x96 grid of the same kernel): k_rhs 320 + 453 + 2 x 1670 =
 # 4113, k_d1 89.8 (4 FLOP per stored difference, 22.46 differences per point at 384x192x384).
+# Large 3D with the production scheme (the general 8th-order kernel, counted on 96x48x96): k_rhs
+# 485 + 544 + 2 x 2209 = 5447, k_d1 252.2 (11 FLOP per stored difference, 22.93 per point).
 # A workload without a capture reports no FLOP rate.
-F_ALG = {"headon": 2950.3, "large3d": 4202.8, "headon8": 3904.9}
-# DRAM bytes (read + write) of the same two launches in that capture, or None
+F_ALG = {"headon": 2950.3, "large3d": 4202.8, "headon8": 3904.9, "large3d8": 5699.2}
+# DRAM bytes (read + write) of the same two launches in that capture; for the large 3D grids the
+# capture's bytes per interior point at 96x48x96 (3337.1 and 5282.0, mostly register-spill lines)
+# times the 28,311,552 points of the full grid
 TRAFFIC = {"headon": 24016640 + 78848 + 92996096 + 452287232,
-           "headon8": 24951296 + 112128 + 90265088 + 329912576}
+           "headon8": 24951296 + 112128 + 90265088 + 329912576,
+           "large3d": round(3337.1 * 28311552), "large3d8": round(5282.0 * 28311552)}
 # FLOPs of the same right-hand side in the point code's source (a host census of the code those counts
 # were taken from: FMA = 2, one division; without the k_d1 pre-pass); a test recomputes it, so that a
 # change of the kernels' arithmetic cannot leave F_ALG behind unnoticed

@@ -37,9 +37,10 @@ FAMILY = {
     "headon": lambda N: W.sinh_cylindrical(N),
     "headon8": lambda N: dict(W.sinh_cylindrical(N), NG=5, ko_sigma=KO8),
     "large3d": lambda N: W.sinh_spherical(N),
+    "large3d8": lambda N: dict(W.sinh_spherical(N), NG=5, ko_sigma=KO8),
 }
 SMALL = {"headon": [(16, 2, 32), (24, 2, 40)], "headon8": [(16, 2, 32), (20, 2, 36)],
-         "large3d": [(12, 10, 8), (16, 12, 10)]}
+         "large3d": [(12, 10, 8), (16, 12, 10)], "large3d8": [(12, 10, 10), (16, 12, 10)]}
 
 
 def _compile(src, name, tmp, extra=()):
