@@ -64,11 +64,11 @@ UNIT = "point-updates/s"
 # A workload without a capture reports no FLOP rate.
 F_ALG = {"headon": 2950.3, "large3d": 4202.8, "headon8": 3904.9, "large3d8": 5699.2}
 # DRAM bytes (read + write) of the same two launches in that capture; for the large 3D grids the
-# capture's bytes per interior point at 96x48x96 (3337.1 and 5282.0, mostly register-spill lines)
+# capture's bytes per interior point at 96x48x96 (3340.6 and 5278.2, mostly register-spill lines)
 # times the 28,311,552 points of the full grid
-TRAFFIC = {"headon": 24016640 + 78848 + 92996096 + 452287232,
-           "headon8": 24951296 + 112128 + 90265088 + 329912576,
-           "large3d": round(3337.1 * 28311552), "large3d8": round(5282.0 * 28311552)}
+TRAFFIC = {"headon": 24017152 + 82688 + 93285120 + 452685824,
+           "headon8": 24949504 + 112128 + 90166272 + 329468672,
+           "large3d": round(3340.6 * 28311552), "large3d8": round(5278.2 * 28311552)}
 # FLOPs of the same right-hand side in the point code's source (a host census of the code those counts
 # were taken from: FMA = 2, one division; without the k_d1 pre-pass); a test recomputes it, so that a
 # change of the kernels' arithmetic cannot leave F_ALG behind unnoticed

@@ -36,6 +36,8 @@ CASES = [
      (0.6, 0.4), ((0.2, 0, 0.4), (0, 0, -0.6)), 1e-10, "rk4", 60),
     ("cyl-order8-ssprk3", dict(W.sinh_cylindrical((40, 2, 64), rho_max=20.0, z_max=20.0), NG=5, ko_sigma=KO8, cfl=0.35),
      (2, 1, 3), (0.5, 0.5), ((0, 0, 0.5), (0, 0, -0.5)), 0.0, "ssprk3", 60),
+    ("sph-general-order8", dict(W.sinh_spherical((20, 12, 10)), NG=5, ko_sigma=KO8, cfl=0.35), (2, 2, 2),
+     (1.0,), ((0.0, 0.0, 0.0),), 1e-10, "ssprk3", 30),
 ]
 
 
