@@ -446,6 +446,11 @@ int nr_server_fetch_digest(nr_server* server, int64_t id, uint64_t* digest);
  *     must hold the inner ghosts' parity copies, as every state of the method.
  *   nr_part_digest: nr_state_digest of the whole grid's state, summed over the
  *     partitions (the same value as for the unsplit grid); synchronises.
+ *   nr_part_hamiltonian: the L2 and Linf norms of the Hamiltonian constraint over
+ *     the interior points in the radius band [h_rmin, h_rmax], as nr_hamiltonian:
+ *     each partition's points into block partials, one fixed-order reduction over
+ *     all of them (the norms agree with the whole grid's to rounding; the summation
+ *     order differs); either output may be NULL, not both; synchronises.
  *   nr_part_query: partitions, messages per phase (0: inner boundary across
  *     partitions; 1..3: halos along axes 0..2), CFL step, device bytes.
  *   nr_part_plan_info / nr_part_plan_boxes / nr_part_plan_records (host only, no
@@ -472,6 +477,7 @@ int nr_part_get_state(nr_part* part, double* dst, int to_host);
 int nr_part_rk4_step(nr_part* part, double dt, int nsteps);
 int nr_part_ssprk3_step(nr_part* part, double dt, int nsteps);
 int nr_part_digest(nr_part* part, uint64_t* out);
+int nr_part_hamiltonian(nr_part* part, double* l2_out, double* linf_out);
 int nr_part_sync(nr_part* part);
 int nr_part_plan_info(int coords, const int Nxx[3], int NG, const int parts[3], int64_t* nparts, int64_t records[4]);
 int nr_part_plan_boxes(int coords, const int Nxx[3], int NG, const int parts[3], int32_t* boxes);

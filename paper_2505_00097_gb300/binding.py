@@ -35,7 +35,7 @@ EXPORTS = (
     "nr_server_fetch_digest", "nr_server_set_starvation_cap", "nr_server_stats",
     "nr_server_set_prefetch", "nr_state_digest",
     "nr_part_create", "nr_part_destroy", "nr_part_query", "nr_part_set_brill_lindquist", "nr_part_set_state",
-    "nr_part_get_state", "nr_part_rk4_step", "nr_part_ssprk3_step", "nr_part_digest", "nr_part_sync",
+    "nr_part_get_state", "nr_part_rk4_step", "nr_part_ssprk3_step", "nr_part_digest", "nr_part_hamiltonian", "nr_part_sync",
     "nr_part_plan_info", "nr_part_plan_boxes", "nr_part_plan_records", "nr_last_error",
 )
 
@@ -164,6 +164,7 @@ def lib() -> ctypes.CDLL:
     L.nr_part_rk4_step.argtypes = [vp, ctypes.c_double, ctypes.c_int]
     L.nr_part_ssprk3_step.argtypes = [vp, ctypes.c_double, ctypes.c_int]
     L.nr_part_digest.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
+    L.nr_part_hamiltonian.argtypes = [vp, dp, dp]
     L.nr_part_sync.argtypes = [vp]
     L.nr_part_plan_info.argtypes = [ctypes.c_int, ip, ctypes.c_int, ip, i64p, i64p]
     L.nr_part_plan_boxes.argtypes = [ctypes.c_int, ip, ctypes.c_int, ip, i32p]
@@ -584,6 +585,12 @@ class PartGrid:
         out = ctypes.c_uint64()
         _check(lib().nr_part_digest(self.h, ctypes.byref(out)))
         return out.value
+
+    def hamiltonian(self):
+        """(l2, linf) of the Hamiltonian constraint over the radius band of the spec"""
+        l2, linf = ctypes.c_double(), ctypes.c_double()
+        _check(lib().nr_part_hamiltonian(self.h, ctypes.byref(l2), ctypes.byref(linf)))
+        return l2.value, linf.value
 
     def sync(self) -> None:
         _check(lib().nr_part_sync(self.h))

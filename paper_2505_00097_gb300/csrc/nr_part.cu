@@ -296,6 +296,11 @@ struct nr_part {
     double* wspeed = nullptr;
     double* mxyz = nullptr;
     double* whole = nullptr;   // staging of a whole-grid state (nr_part_set_state / get_state), on first use
+    // constraint norms: every partition's block partials side by side, one fixed-order reduction
+    double* partials = nullptr;
+    std::vector<int> part_off;   // first partial of each partition
+    int nparts_total = 0;
+    double* hres = nullptr;
     unsigned long long* digest = nullptr;
     std::vector<double> cart_canon;
     cudaGraphExec_t exec = nullptr;
@@ -355,7 +360,7 @@ void free_part(nr_part* s)
             for (void* q : ptrs)
                 if (q) cudaFree(q);
         }
-    void* ptrs[] = {s->finf, s->wspeed, s->mxyz, s->whole, s->digest};
+    void* ptrs[] = {s->finf, s->wspeed, s->mxyz, s->whole, s->digest, s->partials, s->hres};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     if (s->cap) cudaStreamDestroy(s->cap);
@@ -554,6 +559,15 @@ static int nr_part_create_body(int coords, const int Nxx[3], const nr_params* pa
                 return nrk_fail(NR_ECUDA, "partition set-up: %s", cudaGetErrorString(e));
             }
         }
+        s->part_off.assign(s->p.size(), 0);
+        for (size_t q = 0; q < s->p.size(); q++) {
+            s->part_off[q] = s->nparts_total;
+            s->nparts_total += ham_partials_needed(s->p[q].K);
+        }
+        if ((rc = pmalloc(s, &s->partials, 3 * (size_t)s->nparts_total)) || (rc = pmalloc(s, &s->hres, 3))) {
+            free_part(s);
+            return rc;
+        }
         for (int ph = 0; ph < 4; ph++)
             for (const PartMsg& m : plan.msg[ph]) {
                 s->msg[ph].emplace_back();
@@ -711,6 +725,31 @@ int nr_part_digest(nr_part* s, uint64_t* out)
     }
     *out = (uint64_t)total;
     return NR_OK;
+}
+
+static int nr_part_hamiltonian_body(nr_part* s, double* l2_out, double* linf_out)
+{
+    if (!s || (!l2_out && !linf_out)) return nrk_fail(NR_EINVAL, "bad nr_part_hamiltonian arguments");
+    DevGuardP dg(s->device);
+    // each partition's interior points into its slice of the partials (the per-partition reduction
+    // it also runs writes a scratch result nobody reads), then one reduction over all of them
+    for (size_t q = 0; q < s->p.size(); q++) {
+        PartDev& d = s->p[q];
+        PCUDA(launch_ham(d.K, d.y, nullptr, s->P.h_rmin, s->P.h_rmax, s->partials + 3 * (size_t)s->part_off[q],
+                         ham_partials_needed(d.K), s->hres, s->stream));
+    }
+    PCUDA(launch_ham_reduce(s->partials, s->nparts_total, s->hres, s->stream));
+    double r[3];
+    PCUDA(cudaMemcpyAsync(r, s->hres, sizeof r, cudaMemcpyDeviceToHost, s->stream));
+    PCUDA(cudaStreamSynchronize(s->stream));
+    if (l2_out) *l2_out = r[0];
+    if (linf_out) *linf_out = r[1];
+    return NR_OK;
+}
+
+int nr_part_hamiltonian(nr_part* s, double* l2_out, double* linf_out)
+{
+    return nrk_guard("nr_part_hamiltonian", [&] { return nr_part_hamiltonian_body(s, l2_out, linf_out); });
 }
 
 int nr_part_sync(nr_part* s)

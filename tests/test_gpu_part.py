@@ -62,6 +62,10 @@ def test_partitioned_evolution_is_bitwise_the_whole_grid(name, spec, parts, mass
     assert np.all(np.isfinite(a))
     assert np.array_equal(a, b), f"{name}: partitioned state differs after {steps} steps"
     assert pg.digest() == g.digest()
+    # the constraint norms from the partitions' points: the whole grid's up to summation order
+    l2, linf = pg.hamiltonian()
+    l2g, linfg = g.hamiltonian()
+    assert linf == linfg and l2 == pytest.approx(l2g, rel=1e-13)
     pg.close()
     g.close()
 
