@@ -87,6 +87,9 @@ F_METHOD = {"headon": 28967, "headon8": 49631, "large3d": 28970, "large3d8": 496
 # (head-on: k_ham 366 / 238 / 640 DADD / DMUL / DFMA, k_mom 119 / 162 / 269, k_psi4 505 / 483 /
 # 1085; the reductions and ghost copies add < 0.1); absent: not captured
 DIAG_FLOPS = {"headon": {"hamiltonian": 1884.0, "momentum": 819.0, "psi4": 3158.0}}
+# the source census of the constraints' point code those counts were taken with (FMA = 2, one division,
+# the square root of |M| not counted: its expansion is most of the 29 FLOP the momentum count adds)
+DIAG_CENSUS = {"headon": {"hamiltonian": 1883, "momentum": 790}}
 # psi4 modes on the workload's extraction sphere: l <= 8, Gauss-Legendre x uniform nodes
 PSI4_LMAX, PSI4_NTHETA, PSI4_NPHI = 8, 24, 48
 # FP64 pipe of one SM: 2 DFMA per clock (ncu peak_sustained of

@@ -172,7 +172,85 @@ void census(const int* N, const double* ampl, const double* sinhw, double sigma_
     for (int q = 0; q < 12; q++) out[q] = v[q];
 }
 
+// counts of the constraints at every interior point, as k_ham and k_mom run them (inline differences):
+// out[0..3] add, mul, fma, div of ham_core; out[4..7] of mom_core; out[8] sqrt of mom_core; out[9] points
+template <int FAM, int ORD>
+void census_constraints(const int* N, const double* ampl, const double* sinhw, const double* y, long long* out)
+{
+    constexpr int NG = ORD / 2 + 1;
+    const bool cyl = FAM == FAM_CYL;
+    int n[3];
+    long T = 1;
+    double lo[3], hi[3], dx[3];
+    if (cyl) { lo[0] = 0; hi[0] = 1; lo[1] = -M_PI; hi[1] = M_PI; lo[2] = -1; hi[2] = 1; }
+    else { lo[0] = 0; hi[0] = 1; lo[1] = 0; hi[1] = M_PI; lo[2] = -M_PI; hi[2] = M_PI; }
+    for (int d = 0; d < 3; d++) { n[d] = N[d] + 2 * NG; T *= n[d]; dx[d] = (hi[d] - lo[d]) / N[d]; }
+    auto xx = [&](int d, int i) { return lo[d] + ((double)(i - NG) + 0.5) * dx[d]; };
+    const CK* Y = reinterpret_cast<const CK*>(y);
+    double i1d[3], i2d[3];
+    for (int d = 0; d < 3; d++) { i1d[d] = 1.0 / (FD<ORD>::den1.v * dx[d]); i2d[d] = 1.0 / (FD<ORD>::den2.v * dx[d] * dx[d]); }
+    Ops ham{}, mom{};
+    long nint = 0;
+    for (int i2 = NG; i2 < NG + N[2]; i2++)
+        for (int i1 = NG; i1 < NG + N[1]; i1++)
+            for (int i0 = NG; i0 < NG + N[0]; i0++) {
+                const long idx = i0 + (long)n[0] * (i1 + (long)n[1] * i2);
+                PointIn P;
+                P.y = Y + idx; P.T = T;
+                P.st[0] = 1; P.st[1] = n[0]; P.st[2] = (long)n[0] * n[1];
+                P.ox = 0;
+                P.dx = nullptr;
+                P.dy = nullptr;
+                Geo& g = P.g;
+                double f0[4];
+                radial(ampl[0], sinhw[0], true, xx(0, i0), f0);
+                const double s0 = 1.0 / f0[1], a = 1.0 / f0[0];
+                g.a = a;
+                g.d00 = f0[2] / (f0[1] * f0[1]);
+                double s2;
+                if (!cyl) {
+                    const double th = xx(1, i1), isn = 1.0 / std::sin(th), cot = std::cos(th) / std::sin(th);
+                    s2 = a * isn;
+                    g.b = a; g.c = a * cot; g.d22 = 0.0;
+                    g.e0a = -a * a; g.e0b = -a * a; g.e0c = -a * (a * cot); g.e1c = -s2 * s2;
+                } else {
+                    double fz[4];
+                    radial(ampl[2], sinhw[2], true, xx(2, i2), fz);
+                    s2 = 1.0 / fz[1];
+                    g.d22 = fz[2] / (fz[1] * fz[1]);
+                    g.b = 0.0; g.c = 0.0;
+                    g.e0a = -a * a; g.e0b = 0.0; g.e0c = 0.0; g.e1c = 0.0;
+                }
+                const double D0 = s0 * i1d[0], D1 = a * i1d[1], D2 = s2 * i1d[2];
+                g.D[0] = D0; g.D[1] = D1; g.D[2] = D2;
+                g.D2[0] = s0 * s0 * i2d[0]; g.D2[1] = a * a * i2d[1]; g.D2[2] = s2 * s2 * i2d[2];
+                g.DD[0] = D0 * D1; g.DD[1] = D0 * D2; g.DD[2] = D1 * D2;
+                g_ops = Ops{};
+                (void)ham_core<FAM, ORD>(P);
+                ham.add += g_ops.add; ham.mul += g_ops.mul; ham.fma += g_ops.fma; ham.div += g_ops.div;
+                g_ops = Ops{};
+                CK Mv[3];
+                (void)mom_core<FAM, ORD>(P, Mv);
+                mom.add += g_ops.add; mom.mul += g_ops.mul; mom.fma += g_ops.fma; mom.div += g_ops.div;
+                mom.sqrt_ += g_ops.sqrt_;
+                nint++;
+            }
+    const long long v[10] = {ham.add, ham.mul, ham.fma, ham.div, mom.add, mom.mul, mom.fma, mom.div, mom.sqrt_, nint};
+    for (int q = 0; q < 10; q++) out[q] = v[q];
+}
+
 }  // namespace
+
+// the Hamiltonian and momentum constraints' census (census_constraints), 4th or 8th order
+extern "C" int census_diag(int coords, const int* N, const double* ampl, const double* sinhw, int ng, const double* y,
+                           long long* out)
+{
+    const bool cyl = coords == 1;
+    if (ng == 3) { if (cyl) census_constraints<FAM_CYL, 4>(N, ampl, sinhw, y, out); else census_constraints<FAM_SPH, 4>(N, ampl, sinhw, y, out); }
+    else if (ng == 5) { if (cyl) census_constraints<FAM_CYL, 8>(N, ampl, sinhw, y, out); else census_constraints<FAM_SPH, 8>(N, ampl, sinhw, y, out); }
+    else return 1;
+    return 0;
+}
 
 // coords 0/2 spherical-like, 1 cylindrical-like (sinh maps on the radial and z axes); ng 3 or 5;
 // the two-point specialisation where the azimuth holds two points, as the library selects it

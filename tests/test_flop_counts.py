@@ -68,6 +68,8 @@ def kcount(tmp_path_factory):
     dp = ctypes.POINTER(ctypes.c_double)
     L.census_rhs.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int), dp, dp, ctypes.c_double, ctypes.c_double,
                              ctypes.c_double, ctypes.c_int, dp, dp, ctypes.POINTER(ctypes.c_longlong)]
+    L.census_diag.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int), dp, dp, ctypes.c_int, dp,
+                              ctypes.POINTER(ctypes.c_longlong)]
     return L
 
 
@@ -153,3 +155,25 @@ def test_kernel_census_matches_the_benchmark_constants(kcount, wl):
     # FLOP peak a fully busy FP64 pipe reaches (a DADD or DMUL is one FLOP in an FMA's slot)
     instr = (add + mul + fma) / nint + (d_add + d_mul + d_fma) / (diffs * nint) * _stored_differences_per_point(spec)
     assert abs(bench.MIX_CEILING[wl] - total / (2 * instr)) < 5e-4
+
+
+def test_constraint_census_matches_the_benchmark_constants(kcount):
+    """The Hamiltonian and momentum constraints' point code: its census equals bench.DIAG_CENSUS, and the
+    compiled kernels' counts in bench.DIAG_FLOPS are within 0.5 % (Hamiltonian) and 5 % (momentum: the
+    square root's expansion) of it."""
+    spec = W.sinh_cylindrical((16, 2, 32))
+    o = Oracle(spec)
+    y = W.random_state(o.n, seed=5, smooth=True)
+    o.inner_bc(y)
+    out = (ctypes.c_longlong * 10)()
+    dp = ctypes.POINTER(ctypes.c_double)
+    assert kcount.census_diag(spec["coords"], (ctypes.c_int * 3)(*spec["N"]), (ctypes.c_double * 3)(*spec["ampl"]),
+                              (ctypes.c_double * 3)(*spec["sinhw"]), 3, y.ctypes.data_as(dp), out) == 0
+    v = list(out)
+    n = v[9]
+    ham = (v[0] + v[1] + 2 * v[2] + v[3]) / n
+    mom = (v[4] + v[5] + 2 * v[6] + v[7]) / n
+    assert v[3] == n and v[7] == n and v[8] == n      # one division each, one square root for |M|
+    assert ham == bench.DIAG_CENSUS["headon"]["hamiltonian"] and mom == bench.DIAG_CENSUS["headon"]["momentum"]
+    assert abs(bench.DIAG_FLOPS["headon"]["hamiltonian"] / ham - 1.0) <= 0.005
+    assert abs(bench.DIAG_FLOPS["headon"]["momentum"] / mom - 1.0) <= 0.05
