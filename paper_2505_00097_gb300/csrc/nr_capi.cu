@@ -676,6 +676,7 @@ int nrk::grid_from_setup(HostSetup& H, const nr_params& P, nr_grid** out)
         if (e == cudaSuccess) e = cudaMemset(g->y, 0, sizeof(double) * set);
         if (e == cudaSuccess) e = cudaMemset(g->acc, 0, sizeof(double) * set);
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = rhs_kernels_init();   // before any step is captured
         if (e != cudaSuccess) {
             free_grid(g);
             return fail(NR_ECUDA, "grid upload: %s", cudaGetErrorString(e));

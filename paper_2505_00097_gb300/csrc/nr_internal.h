@@ -89,6 +89,10 @@ struct OuterArgs {
 // grids only), then k_rhs
 cudaError_t launch_rhs(const GridK& G, const double* yin, double* d1x, double* d1y, double* out, const double* yn,
                        double* acc, Stage st, cudaStream_t s, OuterArgs oa = OuterArgs());
+// k_rhs runs as many blocks as fit on the device at once, each striding over the tiles; this fills
+// that count for every k_rhs instantiation on the current device (idempotent, not capture-safe: grid
+// creation calls it; until then a launch outside a capture does)
+cudaError_t rhs_kernels_init();
 cudaError_t launch_outer(const GridK& G, const OuterPt* pts, int npts, const double* yin, double* out,
                          const double* yn, double* acc, const double* finf, const double* wspeed, Stage st,
                          cudaStream_t s);

@@ -19,6 +19,8 @@
 #include <math.h>
 
 #include <algorithm>
+#include <atomic>
+#include <mutex>
 
 #include "bssn_point.cuh"
 #include "nr_geo.cuh"
@@ -46,19 +48,76 @@ __global__ void __launch_bounds__(RHS_BX* RHS_BY) k_rhs(GridK G, const double* _
                                                         double* out, const double* yn, double* acc, Stage st,
                                                         OuterArgs oa)
 {
-    // the first oa.nblocks blocks take the pure-outer points, 128 per block
-    if ((int)blockIdx.x < oa.nblocks) {
-        const int t = (int)blockIdx.x * (RHS_BX * RHS_BY) + threadIdx.y * RHS_BX + threadIdx.x;
-        if (t < oa.npts) outer_point_stage<FAM, ORD>(G, oa.pts[t], yin, out, yn, acc, oa.finf, oa.wspeed, st);
-        return;
-    }
-    // the others tile (i0, j = i1 + N1 i2) in 32 x 4 points, flattened into the block index
-    const int b = (int)blockIdx.x - oa.nblocks;
+    // tiles: the first oa.nblocks take the pure-outer points, 128 each; the others tile
+    // (i0, j = i1 + N1 i2) in 32 x 4 points.  Each block strides over the tiles (a grid of the
+    // resident blocks, or one block per tile)
     const int nbx = (G.N0 + RHS_BX - 1) / RHS_BX;
-    const int i = (b % nbx) * RHS_BX + threadIdx.x;
-    const int j = (b / nbx) * RHS_BY + threadIdx.y;
-    if (i >= G.N0 || j >= G.N1 * G.N2) return;
-    rhs_point_stage<FAM, AX, true, ORD>(G, yin, d1x, d1y, out, yn, acc, st, i, j);
+    const int ntiles = oa.nblocks + nbx * ((G.N1 * G.N2 + RHS_BY - 1) / RHS_BY);
+#pragma unroll 1
+    for (int tb = (int)blockIdx.x; tb < ntiles; tb += (int)gridDim.x) {
+        if (tb < oa.nblocks) {
+            const int t = tb * (RHS_BX * RHS_BY) + threadIdx.y * RHS_BX + threadIdx.x;
+            if (t < oa.npts) outer_point_stage<FAM, ORD>(G, oa.pts[t], yin, out, yn, acc, oa.finf, oa.wspeed, st);
+            continue;
+        }
+        const int b = tb - oa.nblocks;
+        const int i = (b % nbx) * RHS_BX + threadIdx.x;
+        const int j = (b / nbx) * RHS_BY + threadIdx.y;
+        if (i < G.N0 && j < G.N1 * G.N2) rhs_point_stage<FAM, AX, true, ORD>(G, yin, d1x, d1y, out, yn, acc, st, i, j);
+    }
+}
+
+// k_rhs blocks resident on the whole device, per instantiation (family x azimuth axis x order), by
+// device; 0: not yet known (a launch then runs one block per tile).  Filled by rhs_kernels_init.
+constexpr int RHS_MAX_DEV = 64;
+constexpr int RHS_VARIANTS = 8;
+std::atomic<int> g_rhs_resident[RHS_MAX_DEV][RHS_VARIANTS];
+std::mutex g_rhs_mu;
+
+template <int FAM, int AX, int ORD>
+constexpr int rhs_variant()
+{
+    return (FAM == FAM_SPH ? 0 : 4) + (AX < 0 ? 0 : 2) + (ORD == 8 ? 1 : 0);
+}
+
+template <int FAM, int AX, int ORD>
+cudaError_t rhs_init_one(int dev, int nsm)
+{
+    const void* f = (const void*)k_rhs<FAM, AX, ORD>;
+    // no shared memory: the whole unified L1 / shared array as L1, for the register spills
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+    int occ = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rhs<FAM, AX, ORD>, RHS_BX * RHS_BY, 0);
+    if (e != cudaSuccess) return e;
+    g_rhs_resident[dev][rhs_variant<FAM, AX, ORD>()].store(occ * nsm);
+    return cudaSuccess;
+}
+
+template <int FAM, int AX, int ORD>
+int rhs_resident()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= RHS_MAX_DEV) return 0;
+    return g_rhs_resident[dev][rhs_variant<FAM, AX, ORD>()].load();
+}
+
+template <int FAM, int AX, int ORD>
+cudaError_t launch_k_rhs(long nb, cudaStream_t s, const GridK& G, const double* yin, double* d1x, double* d1y,
+                         double* out, const double* yn, double* acc, const Stage& st, const OuterArgs& oa)
+{
+    int res = rhs_resident<FAM, AX, ORD>();
+    if (res == 0) {
+        // first launch on this device outside a stream capture: fill the table now
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
+            const cudaError_t e = rhs_kernels_init();
+            if (e != cudaSuccess) return e;
+            res = rhs_resident<FAM, AX, ORD>();
+        }
+    }
+    const dim3 grd((unsigned)(res > 0 && res < nb ? res : nb));
+    k_rhs<FAM, AX, ORD><<<grd, dim3(RHS_BX, RHS_BY), 0, s>>>(G, yin, d1x, d1y, out, yn, acc, st, oa);
+    return cudaGetLastError();
 }
 
 template <int FAM, int ORD>
@@ -317,18 +376,34 @@ cudaError_t launch_rhs_ord(const GridK& G, const double* yin, double* d1x, doubl
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    dim3 blk(RHS_BX, RHS_BY);
     oa.nblocks = (oa.npts + RHS_BX * RHS_BY - 1) / (RHS_BX * RHS_BY);
     const long nb = (long)((G.N0 + RHS_BX - 1) / RHS_BX) * ((G.N1 * G.N2 + RHS_BY - 1) / RHS_BY) + oa.nblocks;
-    dim3 grd((unsigned)nb);
     if (G.fam == FAM_SPH) {
-        if (G.ax == 2) k_rhs<FAM_SPH, 2, ORD><<<grd, blk, 0, s>>>(G, yin, d1x, d1y, out, yn, acc, st, oa);
-        else k_rhs<FAM_SPH, -1, ORD><<<grd, blk, 0, s>>>(G, yin, d1x, d1y, out, yn, acc, st, oa);
-    } else {
-        if (G.ax == 1) k_rhs<FAM_CYL, 1, ORD><<<grd, blk, 0, s>>>(G, yin, d1x, d1y, out, yn, acc, st, oa);
-        else k_rhs<FAM_CYL, -1, ORD><<<grd, blk, 0, s>>>(G, yin, d1x, d1y, out, yn, acc, st, oa);
+        if (G.ax == 2) return launch_k_rhs<FAM_SPH, 2, ORD>(nb, s, G, yin, d1x, d1y, out, yn, acc, st, oa);
+        return launch_k_rhs<FAM_SPH, -1, ORD>(nb, s, G, yin, d1x, d1y, out, yn, acc, st, oa);
     }
-    return cudaGetLastError();
+    if (G.ax == 1) return launch_k_rhs<FAM_CYL, 1, ORD>(nb, s, G, yin, d1x, d1y, out, yn, acc, st, oa);
+    return launch_k_rhs<FAM_CYL, -1, ORD>(nb, s, G, yin, d1x, d1y, out, yn, acc, st, oa);
+}
+
+// the resident-block table of every k_rhs instantiation on the current device (idempotent; not
+// during a stream capture)
+cudaError_t rhs_kernels_init()
+{
+    int dev = 0, nsm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= RHS_MAX_DEV) return cudaSuccess;   // launches there run one block per tile
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(g_rhs_mu);
+    if ((e = rhs_init_one<FAM_SPH, 2, 4>(dev, nsm)) != cudaSuccess) return e;
+    if ((e = rhs_init_one<FAM_SPH, -1, 4>(dev, nsm)) != cudaSuccess) return e;
+    if ((e = rhs_init_one<FAM_CYL, 1, 4>(dev, nsm)) != cudaSuccess) return e;
+    if ((e = rhs_init_one<FAM_CYL, -1, 4>(dev, nsm)) != cudaSuccess) return e;
+    if ((e = rhs_init_one<FAM_SPH, 2, 8>(dev, nsm)) != cudaSuccess) return e;
+    if ((e = rhs_init_one<FAM_SPH, -1, 8>(dev, nsm)) != cudaSuccess) return e;
+    if ((e = rhs_init_one<FAM_CYL, 1, 8>(dev, nsm)) != cudaSuccess) return e;
+    return rhs_init_one<FAM_CYL, -1, 8>(dev, nsm);
 }
 
 cudaError_t launch_rhs(const GridK& G, const double* yin, double* d1x, double* d1y, double* out, const double* yn,

@@ -591,6 +591,7 @@ static int nr_part_create_body(int coords, const int Nxx[3], const nr_params* pa
             e = cudaStreamCreateWithFlags(&s->pstream[q], cudaStreamNonBlocking);
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->pevent[q], cudaEventDisableTiming);
         }
+        if (e == cudaSuccess) e = rhs_kernels_init();   // before any step is captured
         if (e != cudaSuccess) {
             free_part(s);
             return nrk_fail(NR_ECUDA, "partition streams: %s", cudaGetErrorString(e));

@@ -68,11 +68,19 @@ __device__ __forceinline__ void stage_store(const Stage& st, long T, long idx, c
 #pragma unroll
         for (int g = 0; g < NGF; g++) v[g] = fma(st.cacc, k[g], acc[g * T + idx]);
     } else {
+        // every load ahead of the first store: the offsets g T are run-time values, so a store to
+        // acc may alias a later load of acc as far as the compiler can tell, and a load-update-store
+        // loop would wait out one memory latency per gridfunction (measured: 10 % of the launch)
+        double a[NGF];
 #pragma unroll
         for (int g = 0; g < NGF; g++) {
-            const double y0 = yn[g * T + idx];
-            v[g] = fma(st.cnext, k[g], y0);
-            acc[g * T + idx] = fma(st.cacc, k[g], st.mode == MODE_STAGE1 ? y0 : acc[g * T + idx]);
+            v[g] = yn[g * T + idx];
+            a[g] = st.mode == MODE_STAGE1 ? v[g] : acc[g * T + idx];
+        }
+#pragma unroll
+        for (int g = 0; g < NGF; g++) {
+            acc[g * T + idx] = fma(st.cacc, k[g], a[g]);
+            v[g] = fma(st.cnext, k[g], v[g]);
         }
     }
     if (st.enforce) enforce_det(v);
