@@ -42,28 +42,47 @@ __global__ void __launch_bounds__(256) k_d1(GridK G, const double* __restrict__ 
     d1_point<AX, ORD>(G, y, d1x, d1y, (long)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
+// one tile of k_rhs: tile tb < oa.nblocks takes pure-outer points, 128 each; the others tile
+// (i0, j = i1 + N1 i2) in 32 x 4 points
+template <int FAM, int AX, int ORD>
+__device__ __forceinline__ void rhs_tile(const GridK& G, const double* __restrict__ yin, const double* __restrict__ d1x,
+                                         const double* __restrict__ d1y, double* out, const double* yn, double* acc,
+                                         const Stage& st, const OuterArgs& oa, int tb, int nbx)
+{
+    if (tb < oa.nblocks) {
+        const int t = tb * (RHS_BX * RHS_BY) + threadIdx.y * RHS_BX + threadIdx.x;
+        if (t < oa.npts) outer_point_stage<FAM, ORD>(G, oa.pts[t], yin, out, yn, acc, oa.finf, oa.wspeed, st);
+        return;
+    }
+    const int b = tb - oa.nblocks;
+    const int i = (b % nbx) * RHS_BX + threadIdx.x;
+    const int j = (b / nbx) * RHS_BY + threadIdx.y;
+    if (i < G.N0 && j < G.N1 * G.N2) rhs_point_stage<FAM, AX, true, ORD>(G, yin, d1x, d1y, out, yn, acc, st, i, j);
+}
+
+// Whether k_rhs runs a grid of the resident blocks, each striding over the tiles (every warp then
+// keeps its slot for the whole launch): measured faster for the two-point-azimuth kernels; the
+// general kernels, whose loop adds register spills, run one block per tile
+template <int AX>
+__host__ __device__ constexpr bool rhs_strided()
+{
+    return AX >= 0;
+}
+
 template <int FAM, int AX, int ORD>
 __global__ void __launch_bounds__(RHS_BX* RHS_BY) k_rhs(GridK G, const double* __restrict__ yin,
                                                         const double* __restrict__ d1x, const double* __restrict__ d1y,
                                                         double* out, const double* yn, double* acc, Stage st,
                                                         OuterArgs oa)
 {
-    // tiles: the first oa.nblocks take the pure-outer points, 128 each; the others tile
-    // (i0, j = i1 + N1 i2) in 32 x 4 points.  Each block strides over the tiles (a grid of the
-    // resident blocks, or one block per tile)
     const int nbx = (G.N0 + RHS_BX - 1) / RHS_BX;
-    const int ntiles = oa.nblocks + nbx * ((G.N1 * G.N2 + RHS_BY - 1) / RHS_BY);
+    if constexpr (rhs_strided<AX>()) {
+        const int ntiles = oa.nblocks + nbx * ((G.N1 * G.N2 + RHS_BY - 1) / RHS_BY);
 #pragma unroll 1
-    for (int tb = (int)blockIdx.x; tb < ntiles; tb += (int)gridDim.x) {
-        if (tb < oa.nblocks) {
-            const int t = tb * (RHS_BX * RHS_BY) + threadIdx.y * RHS_BX + threadIdx.x;
-            if (t < oa.npts) outer_point_stage<FAM, ORD>(G, oa.pts[t], yin, out, yn, acc, oa.finf, oa.wspeed, st);
-            continue;
-        }
-        const int b = tb - oa.nblocks;
-        const int i = (b % nbx) * RHS_BX + threadIdx.x;
-        const int j = (b / nbx) * RHS_BY + threadIdx.y;
-        if (i < G.N0 && j < G.N1 * G.N2) rhs_point_stage<FAM, AX, true, ORD>(G, yin, d1x, d1y, out, yn, acc, st, i, j);
+        for (int tb = (int)blockIdx.x; tb < ntiles; tb += (int)gridDim.x)
+            rhs_tile<FAM, AX, ORD>(G, yin, d1x, d1y, out, yn, acc, st, oa, tb, nbx);
+    } else {
+        rhs_tile<FAM, AX, ORD>(G, yin, d1x, d1y, out, yn, acc, st, oa, (int)blockIdx.x, nbx);
     }
 }
 
@@ -115,7 +134,7 @@ cudaError_t launch_k_rhs(long nb, cudaStream_t s, const GridK& G, const double* 
             res = rhs_resident<FAM, AX, ORD>();
         }
     }
-    const dim3 grd((unsigned)(res > 0 && res < nb ? res : nb));
+    const dim3 grd((unsigned)(rhs_strided<AX>() && res > 0 && res < nb ? res : nb));
     k_rhs<FAM, AX, ORD><<<grd, dim3(RHS_BX, RHS_BY), 0, s>>>(G, yin, d1x, d1y, out, yn, acc, st, oa);
     return cudaGetLastError();
 }
