@@ -256,9 +256,11 @@ int nr_set_state_compact(nr_grid* grid, const double* src, int from_host);
  * When host_out is pinned (page-locked, hence mapped) host memory, the last
  * stage of the last step stores each point's new values there itself, over the
  * host link while the stage computes, so the read-back costs no separate copy;
- * other host memory takes the gather-and-copy path.  The first such call
- * allocates a rank table of T ints on the device.  Errors: NR_EINVAL,
- * NR_ENOMEM, NR_ECUDA. */
+ * other host memory takes the gather-and-copy path.  The upload of host_in is
+ * not waited for on its own: the steps follow it on the grid's stream, and the
+ * call returns after that stream has drained, on an error too, so host_in may
+ * be reused on return.  The first such call allocates a rank table of T ints
+ * on the device.  Errors: NR_EINVAL, NR_ENOMEM, NR_ECUDA. */
 int nr_step_io(nr_grid* grid, int integrator, double dt, int nsteps, const double* host_in, double* host_out);
 
 /* 64-bit digest of a 24-gridfunction set (y_dev, or the grid-owned state if NULL) at

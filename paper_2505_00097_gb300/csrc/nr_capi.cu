@@ -912,10 +912,9 @@ int nr_get_state_compact(nr_grid* g, double* dst, int to_host)
     return NR_OK;
 }
 
-int nr_set_state_compact(nr_grid* g, const double* src, int from_host)
+// the upload of nr_set_state_compact, enqueued on the grid's stream without waiting for it
+static int set_state_compact_async(nr_grid* g, const double* src, int from_host)
 {
-    if (!g || !src) return fail(NR_EINVAL, "bad nr_set_state_compact arguments");
-    DeviceGuard dg(g->device);
     const long nc = g->n_canon;
     const size_t b = sizeof(double) * NR_NGF * nc;
     const double* from = src;
@@ -928,17 +927,23 @@ int nr_set_state_compact(nr_grid* g, const double* src, int from_host)
     // the ghosts the stencils read now; the azimuthal copies on demand (refresh_ghosts)
     CUDA_OR_FAIL(launch_inner(g->K, g->inner, g->n_inner_stencil, g->y, g->stream));
     g->ghosts_stale = g->n_inner > g->n_inner_stencil;
+    return NR_OK;
+}
+
+int nr_set_state_compact(nr_grid* g, const double* src, int from_host)
+{
+    if (!g || !src) return fail(NR_EINVAL, "bad nr_set_state_compact arguments");
+    DeviceGuard dg(g->device);
+    int rc = set_state_compact_async(g, src, from_host);
+    if (rc) return rc;
     if (from_host) CUDA_OR_FAIL(cudaStreamSynchronize(g->stream));
     return NR_OK;
 }
 
-static int nr_step_io_body(nr_grid* g, int integrator, double dt, int nsteps, const double* host_in, double* host_out)
+// nr_step_io after the upload: the steps and the read-back
+static int step_io_steps(nr_grid* g, int integrator, double dt, int nsteps, double* host_out)
 {
-    if (!g || !(dt > 0.0) || nsteps < 1 || (integrator != NR_RK4 && integrator != NR_SSPRK3))
-        return fail(NR_EINVAL, "bad nr_step_io arguments");
-    DeviceGuard dg(g->device);
     int rc;
-    if (host_in && (rc = nr_set_state_compact(g, host_in, 1))) return rc;
     auto steps = [&](int n) { return integrator == NR_SSPRK3 ? nr_ssprk3_step(g, dt, n) : nr_rk4_step(g, dt, n); };
     if (nsteps > 1 && (rc = steps(nsteps - 1))) return rc;
     cudaPointerAttributes a{};
@@ -970,6 +975,20 @@ static int nr_step_io_body(nr_grid* g, int integrator, double dt, int nsteps, co
     g->ghosts_stale = g->n_inner > g->n_inner_stencil;
     CUDA_OR_FAIL(cudaStreamSynchronize(g->stream));
     return NR_OK;
+}
+
+static int nr_step_io_body(nr_grid* g, int integrator, double dt, int nsteps, const double* host_in, double* host_out)
+{
+    if (!g || !(dt > 0.0) || nsteps < 1 || (integrator != NR_RK4 && integrator != NR_SSPRK3))
+        return fail(NR_EINVAL, "bad nr_step_io arguments");
+    DeviceGuard dg(g->device);
+    // the upload is not waited for: the steps follow it on the same stream, and the call
+    // returns only after the stream has drained
+    int rc = host_in ? set_state_compact_async(g, host_in, 1) : NR_OK;
+    if (rc == NR_OK) rc = step_io_steps(g, integrator, dt, nsteps, host_out);
+    // on an error the upload may still be reading host_in: drain the stream before returning
+    if (rc != NR_OK && host_in) cudaStreamSynchronize(g->stream);
+    return rc;
 }
 
 int nr_step_io(nr_grid* g, int integrator, double dt, int nsteps, const double* host_in, double* host_out)

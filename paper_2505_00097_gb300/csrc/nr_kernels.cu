@@ -102,11 +102,8 @@ constexpr int rhs_variant()
 template <int FAM, int AX, int ORD>
 cudaError_t rhs_init_one(int dev, int nsm)
 {
-    const void* f = (const void*)k_rhs<FAM, AX, ORD>;
-    // no shared memory: the whole unified L1 / shared array as L1, for the register spills
-    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
     int occ = 0;
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rhs<FAM, AX, ORD>, RHS_BX * RHS_BY, 0);
+    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rhs<FAM, AX, ORD>, RHS_BX * RHS_BY, 0);
     if (e != cudaSuccess) return e;
     g_rhs_resident[dev][rhs_variant<FAM, AX, ORD>()].store(occ * nsm);
     return cudaSuccess;
