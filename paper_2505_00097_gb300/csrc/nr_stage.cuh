@@ -62,8 +62,15 @@ __device__ __forceinline__ void stage_store(const Stage& st, long T, long idx, c
     }
     double v[NGF];
     if (st.mode == MODE_SSP) {
+        if (st.cyn == 0.0 && st.cacc == 1.0) {
+            // the first stage, y_1 = y + dt k: the general form's 0 y_n + 1 (.) left out
 #pragma unroll
-        for (int g = 0; g < NGF; g++) v[g] = fma(st.cyn, yn[g * T + idx], st.cacc * fma(st.cnext, k[g], yin[g * T + idx]));
+            for (int g = 0; g < NGF; g++) v[g] = fma(st.cnext, k[g], yin[g * T + idx]);
+        } else {
+#pragma unroll
+            for (int g = 0; g < NGF; g++)
+                v[g] = fma(st.cyn, yn[g * T + idx], st.cacc * fma(st.cnext, k[g], yin[g * T + idx]));
+        }
     } else if (st.mode == MODE_STAGE4) {
 #pragma unroll
         for (int g = 0; g < NGF; g++) v[g] = fma(st.cacc, k[g], acc[g * T + idx]);
