@@ -87,7 +87,8 @@ __global__ void __launch_bounds__(TX* TY) k_batch_stage(const BGrid* __restrict_
     } else {
         const int p = (w - B.w_rhs_end) * (TX * TY) + tid;
         if (p < B.n_outer)
-            outer_point_stage<FAM, ORD>(B.K, B.outer[p], yin, out, yn, B.acc, B.finf, B.wspeed, B.st[stage]);
+            outer_point_stage<FAM, ORD, ssp_first_short<AX>()>(B.K, B.outer[p], yin, out, yn, B.acc, B.finf, B.wspeed,
+                                                               B.st[stage]);
     }
 }
 

@@ -51,7 +51,8 @@ __device__ __forceinline__ void rhs_tile(const GridK& G, const double* __restric
 {
     if (tb < oa.nblocks) {
         const int t = tb * (RHS_BX * RHS_BY) + threadIdx.y * RHS_BX + threadIdx.x;
-        if (t < oa.npts) outer_point_stage<FAM, ORD>(G, oa.pts[t], yin, out, yn, acc, oa.finf, oa.wspeed, st);
+        if (t < oa.npts)
+            outer_point_stage<FAM, ORD, ssp_first_short<AX>()>(G, oa.pts[t], yin, out, yn, acc, oa.finf, oa.wspeed, st);
         return;
     }
     const int b = tb - oa.nblocks;
