@@ -56,7 +56,7 @@ UNIT = "point-updates/s"
 # the kernels' DADD/DMUL/DFMA thread-instruction counts in one ncu capture of
 # that workload's nr_rhs launches: (DADD + DMUL + 2 DFMA) / interior points.  Head-on
 # 256x2x512 (cylindrical, two-point azimuth): k_rhs 215 + 348 + 2 x 1166 = 2895, k_d1 44.3.
-# Head-on with the 8th-order scheme: k_rhs 314 + 409 + 2 x 1517 = 3757, k_d1 122.9.  Large 3D
+# Head-on with the 8th-order scheme: k_rhs 315 + 408 + 2 x 1517 = 3757, k_d1 122.9.  Large 3D
 # (spherical, general; counted on a 96x48x96 grid of the same kernel): k_rhs 320 + 453 + 2 x 1670 =
 # 4113, k_d1 89.8 (4 FLOP per stored difference, 22.46 differences per point at 384x192x384).
 # Large 3D with the production scheme (the general 8th-order kernel, counted on 96x48x96): k_rhs
@@ -66,8 +66,8 @@ F_ALG = {"headon": 2939.3, "large3d": 4202.8, "headon8": 3879.9, "large3d8": 570
 # DRAM bytes (read + write) of the same two launches in that capture; for the large 3D grids the
 # capture's bytes per interior point at 96x48x96 (3275.7 and 5324.5, mostly register-spill lines)
 # times the 28,311,552 points of the full grid
-TRAFFIC = {"headon": 24016640 + 83712 + 93192448 + 507844864,
-           "headon8": 24950016 + 106496 + 97443584 + 503319296,
+TRAFFIC = {"headon": 24016384 + 88832 + 94202624 + 510593792,
+           "headon8": 24951296 + 119552 + 94502400 + 486498304,
            "large3d": round(3275.7 * 28311552), "large3d8": round(5324.5 * 28311552)}
 # FLOPs of the same right-hand side in the point code's source (a host census of the code those counts
 # were taken from: FMA = 2, one division; without the k_d1 pre-pass); a test recomputes it, so that a
