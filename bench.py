@@ -95,9 +95,9 @@ PSI4_LMAX, PSI4_NTHETA, PSI4_NPHI = 8, 24, 48
 # FP64 pipe of one SM: 2 DFMA per clock (ncu peak_sustained of
 # sm__sass_thread_inst_executed_op_dfma_pred_on), i.e. 4 FLOP per clock
 FP64_FLOP_PER_CLK_SM = 4.0
-# algorithmic DRAM bytes per interior point of one fused RK stage launch:
-# stage input (read once) 24x8, y_n 24x8, acc read+write 2x24x8, output 24x8
-B_ALG_STAGE = 5 * 24 * 8
+# algorithmic DRAM bytes per interior point of one RHS evaluation (the nr_rhs the roofline times):
+# the 24 gridfunctions read once and the 24 right-hand sides written once
+B_ALG_RHS = 2 * 24 * 8
 
 
 def parse():
@@ -466,7 +466,9 @@ def run_ours(args, spec, world, rank, local):
             "peak": peak / 1e12,
             "peak_source": f"derived: 2 DFMA/clk/SM x {n_sm} SMs x {mhz:.0f} MHz (median SM clock in the timed region)",
             "probe_tflops": probe / 1e12, "launch_ms": rhs_ms, "points_per_launch": pts,
-            "traffic": TRAFFIC.get(args.workload)}
+            "traffic": TRAFFIC.get(args.workload), "traffic_algorithmic": B_ALG_RHS * pts,
+            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one nr_rhs (k_d1 + k_rhs); "
+                              "the excess over the algorithmic bytes is register-spill lines evicted to DRAM"}
     f_alg = F_ALG.get(args.workload)
     if f_alg:
         ach = f_alg * pts / (rhs_ms * 1e-3)
