@@ -411,8 +411,11 @@ cudaError_t rhs_kernels_init()
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= RHS_MAX_DEV) return cudaSuccess;   // launches there run one block per tile
-    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     std::lock_guard<std::mutex> lk(g_rhs_mu);
+    bool known = true;
+    for (int v = 0; v < RHS_VARIANTS; v++) known = known && g_rhs_resident[dev][v].load() > 0;
+    if (known) return cudaSuccess;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     if ((e = rhs_init_one<FAM_SPH, 2, 4>(dev, nsm)) != cudaSuccess) return e;
     if ((e = rhs_init_one<FAM_SPH, -1, 4>(dev, nsm)) != cudaSuccess) return e;
     if ((e = rhs_init_one<FAM_CYL, 1, 4>(dev, nsm)) != cudaSuccess) return e;
